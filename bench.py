@@ -1,0 +1,344 @@
+#!/usr/bin/env python3
+"""Benchmark: SP2 spectral projection driven by SpAMM on one GB300.
+
+Workload: the N = 4096 tight-binding Hamiltonian on Morton-ordered 3-D
+three-site clusters (h_ij = -exp(-r_ij / 1.2 A), cut at 1e-12, on-site -/+2
+by site parity), Ne = N/2, Gershgorin start, tau = 1e-8, leaf 32.  One step
+is one complete SP2 solve: norm quadtree, culling, leaf products and the
+fused SP2 update for every iteration until the stopping rule fires.
+
+Printed metric: useful SpAMM leaf throughput over the whole solve, i.e.
+2 b^3 x (surviving leaf triples summed over iterations) / solve time, in
+TFLOP/s; `ms_per_step` is the SP2 solve time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp64|ozaki]
+  python bench.py --impl reference ...   (the FP64 CPU oracle, bounded sample)
+
+N > 1 runs independent replicas (one solve per GPU, launched with torchrun);
+value = all ranks' useful FLOPs / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = {"workload": "sp2_tb_hamiltonian", "n": 4096, "leaf": 32, "tau": 1e-8,
+            "ne": 2048, "decay_A": 1.2, "onsite": 2.0, "start": "gershgorin",
+            "stop": "trace+idempotency or stagnation"}
+METRIC = "SpAMM leaf TFLOP/s over the SP2 solve (useful FLOPs of surviving products)"
+UNIT = "TFLOP/s"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def fp64_peak_tflops():
+    """FP64 FMA peak: 152 SMs x 2 DFMA/clk/SM x 2 FLOP x 2.07 GHz = 1.26
+    TFLOP/s (the nominal 1.25 TFLOP/s FP64 rate at the maximum SM clock)."""
+    return 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reduce_max_over_ranks(value: float, world: int, device=None) -> float:
+    """Max of a per-rank float over all ranks (identity for one rank)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum_over_ranks(value: float, world: int, device=None) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_1403_7458_gb300 import spamm, synth
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    spamm.load()
+    prec = spamm.OZAKI_BF16 if args.prec == "ozaki" else spamm.FP64
+    n, b, tau, ne = WORKLOAD["n"], WORKLOAD["leaf"], WORKLOAD["tau"], WORKLOAD["ne"]
+    h = synth.tb_hamiltonian(n, seed=rank)
+    hd = torch.from_numpy(h).to(dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    F = spamm.tree_build(hd, leaf=b)
+    P = None
+
+    def solve(timing=False):
+        nonlocal P
+        P, rep = spamm.sp2_solve(F, ne, tau, P=P, prec=prec, timing=timing)
+        return rep
+
+    for _ in range(args.warmup):
+        solve()
+    torch.cuda.synchronize()
+
+    # ---- device-timed region: inputs resident in HBM ----
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flops = 0.0
+    gemm_ms = 0.0
+    gemm_flops = 0.0
+    iters = 0
+    launches = 0
+    step_ms = []
+    with ClockSampler(local) as clk:
+        _barrier(world)
+        torch.cuda.synchronize()
+        total_ms = 0.0
+        for _ in range(args.steps):
+            flush.zero_()                       # evict L2 between steps
+            ev0.record(stream)
+            rep = solve(timing=True)
+            ev1.record(stream)
+            ev1.synchronize()
+            ms = ev0.elapsed_time(ev1)
+            step_ms.append(ms)
+            total_ms += ms
+            flops += rep["flops_useful"]
+            gemm_ms += rep["ms_gemm"]
+            gemm_flops += rep["flops_useful"]
+            iters += rep["iters"]
+            launches += rep["launches"]
+        torch.cuda.synchronize()
+        _barrier(world)
+    clocks = clk.summary()
+    t_max = reduce_max_over_ranks(total_ms, world, dev)
+    flops_all = reduce_sum_over_ranks(flops, world, dev)
+    value = flops_all / (t_max * 1e-3) / 1e12
+
+    # ---- end to end through the C ABI with host buffers ----
+    h_pin = torch.from_numpy(h).pin_memory()
+    p_pin = torch.empty((n, n), dtype=torch.float64).pin_memory()
+    e2e_flops = 0.0
+    _barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        F2 = spamm.tree_build(h_pin.numpy(), leaf=b)        # host pointer: H2D inside
+        P2, rep2 = spamm.sp2_solve(F2, ne, tau, prec=prec)
+        spamm.to_dense(P2, out=p_pin.numpy())               # host pointer: D2H inside
+        e2e_flops += rep2["flops_useful"]
+        F2.free()
+        P2.free()
+    torch.cuda.synchronize()
+    e2e_s = reduce_max_over_ranks(time.perf_counter() - t0, world, dev)
+    e2e_value = reduce_sum_over_ranks(e2e_flops, world, dev) / e2e_s / 1e12
+
+    # P quality of the last device-timed solve
+    p = spamm.to_dense(P)
+    idem = torch.linalg.norm(p @ p - p).item()
+    trace_err = abs(torch.trace(p).item() - ne)
+
+    # ---- roofline of the dominant kernel (grouped leaf products) ----
+    peaks, peak_src = _peaks()
+    if prec == spamm.FP64:
+        peak = fp64_peak_tflops()
+        bound = "alu"
+        peak_note = "FP64 FMA: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz (nominal 1.25 TFLOP/s)"
+    else:
+        peak = peaks.get("bf16_tflops_sustained", 1700.0)
+        bound = "tensor"
+        peak_note = "bf16 sustained, %s" % peak_src
+    achieved = gemm_flops / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else None
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "kernel": "k_gemm_fp64<32>" if prec == spamm.FP64 else "k_gemm_tc",
+                "peak_source": peak_note,
+                "gemm_share_of_step": gemm_ms / total_ms if total_ms else None}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == spamm.FP64 else "bf16-slices/f32-acc/f64",
+        "data": "synthetic (seeded tight-binding Hamiltonian, Morton-ordered 3-D clusters)",
+        "config": dict(WORKLOAD, prec=args.prec, parallelism="replicas" if world > 1 else "1gpu",
+                       l2="flushed between steps; working set 2 x 134 MB > L2"),
+        "sp2": {"iters_per_solve": iters / args.steps, "solve_ms": t_max / args.steps,
+                "step_ms": step_ms, "idempotency": idem, "trace_err": trace_err},
+        "roofline": roofline,
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * n * n,
+                "d2h_bytes_per_step": 8 * n * n, "seconds": e2e_s},
+        "gpu_launches": launches,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(h, iters=1)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(h=None, iters=1):
+    """The FP64 CPU oracle on the host cores: `iters` SP2 iterations of the
+    same workload (fixed-iteration mode), useful leaf FLOPs / wall time."""
+    import oracle
+    from paper_1403_7458_gb300 import synth
+    n, b, tau, ne = WORKLOAD["n"], WORKLOAD["leaf"], WORKLOAD["tau"], WORKLOAD["ne"]
+    if h is None:
+        h = synth.tb_hamiltonian(n, seed=0)
+    t0 = time.perf_counter()
+    _, hist, _ = oracle.sp2(h, b, ne, tau, fixed_iters=iters)
+    dt = time.perf_counter() - t0
+    flops = 2.0 * b ** 3 * hist[:, oracle.H_TASKS].sum()
+    return {"value": flops / dt / 1e12, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle", "seconds": dt,
+            "sample": "%d SP2 iteration(s) of the N=4096 workload (Gershgorin start, "
+                      "X0^2 by recursive SpAMM)" % iters}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1403_7458_gb300 import synth
+    n, b, tau, ne = WORKLOAD["n"], WORKLOAD["leaf"], WORKLOAD["tau"], WORKLOAD["ne"]
+    h = synth.tb_hamiltonian(n, seed=0)
+    for _ in range(args.warmup):
+        oracle.sp2(h, b, ne, tau, fixed_iters=1)
+    t0 = time.perf_counter()
+    flops = 0.0
+    for _ in range(args.steps):
+        _, hist, _ = oracle.sp2(h, b, ne, tau, fixed_iters=1)
+        flops += 2.0 * b ** 3 * hist[:, oracle.H_TASKS].sum()
+    dt = time.perf_counter() - t0
+    value = flops / dt / 1e12
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(WORKLOAD, prec="fp64", parallelism="cpu"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle",
+                             "sample": "one SP2 iteration (X0^2) of the N=4096 workload per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--prec", choices=["fp64", "ozaki"], default="fp64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,225 @@
+/*
+ * spamm.h -- C ABI of the GB300 (sm_103a) SpAMM / SP2 library.
+ *
+ * The library implements the Sparse Approximate Matrix Multiply (SpAMM) of
+ * Bock, Challacombe and Kale, "Solvers for O(N) Electronic Structure in the
+ * Strong Scaling Limit" (arXiv:1403.7458), Sec. 2, Eqs. 1-4 and Algorithm 1,
+ * and the second-order spectral projection (SP2) loop that the paper drives
+ * with it (Sec. 4).  All arithmetic runs in the library's own CUDA kernels.
+ *
+ * Conventions shared by every entry point
+ *   - Return value: SPAMM_OK (0) or a negative SPAMM_E_* code.  A short text
+ *     for the last failure on the calling thread is in spamm_last_error().
+ *   - Matrices are square, n x n, FP64, row-major with a leading dimension
+ *     (elements, >= n).  Pointers passed as matrix data may be host or device
+ *     memory; the library asks the CUDA runtime which one it is.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  All
+ *     device work is enqueued on it; only the calls documented as blocking
+ *     wait for it.
+ *   - Handles (spamm_mat_t) own their device memory, are created by the
+ *     library and released with spamm_free().  Inputs are never modified.
+ *   - Matrices are cut into b x b leaves (b = 16, 32 or 64).  The leaf grid
+ *     is nb x nb, nb = ceil(n / b); the norm quadtree has depth d with
+ *     2^d >= nb, tier 0 the root, tier d the leaves.  Padding up to 2^d is
+ *     virtual: padding leaves have norm 0 and are never multiplied.  The
+ *     ragged last leaf row and column are zero-filled.
+ */
+#ifndef SPAMM_H
+#define SPAMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define SPAMM_OK 0
+#define SPAMM_E_INVAL (-1)    /* bad argument (size, leaf, tau, pointer)        */
+#define SPAMM_E_NOMEM (-2)    /* device or host allocation failed               */
+#define SPAMM_E_CUDA (-3)     /* a CUDA runtime call failed                     */
+#define SPAMM_E_CAPACITY (-4) /* a caller-sized buffer is too small             */
+#define SPAMM_E_TIMEOUT (-5)  /* a bounded device-side wait gave up             */
+#define SPAMM_E_NOCONV (-6)   /* SP2 reached max_iter; the iterate is returned  */
+#define SPAMM_E_NOTSUP (-7)   /* option combination not built                   */
+
+/* ---- leaf-product precision ------------------------------------------- */
+typedef enum {
+    /* FP64 operands, FP64 fused multiply-add accumulation. */
+    SPAMM_FP64 = 0,
+    /* Exact-slice mixed precision on the tcgen05 tensor cores: every matrix
+     * row (of A) and column (of B) gets a power-of-two scale; the scaled
+     * values are cut into `slices` signed 7-bit integer slices held in BF16;
+     * slice pairs (p, q) with p + q < slices are multiplied with FP32
+     * accumulation in tensor memory (exact for integers below 2^24) and
+     * combined in FP64.  Error-free splitting after Ozaki, Ogita, Oishi and
+     * Rump (2012). */
+    SPAMM_OZAKI_BF16 = 1
+} spamm_prec_t;
+
+/* ---- options ---------------------------------------------------------- */
+#define SPAMM_F_TIMING 1 /* record per-stage device times into spamm_stats_t */
+
+typedef struct {
+    int32_t leaf;   /* leaf edge b: 16, 32 or 64; 0 selects 32            */
+    int32_t prec;   /* spamm_prec_t                                       */
+    int32_t slices; /* slices per operand for SPAMM_OZAKI_BF16 (0 = 5)    */
+    int32_t flags;  /* SPAMM_F_* bits                                     */
+} spamm_opts_t;
+
+typedef struct {
+    int64_t tasks;       /* surviving leaf triples (i, k, j)                 */
+    int64_t candidates;  /* nb^3                                             */
+    double flops_useful; /* 2 b^3 per surviving triple                       */
+    double flops_issued; /* arithmetic issued, incl. slice pairs             */
+    float ms_cull;       /* device time of the cull (with SPAMM_F_TIMING)    */
+    float ms_gemm;       /* device time of the leaf products                 */
+    float ms_norm;       /* device time of the output norms                  */
+    float reserved;
+} spamm_stats_t;
+
+/* ---- matrices --------------------------------------------------------- */
+typedef struct spamm_mat *spamm_mat_t;
+
+/*
+ * Build a matrix handle: leaf storage plus the norm quadtree.
+ *   Eq. 1 (Sec. 2): the quadtree A^t = [[A^{t+1}_11, A^{t+1}_12],
+ *   [A^{t+1}_21, A^{t+1}_22]]; Eq. 2: the leaf Frobenius norms; Eq. 3: a
+ *   parent's norm from its four children.
+ * a      : n x n FP64, row-major, leading dimension lda >= n (host or device).
+ * opts   : leaf size (others ignored here); NULL = defaults.
+ * out    : receives the new handle (caller frees it with spamm_free).
+ * Squared norms are stored.  Each is the exact sum of the exact squares
+ * (resp. of the four children) rounded once to FP64, so its value does not
+ * depend on the order of summation.  Device work is enqueued on `stream`;
+ * a host `a` is copied before the call returns.
+ * Errors: E_INVAL (n < 1, lda < n, bad leaf, NULL a/out), E_NOMEM, E_CUDA.
+ */
+int spamm_tree_build(const double *a, int64_t n, int64_t lda,
+                     const spamm_opts_t *opts, void *stream, spamm_mat_t *out);
+
+/*
+ * C = SpAMM(A, B, tau)  (Eq. 4, Algorithm 1 of Sec. 3.1).
+ * Keeps the leaf triple (i, k, j) iff ||A_ik||^2 ||B_kj||^2 > tau^2, which
+ * is the set the recursive walk of Algorithm 1 reaches (a parent's norm is
+ * never below a child's), and sets C_ij = sum over kept k of A_ik B_kj with
+ * k increasing.  C's norm quadtree is built too.
+ * A, B   : handles of equal n and leaf size.
+ * tau    : >= 0 and finite.
+ * C      : *C == NULL creates a new handle; otherwise *C must have A's shape
+ *          and is overwritten.  C may not alias A or B.
+ * opts   : precision (SPAMM_FP64 or SPAMM_OZAKI_BF16), slices, flags.
+ * stats  : optional; when given the call waits for the stream and fills it.
+ * Errors: E_INVAL, E_NOTSUP, E_NOMEM, E_CUDA, E_CAPACITY (internal list
+ *         overflow, never expected).
+ */
+int spamm_multiply(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t *C,
+                   const spamm_opts_t *opts, spamm_stats_t *stats, void *stream);
+
+/*
+ * Write the matrix to dense row-major storage (host or device), n x n with
+ * leading dimension ld >= n.  Blocking when dst is host memory.
+ */
+int spamm_to_dense(spamm_mat_t M, double *dst, int64_t ld, void *stream);
+
+/*
+ * Copy the squared norms of quadtree tier t (0 = root ... depth = leaves)
+ * to dst (host or device): a 2^t x 2^t row-major grid.  Blocking when dst
+ * is host memory.
+ */
+int spamm_norms(spamm_mat_t M, int32_t tier, double *dst, void *stream);
+
+/* Shape of a handle: n, leaf edge b, leaf grid nb, quadtree depth d. */
+int spamm_info(spamm_mat_t M, int64_t *n, int32_t *leaf, int64_t *nb,
+               int32_t *depth);
+
+/*
+ * The culled task list of SpAMM(A, B, tau), grouped by output leaf (Eq. 4):
+ * for output leaf g = i * nb + j, the surviving k are k_host[off_host[g] ..
+ * off_host[g + 1]) in increasing order.  off_host has nb*nb + 1 entries;
+ * k_host has room for cap entries.  *ntasks receives the total; when it is
+ * larger than cap the call returns E_CAPACITY and k_host is untouched.
+ * Blocking (waits for the stream).  Host buffers.
+ */
+int spamm_task_list(spamm_mat_t A, spamm_mat_t B, double tau, int64_t *off_host,
+                    uint32_t *k_host, int64_t cap, int64_t *ntasks, void *stream);
+
+/* Release a handle (its device memory is freed in stream order). */
+void spamm_free(spamm_mat_t M);
+
+/* Static text for a status code. */
+const char *spamm_strerror(int status);
+
+/* Detail of the last failure on the calling thread ("" if none). */
+const char *spamm_last_error(void);
+
+/* ---- SP2 spectral projection ------------------------------------------ */
+#define SP2_RULE_TRACE_DISTANCE 0 /* X^2 iff |tr X^2 - Ne| < |2trX - trX^2 - Ne| */
+#define SP2_RULE_TRACE_ABOVE 1    /* X^2 iff tr X > Ne                          */
+
+#define SP2_STOP_CONVERGED 0 /* |tr X - Ne| < trace_tol and e < idem_tol       */
+#define SP2_STOP_STAGNATED 1 /* e < 1e-3 and e > 0.5 e(two iterations before)  */
+#define SP2_STOP_FIXED 2     /* fixed_iters iterations done                    */
+#define SP2_STOP_MAXITER 3   /* max_iter reached without a stop                */
+
+typedef struct {
+    int32_t max_iter;    /* 0 selects 100                                    */
+    int32_t rule;        /* SP2_RULE_*                                       */
+    double trace_tol;    /* 0 selects 1e-10                                  */
+    double idem_tol;     /* 0 selects 1e-8                                   */
+    int32_t fixed_iters; /* > 0: run exactly this many iterations            */
+    int32_t leaf;        /* 0 selects 32                                     */
+    int32_t prec;        /* spamm_prec_t of the X^2 products                 */
+    int32_t slices;      /* for SPAMM_OZAKI_BF16 (0 = 5)                     */
+    int32_t flags;       /* SPAMM_F_TIMING: per-stage device times           */
+    int32_t reserved;
+} sp2_opts_t;
+
+/* History columns, one row of SP2_H_COLS doubles per iteration. */
+#define SP2_H_TR 0     /* tr X                                  */
+#define SP2_H_TR2 1    /* tr X^2                                */
+#define SP2_H_IDEM 2   /* e = ||X^2 - X||_F                     */
+#define SP2_H_BRANCH 3 /* 1: X <- X^2, 0: X <- 2X - X^2         */
+#define SP2_H_TASKS 4  /* surviving leaf triples of the product */
+#define SP2_H_TRNEW 5  /* tr of the updated X                   */
+#define SP2_H_COLS 6
+
+typedef struct {
+    int32_t iters;        /* iterations run                               */
+    int32_t stop_reason;  /* SP2_STOP_*                                    */
+    double trace_err;     /* |tr P - Ne|                                   */
+    double idem_err;      /* e of the last iteration                       */
+    double emin, emax;    /* Gershgorin bounds of F                        */
+    int64_t tasks_total;  /* surviving leaf triples over all iterations    */
+    double flops_useful;  /* 2 b^3 tasks_total                             */
+    double ms_total;      /* device time of the whole solve                */
+    double ms_cull;       /* SPAMM_F_TIMING: summed device time of the cull */
+    double ms_gemm;       /*   ... of the leaf products                     */
+    double ms_update;     /*   ... of the SP2 decide + update passes        */
+    int64_t launches;     /* kernels the solve launched                     */
+    double *history;      /* in: optional host buffer of history_cap rows  */
+    int32_t history_cap;  /* in: rows available in history                 */
+    int32_t reserved;
+} sp2_report_t;
+
+/*
+ * P = SP2(F, Ne, tau): second-order spectral projection (Niklasson 2002,
+ * the solver of Sec. 4) with every X^2 formed by SpAMM at threshold tau.
+ * X0 = (emax I - F) / (emax - emin) from Gershgorin bounds; each iteration
+ * forms X^2 = SpAMM(X, X, tau), picks X^2 or 2X - X^2 by `rule` on the
+ * device, and updates X.  Stops as in SP2_STOP_*.
+ * F      : symmetric handle; Ne in (0, n) is the trace of the projector.
+ * P      : *P == NULL creates a new handle; otherwise reused (F's shape).
+ * report : optional; filled when given.
+ * Blocking: waits for the stream once per iteration to read four scalars.
+ * Errors: E_INVAL, E_NOTSUP, E_NOMEM, E_CUDA; E_NOCONV when max_iter is
+ *         reached (P holds the last iterate).
+ */
+int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t *opts,
+              spamm_mat_t *P, sp2_report_t *report, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPAMM_H */

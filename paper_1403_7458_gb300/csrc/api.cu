@@ -1,0 +1,465 @@
+// api.cu -- C ABI entry points: handles, leaf storage, export, errors, and
+// the SpAMM product driver (cull -> leaf products -> output norms).
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "internal.cuh"
+
+// ---------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------
+static thread_local char g_err[512];
+
+void spamm_set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+int spamm_cuda_fail(cudaError_t e, const char *what, const char *file, int line)
+{
+    spamm_set_error("%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+    if (e == cudaErrorMemoryAllocation) return SPAMM_E_NOMEM;
+    return SPAMM_E_CUDA;
+}
+
+extern "C" const char *spamm_strerror(int status)
+{
+    switch (status) {
+    case SPAMM_OK: return "ok";
+    case SPAMM_E_INVAL: return "invalid argument";
+    case SPAMM_E_NOMEM: return "out of memory";
+    case SPAMM_E_CUDA: return "CUDA runtime error";
+    case SPAMM_E_CAPACITY: return "buffer too small";
+    case SPAMM_E_TIMEOUT: return "device-side wait timed out";
+    case SPAMM_E_NOCONV: return "SP2 did not converge within max_iter";
+    case SPAMM_E_NOTSUP: return "option not supported";
+    default: return "unknown status";
+    }
+}
+
+extern "C" const char *spamm_last_error(void) { return g_err; }
+
+static thread_local int64_t g_launches = 0;
+void spamm_note_launches(int64_t k) { g_launches += k; }
+int64_t spamm_launch_count() { return g_launches; }
+
+// ---------------------------------------------------------------------------
+// Memory (stream-ordered allocator)
+// ---------------------------------------------------------------------------
+int spamm_alloc(void **p, size_t bytes, cudaStream_t s)
+{
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(p, bytes, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        spamm_set_error("cudaMallocAsync(%zu bytes): %s", bytes, cudaGetErrorString(e));
+        return SPAMM_E_NOMEM;
+    }
+    return SPAMM_OK;
+}
+
+void spamm_release(void *p, cudaStream_t s)
+{
+    if (p) cudaFreeAsync(p, s);
+}
+
+int spamm_num_sms()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+static bool valid_leaf(int b) { return b == 16 || b == 32 || b == 64; }
+
+static int depth_of(int64_t nb)
+{
+    int d = 0;
+    while ((int64_t(1) << d) < nb) d++;
+    return d;
+}
+
+namespace {
+
+__global__ void k_iota_slots(int32_t *slot, int64_t count)
+{
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < count) slot[g] = (int32_t)g;
+}
+
+// Dense row-major n x n (leading dimension lda) -> leaf storage, zero-filling
+// the ragged edge.  One thread per element of the padded nb*b square.
+__global__ void k_pack(const double *__restrict__ a, int64_t n, int64_t lda, int b, int64_t nb,
+                       const int32_t *__restrict__ slot, double *__restrict__ leaf)
+{
+    int64_t Np = nb * b;
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= Np * Np) return;
+    int64_t r = q / Np, c = q % Np;
+    double v = (r < n && c < n) ? a[r * lda + c] : 0.0;
+    int32_t s = slot[(r / b) * nb + c / b];
+    if (s >= 0) leaf[(int64_t)s * b * b + (r % b) * b + (c % b)] = v;
+}
+
+__global__ void k_unpack(const double *__restrict__ leaf, const int32_t *__restrict__ slot,
+                         int64_t n, int b, int64_t nb, double *__restrict__ dst, int64_t ld)
+{
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n * n) return;
+    int64_t r = q / n, c = q % n;
+    int32_t s = slot[(r / b) * nb + c / b];
+    dst[r * ld + c] = s >= 0 ? leaf[(int64_t)s * b * b + (r % b) * b + (c % b)] : 0.0;
+}
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+unsigned blocks_for(int64_t count, int threads) { return (unsigned)((count + threads - 1) / threads); }
+
+}  // namespace
+
+int spamm_mat_alloc(spamm_mat_t m, int64_t n, int b, cudaStream_t s)
+{
+    m->n = n;
+    m->b = b;
+    m->nb = (n + b - 1) / b;
+    m->depth = depth_of(m->nb);
+    m->P = int64_t(1) << m->depth;
+    m->nslots = m->nb * m->nb;
+    m->stream = s;
+    cudaGetDevice(&m->device);
+    int rc;
+    if ((rc = spamm_alloc((void **)&m->leaf, sizeof(double) * m->nslots * b * b, s))) return rc;
+    if ((rc = spamm_alloc((void **)&m->slot, sizeof(int32_t) * m->nb * m->nb, s))) return rc;
+    if ((rc = spamm_alloc((void **)&m->n2, sizeof(double) * tier_offset(m->depth + 1), s))) return rc;
+    if ((rc = spamm_alloc((void **)&m->n2T, sizeof(double) * m->P * m->P, s))) return rc;
+    SPAMM_CK(cudaMemsetAsync(m->n2, 0, sizeof(double) * tier_offset(m->depth + 1), s));
+    SPAMM_CK(cudaMemsetAsync(m->n2T, 0, sizeof(double) * m->P * m->P, s));
+    k_iota_slots<<<blocks_for(m->nb * m->nb, 256), 256, 0, s>>>(m->slot, m->nb * m->nb);
+    SPAMM_CK_LAUNCH();
+    return SPAMM_OK;
+}
+
+int spamm_mat_same_shape(spamm_mat_t a, spamm_mat_t b)
+{
+    return a && b && a->n == b->n && a->b == b->b;
+}
+
+static void ws_free(SpammWorkspace *ws, cudaStream_t s)
+{
+    spamm_release(ws->counts, s);
+    spamm_release(ws->off, s);
+    spamm_release(ws->klist, s);
+    spamm_release(ws->counter, s);
+    spamm_release(ws->tr_part, s);
+    *ws = SpammWorkspace();
+}
+
+extern "C" void spamm_free(spamm_mat_t m)
+{
+    if (!m) return;
+    cudaStream_t s = m->stream;
+    spamm_release(m->leaf, s);
+    spamm_release(m->slot, s);
+    spamm_release(m->n2, s);
+    spamm_release(m->n2T, s);
+    ws_free(&m->ws, s);
+    delete m;
+}
+
+extern "C" int spamm_tree_build(const double *a, int64_t n, int64_t lda, const spamm_opts_t *opts,
+                                void *stream, spamm_mat_t *out)
+{
+    if (!out) {
+        spamm_set_error("spamm_tree_build: out is NULL");
+        return SPAMM_E_INVAL;
+    }
+    *out = nullptr;
+    int b = opts && opts->leaf ? opts->leaf : 32;
+    if (!a || n < 1 || lda < n || !valid_leaf(b) || (n + b - 1) / b > (int64_t(1) << 15)) {
+        spamm_set_error("spamm_tree_build: bad arguments (n=%lld lda=%lld leaf=%d)", (long long)n,
+                        (long long)lda, b);
+        return SPAMM_E_INVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    spamm_mat_t m = new spamm_mat();
+    int rc = spamm_mat_alloc(m, n, b, s);
+    if (rc) {
+        spamm_free(m);
+        return rc;
+    }
+    const double *src = a;
+    double *staging = nullptr;
+    if (!is_device_ptr(a)) {
+        if ((rc = spamm_alloc((void **)&staging, sizeof(double) * n * n, s))) {
+            spamm_free(m);
+            return rc;
+        }
+        cudaError_t e = cudaMemcpy2DAsync(staging, sizeof(double) * n, a, sizeof(double) * lda,
+                                          sizeof(double) * n, n, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) {
+            spamm_release(staging, s);
+            spamm_free(m);
+            return spamm_cuda_fail(e, "cudaMemcpy2DAsync(H2D)", __FILE__, __LINE__);
+        }
+        src = staging;
+        lda = n;
+    }
+    int64_t Np = m->nb * b;
+    k_pack<<<blocks_for(Np * Np, 256), 256, 0, s>>>(src, n, lda, b, m->nb, m->slot, m->leaf);
+    spamm_note_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (staging) spamm_release(staging, s);
+    if (e != cudaSuccess) {
+        spamm_free(m);
+        return spamm_cuda_fail(e, "k_pack", __FILE__, __LINE__);
+    }
+    if ((rc = launch_leaf_norms(m, s))) {
+        spamm_free(m);
+        return rc;
+    }
+    if (staging) {
+        // the caller may reuse its host buffer as soon as we return
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) {
+            spamm_free(m);
+            return spamm_cuda_fail(e, "cudaStreamSynchronize", __FILE__, __LINE__);
+        }
+    }
+    *out = m;
+    return SPAMM_OK;
+}
+
+extern "C" int spamm_to_dense(spamm_mat_t m, double *dst, int64_t ld, void *stream)
+{
+    if (!m || !dst || ld < m->n) {
+        spamm_set_error("spamm_to_dense: bad arguments");
+        return SPAMM_E_INVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t n = m->n;
+    if (is_device_ptr(dst)) {
+        k_unpack<<<blocks_for(n * n, 256), 256, 0, s>>>(m->leaf, m->slot, n, m->b, m->nb, dst, ld);
+        SPAMM_CK_LAUNCH();
+        return SPAMM_OK;
+    }
+    double *tmp = nullptr;
+    int rc = spamm_alloc((void **)&tmp, sizeof(double) * n * n, s);
+    if (rc) return rc;
+    k_unpack<<<blocks_for(n * n, 256), 256, 0, s>>>(m->leaf, m->slot, n, m->b, m->nb, tmp, n);
+    spamm_note_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(dst, sizeof(double) * ld, tmp, sizeof(double) * n, sizeof(double) * n,
+                              n, cudaMemcpyDeviceToHost, s);
+    spamm_release(tmp, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return spamm_cuda_fail(e, "spamm_to_dense copy", __FILE__, __LINE__);
+    return SPAMM_OK;
+}
+
+extern "C" int spamm_norms(spamm_mat_t m, int32_t tier, double *dst, void *stream)
+{
+    if (!m || !dst || tier < 0 || tier > m->depth) {
+        spamm_set_error("spamm_norms: bad arguments");
+        return SPAMM_E_INVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t W = int64_t(1) << tier;
+    SPAMM_CK(cudaMemcpyAsync(dst, m->n2 + tier_offset(tier), sizeof(double) * W * W,
+                             cudaMemcpyDefault, s));
+    if (!is_device_ptr(dst)) SPAMM_CK(cudaStreamSynchronize(s));
+    return SPAMM_OK;
+}
+
+extern "C" int spamm_info(spamm_mat_t m, int64_t *n, int32_t *leaf, int64_t *nb, int32_t *depth)
+{
+    if (!m) {
+        spamm_set_error("spamm_info: NULL handle");
+        return SPAMM_E_INVAL;
+    }
+    if (n) *n = m->n;
+    if (leaf) *leaf = m->b;
+    if (nb) *nb = m->nb;
+    if (depth) *depth = m->depth;
+    return SPAMM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// SpAMM product
+// ---------------------------------------------------------------------------
+static int check_tau(double tau)
+{
+    if (!(tau >= 0.0) || tau > 1e300) {
+        spamm_set_error("tau must be finite and >= 0 (got %g)", tau);
+        return SPAMM_E_INVAL;
+    }
+    return SPAMM_OK;
+}
+
+int ws_reserve_groups(SpammWorkspace *ws, int64_t groups, int64_t nb, cudaStream_t s)
+{
+    int rc;
+    if (ws->groups_cap < groups) {
+        spamm_release(ws->counts, s);
+        spamm_release(ws->off, s);
+        ws->counts = nullptr;
+        ws->off = nullptr;
+        ws->groups_cap = 0;
+        if ((rc = spamm_alloc((void **)&ws->counts, sizeof(int32_t) * groups, s))) return rc;
+        if ((rc = spamm_alloc((void **)&ws->off, sizeof(int64_t) * (groups + 1), s))) return rc;
+        ws->groups_cap = groups;
+    }
+    if (!ws->counter) {
+        if ((rc = spamm_alloc((void **)&ws->counter, sizeof(int32_t) * 16, s))) return rc;
+        SPAMM_CK(cudaMemsetAsync(ws->counter, 0, sizeof(int32_t) * 16, s));
+    }
+    if (ws->tr_cap < nb) {
+        spamm_release(ws->tr_part, s);
+        ws->tr_part = nullptr;
+        ws->tr_cap = 0;
+        if ((rc = spamm_alloc((void **)&ws->tr_part, sizeof(double) * nb, s))) return rc;
+        ws->tr_cap = nb;
+    }
+    return SPAMM_OK;
+}
+
+int spamm_multiply_into(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t C,
+                        const spamm_opts_t *opts, double *tr_part, cudaStream_t s,
+                        bool need_total, int64_t *tasks_out, bool build_pyramid,
+                        cudaEvent_t *ev)
+{
+    int prec = opts ? opts->prec : SPAMM_FP64;
+    if (ev) SPAMM_CK(cudaEventRecord(ev[0], s));
+    SpammWorkspace *ws = &C->ws;
+    int rc = ws_reserve_groups(ws, A->nb * A->nb, A->nb, s);
+    if (rc) return rc;
+    int64_t total = -1;
+    rc = spamm_cull(A, B, tau, ws, A->nb, A->P, s, need_total, &total);
+    if (rc) return rc;
+    if (ev) SPAMM_CK(cudaEventRecord(ev[1], s));
+    if (prec == SPAMM_FP64) {
+        rc = launch_gemm_fp64(A, B, C, ws, tr_part, s);
+    } else {
+        spamm_set_error("precision mode %d not built", prec);
+        rc = SPAMM_E_NOTSUP;
+    }
+    if (rc) return rc;
+    if (ev) SPAMM_CK(cudaEventRecord(ev[2], s));
+    if (build_pyramid && (rc = launch_pyramid(C, s))) return rc;
+    if (ev) SPAMM_CK(cudaEventRecord(ev[3], s));
+    if (tasks_out) *tasks_out = total;
+    return SPAMM_OK;
+}
+
+extern "C" int spamm_multiply(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t *C,
+                              const spamm_opts_t *opts, spamm_stats_t *stats, void *stream)
+{
+    if (!A || !B || !C || !spamm_mat_same_shape(A, B)) {
+        spamm_set_error("spamm_multiply: NULL handle or shape mismatch");
+        return SPAMM_E_INVAL;
+    }
+    int rc = check_tau(tau);
+    if (rc) return rc;
+    int prec = opts ? opts->prec : SPAMM_FP64;
+    if (prec != SPAMM_FP64) {
+        spamm_set_error("spamm_multiply: precision mode %d not built", prec);
+        return SPAMM_E_NOTSUP;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    bool created = false;
+    if (*C == nullptr) {
+        spamm_mat_t m = new spamm_mat();
+        if ((rc = spamm_mat_alloc(m, A->n, A->b, s))) {
+            spamm_free(m);
+            return rc;
+        }
+        *C = m;
+        created = true;
+    } else if (!spamm_mat_same_shape(*C, A) || *C == A || *C == B) {
+        spamm_set_error("spamm_multiply: C must match A's shape and not alias A or B");
+        return SPAMM_E_INVAL;
+    }
+    bool timing = stats && opts && (opts->flags & SPAMM_F_TIMING);
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    if (timing)
+        for (int q = 0; q < 4 && rc == SPAMM_OK; q++)
+            if (cudaEventCreate(&ev[q]) != cudaSuccess) rc = SPAMM_E_CUDA;
+    int64_t total = -1;
+    if (rc == SPAMM_OK)
+        rc = spamm_multiply_into(A, B, tau, *C, opts, nullptr, s, stats != nullptr, &total, true,
+                                 timing ? ev : nullptr);
+    if (rc == SPAMM_OK && stats) {
+        int64_t nb = A->nb;
+        double b3 = double(A->b) * A->b * A->b;
+        stats->tasks = total;
+        stats->candidates = nb * nb * nb;
+        stats->flops_useful = 2.0 * b3 * double(total);
+        stats->flops_issued = stats->flops_useful;
+        stats->ms_cull = stats->ms_gemm = stats->ms_norm = 0.f;
+        if (timing) {
+            cudaError_t e = cudaEventSynchronize(ev[3]);
+            if (e != cudaSuccess) rc = spamm_cuda_fail(e, "cudaEventSynchronize", __FILE__, __LINE__);
+            cudaEventElapsedTime(&stats->ms_cull, ev[0], ev[1]);
+            cudaEventElapsedTime(&stats->ms_gemm, ev[1], ev[2]);
+            cudaEventElapsedTime(&stats->ms_norm, ev[2], ev[3]);
+        }
+    }
+    for (int q = 0; q < 4; q++)
+        if (ev[q]) cudaEventDestroy(ev[q]);
+    if (rc && created) {
+        spamm_free(*C);
+        *C = nullptr;
+    }
+    return rc;
+}
+
+extern "C" int spamm_task_list(spamm_mat_t A, spamm_mat_t B, double tau, int64_t *off_host,
+                               uint32_t *k_host, int64_t cap, int64_t *ntasks, void *stream)
+{
+    if (!A || !B || !spamm_mat_same_shape(A, B) || !off_host || !ntasks || cap < 0 ||
+        (cap > 0 && !k_host)) {
+        spamm_set_error("spamm_task_list: bad arguments");
+        return SPAMM_E_INVAL;
+    }
+    int rc = check_tau(tau);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    SpammWorkspace ws;
+    int64_t G = A->nb * A->nb;
+    if ((rc = ws_reserve_groups(&ws, G, A->nb, s)) == SPAMM_OK) {
+        int64_t total = -1;
+        rc = spamm_cull(A, B, tau, &ws, A->nb, A->P, s, true, &total);
+        if (rc == SPAMM_OK) {
+            *ntasks = total;
+            cudaError_t e = cudaMemcpyAsync(off_host, ws.off, sizeof(int64_t) * (G + 1),
+                                            cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess && total <= cap && total > 0)
+                e = cudaMemcpyAsync(k_host, ws.klist, sizeof(uint32_t) * total,
+                                    cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) rc = spamm_cuda_fail(e, "task list copy", __FILE__, __LINE__);
+            else if (total > cap) {
+                spamm_set_error("spamm_task_list: %lld tasks, capacity %lld", (long long)total,
+                                (long long)cap);
+                rc = SPAMM_E_CAPACITY;
+            }
+        }
+    }
+    ws_free(&ws, s);
+    return rc;
+}

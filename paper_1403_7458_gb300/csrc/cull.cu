@@ -1,0 +1,136 @@
+// cull.cu -- the SpAMM culling pass (Eq. 4; Algorithm 1's occlusion test).
+//
+// The recursive walk of Algorithm 1 reaches exactly the leaf triples
+// (i, k, j) whose leaf norms pass the test (a parent's squared norm is the
+// rounded sum of its children's and so never smaller), so the task set is
+// decided flat on the leaf tier.  Output is grouped by output leaf
+// g = i * nb + j: the surviving k of group g are klist[off[g] .. off[g+1])
+// in increasing order.
+//
+// Three launches:
+//   count : one warp per group; lanes walk k in steps of 32 and count the
+//           passing candidates with a ballot + popcount;
+//   scan  : exclusive prefix sum of the counts (one block);
+//   emit  : the warps re-test and write each passing k at its ballot rank.
+// Roofline: ALU/latency bound on the candidate tests; HBM/L2 traffic is the
+// two leaf-norm rows per group (16 nb bytes) plus 4 bytes per task written.
+#include "internal.cuh"
+
+namespace {
+
+constexpr int kWarps = 8;
+
+__global__ void __launch_bounds__(kWarps * 32)
+k_cull_count(const double *__restrict__ n2A, const double *__restrict__ n2BT, int64_t nb,
+             int64_t P, double tau2, int32_t *__restrict__ counts)
+{
+    int64_t g = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    int lane = threadIdx.x & 31;
+    if (g >= nb * nb) return;
+    int64_t i = g / nb, j = g % nb;
+    const double *ra = n2A + i * P;
+    const double *rb = n2BT + j * P;
+    int cnt = 0;
+    for (int64_t k0 = 0; k0 < nb; k0 += 32) {
+        int64_t k = k0 + lane;
+        bool p = k < nb && keep_product(__ldg(ra + k), __ldg(rb + k), tau2);
+        cnt += __popc(__ballot_sync(0xffffffffu, p));
+    }
+    if (lane == 0) counts[g] = cnt;
+}
+
+constexpr int kScanThreads = 1024;
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan(const int32_t *__restrict__ counts, int64_t G, int64_t *__restrict__ off)
+{
+    __shared__ int64_t part[kScanThreads];
+    int t = threadIdx.x;
+    int64_t chunk = (G + kScanThreads - 1) / kScanThreads;
+    int64_t lo = t * chunk, hi = lo + chunk < G ? lo + chunk : G;
+    int64_t s = 0;
+    for (int64_t q = lo; q < hi; q++) s += counts[q];
+    part[t] = s;
+    __syncthreads();
+    // Hillis-Steele inclusive scan over the 1024 partial sums
+    for (int o = 1; o < kScanThreads; o <<= 1) {
+        int64_t v = t >= o ? part[t - o] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int64_t run = part[t] - s;
+    for (int64_t q = lo; q < hi; q++) {
+        off[q] = run;
+        run += counts[q];
+    }
+    if (t == kScanThreads - 1) off[G] = part[t];
+}
+
+__global__ void __launch_bounds__(kWarps * 32)
+k_cull_emit(const double *__restrict__ n2A, const double *__restrict__ n2BT, int64_t nb,
+            int64_t P, double tau2, const int64_t *__restrict__ off, uint32_t *__restrict__ klist,
+            int64_t cap, int32_t *__restrict__ err)
+{
+    int64_t g = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    int lane = threadIdx.x & 31;
+    if (g >= nb * nb) return;
+    int64_t i = g / nb, j = g % nb;
+    const double *ra = n2A + i * P;
+    const double *rb = n2BT + j * P;
+    int64_t base = off[g];
+    if (off[g + 1] > cap) {
+        if (lane == 0) atomicExch(err, 1);
+        return;
+    }
+    unsigned lt = (1u << lane) - 1u;
+    for (int64_t k0 = 0; k0 < nb; k0 += 32) {
+        int64_t k = k0 + lane;
+        bool p = k < nb && keep_product(__ldg(ra + k), __ldg(rb + k), tau2);
+        unsigned m = __ballot_sync(0xffffffffu, p);
+        if (p) klist[base + __popc(m & lt)] = (uint32_t)k;
+        base += __popc(m);
+    }
+}
+
+}  // namespace
+
+// Worst-case list sizes up to this many bytes are reserved without asking the
+// device for the exact count.
+static const int64_t kEagerListBytes = int64_t(512) << 20;
+
+int spamm_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, int64_t nb,
+               int64_t P, cudaStream_t s, bool need_total, int64_t *total_host)
+{
+    int64_t G = nb * nb;
+    double tau2 = tau * tau;
+    unsigned blocks = (unsigned)((G + kWarps - 1) / kWarps);
+    k_cull_count<<<blocks, kWarps * 32, 0, s>>>(A->n2 + tier_offset(A->depth), B->n2T, nb, P, tau2,
+                                                ws->counts);
+    SPAMM_CK_LAUNCH();
+    k_scan<<<1, kScanThreads, 0, s>>>(ws->counts, G, ws->off);
+    SPAMM_CK_LAUNCH();
+    int64_t worst = G * nb;
+    int64_t total = -1;
+    if (need_total || (ws->klist_cap < worst && worst * 4 > kEagerListBytes)) {
+        SPAMM_CK(cudaMemcpyAsync(&total, ws->off + G, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        SPAMM_CK(cudaStreamSynchronize(s));
+    }
+    int64_t want = total >= 0 ? total : worst;
+    if (ws->klist_cap < want) {
+        int64_t cap = want;
+        if (total >= 0 && worst * 4 <= kEagerListBytes) cap = worst;
+        else if (total >= 0) cap = want + want / 4 < worst ? want + want / 4 : worst;
+        spamm_release(ws->klist, s);
+        ws->klist = nullptr;
+        ws->klist_cap = 0;
+        int rc = spamm_alloc((void **)&ws->klist, sizeof(uint32_t) * (cap > 0 ? cap : 1), s);
+        if (rc) return rc;
+        ws->klist_cap = cap;
+    }
+    k_cull_emit<<<blocks, kWarps * 32, 0, s>>>(A->n2 + tier_offset(A->depth), B->n2T, nb, P, tau2,
+                                               ws->off, ws->klist, ws->klist_cap, ws->counter + 8);
+    SPAMM_CK_LAUNCH();
+    if (total_host) *total_host = total;
+    return SPAMM_OK;
+}

@@ -1,0 +1,220 @@
+// gemm_fp64.cu -- grouped FP64 leaf products C_ij = sum_{k in S_ij} A_ik B_kj
+// (the dense leaf product of Algorithm 1, applied to every surviving triple).
+//
+// Output-stationary: one CTA owns one output leaf (i, j) at a time, so no two
+// CTAs write the same C leaf and no lock or atomic on C is needed (the paper's
+// OpenMP lock on C has no counterpart here).  CTAs are persistent and pull
+// output leaves from a device counter.  For each surviving k, the A_ik and
+// B_kj leaves are staged into shared memory with cp.async (double-buffered)
+// and multiplied with FP64 fused multiply-adds, k increasing.  The epilogue
+// writes C_ij, its exact squared norm (leaf tier of C's quadtree), and for
+// diagonal leaves the partial trace used by SP2.
+//
+// Roofline: FP64 pipe bound (2 b^3 FLOP per task; operands 16 b^2 bytes per
+// task, mostly served from L2).
+#include "internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+struct GemmArgs {
+    const double *leafA;
+    const int32_t *slotA;
+    const double *leafB;
+    const int32_t *slotB;
+    double *leafC;
+    const int32_t *slotC;
+    int64_t nb;
+    int64_t P;
+    const int64_t *off;
+    const uint32_t *klist;
+    int32_t *counter;
+    double *n2C;
+    double *n2CT;
+    double *tr_part;
+};
+
+template <int B>
+struct Tile {
+    // rows x cols of outputs per thread
+    static constexpr int TR = B == 64 ? 4 : 1;
+    static constexpr int TC = B == 16 ? 1 : 4;
+    static constexpr int COLT = B / TC;  // threads along a row
+};
+
+template <int B>
+__device__ __forceinline__ void stage_leaf(double *dst, const double *src, int tid)
+{
+    constexpr int chunks = B * B / 2;  // 16-byte chunks
+    for (int q = tid; q < chunks; q += kThreads) cp_async16(dst + 2 * q, src + 2 * q);
+}
+
+template <int B>
+__global__ void __launch_bounds__(kThreads) k_gemm_fp64(GemmArgs g)
+{
+    using T = Tile<B>;
+    extern __shared__ __align__(16) double smem[];
+    double *As = smem;               // [2][B*B]
+    double *Bs = smem + 2 * B * B;   // [2][B*B]
+    __shared__ int64_t s_group;
+    __shared__ int s_red_i[kThreads / 32];
+    __shared__ u128 s_red_u[kThreads / 32];
+
+    const int tid = threadIdx.x;
+    const int r0 = (tid / T::COLT) * T::TR;
+    const int c0 = (tid % T::COLT) * T::TC;
+    const int64_t G = g.nb * g.nb;
+
+    for (;;) {
+        if (tid == 0) s_group = atomicAdd(g.counter, 1);
+        __syncthreads();
+        const int64_t grp = s_group;
+        if (grp >= G) break;
+        const int64_t i = grp / g.nb, j = grp % g.nb;
+        const int64_t t0 = g.off[grp], t1 = g.off[grp + 1];
+
+        double acc[T::TR][T::TC];
+#pragma unroll
+        for (int a = 0; a < T::TR; a++)
+#pragma unroll
+            for (int b = 0; b < T::TC; b++) acc[a][b] = 0.0;
+
+        if (t1 > t0) {
+            {
+                uint32_t k = g.klist[t0];
+                stage_leaf<B>(As, g.leafA + (int64_t)g.slotA[i * g.nb + k] * B * B, tid);
+                stage_leaf<B>(Bs, g.leafB + (int64_t)g.slotB[(int64_t)k * g.nb + j] * B * B, tid);
+                cp_async_commit();
+            }
+            for (int64_t t = t0; t < t1; t++) {
+                const int st = (int)((t - t0) & 1);
+                if (t + 1 < t1) {
+                    uint32_t k = g.klist[t + 1];
+                    stage_leaf<B>(As + (st ^ 1) * B * B,
+                                  g.leafA + (int64_t)g.slotA[i * g.nb + k] * B * B, tid);
+                    stage_leaf<B>(Bs + (st ^ 1) * B * B,
+                                  g.leafB + (int64_t)g.slotB[(int64_t)k * g.nb + j] * B * B, tid);
+                }
+                cp_async_commit();
+                cp_async_wait1();
+                __syncthreads();
+                const double *a_s = As + st * B * B;
+                const double *b_s = Bs + st * B * B;
+#pragma unroll 4
+                for (int l = 0; l < B; l++) {
+                    double av[T::TR], bv[T::TC];
+#pragma unroll
+                    for (int a = 0; a < T::TR; a++) av[a] = a_s[(r0 + a) * B + l];
+#pragma unroll
+                    for (int b = 0; b < T::TC; b++) bv[b] = b_s[l * B + c0 + b];
+#pragma unroll
+                    for (int a = 0; a < T::TR; a++)
+#pragma unroll
+                        for (int b = 0; b < T::TC; b++) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+                }
+                __syncthreads();
+            }
+        }
+
+        // ---- epilogue: store C_ij, its squared norm and (diagonal) trace ----
+        double *Cs = As;  // reuse stage 0 of A
+#pragma unroll
+        for (int a = 0; a < T::TR; a++)
+#pragma unroll
+            for (int b = 0; b < T::TC; b++) Cs[(r0 + a) * B + c0 + b] = acc[a][b];
+        __syncthreads();
+        double *dst = g.leafC + (int64_t)g.slotC[grp] * B * B;
+        int emax = 0;
+        for (int q = tid; q < B * B / 2; q += kThreads) {
+            double2 v = reinterpret_cast<const double2 *>(Cs)[q];
+            reinterpret_cast<double2 *>(dst)[q] = v;
+            emax = max(emax, max(exp_key(v.x), exp_key(v.y)));
+        }
+        emax = warp_max_int(emax);
+        if ((tid & 31) == 0) s_red_i[tid >> 5] = emax;
+        __syncthreads();
+        emax = 0;
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; w++) emax = max(emax, s_red_i[w]);
+        u128 accn = 0;
+        if (emax > 0)
+            for (int q = tid; q < B * B; q += kThreads) accn += sq_term(Cs[q], emax);
+        accn = warp_sum_u128(accn);
+        if ((tid & 31) == 0) s_red_u[tid >> 5] = accn;
+        __syncthreads();
+        if (tid == 0) {
+            u128 tot = 0;
+            for (int w = 0; w < kThreads / 32; w++) tot += s_red_u[w];
+            double r = emax > 0 ? sq_sum_round(tot, emax) : 0.0;
+            g.n2C[i * g.P + j] = r;
+            g.n2CT[j * g.P + i] = r;
+            if (i == j && g.tr_part) {
+                double tr = 0.0;
+                for (int q = 0; q < B; q++) tr += Cs[q * B + q];
+                g.tr_part[i] = tr;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int B>
+int launch_b(const GemmArgs &args, cudaStream_t s)
+{
+    size_t smem = sizeof(double) * 4 * B * B;
+    static int configured = 0;
+    if (!configured) {
+        SPAMM_CK(cudaFuncSetAttribute(k_gemm_fp64<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+        configured = 1;
+    }
+    int per_sm = 0;
+    SPAMM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gemm_fp64<B>, kThreads, smem));
+    if (per_sm < 1) per_sm = 1;
+    int64_t G = args.nb * args.nb;
+    int64_t grid = (int64_t)spamm_num_sms() * per_sm;
+    if (grid > G) grid = G;
+    k_gemm_fp64<B><<<(unsigned)grid, kThreads, smem, s>>>(args);
+    SPAMM_CK_LAUNCH();
+    return SPAMM_OK;
+}
+
+}  // namespace
+
+int launch_gemm_fp64(spamm_mat_t A, spamm_mat_t B, spamm_mat_t C, SpammWorkspace *ws,
+                     double *tr_part, cudaStream_t s)
+{
+    GemmArgs g;
+    g.leafA = A->leaf;
+    g.slotA = A->slot;
+    g.leafB = B->leaf;
+    g.slotB = B->slot;
+    g.leafC = C->leaf;
+    g.slotC = C->slot;
+    g.nb = A->nb;
+    g.P = A->P;
+    g.off = ws->off;
+    g.klist = ws->klist;
+    g.counter = ws->counter;
+    g.n2C = C->n2 + tier_offset(C->depth);
+    g.n2CT = C->n2T;
+    g.tr_part = tr_part;
+    SPAMM_CK(cudaMemsetAsync(ws->counter, 0, sizeof(int32_t), s));
+    switch (A->b) {
+    case 16: return launch_b<16>(g, s);
+    case 32: return launch_b<32>(g, s);
+    case 64: return launch_b<64>(g, s);
+    default:
+        spamm_set_error("leaf size %d not built", A->b);
+        return SPAMM_E_NOTSUP;
+    }
+}

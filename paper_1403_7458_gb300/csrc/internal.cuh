@@ -1,0 +1,249 @@
+// internal.cuh -- shared declarations of the CUDA SpAMM / SP2 library.
+//
+// Layout in HBM (one handle = one n x n matrix):
+//   leaf   : nslots leaves, each b x b FP64 row-major and contiguous
+//            (leaf (i, k) lives at slot[i * nb + k]; dense handles use
+//            slot = i * nb + k, so a block row of leaves is contiguous);
+//   slot   : nb x nb int32 slot map (-1 = absent leaf);
+//   n2     : squared norms of the whole quadtree (Sec. 2, Eqs. 1-3), tiers
+//            t = 0..d concatenated, tier t a 2^t x 2^t row-major grid at
+//            offset (4^t - 1) / 3; the leaf tier is P x P, P = 2^d;
+//   n2T    : the leaf tier transposed (n2T[j * P + k] = n2[k][j]) so that a
+//            warp reading B's column of leaf norms reads contiguous memory.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "spamm.h"
+
+// ---------------------------------------------------------------------------
+// Handle and workspace
+// ---------------------------------------------------------------------------
+struct SpammWorkspace {
+    // task list (grouped by output leaf g = i * nb + j)
+    int32_t *counts = nullptr;   // nb*nb
+    int64_t *off = nullptr;      // nb*nb + 1
+    uint32_t *klist = nullptr;   // capacity entries
+    int64_t klist_cap = 0;
+    int64_t groups_cap = 0;
+    int32_t *counter = nullptr;  // work counters and error flags (16 ints)
+    double *tr_part = nullptr;   // per leaf row partial traces (nb)
+    int64_t tr_cap = 0;
+};
+
+struct spamm_mat {
+    int64_t n = 0;
+    int b = 0;
+    int64_t nb = 0;
+    int depth = 0;
+    int64_t P = 0;
+    int64_t nslots = 0;
+    double *leaf = nullptr;
+    int32_t *slot = nullptr;
+    double *n2 = nullptr;
+    double *n2T = nullptr;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    SpammWorkspace ws;  // used when this handle is the output of a product
+};
+
+// ---------------------------------------------------------------------------
+// Host helpers (api.cu)
+// ---------------------------------------------------------------------------
+void spamm_set_error(const char *fmt, ...);
+int spamm_cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+int spamm_alloc(void **p, size_t bytes, cudaStream_t s);
+void spamm_release(void *p, cudaStream_t s);
+
+#define SPAMM_CK(call)                                                        \
+    do {                                                                      \
+        cudaError_t e_ = (call);                                              \
+        if (e_ != cudaSuccess) return spamm_cuda_fail(e_, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define SPAMM_CK_LAUNCH()          \
+    do {                           \
+        spamm_note_launches(1);    \
+        SPAMM_CK(cudaGetLastError()); \
+    } while (0)
+
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+static inline int64_t tier_offset(int t) { return ((int64_t(1) << (2 * t)) - 1) / 3; }
+
+int spamm_num_sms();
+int spamm_mat_alloc(spamm_mat_t m, int64_t n, int b, cudaStream_t s);
+int spamm_mat_same_shape(spamm_mat_t a, spamm_mat_t b);
+
+// Norms (norms.cu)
+int launch_leaf_norms(spamm_mat_t m, cudaStream_t s);
+int launch_pyramid(spamm_mat_t m, cudaStream_t s);
+
+// Cull (cull.cu): fills ws.off / ws.klist for SpAMM(A, B, tau) into C's workspace.
+// On return *total_host is the number of tasks when `need_total` is set (blocking),
+// otherwise -1.
+int spamm_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws,
+               int64_t nb, int64_t P, cudaStream_t s, bool need_total, int64_t *total_host);
+int ws_reserve_groups(SpammWorkspace *ws, int64_t groups, int64_t nb, cudaStream_t s);
+
+// C = SpAMM(A, B, tau) into an existing handle (api.cu).  ev (optional, 4
+// events) is recorded before the cull, before the products, before and after
+// C's upper norm tiers.
+int spamm_multiply_into(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t C,
+                        const spamm_opts_t *opts, double *tr_part, cudaStream_t s,
+                        bool need_total, int64_t *tasks_out, bool build_pyramid,
+                        cudaEvent_t *ev);
+
+// Count of kernels this library launched (for reports).
+void spamm_note_launches(int64_t k);
+int64_t spamm_launch_count();
+
+// Leaf products (gemm_fp64.cu)
+int launch_gemm_fp64(spamm_mat_t A, spamm_mat_t B, spamm_mat_t C, SpammWorkspace *ws,
+                     double *tr_part, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+
+typedef unsigned __int128 u128;
+
+// Exponent key and integer significand of |x| (IEEE binary64):
+// |x| = m * 2^(e - 1075) with e >= 1; m = 0 for x = 0.
+__device__ __forceinline__ void dbl_decompose(double x, uint64_t &m, int &e)
+{
+    uint64_t u = (uint64_t)__double_as_longlong(x);
+    int E = (int)((u >> 52) & 0x7ff);
+    uint64_t f = u & 0xFFFFFFFFFFFFFull;
+    if (E == 0) {
+        m = f;
+        e = 1;
+    } else {
+        m = f | (1ull << 52);
+        e = E;
+    }
+}
+
+// RN(S * 2^k) for an unsigned 128-bit integer S (round to nearest, ties to
+// even).  Exact whenever the result is a normal double.
+__device__ __forceinline__ double u128_round_scaled(u128 S, int k)
+{
+    if (S == 0) return 0.0;
+    uint64_t hi = (uint64_t)(S >> 64), lo = (uint64_t)S;
+    int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+    uint64_t mant;
+    if (msb <= 52) {
+        mant = lo;
+    } else {
+        int sh = msb - 52;
+        mant = (uint64_t)(S >> sh);
+        u128 rem = S & ((((u128)1) << sh) - 1);
+        u128 half = ((u128)1) << (sh - 1);
+        if (rem > half || (rem == half && (mant & 1))) mant++;
+        if (mant == (1ull << 53)) {
+            mant >>= 1;
+            sh++;
+        }
+        k += sh;
+    }
+    if (mant >= (1ull << 52)) {
+        int be = k + 52 + 1023;
+        if (be >= 1 && be <= 2046)
+            return __longlong_as_double((long long)(((uint64_t)be << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+    }
+    return ldexp((double)mant, k);
+}
+
+// Exact fixed-point accumulation of squares: with emax the largest exponent
+// key in a set of doubles, x^2 contributes floor(m^2 * 2^10 / 4^(emax - e))
+// units of 2^(2 emax - 2160).  Every term is truncated on its own, so the sum
+// is independent of the order of accumulation; the truncation is below 2^-104
+// of the result, far inside one FP64 rounding.
+__device__ __forceinline__ u128 sq_term(double x, int emax)
+{
+    uint64_t m;
+    int e;
+    dbl_decompose(x, m, e);
+    if (m == 0) return 0;
+    int sh = 2 * (emax - e);
+    if (sh >= 120) return 0;
+    u128 t = ((u128)m * (u128)m) << 10;
+    return t >> sh;
+}
+
+__device__ __forceinline__ int exp_key(double x)
+{
+    uint64_t m;
+    int e;
+    dbl_decompose(x, m, e);
+    return m ? e : 0;
+}
+
+__device__ __forceinline__ double sq_sum_round(u128 S, int emax)
+{
+    return u128_round_scaled(S, 2 * emax - 2160);
+}
+
+// Same scheme for non-negative doubles themselves (a parent's four children).
+__device__ __forceinline__ u128 val_term(double x, int emax)
+{
+    uint64_t m;
+    int e;
+    dbl_decompose(x, m, e);
+    if (m == 0) return 0;
+    int sh = emax - e;
+    if (sh >= 120) return 0;
+    u128 t = ((u128)m) << 63;
+    return t >> sh;
+}
+
+__device__ __forceinline__ double val_sum_round(u128 S, int emax)
+{
+    return u128_round_scaled(S, emax - 1075 - 63);
+}
+
+__device__ __forceinline__ u128 shfl_xor_u128(u128 v, int mask)
+{
+    uint64_t lo = (uint64_t)v, hi = (uint64_t)(v >> 64);
+    lo = __shfl_xor_sync(0xffffffffu, lo, mask);
+    hi = __shfl_xor_sync(0xffffffffu, hi, mask);
+    return ((u128)hi << 64) | lo;
+}
+
+__device__ __forceinline__ u128 warp_sum_u128(u128 v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += shfl_xor_u128(v, o);
+    return v;
+}
+
+__device__ __forceinline__ int warp_max_int(int v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// The culling predicate of Eq. 4 on squared norms, n2a * n2b > tau2, decided
+// exactly as the FP64 expression would be.  Most candidates are settled from
+// the exponent fields alone (integer work); the FP64 product is formed only
+// when the exponents leave the outcome open.
+__device__ __forceinline__ bool keep_product(double n2a, double n2b, double tau2)
+{
+    uint64_t ua = (uint64_t)__double_as_longlong(n2a);
+    uint64_t ub = (uint64_t)__double_as_longlong(n2b);
+    uint64_t ut = (uint64_t)__double_as_longlong(tau2);
+    int ea = (int)(ua >> 52) & 0x7ff, eb = (int)(ub >> 52) & 0x7ff, et = (int)(ut >> 52) & 0x7ff;
+    if (ua == 0 || ub == 0) return false;  // +0 norm: product is 0, never > tau2 >= 0
+    if (ea != 0 && eb != 0 && et != 0 && ea != 0x7ff && eb != 0x7ff && et != 0x7ff) {
+        // n2a in [2^(ea-1023), 2^(ea-1022)), same for n2b, tau2 in [2^(et-1023), ...)
+        int lo = ea + eb - 2046;  // product in [2^lo, 2^(lo+2))
+        int tl = et - 1023;
+        if (lo + 2 <= tl) return false;  // RN(product) <= 2^(lo+2) <= tau2
+        if (lo >= tl + 1) return true;   // RN(product) >= 2^lo > tau2
+    }
+    return n2a * n2b > tau2;
+}
+
+#endif  // __CUDACC__

@@ -1,0 +1,415 @@
+// sp2.cu -- the SP2 spectral projection loop (Niklasson 2002, the solver the
+// paper drives with SpAMM in Sec. 4).
+//
+// Per solve:
+//   gershgorin : one thread per matrix row sums |f_ij| (j != i) in column
+//                order; a one-block kernel takes min / max of f_ii -/+ sum;
+//   x0         : X0 = (emax I - F) / (emax - emin), fused with X0's leaf norms
+//                and its trace.
+// Per iteration (all on the device, the host reads five scalars):
+//   cull + leaf products : X2 = SpAMM(X, X, tau), diagonal leaves also emit
+//                          their traces;
+//   decide               : one block sums those traces in a fixed order and
+//                          picks X2 or 2X - X2;
+//   update               : one warp per leaf writes the new X in place, its
+//                          exact squared norm, the partial ||X2 - X||_F^2 and
+//                          the diagonal traces; the last block to finish
+//                          reduces the partials in a fixed order.
+// Every reduction has a fixed order, so two runs give identical bits.
+#include <math.h>
+#include <string.h>
+
+#include "internal.cuh"
+
+namespace {
+
+struct Sp2State {
+    double emin, emax;
+    double t1;      // tr X
+    double t2;      // tr X^2
+    double e;       // ||X^2 - X||_F
+    double tn;      // tr of the updated X
+    int64_t tasks;  // surviving triples of this iteration's product
+    int32_t branch; // 1: X <- X^2
+    int32_t done;   // last-block ticket
+};
+
+constexpr int kWarps = 8;
+constexpr int kRedThreads = 1024;
+
+__global__ void k_gershgorin_rows(const double *__restrict__ leaf, const int32_t *__restrict__ slot,
+                                  int64_t n, int b, int64_t nb, double *__restrict__ lo,
+                                  double *__restrict__ hi)
+{
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    int64_t I = r / b, rr = r % b;
+    double s = 0.0, d = 0.0;
+    for (int64_t K = 0; K < nb; K++) {
+        int32_t sl = slot[I * nb + K];
+        if (sl < 0) continue;
+        const double *row = leaf + (int64_t)sl * b * b + rr * b;
+        for (int c = 0; c < b; c++) {
+            int64_t col = K * b + c;
+            if (col >= n) break;
+            double v = row[c];
+            if (col == r) d = v;
+            else s += fabs(v);
+        }
+    }
+    lo[r] = d - s;
+    hi[r] = d + s;
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+k_gershgorin_bounds(const double *__restrict__ lo, const double *__restrict__ hi, int64_t n,
+                    Sp2State *st)
+{
+    __shared__ double smin[kRedThreads], smax[kRedThreads];
+    double a = INFINITY, z = -INFINITY;
+    for (int64_t q = threadIdx.x; q < n; q += kRedThreads) {
+        a = fmin(a, lo[q]);
+        z = fmax(z, hi[q]);
+    }
+    smin[threadIdx.x] = a;
+    smax[threadIdx.x] = z;
+    __syncthreads();
+    for (int o = kRedThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + o]);
+            smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        st->emin = smin[0];
+        st->emax = smax[0];
+        st->done = 0;
+    }
+}
+
+// Fixed-order sum of v[0..count) by one block: thread t adds v[t], v[t+T], ...
+// in order, then a fixed binary tree.  Result valid in thread 0.
+__device__ double block_sum_fixed(const double *v, int64_t count, double *sbuf)
+{
+    double a = 0.0;
+    for (int64_t q = threadIdx.x; q < count; q += blockDim.x) a += __ldcg(v + q);
+    sbuf[threadIdx.x] = a;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sbuf[threadIdx.x] += sbuf[threadIdx.x + o];
+        __syncthreads();
+    }
+    double r = sbuf[0];
+    __syncthreads();
+    return r;
+}
+
+// Elementwise pass over all leaves of X, one warp per leaf.
+//   mode 0: X <- (emax I - F) / (emax - emin)          (src = F)
+//   mode 1: X <- X2 if branch else 2 X - X2            (src = X2)
+// Writes the leaf's squared norm (exact, once rounded), its partial
+// ||X2 - X||^2 (mode 1) and, for diagonal leaves, its trace.  The last block
+// reduces the partials and stores e and the new trace in the state.
+__global__ void __launch_bounds__(kWarps * 32)
+k_sp2_elementwise(int mode, double *__restrict__ X, const double *__restrict__ src,
+                  const int32_t *__restrict__ slot, int64_t n, int64_t nb, int64_t P, int b,
+                  double *__restrict__ n2, double *__restrict__ n2T, double *__restrict__ idem_part,
+                  double *__restrict__ diag_part, Sp2State *st)
+{
+    __shared__ double sred[kWarps * 32];
+    __shared__ bool s_last;
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const int bb = b * b;
+    const bool take_sq = st->branch != 0;
+    const double emax = st->emax, range = st->emax - st->emin;
+    if (w < nb * nb) {
+        const int64_t I = w / nb, K = w % nb;
+        const int64_t base = (int64_t)slot[w] * bb;
+        double *x = X + base;
+        const double *y = src + base;
+        const bool diag = I == K;
+        double idem = 0.0;
+        int ek = 0;
+        for (int q = lane; q < bb; q += 32) {
+            double yv = y[q], nv;
+            if (mode == 0) {
+                const int r = q / b;
+                nv = ((diag && r == q % b && I * b + r < n) ? emax : 0.0) - yv;
+                nv = nv / range;
+            } else {
+                double xv = x[q];
+                double d = yv - xv;
+                idem = fma(d, d, idem);
+                nv = take_sq ? yv : fma(2.0, xv, -yv);
+            }
+            x[q] = nv;
+            ek = max(ek, exp_key(nv));
+        }
+        ek = warp_max_int(ek);
+        __syncwarp();
+        u128 acc = 0;
+        double dsum = 0.0;
+        if (ek > 0)
+            for (int q = lane; q < bb; q += 32) acc += sq_term(x[q], ek);
+        if (diag)
+            for (int r = lane; r < b; r += 32) dsum += x[r * b + r];
+        acc = warp_sum_u128(acc);
+        for (int o = 16; o > 0; o >>= 1) {
+            idem += __shfl_xor_sync(0xffffffffu, idem, o);
+            dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+        }
+        if (lane == 0) {
+            double r = ek > 0 ? sq_sum_round(acc, ek) : 0.0;
+            n2[I * P + K] = r;
+            n2T[K * P + I] = r;
+            idem_part[w] = idem;
+            if (diag) diag_part[I] = dsum;
+        }
+    }
+    // last block reduces
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&st->done, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double e2 = block_sum_fixed(idem_part, nb * nb, sred);
+    double tn = block_sum_fixed(diag_part, nb, sred);
+    if (threadIdx.x == 0) {
+        if (mode == 1) st->e = sqrt(e2);
+        st->tn = tn;
+        st->done = 0;
+    }
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+k_sp2_decide(const double *__restrict__ tr_part, int64_t nb, const int64_t *__restrict__ off_end,
+             double Ne, int rule, Sp2State *st)
+{
+    __shared__ double sred[kRedThreads];
+    double t2 = block_sum_fixed(tr_part, nb, sred);
+    if (threadIdx.x == 0) {
+        double t1 = st->tn;
+        int take;
+        if (rule == SP2_RULE_TRACE_ABOVE) take = t1 > Ne;
+        else take = fabs(t2 - Ne) < fabs(2.0 * t1 - t2 - Ne);
+        st->t1 = t1;
+        st->t2 = t2;
+        st->branch = take;
+        st->tasks = *off_end;
+    }
+}
+
+struct Sp2Scratch {
+    Sp2State *st = nullptr;
+    double *lo = nullptr, *hi = nullptr;
+    double *idem_part = nullptr, *diag_part = nullptr, *tr_part = nullptr;
+    Sp2State *host = nullptr;
+    void release(cudaStream_t s)
+    {
+        spamm_release(st, s);
+        spamm_release(lo, s);
+        spamm_release(hi, s);
+        spamm_release(idem_part, s);
+        spamm_release(diag_part, s);
+        spamm_release(tr_part, s);
+        if (host) cudaFreeHost(host);
+    }
+};
+
+}  // namespace
+
+extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t *opts,
+                         spamm_mat_t *Pout, sp2_report_t *report, void *stream)
+{
+    if (!F || !Pout || !(Ne > 0.0) || !(Ne < (double)F->n) || !(tau >= 0.0) || tau > 1e300) {
+        spamm_set_error("sp2_solve: bad arguments (Ne must be in (0, n), tau finite >= 0)");
+        return SPAMM_E_INVAL;
+    }
+    sp2_opts_t o;
+    memset(&o, 0, sizeof(o));
+    if (opts) o = *opts;
+    if (o.max_iter <= 0) o.max_iter = 100;
+    if (o.trace_tol <= 0) o.trace_tol = 1e-10;
+    if (o.idem_tol <= 0) o.idem_tol = 1e-8;
+    if (o.leaf && o.leaf != F->b) {
+        spamm_set_error("sp2_solve: opts.leaf (%d) differs from F's leaf size (%d)", o.leaf, F->b);
+        return SPAMM_E_INVAL;
+    }
+    if (o.prec != SPAMM_FP64) {
+        spamm_set_error("sp2_solve: precision mode %d not built", o.prec);
+        return SPAMM_E_NOTSUP;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t nb = F->nb, G = nb * nb;
+    int rc;
+    bool created = false;
+    if (*Pout == nullptr) {
+        spamm_mat_t m = new spamm_mat();
+        if ((rc = spamm_mat_alloc(m, F->n, F->b, s))) {
+            spamm_free(m);
+            return rc;
+        }
+        *Pout = m;
+        created = true;
+    } else if (!spamm_mat_same_shape(*Pout, F) || *Pout == F) {
+        spamm_set_error("sp2_solve: P must match F's shape and not alias F");
+        return SPAMM_E_INVAL;
+    }
+    spamm_mat_t X = *Pout;
+    spamm_mat_t X2 = new spamm_mat();
+    Sp2Scratch sc;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t evs[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    const bool timing = (o.flags & SPAMM_F_TIMING) != 0;
+    double ms_cull = 0.0, ms_gemm = 0.0, ms_update = 0.0;
+    const int64_t launches0 = spamm_launch_count();
+    int it = 0, reason = SP2_STOP_MAXITER;
+    double ehist[3] = {INFINITY, INFINITY, INFINITY};
+    int64_t tasks_total = 0;
+    Sp2State h;
+    memset(&h, 0, sizeof(h));
+    spamm_opts_t mo;
+    memset(&mo, 0, sizeof(mo));
+    mo.leaf = F->b;
+    mo.prec = o.prec;
+    mo.slices = o.slices;
+    const int limit = o.fixed_iters > 0 ? o.fixed_iters : o.max_iter;
+    unsigned ew_blocks = (unsigned)((G + kWarps - 1) / kWarps);
+
+#define SP2_TRY(x)                 \
+    do {                           \
+        if ((rc = (x))) goto done; \
+    } while (0)
+#define SP2_LAUNCHED()                      \
+    do {                                    \
+        spamm_note_launches(1);             \
+        SP2_CUDA(cudaGetLastError());       \
+    } while (0)
+#define SP2_CUDA(x)                                                           \
+    do {                                                                      \
+        cudaError_t e_ = (x);                                                 \
+        if (e_ != cudaSuccess) {                                              \
+            rc = spamm_cuda_fail(e_, #x, __FILE__, __LINE__);                 \
+            goto done;                                                        \
+        }                                                                     \
+    } while (0)
+
+    SP2_TRY(spamm_mat_alloc(X2, F->n, F->b, s));
+    SP2_TRY(spamm_alloc((void **)&sc.st, sizeof(Sp2State), s));
+    SP2_TRY(spamm_alloc((void **)&sc.lo, sizeof(double) * F->n, s));
+    SP2_TRY(spamm_alloc((void **)&sc.hi, sizeof(double) * F->n, s));
+    SP2_TRY(spamm_alloc((void **)&sc.idem_part, sizeof(double) * G, s));
+    SP2_TRY(spamm_alloc((void **)&sc.diag_part, sizeof(double) * nb, s));
+    SP2_TRY(spamm_alloc((void **)&sc.tr_part, sizeof(double) * nb, s));
+    SP2_CUDA(cudaMallocHost((void **)&sc.host, sizeof(Sp2State)));
+    SP2_CUDA(cudaMemsetAsync(sc.st, 0, sizeof(Sp2State), s));
+    SP2_CUDA(cudaEventCreate(&ev0));
+    SP2_CUDA(cudaEventCreate(&ev1));
+    if (timing)
+        for (int q = 0; q < 5; q++) SP2_CUDA(cudaEventCreate(&evs[q]));
+    SP2_CUDA(cudaEventRecord(ev0, s));
+
+    k_gershgorin_rows<<<(unsigned)((F->n + 255) / 256), 256, 0, s>>>(F->leaf, F->slot, F->n, F->b,
+                                                                      nb, sc.lo, sc.hi);
+    SP2_LAUNCHED();
+    k_gershgorin_bounds<<<1, kRedThreads, 0, s>>>(sc.lo, sc.hi, F->n, sc.st);
+    SP2_LAUNCHED();
+    k_sp2_elementwise<<<ew_blocks, kWarps * 32, 0, s>>>(0, X->leaf, F->leaf, X->slot, F->n, nb, X->P, X->b,
+                                                        X->n2 + tier_offset(X->depth), X->n2T,
+                                                        sc.idem_part, sc.diag_part, sc.st);
+    SP2_LAUNCHED();
+
+    while (it < limit) {
+        SP2_TRY(spamm_multiply_into(X, X, tau, X2, &mo, sc.tr_part, s, false, nullptr, false,
+                                    timing ? evs : nullptr));
+        k_sp2_decide<<<1, kRedThreads, 0, s>>>(sc.tr_part, nb, X2->ws.off + G, Ne, o.rule, sc.st);
+        SP2_LAUNCHED();
+        k_sp2_elementwise<<<ew_blocks, kWarps * 32, 0, s>>>(
+            1, X->leaf, X2->leaf, X->slot, F->n, nb, X->P, X->b, X->n2 + tier_offset(X->depth),
+            X->n2T, sc.idem_part, sc.diag_part, sc.st);
+        SP2_LAUNCHED();
+        if (timing) SP2_CUDA(cudaEventRecord(evs[4], s));
+        SP2_CUDA(cudaMemcpyAsync(sc.host, sc.st, sizeof(Sp2State), cudaMemcpyDeviceToHost, s));
+        SP2_CUDA(cudaStreamSynchronize(s));
+        h = *sc.host;
+        if (timing) {
+            float a = 0.f, b = 0.f, c = 0.f;
+            cudaEventElapsedTime(&a, evs[0], evs[1]);
+            cudaEventElapsedTime(&b, evs[1], evs[2]);
+            cudaEventElapsedTime(&c, evs[3], evs[4]);
+            ms_cull += a;
+            ms_gemm += b;
+            ms_update += c;
+        }
+        tasks_total += h.tasks;
+        if (report && report->history && it < report->history_cap) {
+            double *row = report->history + (int64_t)it * SP2_H_COLS;
+            row[SP2_H_TR] = h.t1;
+            row[SP2_H_TR2] = h.t2;
+            row[SP2_H_IDEM] = h.e;
+            row[SP2_H_BRANCH] = h.branch ? 1.0 : 0.0;
+            row[SP2_H_TASKS] = (double)h.tasks;
+            row[SP2_H_TRNEW] = h.tn;
+        }
+        ehist[0] = ehist[1];
+        ehist[1] = ehist[2];
+        ehist[2] = h.e;
+        it++;
+        if (o.fixed_iters > 0) {
+            if (it == o.fixed_iters) reason = SP2_STOP_FIXED;
+            continue;
+        }
+        if (fabs(h.tn - Ne) < o.trace_tol && h.e < o.idem_tol) {
+            reason = SP2_STOP_CONVERGED;
+            break;
+        }
+        if (it >= 3 && h.e < 1e-3 && h.e > 0.5 * ehist[0]) {
+            reason = SP2_STOP_STAGNATED;
+            break;
+        }
+    }
+    SP2_TRY(launch_pyramid(X, s));
+    SP2_CUDA(cudaEventRecord(ev1, s));
+    SP2_CUDA(cudaEventSynchronize(ev1));
+    if (it == 0) {  // no iteration: report the start
+        SP2_CUDA(cudaMemcpyAsync(sc.host, sc.st, sizeof(Sp2State), cudaMemcpyDeviceToHost, s));
+        SP2_CUDA(cudaStreamSynchronize(s));
+        h = *sc.host;
+    }
+    if (report) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev0, ev1);
+        report->iters = it;
+        report->stop_reason = reason;
+        report->trace_err = fabs(h.tn - Ne);
+        report->idem_err = h.e;
+        report->emin = h.emin;
+        report->emax = h.emax;
+        report->tasks_total = tasks_total;
+        report->flops_useful = 2.0 * double(F->b) * F->b * F->b * double(tasks_total);
+        report->ms_total = ms;
+        report->ms_cull = ms_cull;
+        report->ms_gemm = ms_gemm;
+        report->ms_update = ms_update;
+        report->launches = spamm_launch_count() - launches0;
+    }
+    rc = reason == SP2_STOP_MAXITER ? SPAMM_E_NOCONV : SPAMM_OK;
+    if (rc == SPAMM_E_NOCONV) spamm_set_error("sp2_solve: %d iterations without convergence", it);
+done:
+    for (int q = 0; q < 5; q++)
+        if (evs[q]) cudaEventDestroy(evs[q]);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    sc.release(s);
+    spamm_free(X2);
+    if (rc && rc != SPAMM_E_NOCONV && created) {
+        spamm_free(*Pout);
+        *Pout = nullptr;
+    }
+    return rc;
+#undef SP2_TRY
+#undef SP2_CUDA
+}

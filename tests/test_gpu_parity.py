@@ -1,0 +1,210 @@
+"""CUDA path vs the CPU oracle, through the C ABI, on identical seeded inputs.
+
+Bars:
+- squared norms of every quadtree tier: bit-exact (both sides round the exact
+  sum once);
+- culled task lists: bit-exact (same predicate, same norms);
+- FP64 leaf products: |C_gpu - C_oracle| <= 2 n u (|A||B|)_ij elementwise
+  (both sum the same kept terms, k increasing, in FP64; the CUDA kernel uses
+  fused multiply-adds, the oracle separate roundings, so each entry can differ
+  by at most the gamma_n bound of either evaluation);
+- SP2: same Gershgorin bounds (same sums, same order), same task counts and
+  branches until X is idempotent to 1e-6 (beyond that the two branch values
+  differ by O(e^2) and rounding may pick either), and
+  ||P_gpu - P_oracle||_F <= 1e-10 + 10 e, with e the oracle's final
+  idempotency error: once X stalls at the SpAMM error floor, each further
+  iteration moves X by O(e) and either side may take the other branch.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1403_7458_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -53
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dev(a):
+    torch = _torch()
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _wide(n, seed):
+    rng = np.random.default_rng(seed)
+    return 10.0 ** rng.uniform(-9, 3, size=(n, n)) * np.where(rng.random((n, n)) < .5, -1., 1.)
+
+
+def _sorted_gpu_tasks(off, k, nb):
+    g = np.repeat(np.arange(nb * nb), np.diff(off))
+    i, j = g // nb, g % nb
+    t = np.stack([i, k.astype(np.int64), j], axis=1)
+    order = np.lexsort((t[:, 1], t[:, 2], t[:, 0]))
+    return t[order]
+
+
+@pytest.mark.parametrize("n,b", [(200, 16), (200, 32), (130, 64), (1024, 32), (33, 32)])
+def test_norm_pyramid_bit_exact(cuda_lib, n, b):
+    a = _wide(n, n + b)
+    A = cuda_lib.tree_build(_dev(a), leaf=b)
+    ref = oracle.norm_pyramid(a, b)
+    assert A.depth == len(ref) - 1
+    for t, r in enumerate(ref):
+        got = cuda_lib.norms(A, t)
+        assert np.array_equal(got, r), (t, np.abs(got - r).max())
+
+
+def test_tree_build_from_host_memory(cuda_lib):
+    a = synth.decaying_matrix(100, 1)
+    A = cuda_lib.tree_build(a, leaf=16)          # numpy = host pointer
+    back = np.zeros((100, 100))
+    cuda_lib.to_dense(A, out=back)
+    assert np.array_equal(back, a)
+    assert np.array_equal(cuda_lib.norms(A, A.depth), oracle.leaf_norms2(a, 16))
+
+
+@pytest.mark.parametrize("n,b,tau", [(1024, 32, 1e-6), (1000, 16, 1e-6), (512, 64, 1e-8),
+                                     (384, 32, 0.0), (384, 32, 1e-2), (256, 32, 1e300)])
+def test_task_list_bit_exact(cuda_lib, n, b, tau):
+    a = synth.decaying_matrix(n, 7)
+    A = cuda_lib.tree_build(_dev(a), leaf=b)
+    off, k = cuda_lib.task_list(A, A, tau)
+    nb = A.nb
+    n2 = oracle.leaf_norms2(a, b)
+    flat = oracle.flat_tasks(n2, n2, nb, tau)
+    got = _sorted_gpu_tasks(off, k, nb)
+    assert got.shape == flat.shape
+    assert np.array_equal(got, flat.astype(np.int64))
+    # k increasing inside every group
+    for g in range(0, nb * nb, max(1, nb * nb // 97)):
+        ks = k[off[g]:off[g + 1]]
+        assert np.all(np.diff(ks.astype(np.int64)) > 0)
+
+
+def test_task_list_matches_recursive_walk_distinct_operands(cuda_lib):
+    n, b, tau = 320, 32, 1e-5
+    a = synth.decaying_matrix(n, 3, decay=1.0)
+    bm = synth.decaying_matrix(n, 4, decay=2.0)
+    A = cuda_lib.tree_build(_dev(a), leaf=b)
+    B = cuda_lib.tree_build(_dev(bm), leaf=b)
+    off, k = cuda_lib.task_list(A, B, tau)
+    _, rec = oracle.spamm(a, bm, b, tau, want_tasks=True)
+    order = np.lexsort((rec[:, 1], rec[:, 2], rec[:, 0]))
+    assert np.array_equal(_sorted_gpu_tasks(off, k, A.nb), rec[order].astype(np.int64))
+
+
+@pytest.mark.parametrize("n,b,tau,seed", [(1024, 32, 1e-6, 0), (1000, 16, 1e-6, 1),
+                                          (640, 64, 1e-8, 2), (300, 32, 0.0, 3),
+                                          (96, 32, 1e-3, 4)])
+def test_spamm_fp64_values(cuda_lib, n, b, tau, seed):
+    a = synth.decaying_matrix(n, seed)
+    bm = synth.decaying_matrix(n, seed + 100, decay=1.2)
+    A = cuda_lib.tree_build(_dev(a), leaf=b)
+    B = cuda_lib.tree_build(_dev(bm), leaf=b)
+    C, st = cuda_lib.multiply(A, B, tau, stats=True)
+    c = cuda_lib.to_dense(C).cpu().numpy()
+    ref, tasks = oracle.spamm(a, bm, b, tau, want_tasks=True)
+    assert st["tasks"] == len(tasks)
+    assert st["flops_useful"] == 2.0 * b ** 3 * len(tasks)
+    bound = 2 * n * U * (np.abs(a) @ np.abs(bm))
+    assert np.all(np.abs(c - ref) <= bound + 1e-300)
+    # C's quadtree is built from the stored leaves
+    for t, r in enumerate(oracle.norm_pyramid(c, b)):
+        assert np.array_equal(cuda_lib.norms(C, t), r)
+
+
+def test_spamm_reuses_output_handle(cuda_lib):
+    a = synth.decaying_matrix(256, 5)
+    A = cuda_lib.tree_build(_dev(a), leaf=32)
+    C, _ = cuda_lib.multiply(A, A, 1e-6)
+    first = cuda_lib.to_dense(C).cpu().numpy()
+    C2, _ = cuda_lib.multiply(A, A, 1e-1, C=C)
+    assert C2 is C
+    ref = oracle.spamm(a, a, 32, 1e-1)
+    assert np.allclose(cuda_lib.to_dense(C).cpu().numpy(), ref, atol=1e-12, rtol=0)
+    assert not np.array_equal(first, cuda_lib.to_dense(C).cpu().numpy())
+
+
+def test_spamm_deterministic(cuda_lib):
+    a = synth.decaying_matrix(768, 6)
+    A = cuda_lib.tree_build(_dev(a), leaf=32)
+    C1, _ = cuda_lib.multiply(A, A, 1e-8)
+    C2, _ = cuda_lib.multiply(A, A, 1e-8)
+    assert np.array_equal(cuda_lib.to_dense(C1).cpu().numpy(), cuda_lib.to_dense(C2).cpu().numpy())
+
+
+@pytest.mark.parametrize("n,b,tau", [(512, 32, 1e-8), (300, 16, 1e-6), (256, 64, 0.0)])
+def test_sp2_fp64_matches_oracle(cuda_lib, n, b, tau):
+    h = synth.tb_hamiltonian(n, n)
+    F = cuda_lib.tree_build(_dev(h), leaf=b)
+    P, rep = cuda_lib.sp2_solve(F, n / 2, tau)
+    p = cuda_lib.to_dense(P).cpu().numpy()
+    p_ref, hist, stop = oracle.sp2(h, b, n / 2, tau)
+    lo, hi = oracle.gershgorin(h)
+    assert rep["emin"] == lo and rep["emax"] == hi       # same sums in the same order
+    assert rep["stop_reason"] == stop
+    assert rep["iters"] == len(hist)
+    gh = rep["history"]
+    # task counts and branches agree until X is idempotent to ~1e-6
+    for r_gpu, r_ref in zip(gh, hist):
+        if r_ref[oracle.H_IDEM] < 1e-6:
+            break
+        assert r_gpu[oracle.H_BRANCH] == r_ref[oracle.H_BRANCH]
+        assert r_gpu[oracle.H_TASKS] == r_ref[oracle.H_TASKS]
+        assert r_gpu[oracle.H_TR] == pytest.approx(r_ref[oracle.H_TR], abs=1e-9)
+    assert np.linalg.norm(p - p_ref) <= 1e-10 + 10 * hist[-1, oracle.H_IDEM]
+
+
+def test_sp2_first_iterations_config1_size(cuda_lib):
+    """N = 4096 tight-binding Hamiltonian, tau = 1e-8: the oracle runs three
+    SP2 iterations (fixed-iteration mode) and the GPU must agree on every
+    task count and branch, with P within 1e-9."""
+    n, b, tau = 4096, 32, 1e-8
+    h = synth.tb_hamiltonian(n, 0)
+    F = cuda_lib.tree_build(_dev(h), leaf=b)
+    P, rep = cuda_lib.sp2_solve(F, n / 2, tau, fixed_iters=3)
+    p_ref, hist, stop = oracle.sp2(h, b, n / 2, tau, fixed_iters=3)
+    gh = rep["history"]
+    assert np.array_equal(gh[:, oracle.H_TASKS], hist[:, oracle.H_TASKS])
+    assert np.array_equal(gh[:, oracle.H_BRANCH], hist[:, oracle.H_BRANCH])
+    p = cuda_lib.to_dense(P).cpu().numpy()
+    assert np.linalg.norm(p - p_ref) <= 1e-9
+
+
+def test_sp2_full_config1_properties(cuda_lib):
+    """Full N = 4096 solve at tau = 1e-8: trace, idempotency and commutation
+    hold at the SpAMM error level (the oracle needs minutes for this size)."""
+    torch = _torch()
+    n, b, tau = 4096, 32, 1e-8
+    h = synth.tb_hamiltonian(n, 0)
+    hd = _dev(h)
+    F = cuda_lib.tree_build(hd, leaf=b)
+    P, rep = cuda_lib.sp2_solve(F, n / 2, tau)
+    assert rep["stop_reason"] in (cuda_lib.STOP_CONVERGED, cuda_lib.STOP_STAGNATED)
+    p = cuda_lib.to_dense(P)
+    assert abs(torch.trace(p).item() - n / 2) < 1e-6
+    assert torch.linalg.norm(p @ p - p).item() < 1e-5
+    assert torch.linalg.norm(hd @ p - p @ hd).item() < 1e-4
+
+
+def test_bad_arguments_raise(cuda_lib):
+    a = synth.decaying_matrix(64, 0)
+    A = cuda_lib.tree_build(_dev(a), leaf=32)
+    B = cuda_lib.tree_build(_dev(synth.decaying_matrix(96, 0)), leaf=32)
+    with pytest.raises(cuda_lib.SpammError) as ei:
+        cuda_lib.multiply(A, B, 1e-6)
+    assert ei.value.status == cuda_lib.E_INVAL
+    with pytest.raises(cuda_lib.SpammError):
+        cuda_lib.multiply(A, A, -1.0)
+    with pytest.raises(cuda_lib.SpammError):
+        cuda_lib.multiply(A, A, float("nan"))
+    with pytest.raises(cuda_lib.SpammError):
+        cuda_lib.tree_build(_dev(a), leaf=24)
+    with pytest.raises(cuda_lib.SpammError):
+        cuda_lib.sp2_solve(A, 64.0, 1e-8)     # Ne must be < n
