@@ -144,6 +144,32 @@ int spamm_info(spamm_mat_t M, int64_t *n, int32_t *leaf, int64_t *nb,
 int spamm_task_list(spamm_mat_t A, spamm_mat_t B, double tau, int64_t *off_host,
                     uint32_t *k_host, int64_t cap, int64_t *ntasks, void *stream);
 
+/*
+ * The culled task list of SpAMM(A, B, tau), like spamm_task_list, for callers
+ * that cannot allocate device memory (codes that give all of HBM to their own
+ * memory pool, and latency-critical loops that cannot afford the implicit
+ * synchronisation of cudaMalloc / cudaFree).  The paper has no counterpart:
+ * this is a deployment variant of the culling pass.  It allocates nothing;
+ * its only scratch is a fixed file-scope device array of
+ * 1024 x 1024 int32 counts (4 MiB, held by every GPU that loads the library
+ * until the process exits).
+ * n2A    : device, leaf-tier squared norms of A, nb rows, row stride lda >= nb
+ *          (e.g. spamm_norms(A, depth, ...) with lda = 2^depth).
+ * n2B    : device, the same for B (row-major, stride ldb >= nb).
+ * nb     : leaf grid, 1 <= nb <= 1024 (larger: SPAMM_E_CAPACITY).
+ * off    : device, nb*nb + 1 int64; off[g] .. off[g+1] are the surviving k of
+ *          output leaf g = i * nb + j; off[nb*nb] is the total.
+ * klist  : device, room for cap uint32 (may be NULL when cap = 0).  When the
+ *          total exceeds cap, groups that do not fit are not written: compare
+ *          off[nb*nb] with cap after the stream reaches this work.
+ * Asynchronous on `stream`.  The first call on a device looks up the scratch
+ * array's device address (once per device).  All calls share the scratch:
+ * calls whose GPU work overlaps (unordered streams) race on it.
+ */
+int spamm_cull_noalloc(const double *n2A, int64_t lda, const double *n2B, int64_t ldb,
+                       int64_t nb, double tau, int64_t *off, uint32_t *klist, int64_t cap,
+                       void *stream);
+
 /* Release a handle (its device memory is freed in stream order). */
 void spamm_free(spamm_mat_t M);
 

@@ -88,6 +88,7 @@ def load():
     lib.spamm_info.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i64),
                                ctypes.POINTER(i32)]
     lib.spamm_task_list.argtypes = [P, P, dbl, P, P, i64, ctypes.POINTER(i64), P]
+    lib.spamm_cull_noalloc.argtypes = [P, i64, P, i64, i64, dbl, P, P, i64, P]
     lib.spamm_free.argtypes = [P]
     lib.spamm_free.restype = None
     lib.spamm_strerror.argtypes = [ctypes.c_int]
@@ -97,7 +98,7 @@ def load():
     lib.sp2_solve.argtypes = [P, dbl, dbl, ctypes.POINTER(_Sp2Opts), H,
                               ctypes.POINTER(_Sp2Report), P]
     for name in ("spamm_tree_build", "spamm_multiply", "spamm_to_dense", "spamm_norms",
-                 "spamm_info", "spamm_task_list", "sp2_solve"):
+                 "spamm_info", "spamm_task_list", "sp2_solve", "spamm_cull_noalloc"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -224,6 +225,18 @@ def task_list(A: Matrix, B: Matrix, tau: float, stream=None):
                                k.ctypes.data_as(ctypes.c_void_p), k.size, ctypes.byref(nt),
                                _stream(stream)), "spamm_task_list")
     return off, k[:nt.value]
+
+
+def cull_noalloc(n2a, n2b, nb: int, tau: float, off, klist, stream=None):
+    """spamm_cull_noalloc on caller-owned CUDA tensors: n2a, n2b (float64,
+    >= nb x nb, row-major), off (int64, nb*nb + 1), klist (int32/uint32-sized,
+    any length).  Asynchronous; off[-1] holds the total."""
+    cap = klist.numel() if klist is not None else 0
+    _check(load().spamm_cull_noalloc(
+        ctypes.c_void_p(n2a.data_ptr()), n2a.stride(0), ctypes.c_void_p(n2b.data_ptr()),
+        n2b.stride(0), nb, float(tau), ctypes.c_void_p(off.data_ptr()),
+        ctypes.c_void_p(klist.data_ptr() if cap else 0), cap, _stream(stream)),
+        "spamm_cull_noalloc")
 
 
 def sp2_solve(F: Matrix, ne: float, tau: float, P: Matrix | None = None, max_iter: int = 100,
