@@ -63,7 +63,7 @@ typedef enum {
 typedef struct {
     int32_t leaf;   /* leaf edge b: 16, 32 or 64; 0 selects 32            */
     int32_t prec;   /* spamm_prec_t                                       */
-    int32_t slices; /* slices per operand for SPAMM_OZAKI_BF16 (0 = 5)    */
+    int32_t slices; /* slices per operand for SPAMM_OZAKI_BF16 (0 = 7)    */
     int32_t flags;  /* SPAMM_F_* bits                                     */
 } spamm_opts_t;
 
@@ -196,7 +196,7 @@ typedef struct {
     int32_t fixed_iters; /* > 0: run exactly this many iterations            */
     int32_t leaf;        /* 0 selects 32                                     */
     int32_t prec;        /* spamm_prec_t of the X^2 products                 */
-    int32_t slices;      /* for SPAMM_OZAKI_BF16 (0 = 5)                     */
+    int32_t slices;      /* for SPAMM_OZAKI_BF16 (0 = 7)                     */
     int32_t flags;       /* SPAMM_F_TIMING: per-stage device times           */
     int32_t reserved;
 } sp2_opts_t;

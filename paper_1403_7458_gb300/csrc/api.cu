@@ -162,6 +162,13 @@ int spamm_mat_same_shape(spamm_mat_t a, spamm_mat_t b)
 
 static void ws_free(SpammWorkspace *ws, cudaStream_t s)
 {
+    spamm_release(ws->tcounts, s);
+    spamm_release(ws->ttasks, s);
+    spamm_release(ws->toff, s);
+    spamm_release(ws->torder, s);
+    spamm_release(ws->tbins, s);
+    spamm_release(ws->tlist, s);
+    spamm_release(ws->zero, s);
     spamm_release(ws->counts, s);
     spamm_release(ws->off, s);
     spamm_release(ws->klist, s);
@@ -178,6 +185,9 @@ extern "C" void spamm_free(spamm_mat_t m)
     spamm_release(m->slot, s);
     spamm_release(m->n2, s);
     spamm_release(m->n2T, s);
+    spamm_release(m->slA, s);
+    spamm_release(m->slB, s);
+    spamm_release(m->scale, s);
     ws_free(&m->ws, s);
     delete m;
 }
@@ -349,18 +359,40 @@ int spamm_multiply_into(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t C,
     int rc = ws_reserve_groups(ws, A->nb * A->nb, A->nb, s);
     if (rc) return rc;
     int64_t total = -1;
-    rc = spamm_cull(A, B, tau, ws, A->nb, A->P, s, need_total, &total);
-    if (rc) return rc;
-    if (ev) SPAMM_CK(cudaEventRecord(ev[1], s));
     if (prec == SPAMM_FP64) {
+        rc = spamm_cull(A, B, tau, ws, A->nb, A->P, s, need_total, &total);
+        if (rc) return rc;
+        ws->task_total = ws->off + A->nb * A->nb;
+        if (ev) SPAMM_CK(cudaEventRecord(ev[1], s));
         rc = launch_gemm_fp64(A, B, C, ws, tr_part, s);
+    } else if (prec == SPAMM_OZAKI_BF16) {
+        const int sl = opts && opts->slices ? opts->slices : 7;
+        if ((rc = launch_slices(A, sl, s))) return rc;
+        if (B != A && (rc = launch_slices(B, sl, s))) return rc;
+        if (ev) SPAMM_CK(cudaEventRecord(ev[1], s));
+        rc = launch_gemm_tc(A, B, C, ws, tau, tr_part, sl, s);
+        if (rc) return rc;
+        const int64_t T = ((A->nb + 3) / 4) * A->nb;
+        ws->task_total = ws->toff + T + 1;
+        if (need_total) {
+            int64_t both[2];
+            SPAMM_CK(cudaMemcpyAsync(both, ws->toff + T, sizeof(int64_t) * 2, cudaMemcpyDeviceToHost, s));
+            SPAMM_CK(cudaStreamSynchronize(s));
+            total = both[1];
+            ws->last_items = both[0];
+        }
     } else {
         spamm_set_error("precision mode %d not built", prec);
         rc = SPAMM_E_NOTSUP;
     }
     if (rc) return rc;
     if (ev) SPAMM_CK(cudaEventRecord(ev[2], s));
-    if (build_pyramid && (rc = launch_pyramid(C, s))) return rc;
+    if (build_pyramid) {
+        // the FP64 epilogue already wrote C's leaf norms; the tensor-core
+        // epilogue does not, so they are formed from the stored leaves
+        rc = prec == SPAMM_FP64 ? launch_pyramid(C, s) : launch_leaf_norms(C, s);
+        if (rc) return rc;
+    }
     if (ev) SPAMM_CK(cudaEventRecord(ev[3], s));
     if (tasks_out) *tasks_out = total;
     return SPAMM_OK;
@@ -376,8 +408,13 @@ extern "C" int spamm_multiply(spamm_mat_t A, spamm_mat_t B, double tau, spamm_ma
     int rc = check_tau(tau);
     if (rc) return rc;
     int prec = opts ? opts->prec : SPAMM_FP64;
-    if (prec != SPAMM_FP64) {
-        spamm_set_error("spamm_multiply: precision mode %d not built", prec);
+    if (prec != SPAMM_FP64 && prec != SPAMM_OZAKI_BF16) {
+        spamm_set_error("spamm_multiply: unknown precision mode %d", prec);
+        return SPAMM_E_NOTSUP;
+    }
+    if (prec == SPAMM_OZAKI_BF16 &&
+        (A->b != 32 || !tc_slices_ok(opts && opts->slices ? opts->slices : 7))) {
+        spamm_set_error("spamm_multiply: the tensor-core path needs leaf 32 and slices in 3..7");
         return SPAMM_E_NOTSUP;
     }
     cudaStream_t s = (cudaStream_t)stream;
@@ -410,6 +447,10 @@ extern "C" int spamm_multiply(spamm_mat_t A, spamm_mat_t B, double tau, spamm_ma
         stats->candidates = nb * nb * nb;
         stats->flops_useful = 2.0 * b3 * double(total);
         stats->flops_issued = stats->flops_useful;
+        if (prec == SPAMM_OZAKI_BF16) {
+            const int sl = opts && opts->slices ? opts->slices : 7;
+            stats->flops_issued = 2.0 * 128 * 32 * 32 * (sl * (sl + 1) / 2) * double((*C)->ws.last_items);
+        }
         stats->ms_cull = stats->ms_gemm = stats->ms_norm = 0.f;
         if (timing) {
             cudaError_t e = cudaEventSynchronize(ev[3]);

@@ -30,6 +30,18 @@ struct SpammWorkspace {
     int32_t *counter = nullptr;  // work counters and error flags (16 ints)
     double *tr_part = nullptr;   // per leaf row partial traces (nb)
     int64_t tr_cap = 0;
+    // tensor-core path: tile work lists (tile t = I * nb + j, I = i / 4)
+    int32_t *tcounts = nullptr;  // work items per tile
+    int32_t *ttasks = nullptr;   // surviving triples per tile
+    int64_t *toff = nullptr;     // T + 2: offsets, then the triple total
+    int32_t *torder = nullptr;   // heaviest-first tile order
+    int32_t *tbins = nullptr;    // nb + 1 histogram bins
+    uint32_t *tlist = nullptr;   // k | mask << 24
+    int64_t tile_cap = 0, tlist_cap = 0;
+    uint16_t *zero = nullptr;    // one zero leaf (all slices)
+    size_t zero_bytes = 0;
+    const int64_t *task_total = nullptr;  // device: surviving triples of the last cull
+    int64_t last_items = 0;               // host copy: tile work items of the last product
 };
 
 struct spamm_mat {
@@ -45,6 +57,11 @@ struct spamm_mat {
     double *n2T = nullptr;
     cudaStream_t stream = nullptr;
     int device = 0;
+    // exact BF16 slices for the tensor-core path (slice.cu)
+    uint16_t *slA = nullptr;          // A role, s*1024 BF16 per slot
+    uint16_t *slB = nullptr;          // B role
+    int sl_s = 0;
+    unsigned long long *scale = nullptr;  // [0] max |x| bits, [1] (int32) sigma
     SpammWorkspace ws;  // used when this handle is the output of a product
 };
 
@@ -99,6 +116,12 @@ int spamm_multiply_into(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t C,
 // Count of kernels this library launched (for reports).
 void spamm_note_launches(int64_t k);
 int64_t spamm_launch_count();
+
+// Tensor-core path (slice.cu, gemm_tc.cu)
+int launch_slices(spamm_mat_t m, int s, cudaStream_t st);
+int launch_gemm_tc(spamm_mat_t A, spamm_mat_t B, spamm_mat_t C, SpammWorkspace *ws, double tau,
+                   double *tr_part, int slices, cudaStream_t s);
+int tc_slices_ok(int s);
 
 // Leaf products (gemm_fp64.cu)
 int launch_gemm_fp64(spamm_mat_t A, spamm_mat_t B, spamm_mat_t C, SpammWorkspace *ws,

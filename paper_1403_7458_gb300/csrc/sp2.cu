@@ -238,8 +238,10 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
         spamm_set_error("sp2_solve: opts.leaf (%d) differs from F's leaf size (%d)", o.leaf, F->b);
         return SPAMM_E_INVAL;
     }
-    if (o.prec != SPAMM_FP64) {
-        spamm_set_error("sp2_solve: precision mode %d not built", o.prec);
+    if (o.prec != SPAMM_FP64 &&
+        !(o.prec == SPAMM_OZAKI_BF16 && F->b == 32 && tc_slices_ok(o.slices ? o.slices : 7))) {
+        spamm_set_error("sp2_solve: precision mode %d (leaf %d, slices %d) not built", o.prec, F->b,
+                        o.slices);
         return SPAMM_E_NOTSUP;
     }
     cudaStream_t s = (cudaStream_t)stream;
@@ -325,7 +327,7 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
     while (it < limit) {
         SP2_TRY(spamm_multiply_into(X, X, tau, X2, &mo, sc.tr_part, s, false, nullptr, false,
                                     timing ? evs : nullptr));
-        k_sp2_decide<<<1, kRedThreads, 0, s>>>(sc.tr_part, nb, X2->ws.off + G, Ne, o.rule, sc.st);
+        k_sp2_decide<<<1, kRedThreads, 0, s>>>(sc.tr_part, nb, X2->ws.task_total, Ne, o.rule, sc.st);
         SP2_LAUNCHED();
         k_sp2_elementwise<<<ew_blocks, kWarps * 32, 0, s>>>(
             1, X->leaf, X2->leaf, X->slot, F->n, nb, X->P, X->b, X->n2 + tier_offset(X->depth),

@@ -1,0 +1,145 @@
+"""Mixed-precision (exact BF16 slices on tcgen05) SpAMM and SP2 vs references.
+
+1. Bit-exact against a test-side integer model of the same arithmetic: each
+   element scaled by the matrix's power of two 2^-sigma (max|x| < 2^sigma),
+   rounded half-up to X = round(|x| 2^(7s - sigma)), cut into base-128 digits;
+   slice pairs p + q < s summed exactly per diagonal d = p + q;
+   C = RN(2^(sigmaA + sigmaB - 7s - 7) sum_d S_d 128^(s-1-d)).  The model
+   also confirms every |S_d| stays below 2^24, where FP32 sums are exact.
+2. Against the FP64 oracle (the definition of SpAMM) within the rigorous
+   elementwise bound of the slicing:
+     |dC_ij| <= sum_l over kept leaves of (|a_il| eb + ea |b_lj| + ea eb
+                + (s-1) 2^(sigmaA+sigmaB-7s)) + 2^-52 |C_ij|,
+   ea = 2^(sigmaA-7s-1), eb = 2^(sigmaB-7s-1) (rounding of each element),
+   the (s-1) term bounding the dropped pairs p + q >= s.
+3. SP2: ||P_mixed - P_FP64||_F <= 1e-6 (the target accuracy), with the
+   same stopping rule.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1403_7458_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _sigma(a):
+    mx = np.abs(a).max()
+    return 0 if mx == 0 else math.frexp(mx)[1]
+
+
+def _digits(a, s):
+    sig = _sigma(a)
+    X = np.floor(np.abs(a) * 2.0 ** (7 * s - sig) + 0.5).astype(np.int64)
+    sign = np.where(a < 0, -1, 1).astype(np.int64)
+    d = []
+    for p in range(s):
+        v = X >> (7 * (s - 1 - p))
+        if p > 0:
+            v = v & 127
+        d.append(sign * v)
+    return d, sig
+
+
+def _model(a, b, leaf, tau, s):
+    """Exact integer model of the sliced leaf products over the oracle's
+    task list (same predicate, same norms)."""
+    n = a.shape[0]
+    _, tasks = oracle.spamm(a, b, leaf, tau, want_tasks=True)
+    da, sa = _digits(a, s)
+    db, sb = _digits(b, s)
+    nb = -(-n // leaf)
+    npad = nb * leaf
+    pad = lambda m: np.pad(m, ((0, npad - n), (0, npad - n)))
+    da = [pad(x) for x in da]
+    db = [pad(x) for x in db]
+    S = np.zeros((s, npad, npad), dtype=np.int64)
+    for i, k, j in tasks:
+        ri, rk, rj = slice(i * leaf, (i + 1) * leaf), slice(k * leaf, (k + 1) * leaf), slice(j * leaf, (j + 1) * leaf)
+        for p in range(s):
+            for q in range(s - p):
+                S[p + q, ri, rj] += da[p][ri, rk] @ db[q][rk, rj]
+    assert np.abs(S).max() < 2 ** 24, "model: FP32 sums would not be exact"
+    cint = np.zeros((npad, npad), dtype=object)
+    for d in range(s):
+        cint = cint + S[d].astype(object) * (128 ** (s - 1 - d))
+    e = sa + sb - 7 * s - 7
+    c = np.vectorize(lambda v: math.ldexp(float(v), e))(cint).astype(np.float64)
+    return c[:n, :n], tasks, sa, sb
+
+
+@pytest.mark.parametrize("n,tau,s,seed", [(256, 1e-6, 5, 0), (200, 1e-4, 4, 1), (320, 1e-8, 6, 2),
+                                          (130, 0.0, 3, 3), (256, 1e-6, 7, 4)])
+def test_mixed_spamm_bit_exact_vs_integer_model(cuda_lib, n, tau, s, seed):
+    a = synth.decaying_matrix(n, seed)
+    b = synth.decaying_matrix(n, seed + 50, decay=1.3)
+    A = cuda_lib.tree_build(_dev(a), leaf=32)
+    B = cuda_lib.tree_build(_dev(b), leaf=32)
+    C, st = cuda_lib.multiply(A, B, tau, prec=cuda_lib.OZAKI_BF16, slices=s, stats=True)
+    got = cuda_lib.to_dense(C).cpu().numpy()
+    want, tasks, _, _ = _model(a, b, 32, tau, s)
+    assert st["tasks"] == len(tasks)
+    assert np.array_equal(got, want), np.abs(got - want).max()
+
+
+@pytest.mark.parametrize("n,tau,s", [(512, 1e-6, 5), (384, 1e-8, 6), (256, 1e-3, 4)])
+def test_mixed_spamm_within_slicing_bound_of_fp64(cuda_lib, n, tau, s):
+    a = synth.decaying_matrix(n, 9)
+    A = cuda_lib.tree_build(_dev(a), leaf=32)
+    C, _ = cuda_lib.multiply(A, A, tau, prec=cuda_lib.OZAKI_BF16, slices=s)
+    got = cuda_lib.to_dense(C).cpu().numpy()
+    ref, tasks = oracle.spamm(a, a, 32, tau, want_tasks=True)
+    sg = _sigma(a)
+    ea = eb = 2.0 ** (sg - 7 * s - 1)
+    # per output element: sum over kept leaves of the per-term bound
+    nb = -(-n // 32)
+    keep = np.zeros((nb, nb, nb), dtype=bool)
+    keep[tasks[:, 0], tasks[:, 1], tasks[:, 2]] = True
+    absA = np.abs(np.pad(a, ((0, nb * 32 - n),) * 2))
+    bound = np.zeros((nb * 32, nb * 32))
+    for i in range(nb):
+        for j in range(nb):
+            ks = np.nonzero(keep[i, :, j])[0]
+            if len(ks) == 0:
+                continue
+            cols = np.concatenate([np.arange(k * 32, k * 32 + 32) for k in ks])
+            Ai = absA[i * 32:(i + 1) * 32][:, cols]
+            Bj = absA[cols][:, j * 32:(j + 1) * 32]
+            bound[i * 32:(i + 1) * 32, j * 32:(j + 1) * 32] = (
+                Ai.sum(axis=1)[:, None] * eb + ea * Bj.sum(axis=0)[None, :]
+                + len(cols) * (ea * eb + (s - 1) * 2.0 ** (2 * sg - 7 * s)))
+    bound = bound[:n, :n] + 2.0 ** -52 * np.abs(ref)
+    assert np.all(np.abs(got - ref) <= bound)
+
+
+def test_mixed_rejects_unsupported(cuda_lib):
+    a = synth.decaying_matrix(64, 0)
+    A16 = cuda_lib.tree_build(_dev(a), leaf=16)
+    with pytest.raises(cuda_lib.SpammError) as ei:
+        cuda_lib.multiply(A16, A16, 1e-6, prec=cuda_lib.OZAKI_BF16)
+    assert ei.value.status == cuda_lib.E_NOTSUP
+    A = cuda_lib.tree_build(_dev(a), leaf=32)
+    with pytest.raises(cuda_lib.SpammError):
+        cuda_lib.multiply(A, A, 1e-6, prec=cuda_lib.OZAKI_BF16, slices=9)
+
+
+@pytest.mark.parametrize("n,s", [(1024, 6), (1024, 7), (4096, 6)])
+def test_mixed_sp2_matches_fp64_sp2(cuda_lib, n, s):
+    h = synth.tb_hamiltonian(n, 1)
+    F = cuda_lib.tree_build(_dev(h), leaf=32)
+    P64, r64 = cuda_lib.sp2_solve(F, n / 2, 1e-8)
+    Pm, rm = cuda_lib.sp2_solve(F, n / 2, 1e-8, prec=cuda_lib.OZAKI_BF16, slices=s,
+                                fixed_iters=r64["iters"])
+    p64 = cuda_lib.to_dense(P64).cpu().numpy()
+    pm = cuda_lib.to_dense(Pm).cpu().numpy()
+    assert np.linalg.norm(pm - p64) <= 1e-6
+    assert abs(np.trace(pm) - n / 2) < 1e-6
+    assert np.linalg.norm(pm @ pm - pm) < 1e-5
