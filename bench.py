@@ -9,9 +9,13 @@ fused SP2 update for every iteration until the stopping rule fires.
 
 Printed metric: useful SpAMM leaf throughput over the whole solve, i.e.
 2 b^3 x (surviving leaf triples summed over iterations) / solve time, in
-TFLOP/s; `ms_per_step` is the SP2 solve time.
+TFLOP/s; `ms_per_step` is the SP2 solve time.  The timed steps use the
+mixed-precision leaf products (exact BF16 slices on the tensor cores, FP64
+norms, traces and updates); the same workload is then solved with FP64 leaf
+products, and the line reports that solve time, the speedup and
+||P_mixed - P_FP64||_F.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp64|ozaki]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec ozaki|fp64] [--slices S]
   python bench.py --impl reference ...   (the FP64 CPU oracle, bounded sample)
 
 N > 1 runs independent replicas (one solve per GPU, launched with torchrun);
@@ -159,6 +163,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=dev)
     spamm.load()
     prec = spamm.OZAKI_BF16 if args.prec == "ozaki" else spamm.FP64
+    slices = args.slices if prec == spamm.OZAKI_BF16 else 0
     n, b, tau, ne = WORKLOAD["n"], WORKLOAD["leaf"], WORKLOAD["tau"], WORKLOAD["ne"]
     h = synth.tb_hamiltonian(n, seed=rank)
     hd = torch.from_numpy(h).to(dev)
@@ -166,23 +171,18 @@ def run_ours(args):
     F = spamm.tree_build(hd, leaf=b)
     P = None
 
-    def solve(timing=False):
-        nonlocal P
-        P, rep = spamm.sp2_solve(F, ne, tau, P=P, prec=prec, timing=timing)
-        return rep
+    def solve(timing=False, p=prec, sl=slices, out=None):
+        return spamm.sp2_solve(F, ne, tau, P=out, prec=p, slices=sl, timing=timing)
 
     for _ in range(args.warmup):
-        solve()
+        P, _ = solve(out=P)
     torch.cuda.synchronize()
 
     # ---- device-timed region: inputs resident in HBM ----
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    flops = 0.0
-    gemm_ms = 0.0
-    gemm_flops = 0.0
-    iters = 0
-    launches = 0
+    flops = gemm_ms = 0.0
+    iters = launches = 0
     step_ms = []
     with ClockSampler(local) as clk:
         _barrier(world)
@@ -191,7 +191,7 @@ def run_ours(args):
         for _ in range(args.steps):
             flush.zero_()                       # evict L2 between steps
             ev0.record(stream)
-            rep = solve(timing=True)
+            P, rep = solve(timing=True, out=P)
             ev1.record(stream)
             ev1.synchronize()
             ms = ev0.elapsed_time(ev1)
@@ -199,7 +199,6 @@ def run_ours(args):
             total_ms += ms
             flops += rep["flops_useful"]
             gemm_ms += rep["ms_gemm"]
-            gemm_flops += rep["flops_useful"]
             iters += rep["iters"]
             launches += rep["launches"]
         torch.cuda.synchronize()
@@ -208,6 +207,28 @@ def run_ours(args):
     t_max = reduce_max_over_ranks(total_ms, world, dev)
     flops_all = reduce_sum_over_ranks(flops, world, dev)
     value = flops_all / (t_max * 1e-3) / 1e12
+    p_main = spamm.to_dense(P)
+    idem = torch.linalg.norm(p_main @ p_main - p_main).item()
+    trace_err = abs(torch.trace(p_main).item() - ne)
+    stop_reason = rep["stop_reason"]
+
+    # ---- the same workload with FP64 leaf products ----
+    fp64 = None
+    if prec != spamm.FP64 and not args.no_fp64_leg:
+        P64, _ = solve(p=spamm.FP64, sl=0)
+        f_ms = []
+        for _ in range(2):
+            flush.zero_()
+            ev0.record(stream)
+            P64, r64 = solve(p=spamm.FP64, sl=0, out=P64)
+            ev1.record(stream)
+            ev1.synchronize()
+            f_ms.append(ev0.elapsed_time(ev1))
+        p64 = spamm.to_dense(P64)
+        fp64 = {"solve_ms": sum(f_ms) / len(f_ms), "iters": r64["iters"],
+                "speedup_mixed_vs_fp64": (sum(f_ms) / len(f_ms)) / (t_max / args.steps),
+                "dP_fro_mixed_vs_fp64": torch.linalg.norm(p_main - p64).item(),
+                "value_fp64": r64["flops_useful"] / (r64["ms_total"] * 1e-3) / 1e12}
 
     # ---- end to end through the C ABI with host buffers ----
     h_pin = torch.from_numpy(h).pin_memory()
@@ -218,7 +239,7 @@ def run_ours(args):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         F2 = spamm.tree_build(h_pin.numpy(), leaf=b)        # host pointer: H2D inside
-        P2, rep2 = spamm.sp2_solve(F2, ne, tau, prec=prec)
+        P2, rep2 = spamm.sp2_solve(F2, ne, tau, prec=prec, slices=slices)
         spamm.to_dense(P2, out=p_pin.numpy())               # host pointer: D2H inside
         e2e_flops += rep2["flops_useful"]
         F2.free()
@@ -227,27 +248,27 @@ def run_ours(args):
     e2e_s = reduce_max_over_ranks(time.perf_counter() - t0, world, dev)
     e2e_value = reduce_sum_over_ranks(e2e_flops, world, dev) / e2e_s / 1e12
 
-    # P quality of the last device-timed solve
-    p = spamm.to_dense(P)
-    idem = torch.linalg.norm(p @ p - p).item()
-    trace_err = abs(torch.trace(p).item() - ne)
-
     # ---- roofline of the dominant kernel (grouped leaf products) ----
     peaks, peak_src = _peaks()
     if prec == spamm.FP64:
         peak = fp64_peak_tflops()
         bound = "alu"
+        kern = "k_gemm_fp64<32>"
         peak_note = "FP64 FMA: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz (nominal 1.25 TFLOP/s)"
+        alg_flops = flops
     else:
         peak = peaks.get("bf16_tflops_sustained", 1700.0)
         bound = "tensor"
-        peak_note = "bf16 sustained, %s" % peak_src
-    achieved = gemm_flops / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else None
+        kern = "k_gemm_tc<%d>" % slices
+        peak_note = "bf16 tensor, sustained, %s (MEASURED_PEAKS.json)" % peak_src
+        # tensor work of the surviving products: every kept slice pair
+        alg_flops = flops * slices * (slices + 1) / 2
+    achieved = alg_flops / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else None
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": None,
-                "kernel": "k_gemm_fp64<32>" if prec == spamm.FP64 else "k_gemm_tc",
-                "peak_source": peak_note,
-                "gemm_share_of_step": gemm_ms / total_ms if total_ms else None}
+                "kernel": kern, "peak_source": peak_note,
+                "useful_leaf_tflops_in_kernel": flops / (gemm_ms * 1e-3) / 1e12 if gemm_ms else None,
+                "kernel_share_of_step": gemm_ms / total_ms if total_ms else None}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -256,10 +277,13 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if prec == spamm.FP64 else "bf16-slices/f32-acc/f64",
         "data": "synthetic (seeded tight-binding Hamiltonian, Morton-ordered 3-D clusters)",
-        "config": dict(WORKLOAD, prec=args.prec, parallelism="replicas" if world > 1 else "1gpu",
-                       l2="flushed between steps; working set 2 x 134 MB > L2"),
+        "config": dict(WORKLOAD, prec=args.prec, slices=slices,
+                       parallelism="replicas" if world > 1 else "1gpu",
+                       l2="flushed between steps; working set > L2"),
         "sp2": {"iters_per_solve": iters / args.steps, "solve_ms": t_max / args.steps,
-                "step_ms": step_ms, "idempotency": idem, "trace_err": trace_err},
+                "step_ms": step_ms, "idempotency": idem, "trace_err": trace_err,
+                "stop_reason": stop_reason},
+        "fp64_plain": fp64,
         "roofline": roofline,
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * n * n,
@@ -267,7 +291,7 @@ def run_ours(args):
         "gpu_launches": launches,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(h, iters=1)
+        line["cpu_baseline"] = cpu_baseline(h, iters=args.cpu_iters)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -329,8 +353,11 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--prec", choices=["fp64", "ozaki"], default="fp64")
+    ap.add_argument("--prec", choices=["fp64", "ozaki"], default="ozaki")
+    ap.add_argument("--slices", type=int, default=7)
+    ap.add_argument("--cpu-iters", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-leg", action="store_true")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

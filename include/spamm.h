@@ -59,6 +59,7 @@ typedef enum {
 
 /* ---- options ---------------------------------------------------------- */
 #define SPAMM_F_TIMING 1 /* record per-stage device times into spamm_stats_t */
+#define SPAMM_F_NOSYM 2  /* SP2: form every leaf of X^2 even when F is symmetric */
 
 typedef struct {
     int32_t leaf;   /* leaf edge b: 16, 32 or 64; 0 selects 32            */
@@ -72,7 +73,7 @@ typedef struct {
     int64_t candidates;  /* nb^3                                             */
     double flops_useful; /* 2 b^3 per surviving triple                       */
     double flops_issued; /* arithmetic issued, incl. slice pairs             */
-    float ms_cull;       /* device time of the cull (with SPAMM_F_TIMING)    */
+    float ms_cull;       /* device time of the cull (+ slicing, mixed path)  */
     float ms_gemm;       /* device time of the leaf products                 */
     float ms_norm;       /* device time of the output norms                  */
     float reserved;
@@ -219,10 +220,12 @@ typedef struct {
     int64_t tasks_total;  /* surviving leaf triples over all iterations    */
     double flops_useful;  /* 2 b^3 tasks_total                             */
     double ms_total;      /* device time of the whole solve                */
-    double ms_cull;       /* SPAMM_F_TIMING: summed device time of the cull */
+    double ms_cull;       /* SPAMM_F_TIMING: summed time of cull (+ slicing) */
     double ms_gemm;       /*   ... of the leaf products                     */
     double ms_update;     /*   ... of the SP2 decide + update passes        */
     int64_t launches;     /* kernels the solve launched                     */
+    int32_t symmetric;    /* 1: upper block triangle of X^2 formed + mirrored */
+    int32_t reserved2;
     double *history;      /* in: optional host buffer of history_cap rows  */
     int32_t history_cap;  /* in: rows available in history                 */
     int32_t reserved;
@@ -234,6 +237,10 @@ typedef struct {
  * X0 = (emax I - F) / (emax - emin) from Gershgorin bounds; each iteration
  * forms X^2 = SpAMM(X, X, tau), picks X^2 or 2X - X^2 by `rule` on the
  * device, and updates X.  Stops as in SP2_STOP_*.
+ * With SPAMM_OZAKI_BF16 and an exactly symmetric F, every iterate is exactly
+ * symmetric (the slice arithmetic is exact), so only the upper block triangle
+ * of X^2 is formed and mirrored; the result is bit-identical to forming all
+ * leaves (SPAMM_F_NOSYM in flags forces the full product).
  * F      : symmetric handle; Ne in (0, n) is the trace of the projector.
  * P      : *P == NULL creates a new handle; otherwise reused (F's shape).
  * report : optional; filled when given.

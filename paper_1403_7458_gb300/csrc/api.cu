@@ -164,11 +164,11 @@ static void ws_free(SpammWorkspace *ws, cudaStream_t s)
 {
     spamm_release(ws->tcounts, s);
     spamm_release(ws->ttasks, s);
+    spamm_release(ws->tpairs, s);
     spamm_release(ws->toff, s);
     spamm_release(ws->torder, s);
     spamm_release(ws->tbins, s);
     spamm_release(ws->tlist, s);
-    spamm_release(ws->zero, s);
     spamm_release(ws->counts, s);
     spamm_release(ws->off, s);
     spamm_release(ws->klist, s);
@@ -187,6 +187,7 @@ extern "C" void spamm_free(spamm_mat_t m)
     spamm_release(m->n2T, s);
     spamm_release(m->slA, s);
     spamm_release(m->slB, s);
+    spamm_release(m->zlead, s);
     spamm_release(m->scale, s);
     ws_free(&m->ws, s);
     delete m;
@@ -351,7 +352,7 @@ int ws_reserve_groups(SpammWorkspace *ws, int64_t groups, int64_t nb, cudaStream
 int spamm_multiply_into(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t C,
                         const spamm_opts_t *opts, double *tr_part, cudaStream_t s,
                         bool need_total, int64_t *tasks_out, bool build_pyramid,
-                        cudaEvent_t *ev)
+                        cudaEvent_t *ev, int sym)
 {
     int prec = opts ? opts->prec : SPAMM_FP64;
     if (ev) SPAMM_CK(cudaEventRecord(ev[0], s));
@@ -367,19 +368,27 @@ int spamm_multiply_into(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t C,
         rc = launch_gemm_fp64(A, B, C, ws, tr_part, s);
     } else if (prec == SPAMM_OZAKI_BF16) {
         const int sl = opts && opts->slices ? opts->slices : 7;
-        if ((rc = launch_slices(A, sl, s))) return rc;
-        if (B != A && (rc = launch_slices(B, sl, s))) return rc;
+        const int symm = (sym && A == B) ? 1 : 0;
+        // slices first: the tile cull reads each leaf's leading zero slices
+        if (A == B) {
+            if ((rc = launch_slices(A, sl, true, true, !symm, s))) return rc;
+        } else {
+            if ((rc = launch_slices(A, sl, true, false, false, s))) return rc;
+            if ((rc = launch_slices(B, sl, false, true, true, s))) return rc;
+        }
+        if ((rc = tc_tile_cull(A, B, tau, ws, symm, sl, s))) return rc;
         if (ev) SPAMM_CK(cudaEventRecord(ev[1], s));
-        rc = launch_gemm_tc(A, B, C, ws, tau, tr_part, sl, s);
+        rc = launch_gemm_tc(A, B, C, ws, tr_part, sl, s);
         if (rc) return rc;
         const int64_t T = ((A->nb + 3) / 4) * A->nb;
         ws->task_total = ws->toff + T + 1;
         if (need_total) {
-            int64_t both[2];
-            SPAMM_CK(cudaMemcpyAsync(both, ws->toff + T, sizeof(int64_t) * 2, cudaMemcpyDeviceToHost, s));
+            int64_t both[3];
+            SPAMM_CK(cudaMemcpyAsync(both, ws->toff + T, sizeof(int64_t) * 3, cudaMemcpyDeviceToHost, s));
             SPAMM_CK(cudaStreamSynchronize(s));
             total = both[1];
             ws->last_items = both[0];
+            ws->last_pairs = both[2];
         }
     } else {
         spamm_set_error("precision mode %d not built", prec);
@@ -449,7 +458,8 @@ extern "C" int spamm_multiply(spamm_mat_t A, spamm_mat_t B, double tau, spamm_ma
         stats->flops_issued = stats->flops_useful;
         if (prec == SPAMM_OZAKI_BF16) {
             const int sl = opts && opts->slices ? opts->slices : 7;
-            stats->flops_issued = 2.0 * 128 * 32 * 32 * (sl * (sl + 1) / 2) * double((*C)->ws.last_items);
+            (void)sl;
+            stats->flops_issued = 2.0 * 128 * 32 * 32 * double((*C)->ws.last_pairs);
         }
         stats->ms_cull = stats->ms_gemm = stats->ms_norm = 0.f;
         if (timing) {

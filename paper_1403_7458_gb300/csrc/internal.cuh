@@ -33,15 +33,17 @@ struct SpammWorkspace {
     // tensor-core path: tile work lists (tile t = I * nb + j, I = i / 4)
     int32_t *tcounts = nullptr;  // work items per tile
     int32_t *ttasks = nullptr;   // surviving triples per tile
+    int32_t *tpairs = nullptr;   // slice-pair work per tile (sum of m(m+1)/2)
     int64_t *toff = nullptr;     // T + 2: offsets, then the triple total
     int32_t *torder = nullptr;   // heaviest-first tile order
     int32_t *tbins = nullptr;    // nb + 1 histogram bins
     uint32_t *tlist = nullptr;   // k | mask << 24
     int64_t tile_cap = 0, tlist_cap = 0;
-    uint16_t *zero = nullptr;    // one zero leaf (all slices)
-    size_t zero_bytes = 0;
     const int64_t *task_total = nullptr;  // device: surviving triples of the last cull
     int64_t last_items = 0;               // host copy: tile work items of the last product
+    int64_t last_pairs = 0;               // host copy: slice-pair MMA work (units of 128x32x32)
+    int64_t tactive = 0;                  // tiles in the order list of the last tile cull
+    int tsym = 0;                         // last tile cull was symmetric
 };
 
 struct spamm_mat {
@@ -58,8 +60,10 @@ struct spamm_mat {
     cudaStream_t stream = nullptr;
     int device = 0;
     // exact BF16 slices for the tensor-core path (slice.cu)
-    uint16_t *slA = nullptr;          // A role, s*1024 BF16 per slot
-    uint16_t *slB = nullptr;          // B role
+    uint16_t *slA = nullptr;          // A operand, tile-major [I][k][p][L] (4 leaf rows per block)
+    uint16_t *slB = nullptr;          // per-leaf [p][..] array (B operand)
+    int slB_transposed = -1;          // layout of slB: 1 = B-role (transposed), 0 = A-role
+    uint8_t *zlead = nullptr;         // leading all-zero slices per slot
     int sl_s = 0;
     unsigned long long *scale = nullptr;  // [0] max |x| bits, [1] (int32) sigma
     SpammWorkspace ws;  // used when this handle is the output of a product
@@ -108,18 +112,22 @@ int ws_reserve_groups(SpammWorkspace *ws, int64_t groups, int64_t nb, cudaStream
 // C = SpAMM(A, B, tau) into an existing handle (api.cu).  ev (optional, 4
 // events) is recorded before the cull, before the products, before and after
 // C's upper norm tiers.
+// sym: A == B is exactly symmetric; the tensor-core path then forms only the
+// upper block triangle of C and mirrors it (bit-identical, half the work).
 int spamm_multiply_into(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t C,
                         const spamm_opts_t *opts, double *tr_part, cudaStream_t s,
                         bool need_total, int64_t *tasks_out, bool build_pyramid,
-                        cudaEvent_t *ev);
+                        cudaEvent_t *ev, int sym = 0);
 
 // Count of kernels this library launched (for reports).
 void spamm_note_launches(int64_t k);
 int64_t spamm_launch_count();
 
 // Tensor-core path (slice.cu, gemm_tc.cu)
-int launch_slices(spamm_mat_t m, int s, cudaStream_t st);
-int launch_gemm_tc(spamm_mat_t A, spamm_mat_t B, spamm_mat_t C, SpammWorkspace *ws, double tau,
+int launch_slices(spamm_mat_t m, int s, bool tile_a, bool per_leaf, bool transposed, cudaStream_t st);
+int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, int sym, int slices,
+                 cudaStream_t s);
+int launch_gemm_tc(spamm_mat_t A, spamm_mat_t B, spamm_mat_t C, SpammWorkspace *ws,
                    double *tr_part, int slices, cudaStream_t s);
 int tc_slices_ok(int s);
 

@@ -9,12 +9,16 @@
 // sums of such products stay exact while they are below 2^24.
 // (Error-free splitting after Ozaki, Ogita, Oishi and Rump, 2012.)
 //
-// Two layouts per leaf (b = 32, 2s KB each), both made of 8 x 8 "core
-// matrices" of BF16 (16-byte rows) as the tcgen05 K-major operand wants:
-//   A role : [g = r/8][p][cc = l/8][8 x 8]   rows r of the leaf, K = columns l
+// Two layouts per leaf (b = 32, 2s KB each), both slice-major and made of
+// 8 x 8 "core matrices" of BF16 (16-byte rows) as the tcgen05 K-major
+// operand wants; slice p occupies bytes [2048 p, 2048 (p + 1)):
+//   A role : [p][g = r/8][cc = l/8][8 x 8]   rows r of the leaf, K = columns l
 //   B role : [q][g = c/8][cc = l/8][8 x 8]   N = columns c, K = rows l
-// so that a stage of four A leaves has a uniform 8-row stride of s*512 bytes
-// for every slice p, and B slices 0..s-1-p are one contiguous N-prefix.
+// The B-role image of leaf (k, j) equals the A-role image of its transpose,
+// so for a symmetric matrix the A-role array serves both operands.
+//
+// Per leaf the number z of leading all-zero slices (every digit d_p, p < z,
+// is 0) is recorded: slice pairs touching them contribute exactly nothing.
 //
 // Roofline: HBM-bound; per element 8 B read, 4s B written (both roles).
 #include "internal.cuh"
@@ -50,21 +54,29 @@ __device__ __forceinline__ int sigma_of(unsigned long long maxbits)
 
 template <int S>
 __global__ void __launch_bounds__(256)
-k_slice(const double *__restrict__ leaf, int64_t nslots, const unsigned long long *__restrict__ maxbits,
-        int32_t *__restrict__ sigma_out, uint16_t *__restrict__ slA, uint16_t *__restrict__ slB)
+k_slice(const double *__restrict__ leaf, const int32_t *__restrict__ slot, int64_t nb, int64_t rows,
+        const unsigned long long *__restrict__ maxbits, int32_t *__restrict__ sigma_out,
+        uint16_t *__restrict__ tileA, uint16_t *__restrict__ perleaf, int perleaf_transposed,
+        uint8_t *__restrict__ zlead)
 {
     constexpr int B = 32;
     __shared__ __align__(16) uint16_t sa[S * 1024];
-    __shared__ __align__(16) uint16_t sb[S * 1024];
+    __shared__ unsigned long long s_xmax;
     const int sigma = sigma_of(*maxbits);
     if (blockIdx.x == 0 && threadIdx.x == 0 && sigma_out) *sigma_out = sigma;
-    for (int64_t slot = blockIdx.x; slot < nslots; slot += gridDim.x) {
-        const double *src = leaf + slot * (B * B);
+    // positions (i, k) over rows = 4 * ceil(nb / 4) padded leaf rows
+    for (int64_t pos = blockIdx.x; pos < rows * nb; pos += gridDim.x) {
+        const int64_t i = pos / nb, k = pos % nb;
+        const int32_t sl = i < nb ? slot[i * nb + k] : -1;
+        if (threadIdx.x == 0) s_xmax = 0;
+        __syncthreads();
+        unsigned long long xmax = 0;
+        const double *src = leaf + (int64_t)(sl < 0 ? 0 : sl) * (B * B);
         for (int q = threadIdx.x; q < B * B; q += blockDim.x) {
             const int r = q / B, l = q % B;
-            uint64_t m;
-            int e;
-            const double x = src[q];
+            uint64_t m = 0;
+            int e = 1;
+            const double x = sl >= 0 ? src[q] : 0.0;
             dbl_decompose(x, m, e);
             uint64_t X = 0;
             if (m) {
@@ -73,27 +85,44 @@ k_slice(const double *__restrict__ leaf, int64_t nslots, const unsigned long lon
                 else if (sh < 64) X = (m >> sh) + ((m >> (sh - 1)) & 1ull);
             }
             const bool neg = x < 0.0;
+            xmax = X > xmax ? X : xmax;
 #pragma unroll
             for (int p = 0; p < S; p++) {
                 uint32_t d = (uint32_t)(X >> (7 * (S - 1 - p)));
                 if (p > 0) d &= 127u;
                 // integer d <= 128 -> BF16 bits (exact): via float
-                float f = neg ? -(float)d : (float)d;
-                uint16_t h = (uint16_t)(__float_as_uint(f) >> 16);
-                // A role: [g][p][cc][ri][li]
-                sa[((r >> 3) * S + p) * 256 + (l >> 3) * 64 + (r & 7) * 8 + (l & 7)] = h;
-                // B role: element (row r = K index, column l = N index)
-                sb[(p * 4 + (l >> 3)) * 256 + (r >> 3) * 64 + (l & 7) * 8 + (r & 7)] = h;
+                const float f = neg ? -(float)d : (float)d;
+                const uint16_t h = (uint16_t)(__float_as_uint(f) >> 16);
+                // [p][g][cc][8 x 8]; transposed: element (r, l) stored as (l, r)
+                if (!perleaf_transposed || !perleaf)
+                    sa[(p * 4 + (r >> 3)) * 256 + (l >> 3) * 64 + (r & 7) * 8 + (l & 7)] = h;
+                else
+                    sa[(p * 4 + (l >> 3)) * 256 + (r >> 3) * 64 + (l & 7) * 8 + (r & 7)] = h;
             }
         }
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long v = __shfl_xor_sync(0xffffffffu, xmax, o);
+            xmax = v > xmax ? v : xmax;
+        }
+        if ((threadIdx.x & 31) == 0 && xmax) atomicMax(&s_xmax, xmax);
         __syncthreads();
-        uint4 *da = reinterpret_cast<uint4 *>(slA + slot * (S * 1024));
-        uint4 *db = reinterpret_cast<uint4 *>(slB + slot * (S * 1024));
-        const uint4 *ssa = reinterpret_cast<const uint4 *>(sa);
-        const uint4 *ssb = reinterpret_cast<const uint4 *>(sb);
-        for (int q = threadIdx.x; q < S * 1024 / 8; q += blockDim.x) {
-            if (slA) da[q] = ssa[q];
-            if (slB) db[q] = ssb[q];
+        if (threadIdx.x == 0 && zlead && sl >= 0) {
+            // leading zero slices: X < 2^(7 (S - z)) for every element
+            const unsigned long long xm = s_xmax;
+            const int bits = xm ? 64 - __clzll((long long)xm) : 0;
+            const int z = S - (bits + 6) / 7;
+            zlead[sl] = (uint8_t)(z < 0 ? 0 : z);
+        }
+        const uint4 *ss = reinterpret_cast<const uint4 *>(sa);
+        if (perleaf && sl >= 0) {
+            uint4 *d = reinterpret_cast<uint4 *>(perleaf + (int64_t)sl * (S * 1024));
+            for (int q = threadIdx.x; q < S * 128; q += blockDim.x) d[q] = ss[q];
+        }
+        if (tileA && !perleaf_transposed) {
+            // tile-major: block (I, k) holds [p][L][2 KB] for its four rows
+            const int64_t I = i >> 2, L = i & 3;
+            uint4 *d = reinterpret_cast<uint4 *>(tileA + ((I * nb + k) * S * 4 + L) * 1024);
+            for (int q = threadIdx.x; q < S * 128; q += blockDim.x) d[(q >> 7) * 512 + (q & 127)] = ss[q];
         }
         __syncthreads();
     }
@@ -101,43 +130,72 @@ k_slice(const double *__restrict__ leaf, int64_t nslots, const unsigned long lon
 
 }  // namespace
 
-int launch_slices(spamm_mat_t m, int s, cudaStream_t st)
+// Slices of matrix m: `tile_a` asks for the tile-major A-operand array,
+// `per_leaf` for the per-leaf array (transposed = B-operand layout).  A matrix
+// that serves as both operands of a non-symmetric product needs the A array
+// and the transposed per-leaf array; a symmetric product uses the untransposed
+// per-leaf array of the transpose leaf as its B operand.
+int launch_slices(spamm_mat_t m, int s, bool tile_a, bool per_leaf, bool transposed, cudaStream_t st)
 {
     if (m->b != 32) {
         spamm_set_error("tensor-core path is built for leaf 32 (got %d)", m->b);
         return SPAMM_E_NOTSUP;
     }
     int rc;
-    const size_t per = (size_t)s * 1024;  // BF16 elements per leaf per role
-    if (!m->slA || m->sl_s != s) {
+    const size_t per = (size_t)s * 1024;  // BF16 elements per leaf
+    const int64_t rows = ((m->nb + 3) / 4) * 4;
+    if (m->sl_s != s) {
         spamm_release(m->slA, st);
         spamm_release(m->slB, st);
+        spamm_release(m->zlead, st);
         m->slA = m->slB = nullptr;
-        if ((rc = spamm_alloc((void **)&m->slA, sizeof(uint16_t) * per * m->nslots, st))) return rc;
-        if ((rc = spamm_alloc((void **)&m->slB, sizeof(uint16_t) * per * m->nslots, st))) return rc;
-        if (!m->scale) {
-            if ((rc = spamm_alloc((void **)&m->scale, 16, st))) return rc;
-        }
+        m->zlead = nullptr;
         m->sl_s = s;
+        m->slB_transposed = -1;
+    }
+    if (!m->zlead && (rc = spamm_alloc((void **)&m->zlead, m->nslots, st))) return rc;
+    if (!m->scale) {
+        if ((rc = spamm_alloc((void **)&m->scale, 16, st))) return rc;
+    }
+    if (tile_a && !m->slA) {
+        if ((rc = spamm_alloc((void **)&m->slA, sizeof(uint16_t) * per * rows * m->nb, st))) return rc;
+    }
+    if (per_leaf && !m->slB) {
+        if ((rc = spamm_alloc((void **)&m->slB, sizeof(uint16_t) * per * m->nslots, st))) return rc;
     }
     SPAMM_CK(cudaMemsetAsync(m->scale, 0, sizeof(unsigned long long), st));
     const int64_t count = m->nslots * 1024;
-    int blocks = spamm_num_sms() * 8;
+    const int blocks = spamm_num_sms() * 8;
     k_absmax<<<blocks, 256, 0, st>>>(m->leaf, count, reinterpret_cast<unsigned long long *>(m->scale));
     SPAMM_CK_LAUNCH();
     unsigned long long *mx = reinterpret_cast<unsigned long long *>(m->scale);
     int32_t *sig = reinterpret_cast<int32_t *>(m->scale + 1);
-    unsigned grid = (unsigned)(m->nslots < 65535 * 4 ? m->nslots : 65535 * 4);
-    switch (s) {
-    case 3: k_slice<3><<<grid, 256, 0, st>>>(m->leaf, m->nslots, mx, sig, m->slA, m->slB); break;
-    case 4: k_slice<4><<<grid, 256, 0, st>>>(m->leaf, m->nslots, mx, sig, m->slA, m->slB); break;
-    case 5: k_slice<5><<<grid, 256, 0, st>>>(m->leaf, m->nslots, mx, sig, m->slA, m->slB); break;
-    case 6: k_slice<6><<<grid, 256, 0, st>>>(m->leaf, m->nslots, mx, sig, m->slA, m->slB); break;
-    case 7: k_slice<7><<<grid, 256, 0, st>>>(m->leaf, m->nslots, mx, sig, m->slA, m->slB); break;
-    default:
-        spamm_set_error("slices must be in 3..7 (got %d)", s);
-        return SPAMM_E_INVAL;
+    const int64_t npos = rows * m->nb;
+    const unsigned grid = (unsigned)(npos < 65535 * 4 ? npos : 65535 * 4);
+    // the tile-major array and a transposed per-leaf array need two passes
+    const int passes = (tile_a && per_leaf && transposed) ? 2 : 1;
+    for (int pass = 0; pass < passes; pass++) {
+        uint16_t *ta = (tile_a && pass == 0) ? m->slA : nullptr;
+        uint16_t *pl = (per_leaf && (passes == 1 || pass == 1)) ? m->slB : nullptr;
+        const int tr = pl && transposed ? 1 : 0;
+        uint8_t *zl = pass == 0 ? m->zlead : nullptr;
+#define SPAMM_SLICE_CASE(SS)                                                                          \
+    case SS:                                                                                          \
+        k_slice<SS><<<grid, 256, 0, st>>>(m->leaf, m->slot, m->nb, rows, mx, sig, ta, pl, tr, zl);    \
+        break;
+        switch (s) {
+            SPAMM_SLICE_CASE(3)
+            SPAMM_SLICE_CASE(4)
+            SPAMM_SLICE_CASE(5)
+            SPAMM_SLICE_CASE(6)
+            SPAMM_SLICE_CASE(7)
+        default:
+            spamm_set_error("slices must be in 3..7 (got %d)", s);
+            return SPAMM_E_INVAL;
+        }
+#undef SPAMM_SLICE_CASE
+        SPAMM_CK_LAUNCH();
     }
-    SPAMM_CK_LAUNCH();
+    if (per_leaf) m->slB_transposed = transposed ? 1 : 0;
     return SPAMM_OK;
 }

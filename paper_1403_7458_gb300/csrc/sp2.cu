@@ -61,6 +61,32 @@ __global__ void k_gershgorin_rows(const double *__restrict__ leaf, const int32_t
     hi[r] = d + s;
 }
 
+// Exact symmetry test of a leaf-stored matrix: one warp per leaf (I, K) with
+// I <= K compares it with the transpose of leaf (K, I).
+__global__ void k_symmetry(const double *__restrict__ leaf, const int32_t *__restrict__ slot, int64_t nb,
+                           int b, int32_t *__restrict__ asym)
+{
+    const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (w >= nb * nb) return;
+    const int64_t I = w / nb, K = w % nb;
+    if (I > K) return;
+    const int32_t s1 = slot[I * nb + K], s2 = slot[K * nb + I];
+    if ((s1 < 0) != (s2 < 0)) {
+        if (lane == 0) atomicExch(asym, 1);
+        return;
+    }
+    if (s1 < 0) return;
+    const double *a = leaf + (int64_t)s1 * b * b, *t = leaf + (int64_t)s2 * b * b;
+    bool bad = false;
+    for (int q = lane; q < b * b; q += 32) {
+        const int r = q / b, c = q % b;
+        // compare bit patterns: exact equality, NaN-safe
+        bad |= __double_as_longlong(a[q]) != __double_as_longlong(t[c * b + r]);
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicExch(asym, 1);
+}
+
 __global__ void __launch_bounds__(kRedThreads)
 k_gershgorin_bounds(const double *__restrict__ lo, const double *__restrict__ hi, int64_t n,
                     Sp2State *st)
@@ -206,6 +232,7 @@ struct Sp2Scratch {
     Sp2State *st = nullptr;
     double *lo = nullptr, *hi = nullptr;
     double *idem_part = nullptr, *diag_part = nullptr, *tr_part = nullptr;
+    int32_t *flag = nullptr;
     Sp2State *host = nullptr;
     void release(cudaStream_t s)
     {
@@ -215,6 +242,7 @@ struct Sp2Scratch {
         spamm_release(idem_part, s);
         spamm_release(diag_part, s);
         spamm_release(tr_part, s);
+        spamm_release(flag, s);
         if (host) cudaFreeHost(host);
     }
 };
@@ -268,6 +296,7 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
     const bool timing = (o.flags & SPAMM_F_TIMING) != 0;
     double ms_cull = 0.0, ms_gemm = 0.0, ms_update = 0.0;
     const int64_t launches0 = spamm_launch_count();
+    bool sym = false;
     int it = 0, reason = SP2_STOP_MAXITER;
     double ehist[3] = {INFINITY, INFINITY, INFINITY};
     int64_t tasks_total = 0;
@@ -306,6 +335,7 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
     SP2_TRY(spamm_alloc((void **)&sc.idem_part, sizeof(double) * G, s));
     SP2_TRY(spamm_alloc((void **)&sc.diag_part, sizeof(double) * nb, s));
     SP2_TRY(spamm_alloc((void **)&sc.tr_part, sizeof(double) * nb, s));
+    SP2_TRY(spamm_alloc((void **)&sc.flag, sizeof(int32_t) * 4, s));
     SP2_CUDA(cudaMallocHost((void **)&sc.host, sizeof(Sp2State)));
     SP2_CUDA(cudaMemsetAsync(sc.st, 0, sizeof(Sp2State), s));
     SP2_CUDA(cudaEventCreate(&ev0));
@@ -314,6 +344,15 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
         for (int q = 0; q < 5; q++) SP2_CUDA(cudaEventCreate(&evs[q]));
     SP2_CUDA(cudaEventRecord(ev0, s));
 
+    if (o.prec == SPAMM_OZAKI_BF16 && !(o.flags & SPAMM_F_NOSYM)) {
+        SP2_CUDA(cudaMemsetAsync(sc.flag, 0, sizeof(int32_t), s));
+        k_symmetry<<<(unsigned)((G + 7) / 8), 256, 0, s>>>(F->leaf, F->slot, nb, F->b, sc.flag);
+        SP2_LAUNCHED();
+        int32_t asym = 1;
+        SP2_CUDA(cudaMemcpyAsync(&asym, sc.flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        SP2_CUDA(cudaStreamSynchronize(s));
+        sym = asym == 0;
+    }
     k_gershgorin_rows<<<(unsigned)((F->n + 255) / 256), 256, 0, s>>>(F->leaf, F->slot, F->n, F->b,
                                                                       nb, sc.lo, sc.hi);
     SP2_LAUNCHED();
@@ -326,7 +365,7 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
 
     while (it < limit) {
         SP2_TRY(spamm_multiply_into(X, X, tau, X2, &mo, sc.tr_part, s, false, nullptr, false,
-                                    timing ? evs : nullptr));
+                                    timing ? evs : nullptr, sym ? 1 : 0));
         k_sp2_decide<<<1, kRedThreads, 0, s>>>(sc.tr_part, nb, X2->ws.task_total, Ne, o.rule, sc.st);
         SP2_LAUNCHED();
         k_sp2_elementwise<<<ew_blocks, kWarps * 32, 0, s>>>(
@@ -397,6 +436,7 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
         report->ms_gemm = ms_gemm;
         report->ms_update = ms_update;
         report->launches = spamm_launch_count() - launches0;
+        report->symmetric = sym ? 1 : 0;
     }
     rc = reason == SP2_STOP_MAXITER ? SPAMM_E_NOCONV : SPAMM_OK;
     if (rc == SPAMM_E_NOCONV) spamm_set_error("sp2_solve: %d iterations without convergence", it);

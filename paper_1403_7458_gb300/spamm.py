@@ -26,6 +26,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libspamm.so")
 OK, E_INVAL, E_NOMEM, E_CUDA, E_CAPACITY, E_TIMEOUT, E_NOCONV, E_NOTSUP = 0, -1, -2, -3, -4, -5, -6, -7
 FP64, OZAKI_BF16 = 0, 1
 F_TIMING = 1
+F_NOSYM = 2
 RULE_TRACE_DISTANCE, RULE_TRACE_ABOVE = 0, 1
 STOP_CONVERGED, STOP_STAGNATED, STOP_FIXED, STOP_MAXITER = 0, 1, 2, 3
 H_COLS = 6
@@ -67,7 +68,8 @@ class _Sp2Report(ctypes.Structure):
                 ("tasks_total", ctypes.c_int64), ("flops_useful", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("ms_cull", ctypes.c_double),
                 ("ms_gemm", ctypes.c_double), ("ms_update", ctypes.c_double),
-                ("launches", ctypes.c_int64), ("history", ctypes.POINTER(ctypes.c_double)),
+                ("launches", ctypes.c_int64), ("symmetric", ctypes.c_int32),
+                ("reserved2", ctypes.c_int32), ("history", ctypes.POINTER(ctypes.c_double)),
                 ("history_cap", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
@@ -242,10 +244,10 @@ def cull_noalloc(n2a, n2b, nb: int, tau: float, off, klist, stream=None):
 def sp2_solve(F: Matrix, ne: float, tau: float, P: Matrix | None = None, max_iter: int = 100,
               rule: int = RULE_TRACE_DISTANCE, trace_tol: float = 1e-10, idem_tol: float = 1e-8,
               fixed_iters: int = 0, prec: int = FP64, slices: int = 0, timing: bool = False,
-              stream=None):
+              symmetric: bool = True, stream=None):
     """P = SP2(F, Ne, tau).  Returns (P, report dict with a 'history' array)."""
     opts = _Sp2Opts(max_iter, rule, trace_tol, idem_tol, fixed_iters, F.leaf, prec, slices,
-                    F_TIMING if timing else 0, 0)
+                    (F_TIMING if timing else 0) | (0 if symmetric else F_NOSYM), 0)
     cap = fixed_iters if fixed_iters > 0 else max_iter
     hist = np.zeros((max(cap, 1), H_COLS))
     rep = _Sp2Report()
@@ -257,7 +259,7 @@ def sp2_solve(F: Matrix, ne: float, tau: float, P: Matrix | None = None, max_ite
     _check(rc, "sp2_solve", allow=(E_NOCONV,))
     out = P if P is not None else Matrix(h.value)
     report = {k: getattr(rep, k) for k, _ in _Sp2Report._fields_
-              if k not in ("history", "history_cap", "reserved")}
+              if k not in ("history", "history_cap", "reserved", "reserved2")}
     report["history"] = hist[:rep.iters].copy()
     report["converged"] = rc == OK
     return out, report

@@ -143,3 +143,29 @@ def test_mixed_sp2_matches_fp64_sp2(cuda_lib, n, s):
     assert np.linalg.norm(pm - p64) <= 1e-6
     assert abs(np.trace(pm) - n / 2) < 1e-6
     assert np.linalg.norm(pm @ pm - pm) < 1e-5
+
+
+def test_mixed_sp2_symmetric_mode_is_bit_identical(cuda_lib):
+    """Forming only the upper block triangle of X^2 and mirroring it gives
+    the same bits as forming every leaf (exact slice arithmetic on an exactly
+    symmetric iterate)."""
+    n = 1000
+    h = synth.tb_hamiltonian(n, 4)
+    F = cuda_lib.tree_build(_dev(h), leaf=32)
+    Ps, rs = cuda_lib.sp2_solve(F, n / 2, 1e-8, prec=cuda_lib.OZAKI_BF16, fixed_iters=12)
+    Pf, rf = cuda_lib.sp2_solve(F, n / 2, 1e-8, prec=cuda_lib.OZAKI_BF16, fixed_iters=12,
+                                symmetric=False)
+    assert rs["symmetric"] == 1 and rf["symmetric"] == 0
+    ps = cuda_lib.to_dense(Ps).cpu().numpy()
+    assert np.array_equal(ps, cuda_lib.to_dense(Pf).cpu().numpy())
+    assert np.array_equal(ps, ps.T)
+    assert np.array_equal(rs["history"], rf["history"])
+
+
+def test_mixed_sp2_asymmetric_input_uses_full_product(cuda_lib):
+    n = 256
+    h = synth.tb_hamiltonian(n, 5)
+    h[3, 7] += 1e-13                      # no longer exactly symmetric
+    F = cuda_lib.tree_build(_dev(h), leaf=32)
+    P, r = cuda_lib.sp2_solve(F, n / 2, 1e-8, prec=cuda_lib.OZAKI_BF16, fixed_iters=4)
+    assert r["symmetric"] == 0
