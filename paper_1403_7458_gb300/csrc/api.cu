@@ -371,10 +371,10 @@ int spamm_multiply_into(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t C,
         const int symm = (sym && A == B) ? 1 : 0;
         // slices first: the tile cull reads each leaf's leading zero slices
         if (A == B) {
-            if ((rc = launch_slices(A, sl, true, true, !symm, s))) return rc;
+            if ((rc = launch_slices(A, sl, true, true, !symm, s, ws->stop))) return rc;
         } else {
-            if ((rc = launch_slices(A, sl, true, false, false, s))) return rc;
-            if ((rc = launch_slices(B, sl, false, true, true, s))) return rc;
+            if ((rc = launch_slices(A, sl, true, false, false, s, ws->stop))) return rc;
+            if ((rc = launch_slices(B, sl, false, true, true, s, ws->stop))) return rc;
         }
         if ((rc = tc_tile_cull(A, B, tau, ws, symm, sl, s))) return rc;
         if (ev) SPAMM_CK(cudaEventRecord(ev[1], s));

@@ -21,9 +21,11 @@ namespace {
 constexpr int kWarps = 8;
 
 __global__ void __launch_bounds__(kWarps * 32)
-k_cull_count(const double *__restrict__ n2A, const double *__restrict__ n2BT, int64_t nb,
-             int64_t P, double tau2, int32_t *__restrict__ counts)
+k_cull_count(const int32_t *__restrict__ stop, const double *__restrict__ n2A,
+             const double *__restrict__ n2BT, int64_t nb, int64_t P, double tau2,
+             int32_t *__restrict__ counts)
 {
+    if (stop && *stop) return;  // the SP2 loop has already stopped
     int64_t g = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
     int lane = threadIdx.x & 31;
     if (g >= nb * nb) return;
@@ -42,8 +44,10 @@ k_cull_count(const double *__restrict__ n2A, const double *__restrict__ n2BT, in
 constexpr int kScanThreads = 1024;
 
 __global__ void __launch_bounds__(kScanThreads)
-k_scan(const int32_t *__restrict__ counts, int64_t G, int64_t *__restrict__ off)
+k_scan(const int32_t *__restrict__ stop, const int32_t *__restrict__ counts, int64_t G,
+       int64_t *__restrict__ off)
 {
+    if (stop && *stop) return;  // the SP2 loop has already stopped
     __shared__ int64_t part[kScanThreads];
     int t = threadIdx.x;
     int64_t chunk = (G + kScanThreads - 1) / kScanThreads;
@@ -68,10 +72,12 @@ k_scan(const int32_t *__restrict__ counts, int64_t G, int64_t *__restrict__ off)
 }
 
 __global__ void __launch_bounds__(kWarps * 32)
-k_cull_emit(const double *__restrict__ n2A, const double *__restrict__ n2BT, int64_t nb,
-            int64_t P, double tau2, const int64_t *__restrict__ off, uint32_t *__restrict__ klist,
-            int64_t cap, int32_t *__restrict__ err)
+k_cull_emit(const int32_t *__restrict__ stop, const double *__restrict__ n2A,
+            const double *__restrict__ n2BT, int64_t nb, int64_t P, double tau2,
+            const int64_t *__restrict__ off, uint32_t *__restrict__ klist, int64_t cap,
+            int32_t *__restrict__ err)
 {
+    if (stop && *stop) return;  // the SP2 loop has already stopped
     int64_t g = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
     int lane = threadIdx.x & 31;
     if (g >= nb * nb) return;
@@ -105,10 +111,10 @@ int spamm_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, int
     int64_t G = nb * nb;
     double tau2 = tau * tau;
     unsigned blocks = (unsigned)((G + kWarps - 1) / kWarps);
-    k_cull_count<<<blocks, kWarps * 32, 0, s>>>(A->n2 + tier_offset(A->depth), B->n2T, nb, P, tau2,
+    k_cull_count<<<blocks, kWarps * 32, 0, s>>>(ws->stop, A->n2 + tier_offset(A->depth), B->n2T, nb, P, tau2,
                                                 ws->counts);
     SPAMM_CK_LAUNCH();
-    k_scan<<<1, kScanThreads, 0, s>>>(ws->counts, G, ws->off);
+    k_scan<<<1, kScanThreads, 0, s>>>(ws->stop, ws->counts, G, ws->off);
     SPAMM_CK_LAUNCH();
     int64_t worst = G * nb;
     int64_t total = -1;
@@ -128,7 +134,7 @@ int spamm_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, int
         if (rc) return rc;
         ws->klist_cap = cap;
     }
-    k_cull_emit<<<blocks, kWarps * 32, 0, s>>>(A->n2 + tier_offset(A->depth), B->n2T, nb, P, tau2,
+    k_cull_emit<<<blocks, kWarps * 32, 0, s>>>(ws->stop, A->n2 + tier_offset(A->depth), B->n2T, nb, P, tau2,
                                                ws->off, ws->klist, ws->klist_cap, ws->counter + 8);
     SPAMM_CK_LAUNCH();
     if (total_host) *total_host = total;

@@ -41,6 +41,7 @@ struct GemmArgs {
     double *n2C;
     double *n2CT;
     double *tr_part;
+    const int32_t *stop;  // set once an SP2 loop has stopped: nothing to do
 };
 
 template <int B>
@@ -69,6 +70,7 @@ __global__ void __launch_bounds__(kThreads) k_gemm_fp64(GemmArgs g)
     __shared__ int s_red_i[kThreads / 32];
     __shared__ u128 s_red_u[kThreads / 32];
 
+    if (g.stop && *g.stop) return;
     const int tid = threadIdx.x;
     const int r0 = (tid / T::COLT) * T::TR;
     const int c0 = (tid % T::COLT) * T::TC;
@@ -208,6 +210,7 @@ int launch_gemm_fp64(spamm_mat_t A, spamm_mat_t B, spamm_mat_t C, SpammWorkspace
     g.n2C = C->n2 + tier_offset(C->depth);
     g.n2CT = C->n2T;
     g.tr_part = tr_part;
+    g.stop = ws->stop;
     SPAMM_CK(cudaMemsetAsync(ws->counter, 0, sizeof(int32_t), s));
     switch (A->b) {
     case 16: return launch_b<16>(g, s);

@@ -53,9 +53,10 @@ constexpr int kThreads = 192;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kAccStride = 256;
 constexpr long long kTimeoutCycles = 8000000000ll;  // about 4 s at 2 GHz per wait
-// Tile order: false = row-major over (I, j), so the CTAs running at the same
-// time share A leaf rows and B leaf columns in L2; true = heaviest first.
-constexpr bool kHeaviestFirst = false;
+// Tile order: true = heaviest first (tiles are handed out dynamically, so
+// this is longest-processing-time-first scheduling); false = row-major.
+constexpr bool kHeaviestFirst = true;
+constexpr int kTileRing = 4;  // tiles handed from the producer to the other roles
 
 // ---------------------------------------------------------------------------
 // tile cull: work lists of (k | mask << 24), grouped by tile t = I * nb + j
@@ -69,6 +70,7 @@ struct CullArgs {
     int64_t nb, P, nI;
     double tau2;
     int sym, S;
+    const int32_t *stop;  // set once an SP2 loop has stopped: nothing to do
 };
 
 // Work item of tile (I, j) at k: k | mask << 15 | zA << 19 | zB << 22, or 0
@@ -107,6 +109,7 @@ __global__ void __launch_bounds__(kWarps * 32)
 k_tile_count(CullArgs c, int32_t *__restrict__ counts, int32_t *__restrict__ tasks,
              int32_t *__restrict__ pairs)
 {
+    if (c.stop && *c.stop) return;
     const int64_t t = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (t >= c.nI * c.nb) return;
@@ -133,6 +136,7 @@ __global__ void __launch_bounds__(kWarps * 32)
 k_tile_emit(CullArgs c, const int64_t *__restrict__ off, uint32_t *__restrict__ list, int64_t cap,
             int32_t *__restrict__ err)
 {
+    if (c.stop && *c.stop) return;
     const int64_t t = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (t >= c.nI * c.nb) return;
@@ -157,13 +161,14 @@ constexpr int kScanThreads = 1024;
 
 // exclusive scan of counts -> off (one block), plus the total of `tasks`
 __global__ void __launch_bounds__(kScanThreads)
-k_tile_scan(const int32_t *__restrict__ counts, const int32_t *__restrict__ tasks,
+k_tile_scan(const int32_t *__restrict__ stop, const int32_t *__restrict__ counts, const int32_t *__restrict__ tasks,
             const int32_t *__restrict__ pairs, int64_t G, int64_t *__restrict__ off,
             int64_t *__restrict__ task_total, int64_t *__restrict__ pair_total)
 {
     __shared__ int64_t part[kScanThreads];
     __shared__ int64_t tpart[kScanThreads];
     __shared__ int64_t ppart[kScanThreads];
+    if (stop && *stop) return;  // the SP2 loop has already stopped
     const int t = threadIdx.x;
     const int64_t chunk = (G + kScanThreads - 1) / kScanThreads;
     const int64_t lo = t * chunk, hi = lo + chunk < G ? lo + chunk : G;
@@ -204,14 +209,17 @@ k_tile_scan(const int32_t *__restrict__ counts, const int32_t *__restrict__ task
 
 // Heaviest-first tile order (counting sort on the work-list length):
 // hist -> descending exclusive scan -> scatter.
-__global__ void k_tile_hist(const int32_t *__restrict__ counts, int64_t G, int32_t *__restrict__ bins)
+__global__ void k_tile_hist(const int32_t *__restrict__ stop, const int32_t *__restrict__ counts, int64_t nb,
+                            int64_t G, int sym, int32_t *__restrict__ bins)
 {
+    if (stop && *stop) return;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < G) atomicAdd(bins + counts[t], 1);
+    if (t < G && !(sym && t % nb < 4 * (t / nb))) atomicAdd(bins + counts[t], 1);
 }
 
-__global__ void k_tile_bins_scan(int32_t *__restrict__ bins, int64_t nbins)
+__global__ void k_tile_bins_scan(const int32_t *__restrict__ stop, int32_t *__restrict__ bins, int64_t nbins)
 {
+    if (stop && *stop) return;
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         int32_t run = 0;
         for (int64_t c = nbins - 1; c >= 0; c--) {
@@ -236,11 +244,12 @@ __global__ void k_tile_natural(int64_t nb, int64_t nI, int sym, int32_t *__restr
     }
 }
 
-__global__ void k_tile_scatter(const int32_t *__restrict__ counts, int64_t G, int32_t *__restrict__ bins,
-                               int32_t *__restrict__ order)
+__global__ void k_tile_scatter(const int32_t *__restrict__ stop, const int32_t *__restrict__ counts, int64_t nb,
+                               int64_t G, int sym, int32_t *__restrict__ bins, int32_t *__restrict__ order)
 {
+    if (stop && *stop) return;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < G) order[atomicAdd(bins + counts[t], 1)] = (int32_t)t;
+    if (t < G && !(sym && t % nb < 4 * (t / nb))) order[atomicAdd(bins + counts[t], 1)] = (int32_t)t;
 }
 
 // ---------------------------------------------------------------------------
@@ -379,10 +388,12 @@ struct TcArgs {
     const int32_t *sigB;
     double *tr_part;       // diagonal-leaf traces (may be null)
     int32_t *err;          // error word (timeout)
+    int32_t *next_tile;    // dynamic scheduler: next position in `order` (zeroed per launch)
     int64_t nb;
     int64_t nI;
     int64_t T;             // tiles in the order list
     int sym;               // symmetric product: upper block triangle + mirror
+    const int32_t *stop;   // set once an SP2 loop has stopped: nothing to do
 };
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
@@ -412,9 +423,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcArgs g)
     __shared__ __align__(8) uint64_t accf_bar[2], acce_bar[2], done_bar;
     __shared__ uint32_t slot_off[kSlots];  // ring byte offset of each in-flight item
     __shared__ uint32_t slot_w[kSlots];    // its work-list entry
+    __shared__ int32_t tile_q[kTileRing];  // tiles handed out, -1 = no more
+    __shared__ __align__(8) uint64_t tfull_bar[kTileRing], tempty_bar[kTileRing];
     __shared__ uint32_t tmem_holder;
     __shared__ int abort_flag;
 
+    if (g.stop && *g.stop) return;  // before any barrier or TMEM is touched
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t T = g.T;
 
@@ -428,6 +442,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcArgs g)
             mbar_init(smem_u32(&acce_bar[q]), 4);
         }
         mbar_init(smem_u32(&done_bar), 1);
+        for (int q = 0; q < kTileRing; q++) {
+            mbar_init(smem_u32(&tfull_bar[q]), 1);
+            mbar_init(smem_u32(&tempty_bar[q]), 5);  // MMA warp + four epilogue warps
+        }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -454,8 +472,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcArgs g)
         unsigned long long end_ptr[kSlots];
         uint32_t issued = 0, released = 0;
         bool ok = true;
-        for (int64_t it = blockIdx.x; it < T && ok; it += gridDim.x) {
-            const int64_t t = g.order[it];
+        uint32_t tq = 0, tph = 0;
+        for (;;) {
+            // take the next tile and hand it to the MMA and epilogue warps
+            int32_t tt = -1;
+            int tgood = 1;
+            if (lane == 0) {
+                if (!mbar_wait(smem_u32(&tempty_bar[tq]), tph ^ 1, abort_v)) {
+                    tgood = 0;
+                } else {
+                    const int32_t pos = atomicAdd(g.next_tile, 1);
+                    tt = pos < T ? g.order[pos] : -1;
+                    tile_q[tq] = tt;
+                    mbar_arrive(smem_u32(&tfull_bar[tq]));
+                }
+            }
+            tt = __shfl_sync(0xffffffffu, tt, 0);
+            if (!__shfl_sync(0xffffffffu, tgood, 0)) {
+                ok = false;
+                break;
+            }
+            if (++tq == kTileRing) {
+                tq = 0;
+                tph ^= 1;
+            }
+            if (tt < 0) break;
+            const int64_t t = tt;
             const int64_t I = t / g.nb, j = t % g.nb;
             const int64_t e0 = g.off[t], e1 = g.off[t + 1];
             for (int64_t base = e0; base < e1 && ok; base += 32) {
@@ -534,8 +576,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcArgs g)
         // a landed stage before the MMAs read it.
         uint32_t consumed = 0, acc = 0, aph = 0;
         bool ok = true;
-        for (int64_t it = blockIdx.x; it < T && ok; it += gridDim.x) {
-            const int64_t t = g.order[it];
+        uint32_t tq = 0, tph = 0;
+        for (;;) {
+            int32_t tt = -1;
+            int tgood = 1;
+            if (lane == 0) {
+                tgood = mbar_wait(smem_u32(&tfull_bar[tq]), tph, abort_v);
+                if (tgood) {
+                    tt = tile_q[tq];
+                    mbar_arrive(smem_u32(&tempty_bar[tq]));
+                }
+            }
+            tt = __shfl_sync(0xffffffffu, tt, 0);
+            if (!__shfl_sync(0xffffffffu, tgood, 0)) {
+                ok = false;
+                break;
+            }
+            if (++tq == kTileRing) {
+                tq = 0;
+                tph ^= 1;
+            }
+            if (tt < 0) break;
+            const int64_t t = tt;
             // the accumulator was zeroed by the epilogue (phase u of its barrier)
             int good = 1;
             if (lane == 0) good = mbar_wait(smem_u32(&acce_bar[acc]), aph, abort_v);
@@ -631,8 +693,29 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcArgs g)
             mbar_arrive(smem_u32(&acce_bar[1]));
         }
         uint32_t acc = 0, aph = 0;
-        for (int64_t it = blockIdx.x; it < T; it += gridDim.x) {
-            const int64_t t = g.order[it];
+        uint32_t tq = 0, tph = 0;
+        for (;;) {
+            int32_t tt = -1;
+            int tgood = 1;
+            if (lane == 0) {
+                tgood = mbar_wait(smem_u32(&tfull_bar[tq]), tph, abort_v);
+                if (tgood) {
+                    tt = tile_q[tq];
+                    mbar_arrive(smem_u32(&tempty_bar[tq]));
+                }
+            }
+            tt = __shfl_sync(0xffffffffu, tt, 0);
+            if (!__shfl_sync(0xffffffffu, tgood, 0)) {
+                if (lane == 0) atomicExch(g.err, 1);
+                abort_flag = 1;
+                break;
+            }
+            if (++tq == kTileRing) {
+                tq = 0;
+                tph ^= 1;
+            }
+            if (tt < 0) break;
+            const int64_t t = tt;
             const int64_t I = t / g.nb, j = t % g.nb;
             const bool has_work = g.off[t + 1] > g.off[t];
             if (!mbar_wait(smem_u32(&accf_bar[acc]), aph, abort_v)) {
@@ -766,11 +849,12 @@ int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, i
     c.tau2 = tau * tau;
     c.sym = sym;
     c.S = slices;
+    c.stop = ws->stop;
     const unsigned blocks = (unsigned)((T + kWarps - 1) / kWarps);
     k_tile_count<<<blocks, kWarps * 32, 0, s>>>(c, ws->tcounts, ws->ttasks, ws->tpairs);
     SPAMM_CK_LAUNCH();
     // toff[0..T] offsets, toff[T+1] surviving triples, toff[T+2] slice-pair work
-    k_tile_scan<<<1, kScanThreads, 0, s>>>(ws->tcounts, ws->ttasks, ws->tpairs, T, ws->toff, ws->toff + T + 1,
+    k_tile_scan<<<1, kScanThreads, 0, s>>>(ws->stop, ws->tcounts, ws->ttasks, ws->tpairs, T, ws->toff, ws->toff + T + 1,
                                            ws->toff + T + 2);
     SPAMM_CK_LAUNCH();
     const int64_t worst = T * nb;
@@ -785,13 +869,14 @@ int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, i
     SPAMM_CK_LAUNCH();
     ws->tsym = sym;
     ws->tactive = sym ? nI * nb - 2 * nI * (nI - 1) : T;
-    if (kHeaviestFirst && !sym) {
+    if (kHeaviestFirst) {
         SPAMM_CK(cudaMemsetAsync(ws->tbins, 0, sizeof(int32_t) * (nb + 1), s));
-        k_tile_hist<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(ws->tcounts, T, ws->tbins);
+        k_tile_hist<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(ws->stop, ws->tcounts, nb, T, sym, ws->tbins);
         SPAMM_CK_LAUNCH();
-        k_tile_bins_scan<<<1, 32, 0, s>>>(ws->tbins, nb + 1);
+        k_tile_bins_scan<<<1, 32, 0, s>>>(ws->stop, ws->tbins, nb + 1);
         SPAMM_CK_LAUNCH();
-        k_tile_scatter<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(ws->tcounts, T, ws->tbins, ws->torder);
+        k_tile_scatter<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(ws->stop, ws->tcounts, nb, T, sym, ws->tbins,
+                                                                     ws->torder);
         SPAMM_CK_LAUNCH();
     } else {
         k_tile_natural<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(nb, nI, sym, ws->torder);
@@ -827,6 +912,9 @@ int launch_gemm_tc(spamm_mat_t A, spamm_mat_t B, spamm_mat_t C, SpammWorkspace *
     a.nI = (A->nb + 3) / 4;
     a.T = ws->tactive;
     a.sym = ws->tsym;
+    a.stop = ws->stop;
+    a.next_tile = ws->counter + 10;
+    SPAMM_CK(cudaMemsetAsync(a.next_tile, 0, sizeof(int32_t), s));
     switch (slices) {
     case 3: return launch_tc_s<3>(a, s);
     case 4: return launch_tc_s<4>(a, s);

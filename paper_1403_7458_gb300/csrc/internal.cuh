@@ -43,6 +43,7 @@ struct SpammWorkspace {
     int64_t last_items = 0;               // host copy: tile work items of the last product
     int64_t last_pairs = 0;               // host copy: slice-pair MMA work (units of 128x32x32)
     int64_t tactive = 0;                  // tiles in the order list of the last tile cull
+    const int32_t *stop = nullptr;        // device flag: when set, the product's kernels return at once
     int tsym = 0;                         // last tile cull was symmetric
 };
 
@@ -124,7 +125,8 @@ void spamm_note_launches(int64_t k);
 int64_t spamm_launch_count();
 
 // Tensor-core path (slice.cu, gemm_tc.cu)
-int launch_slices(spamm_mat_t m, int s, bool tile_a, bool per_leaf, bool transposed, cudaStream_t st);
+int launch_slices(spamm_mat_t m, int s, bool tile_a, bool per_leaf, bool transposed, cudaStream_t st,
+                  const int32_t *stop = nullptr);
 int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, int sym, int slices,
                  cudaStream_t s);
 int launch_gemm_tc(spamm_mat_t A, spamm_mat_t B, spamm_mat_t C, SpammWorkspace *ws,

@@ -27,9 +27,10 @@ namespace {
 
 // max |x| over the stored leaves, as the IEEE bit pattern (monotone for
 // non-negative doubles), by integer atomicMax: exact and order-free.
-__global__ void k_absmax(const double *__restrict__ leaf, int64_t count,
+__global__ void k_absmax(const int32_t *__restrict__ stop, const double *__restrict__ leaf, int64_t count,
                          unsigned long long *__restrict__ out)
 {
+    if (stop && *stop) return;  // the SP2 loop has already stopped
     unsigned long long m = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < count; q += stride) {
@@ -54,7 +55,8 @@ __device__ __forceinline__ int sigma_of(unsigned long long maxbits)
 
 template <int S>
 __global__ void __launch_bounds__(256)
-k_slice(const double *__restrict__ leaf, const int32_t *__restrict__ slot, int64_t nb, int64_t rows,
+k_slice(const int32_t *__restrict__ stop, const double *__restrict__ leaf, const int32_t *__restrict__ slot,
+        int64_t nb, int64_t rows,
         const unsigned long long *__restrict__ maxbits, int32_t *__restrict__ sigma_out,
         uint16_t *__restrict__ tileA, uint16_t *__restrict__ perleaf, int perleaf_transposed,
         uint8_t *__restrict__ zlead)
@@ -62,6 +64,7 @@ k_slice(const double *__restrict__ leaf, const int32_t *__restrict__ slot, int64
     constexpr int B = 32;
     __shared__ __align__(16) uint16_t sa[S * 1024];
     __shared__ unsigned long long s_xmax;
+    if (stop && *stop) return;  // the SP2 loop has already stopped
     const int sigma = sigma_of(*maxbits);
     if (blockIdx.x == 0 && threadIdx.x == 0 && sigma_out) *sigma_out = sigma;
     // positions (i, k) over rows = 4 * ceil(nb / 4) padded leaf rows
@@ -135,7 +138,8 @@ k_slice(const double *__restrict__ leaf, const int32_t *__restrict__ slot, int64
 // that serves as both operands of a non-symmetric product needs the A array
 // and the transposed per-leaf array; a symmetric product uses the untransposed
 // per-leaf array of the transpose leaf as its B operand.
-int launch_slices(spamm_mat_t m, int s, bool tile_a, bool per_leaf, bool transposed, cudaStream_t st)
+int launch_slices(spamm_mat_t m, int s, bool tile_a, bool per_leaf, bool transposed, cudaStream_t st,
+                  const int32_t *stop)
 {
     if (m->b != 32) {
         spamm_set_error("tensor-core path is built for leaf 32 (got %d)", m->b);
@@ -166,7 +170,7 @@ int launch_slices(spamm_mat_t m, int s, bool tile_a, bool per_leaf, bool transpo
     SPAMM_CK(cudaMemsetAsync(m->scale, 0, sizeof(unsigned long long), st));
     const int64_t count = m->nslots * 1024;
     const int blocks = spamm_num_sms() * 8;
-    k_absmax<<<blocks, 256, 0, st>>>(m->leaf, count, reinterpret_cast<unsigned long long *>(m->scale));
+    k_absmax<<<blocks, 256, 0, st>>>(stop, m->leaf, count, reinterpret_cast<unsigned long long *>(m->scale));
     SPAMM_CK_LAUNCH();
     unsigned long long *mx = reinterpret_cast<unsigned long long *>(m->scale);
     int32_t *sig = reinterpret_cast<int32_t *>(m->scale + 1);
@@ -181,7 +185,7 @@ int launch_slices(spamm_mat_t m, int s, bool tile_a, bool per_leaf, bool transpo
         uint8_t *zl = pass == 0 ? m->zlead : nullptr;
 #define SPAMM_SLICE_CASE(SS)                                                                          \
     case SS:                                                                                          \
-        k_slice<SS><<<grid, 256, 0, st>>>(m->leaf, m->slot, m->nb, rows, mx, sig, ta, pl, tr, zl);    \
+        k_slice<SS><<<grid, 256, 0, st>>>(stop, m->leaf, m->slot, m->nb, rows, mx, sig, ta, pl, tr, zl);    \
         break;
         switch (s) {
             SPAMM_SLICE_CASE(3)

@@ -6,7 +6,8 @@
 //                order; a one-block kernel takes min / max of f_ii -/+ sum;
 //   x0         : X0 = (emax I - F) / (emax - emin), fused with X0's leaf norms
 //                and its trace.
-// Per iteration (all on the device, the host reads five scalars):
+// Per iteration (all on the device; the host enqueues iterations in batches
+// and reads the state once per batch):
 //   cull + leaf products : X2 = SpAMM(X, X, tau), diagonal leaves also emit
 //                          their traces;
 //   decide               : one block sums those traces in a fixed order and
@@ -14,10 +15,16 @@
 //   update               : one warp per leaf writes the new X in place, its
 //                          exact squared norm, the partial ||X2 - X||_F^2 and
 //                          the diagonal traces; the last block to finish
-//                          reduces the partials in a fixed order.
+//                          reduces the partials in a fixed order, records the
+//                          iteration's history row and applies the stopping
+//                          rule; once it stops, every later kernel of the
+//                          batch returns at once.
 // Every reduction has a fixed order, so two runs give identical bits.
 #include <math.h>
+#include <stddef.h>
 #include <string.h>
+
+#include <vector>
 
 #include "internal.cuh"
 
@@ -25,17 +32,29 @@ namespace {
 
 struct Sp2State {
     double emin, emax;
-    double t1;      // tr X
-    double t2;      // tr X^2
-    double e;       // ||X^2 - X||_F
-    double tn;      // tr of the updated X
-    int64_t tasks;  // surviving triples of this iteration's product
-    int32_t branch; // 1: X <- X^2
-    int32_t done;   // last-block ticket
+    double t1;       // tr X
+    double t2;       // tr X^2
+    double e;        // ||X^2 - X||_F
+    double tn;       // tr of the updated X
+    int64_t tasks;   // surviving triples of this iteration's product
+    int32_t branch;  // 1: X <- X^2
+    int32_t done;    // last-block ticket
+    int32_t stopped; // set by the stopping rule; later kernels return at once
+    int32_t reason;  // SP2_STOP_*
+    int32_t iter;    // iterations completed
+    int32_t pad;
+    double ehist[3]; // e of the last three iterations
+};
+
+// Stopping rule parameters (same rule as the host-side description in spamm.h)
+struct Sp2Rule {
+    double Ne, trace_tol, idem_tol;
+    int32_t fixed_iters, max_iter;
 };
 
 constexpr int kWarps = 8;
 constexpr int kRedThreads = 1024;
+constexpr int kBatch = 4;  // SP2 iterations enqueued between reads of the state
 
 __global__ void k_gershgorin_rows(const double *__restrict__ leaf, const int32_t *__restrict__ slot,
                                   int64_t n, int b, int64_t nb, double *__restrict__ lo,
@@ -111,6 +130,10 @@ k_gershgorin_bounds(const double *__restrict__ lo, const double *__restrict__ hi
         st->emin = smin[0];
         st->emax = smax[0];
         st->done = 0;
+        st->stopped = 0;
+        st->reason = SP2_STOP_MAXITER;
+        st->iter = 0;
+        st->ehist[0] = st->ehist[1] = st->ehist[2] = INFINITY;
     }
 }
 
@@ -141,10 +164,11 @@ __global__ void __launch_bounds__(kWarps * 32)
 k_sp2_elementwise(int mode, double *__restrict__ X, const double *__restrict__ src,
                   const int32_t *__restrict__ slot, int64_t n, int64_t nb, int64_t P, int b,
                   double *__restrict__ n2, double *__restrict__ n2T, double *__restrict__ idem_part,
-                  double *__restrict__ diag_part, Sp2State *st)
+                  double *__restrict__ diag_part, Sp2State *st, Sp2Rule rule, double *__restrict__ hist)
 {
     __shared__ double sred[kWarps * 32];
     __shared__ bool s_last;
+    if (mode == 1 && *(volatile int32_t *)&st->stopped) return;
     const int lane = threadIdx.x & 31;
     const int64_t w = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int bb = b * b;
@@ -204,9 +228,39 @@ k_sp2_elementwise(int mode, double *__restrict__ X, const double *__restrict__ s
     double e2 = block_sum_fixed(idem_part, nb * nb, sred);
     double tn = block_sum_fixed(diag_part, nb, sred);
     if (threadIdx.x == 0) {
-        if (mode == 1) st->e = sqrt(e2);
         st->tn = tn;
         st->done = 0;
+        if (mode == 1) {
+            const double e = sqrt(e2);
+            st->e = e;
+            const int it = st->iter + 1;
+            double *row = hist + (int64_t)(it - 1) * SP2_H_COLS;
+            row[SP2_H_TR] = st->t1;
+            row[SP2_H_TR2] = st->t2;
+            row[SP2_H_IDEM] = e;
+            row[SP2_H_BRANCH] = st->branch ? 1.0 : 0.0;
+            row[SP2_H_TASKS] = (double)st->tasks;
+            row[SP2_H_TRNEW] = tn;
+            st->ehist[0] = st->ehist[1];
+            st->ehist[1] = st->ehist[2];
+            st->ehist[2] = e;
+            st->iter = it;
+            if (rule.fixed_iters > 0) {
+                if (it >= rule.fixed_iters) {
+                    st->stopped = 1;
+                    st->reason = SP2_STOP_FIXED;
+                }
+            } else if (fabs(tn - rule.Ne) < rule.trace_tol && e < rule.idem_tol) {
+                st->stopped = 1;
+                st->reason = SP2_STOP_CONVERGED;
+            } else if (it >= 3 && e < 1e-3 && e > 0.5 * st->ehist[0]) {
+                st->stopped = 1;
+                st->reason = SP2_STOP_STAGNATED;
+            } else if (it >= rule.max_iter) {
+                st->stopped = 1;
+                st->reason = SP2_STOP_MAXITER;
+            }
+        }
     }
 }
 
@@ -215,6 +269,7 @@ k_sp2_decide(const double *__restrict__ tr_part, int64_t nb, const int64_t *__re
              double Ne, int rule, Sp2State *st)
 {
     __shared__ double sred[kRedThreads];
+    if (*(volatile int32_t *)&st->stopped) return;
     double t2 = block_sum_fixed(tr_part, nb, sred);
     if (threadIdx.x == 0) {
         double t1 = st->tn;
@@ -232,6 +287,7 @@ struct Sp2Scratch {
     Sp2State *st = nullptr;
     double *lo = nullptr, *hi = nullptr;
     double *idem_part = nullptr, *diag_part = nullptr, *tr_part = nullptr;
+    double *hist = nullptr;
     int32_t *flag = nullptr;
     Sp2State *host = nullptr;
     void release(cudaStream_t s)
@@ -243,6 +299,7 @@ struct Sp2Scratch {
         spamm_release(diag_part, s);
         spamm_release(tr_part, s);
         spamm_release(flag, s);
+        spamm_release(hist, s);
         if (host) cudaFreeHost(host);
     }
 };
@@ -292,13 +349,12 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
     spamm_mat_t X2 = new spamm_mat();
     Sp2Scratch sc;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    cudaEvent_t evs[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t evs[5 * kBatch] = {};
     const bool timing = (o.flags & SPAMM_F_TIMING) != 0;
     double ms_cull = 0.0, ms_gemm = 0.0, ms_update = 0.0;
     const int64_t launches0 = spamm_launch_count();
     bool sym = false;
     int it = 0, reason = SP2_STOP_MAXITER;
-    double ehist[3] = {INFINITY, INFINITY, INFINITY};
     int64_t tasks_total = 0;
     Sp2State h;
     memset(&h, 0, sizeof(h));
@@ -336,12 +392,13 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
     SP2_TRY(spamm_alloc((void **)&sc.diag_part, sizeof(double) * nb, s));
     SP2_TRY(spamm_alloc((void **)&sc.tr_part, sizeof(double) * nb, s));
     SP2_TRY(spamm_alloc((void **)&sc.flag, sizeof(int32_t) * 4, s));
+    SP2_TRY(spamm_alloc((void **)&sc.hist, sizeof(double) * SP2_H_COLS * limit, s));
     SP2_CUDA(cudaMallocHost((void **)&sc.host, sizeof(Sp2State)));
     SP2_CUDA(cudaMemsetAsync(sc.st, 0, sizeof(Sp2State), s));
     SP2_CUDA(cudaEventCreate(&ev0));
     SP2_CUDA(cudaEventCreate(&ev1));
     if (timing)
-        for (int q = 0; q < 5; q++) SP2_CUDA(cudaEventCreate(&evs[q]));
+        for (int q = 0; q < 5 * kBatch; q++) SP2_CUDA(cudaEventCreate(&evs[q]));
     SP2_CUDA(cudaEventRecord(ev0, s));
 
     if (o.prec == SPAMM_OZAKI_BF16 && !(o.flags & SPAMM_F_NOSYM)) {
@@ -360,66 +417,65 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
     SP2_LAUNCHED();
     k_sp2_elementwise<<<ew_blocks, kWarps * 32, 0, s>>>(0, X->leaf, F->leaf, X->slot, F->n, nb, X->P, X->b,
                                                         X->n2 + tier_offset(X->depth), X->n2T,
-                                                        sc.idem_part, sc.diag_part, sc.st);
+                                                        sc.idem_part, sc.diag_part, sc.st,
+                                                        Sp2Rule{Ne, 0, 0, 0, 1}, sc.hist);
     SP2_LAUNCHED();
 
-    while (it < limit) {
-        SP2_TRY(spamm_multiply_into(X, X, tau, X2, &mo, sc.tr_part, s, false, nullptr, false,
-                                    timing ? evs : nullptr, sym ? 1 : 0));
-        k_sp2_decide<<<1, kRedThreads, 0, s>>>(sc.tr_part, nb, X2->ws.task_total, Ne, o.rule, sc.st);
-        SP2_LAUNCHED();
-        k_sp2_elementwise<<<ew_blocks, kWarps * 32, 0, s>>>(
-            1, X->leaf, X2->leaf, X->slot, F->n, nb, X->P, X->b, X->n2 + tier_offset(X->depth),
-            X->n2T, sc.idem_part, sc.diag_part, sc.st);
-        SP2_LAUNCHED();
-        if (timing) SP2_CUDA(cudaEventRecord(evs[4], s));
-        SP2_CUDA(cudaMemcpyAsync(sc.host, sc.st, sizeof(Sp2State), cudaMemcpyDeviceToHost, s));
+    // X2's product kernels return at once when the device rule has stopped
+    X2->ws.stop = reinterpret_cast<const int32_t *>(reinterpret_cast<const char *>(sc.st) +
+                                                    offsetof(Sp2State, stopped));
+    {
+        const Sp2Rule rule{Ne, o.trace_tol, o.idem_tol, o.fixed_iters, o.max_iter};
+        int enq = 0;
+        while (enq < limit) {
+            const int batch = limit - enq < kBatch ? limit - enq : kBatch;
+            for (int q = 0; q < batch; q++) {
+                cudaEvent_t *ev = timing ? evs + 5 * q : nullptr;
+                SP2_TRY(spamm_multiply_into(X, X, tau, X2, &mo, sc.tr_part, s, false, nullptr, false, ev,
+                                            sym ? 1 : 0));
+                k_sp2_decide<<<1, kRedThreads, 0, s>>>(sc.tr_part, nb, X2->ws.task_total, Ne, o.rule, sc.st);
+                SP2_LAUNCHED();
+                k_sp2_elementwise<<<ew_blocks, kWarps * 32, 0, s>>>(
+                    1, X->leaf, X2->leaf, X->slot, F->n, nb, X->P, X->b, X->n2 + tier_offset(X->depth),
+                    X->n2T, sc.idem_part, sc.diag_part, sc.st, rule, sc.hist);
+                SP2_LAUNCHED();
+                if (timing) SP2_CUDA(cudaEventRecord(ev[4], s));
+            }
+            enq += batch;
+            const int before = h.iter;
+            SP2_CUDA(cudaMemcpyAsync(sc.host, sc.st, sizeof(Sp2State), cudaMemcpyDeviceToHost, s));
+            SP2_CUDA(cudaStreamSynchronize(s));
+            h = *sc.host;
+            if (timing) {
+                for (int q = 0; q < h.iter - before && q < batch; q++) {
+                    float a = 0.f, b = 0.f, c = 0.f;
+                    cudaEventElapsedTime(&a, evs[5 * q + 0], evs[5 * q + 1]);
+                    cudaEventElapsedTime(&b, evs[5 * q + 1], evs[5 * q + 2]);
+                    cudaEventElapsedTime(&c, evs[5 * q + 3], evs[5 * q + 4]);
+                    ms_cull += a;
+                    ms_gemm += b;
+                    ms_update += c;
+                }
+            }
+            if (h.stopped) break;
+        }
+    }
+    X2->ws.stop = nullptr;
+    it = h.iter;
+    reason = h.stopped ? h.reason : SP2_STOP_MAXITER;
+    if (it > 0) {
+        std::vector<double> hrows((size_t)it * SP2_H_COLS);
+        SP2_CUDA(cudaMemcpyAsync(hrows.data(), sc.hist, sizeof(double) * hrows.size(), cudaMemcpyDeviceToHost, s));
         SP2_CUDA(cudaStreamSynchronize(s));
-        h = *sc.host;
-        if (timing) {
-            float a = 0.f, b = 0.f, c = 0.f;
-            cudaEventElapsedTime(&a, evs[0], evs[1]);
-            cudaEventElapsedTime(&b, evs[1], evs[2]);
-            cudaEventElapsedTime(&c, evs[3], evs[4]);
-            ms_cull += a;
-            ms_gemm += b;
-            ms_update += c;
-        }
-        tasks_total += h.tasks;
-        if (report && report->history && it < report->history_cap) {
-            double *row = report->history + (int64_t)it * SP2_H_COLS;
-            row[SP2_H_TR] = h.t1;
-            row[SP2_H_TR2] = h.t2;
-            row[SP2_H_IDEM] = h.e;
-            row[SP2_H_BRANCH] = h.branch ? 1.0 : 0.0;
-            row[SP2_H_TASKS] = (double)h.tasks;
-            row[SP2_H_TRNEW] = h.tn;
-        }
-        ehist[0] = ehist[1];
-        ehist[1] = ehist[2];
-        ehist[2] = h.e;
-        it++;
-        if (o.fixed_iters > 0) {
-            if (it == o.fixed_iters) reason = SP2_STOP_FIXED;
-            continue;
-        }
-        if (fabs(h.tn - Ne) < o.trace_tol && h.e < o.idem_tol) {
-            reason = SP2_STOP_CONVERGED;
-            break;
-        }
-        if (it >= 3 && h.e < 1e-3 && h.e > 0.5 * ehist[0]) {
-            reason = SP2_STOP_STAGNATED;
-            break;
+        for (int q = 0; q < it; q++) tasks_total += (int64_t)hrows[(size_t)q * SP2_H_COLS + SP2_H_TASKS];
+        if (report && report->history) {
+            const int rows = it < report->history_cap ? it : report->history_cap;
+            memcpy(report->history, hrows.data(), sizeof(double) * rows * SP2_H_COLS);
         }
     }
     SP2_TRY(launch_pyramid(X, s));
     SP2_CUDA(cudaEventRecord(ev1, s));
     SP2_CUDA(cudaEventSynchronize(ev1));
-    if (it == 0) {  // no iteration: report the start
-        SP2_CUDA(cudaMemcpyAsync(sc.host, sc.st, sizeof(Sp2State), cudaMemcpyDeviceToHost, s));
-        SP2_CUDA(cudaStreamSynchronize(s));
-        h = *sc.host;
-    }
     if (report) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ev0, ev1);
@@ -441,7 +497,7 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
     rc = reason == SP2_STOP_MAXITER ? SPAMM_E_NOCONV : SPAMM_OK;
     if (rc == SPAMM_E_NOCONV) spamm_set_error("sp2_solve: %d iterations without convergence", it);
 done:
-    for (int q = 0; q < 5; q++)
+    for (int q = 0; q < 5 * kBatch; q++)
         if (evs[q]) cudaEventDestroy(evs[q]);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
