@@ -352,7 +352,7 @@ int ws_reserve_groups(SpammWorkspace *ws, int64_t groups, int64_t nb, cudaStream
 int spamm_multiply_into(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t C,
                         const spamm_opts_t *opts, double *tr_part, cudaStream_t s,
                         bool need_total, int64_t *tasks_out, bool build_pyramid,
-                        cudaEvent_t *ev, int sym)
+                        cudaEvent_t *ev, int sym, bool slices_ready)
 {
     int prec = opts ? opts->prec : SPAMM_FP64;
     if (ev) SPAMM_CK(cudaEventRecord(ev[0], s));
@@ -369,12 +369,15 @@ int spamm_multiply_into(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t C,
     } else if (prec == SPAMM_OZAKI_BF16) {
         const int sl = opts && opts->slices ? opts->slices : 7;
         const int symm = (sym && A == B) ? 1 : 0;
+        const bool unit = opts && (opts->flags & kFlagUnitScale);
         // slices first: the tile cull reads each leaf's leading zero slices
-        if (A == B) {
-            if ((rc = launch_slices(A, sl, true, true, !symm, s, ws->stop))) return rc;
+        if (slices_ready) {
+            // the caller (SP2's fused update) already wrote A's slices
+        } else if (A == B) {
+            if ((rc = launch_slices(A, sl, true, true, !symm, s, ws->stop, unit))) return rc;
         } else {
-            if ((rc = launch_slices(A, sl, true, false, false, s, ws->stop))) return rc;
-            if ((rc = launch_slices(B, sl, false, true, true, s, ws->stop))) return rc;
+            if ((rc = launch_slices(A, sl, true, false, false, s, ws->stop, unit))) return rc;
+            if ((rc = launch_slices(B, sl, false, true, true, s, ws->stop, unit))) return rc;
         }
         if ((rc = tc_tile_cull(A, B, tau, ws, symm, sl, s))) return rc;
         if (ev) SPAMM_CK(cudaEventRecord(ev[1], s));

@@ -66,7 +66,7 @@ struct spamm_mat {
     int slB_transposed = -1;          // layout of slB: 1 = B-role (transposed), 0 = A-role
     uint8_t *zlead = nullptr;         // leading all-zero slices per slot
     int sl_s = 0;
-    unsigned long long *scale = nullptr;  // [0] max |x| bits, [1] (int32) sigma
+    unsigned long long *scale = nullptr;  // [0] max |x| bits, [1] int32 sigma, int32 overflow flag
     SpammWorkspace ws;  // used when this handle is the output of a product
 };
 
@@ -118,7 +118,7 @@ int ws_reserve_groups(SpammWorkspace *ws, int64_t groups, int64_t nb, cudaStream
 int spamm_multiply_into(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t C,
                         const spamm_opts_t *opts, double *tr_part, cudaStream_t s,
                         bool need_total, int64_t *tasks_out, bool build_pyramid,
-                        cudaEvent_t *ev, int sym = 0);
+                        cudaEvent_t *ev, int sym = 0, bool slices_ready = false);
 
 // Count of kernels this library launched (for reports).
 void spamm_note_launches(int64_t k);
@@ -126,7 +126,12 @@ int64_t spamm_launch_count();
 
 // Tensor-core path (slice.cu, gemm_tc.cu)
 int launch_slices(spamm_mat_t m, int s, bool tile_a, bool per_leaf, bool transposed, cudaStream_t st,
-                  const int32_t *stop = nullptr);
+                  const int32_t *stop = nullptr, bool unit_scale = false);
+
+// Internal flag of spamm_opts_t.flags: slice with the fixed scale sigma = 1
+// (the caller guarantees |x| < 2, as SP2 does for its iterates).
+constexpr int32_t kFlagUnitScale = 1 << 30;
+int slices_alloc(spamm_mat_t m, int s, bool tile_a, bool per_leaf, cudaStream_t st);
 int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, int sym, int slices,
                  cudaStream_t s);
 int launch_gemm_tc(spamm_mat_t A, spamm_mat_t B, spamm_mat_t C, SpammWorkspace *ws,
@@ -256,6 +261,36 @@ __device__ __forceinline__ int warp_max_int(int v)
 {
     for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
+}
+
+// Exact slicing (see slice.cu): X = round-half-up(|x| 2^(7S - sigma)) as an
+// integer (X <= 2^(7S) whenever |x| < 2^sigma), and its base-128 digit p as
+// BF16 bits carrying the sign of x (digit 0 unmasked: it may be 128).
+__device__ __forceinline__ uint64_t slice_int(double x, int sigma, int S)
+{
+    uint64_t m;
+    int e;
+    dbl_decompose(x, m, e);
+    if (!m) return 0;
+    const int sh = 1075 + sigma - 7 * S - e;
+    if (sh <= 0) return m << (-sh);
+    if (sh < 64) return (m >> sh) + ((m >> (sh - 1)) & 1ull);
+    return 0;
+}
+
+__device__ __forceinline__ uint16_t slice_digit_bf16(uint64_t X, bool neg, int p, int S)
+{
+    uint32_t d = (uint32_t)(X >> (7 * (S - 1 - p)));
+    if (p > 0) d &= 127u;
+    const float f = neg ? -(float)d : (float)d;  // integer d <= 128: exact in BF16
+    return (uint16_t)(__float_as_uint(f) >> 16);
+}
+
+// Offset (BF16 elements) of leaf element (r, c) inside one slice of the
+// A-role core-matrix layout [g = r/8][cc = c/8][r%8][c%8].
+__device__ __forceinline__ int slice_offset(int r, int c)
+{
+    return (r >> 3) * 256 + (c >> 3) * 64 + (r & 7) * 8 + (c & 7);
 }
 
 // The culling predicate of Eq. 4 on squared norms, n2a * n2b > tau2, decided

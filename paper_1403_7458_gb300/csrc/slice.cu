@@ -44,6 +44,14 @@ __global__ void k_absmax(const int32_t *__restrict__ stop, const double *__restr
     if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
 }
 
+// A fixed scale for callers that bound their matrix: max|x| is taken as 1.0,
+// so sigma = 1 (|x| < 2).
+__global__ void k_unit_scale(const int32_t *__restrict__ stop, unsigned long long *__restrict__ out)
+{
+    if (stop && *stop) return;
+    *out = 0x3FF0000000000000ull;  // bits of 1.0
+}
+
 // sigma: the smallest integer with max|x| < 2^sigma (0 for an all-zero matrix)
 __device__ __forceinline__ int sigma_of(unsigned long long maxbits)
 {
@@ -59,7 +67,7 @@ k_slice(const int32_t *__restrict__ stop, const double *__restrict__ leaf, const
         int64_t nb, int64_t rows,
         const unsigned long long *__restrict__ maxbits, int32_t *__restrict__ sigma_out,
         uint16_t *__restrict__ tileA, uint16_t *__restrict__ perleaf, int perleaf_transposed,
-        uint8_t *__restrict__ zlead)
+        uint8_t *__restrict__ zlead, int32_t *__restrict__ overflow)
 {
     constexpr int B = 32;
     __shared__ __align__(16) uint16_t sa[S * 1024];
@@ -77,30 +85,20 @@ k_slice(const int32_t *__restrict__ stop, const double *__restrict__ leaf, const
         const double *src = leaf + (int64_t)(sl < 0 ? 0 : sl) * (B * B);
         for (int q = threadIdx.x; q < B * B; q += blockDim.x) {
             const int r = q / B, l = q % B;
-            uint64_t m = 0;
-            int e = 1;
             const double x = sl >= 0 ? src[q] : 0.0;
-            dbl_decompose(x, m, e);
-            uint64_t X = 0;
-            if (m) {
-                const int sh = 1075 + sigma - 7 * S - e;
-                if (sh <= 0) X = m << (-sh);
-                else if (sh < 64) X = (m >> sh) + ((m >> (sh - 1)) & 1ull);
-            }
+            const uint64_t X = slice_int(x, sigma, S);
             const bool neg = x < 0.0;
             xmax = X > xmax ? X : xmax;
+            // outside |x| < 2^sigma (possible only with a caller-fixed scale)
+            if (X > (1ull << (7 * S)) || !(fabs(x) <= 1e300)) atomicExch(overflow, 1);
 #pragma unroll
             for (int p = 0; p < S; p++) {
-                uint32_t d = (uint32_t)(X >> (7 * (S - 1 - p)));
-                if (p > 0) d &= 127u;
-                // integer d <= 128 -> BF16 bits (exact): via float
-                const float f = neg ? -(float)d : (float)d;
-                const uint16_t h = (uint16_t)(__float_as_uint(f) >> 16);
+                const uint16_t h = slice_digit_bf16(X, neg, p, S);
                 // [p][g][cc][8 x 8]; transposed: element (r, l) stored as (l, r)
                 if (!perleaf_transposed || !perleaf)
-                    sa[(p * 4 + (r >> 3)) * 256 + (l >> 3) * 64 + (r & 7) * 8 + (l & 7)] = h;
+                    sa[p * 1024 + slice_offset(r, l)] = h;
                 else
-                    sa[(p * 4 + (l >> 3)) * 256 + (r >> 3) * 64 + (l & 7) * 8 + (r & 7)] = h;
+                    sa[p * 1024 + slice_offset(l, r)] = h;
             }
         }
         for (int o = 16; o > 0; o >>= 1) {
@@ -133,13 +131,8 @@ k_slice(const int32_t *__restrict__ stop, const double *__restrict__ leaf, const
 
 }  // namespace
 
-// Slices of matrix m: `tile_a` asks for the tile-major A-operand array,
-// `per_leaf` for the per-leaf array (transposed = B-operand layout).  A matrix
-// that serves as both operands of a non-symmetric product needs the A array
-// and the transposed per-leaf array; a symmetric product uses the untransposed
-// per-leaf array of the transpose leaf as its B operand.
-int launch_slices(spamm_mat_t m, int s, bool tile_a, bool per_leaf, bool transposed, cudaStream_t st,
-                  const int32_t *stop)
+// Storage for the slices of matrix m (kept across calls while s is unchanged).
+int slices_alloc(spamm_mat_t m, int s, bool tile_a, bool per_leaf, cudaStream_t st)
 {
     if (m->b != 32) {
         spamm_set_error("tensor-core path is built for leaf 32 (got %d)", m->b);
@@ -160,6 +153,7 @@ int launch_slices(spamm_mat_t m, int s, bool tile_a, bool per_leaf, bool transpo
     if (!m->zlead && (rc = spamm_alloc((void **)&m->zlead, m->nslots, st))) return rc;
     if (!m->scale) {
         if ((rc = spamm_alloc((void **)&m->scale, 16, st))) return rc;
+        SPAMM_CK(cudaMemsetAsync(m->scale, 0, 16, st));  // max bits, sigma, overflow flag
     }
     if (tile_a && !m->slA) {
         if ((rc = spamm_alloc((void **)&m->slA, sizeof(uint16_t) * per * rows * m->nb, st))) return rc;
@@ -167,10 +161,31 @@ int launch_slices(spamm_mat_t m, int s, bool tile_a, bool per_leaf, bool transpo
     if (per_leaf && !m->slB) {
         if ((rc = spamm_alloc((void **)&m->slB, sizeof(uint16_t) * per * m->nslots, st))) return rc;
     }
-    SPAMM_CK(cudaMemsetAsync(m->scale, 0, sizeof(unsigned long long), st));
+    return SPAMM_OK;
+}
+
+// Slices of matrix m: `tile_a` asks for the tile-major A-operand array,
+// `per_leaf` for the per-leaf array (transposed = B-operand layout).  A matrix
+// that serves as both operands of a non-symmetric product needs the A array
+// and the transposed per-leaf array; a symmetric product uses the untransposed
+// per-leaf array of the transpose leaf as its B operand.
+int launch_slices(spamm_mat_t m, int s, bool tile_a, bool per_leaf, bool transposed, cudaStream_t st,
+                  const int32_t *stop, bool unit_scale)
+{
+    if (m->b != 32) {
+        spamm_set_error("tensor-core path is built for leaf 32 (got %d)", m->b);
+        return SPAMM_E_NOTSUP;
+    }
+    int rc = slices_alloc(m, s, tile_a, per_leaf, st);
+    if (rc) return rc;
+    const int64_t rows = ((m->nb + 3) / 4) * 4;
+    SPAMM_CK(cudaMemsetAsync(m->scale, 0, sizeof(unsigned long long), st));  // max bits
     const int64_t count = m->nslots * 1024;
     const int blocks = spamm_num_sms() * 8;
-    k_absmax<<<blocks, 256, 0, st>>>(stop, m->leaf, count, reinterpret_cast<unsigned long long *>(m->scale));
+    if (unit_scale)
+        k_unit_scale<<<1, 1, 0, st>>>(stop, reinterpret_cast<unsigned long long *>(m->scale));
+    else
+        k_absmax<<<blocks, 256, 0, st>>>(stop, m->leaf, count, reinterpret_cast<unsigned long long *>(m->scale));
     SPAMM_CK_LAUNCH();
     unsigned long long *mx = reinterpret_cast<unsigned long long *>(m->scale);
     int32_t *sig = reinterpret_cast<int32_t *>(m->scale + 1);
@@ -185,7 +200,8 @@ int launch_slices(spamm_mat_t m, int s, bool tile_a, bool per_leaf, bool transpo
         uint8_t *zl = pass == 0 ? m->zlead : nullptr;
 #define SPAMM_SLICE_CASE(SS)                                                                          \
     case SS:                                                                                          \
-        k_slice<SS><<<grid, 256, 0, st>>>(stop, m->leaf, m->slot, m->nb, rows, mx, sig, ta, pl, tr, zl);    \
+        k_slice<SS><<<grid, 256, 0, st>>>(stop, m->leaf, m->slot, m->nb, rows, mx, sig, ta, pl, tr, zl,    \
+                                          sig + 1);                                                    \
         break;
         switch (s) {
             SPAMM_SLICE_CASE(3)

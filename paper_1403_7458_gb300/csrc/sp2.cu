@@ -154,6 +154,58 @@ __device__ double block_sum_fixed(const double *v, int64_t count, double *sbuf)
     return r;
 }
 
+// The last block to finish an elementwise pass reduces the per-leaf partials
+// in a fixed order, records the iteration's history row and applies the
+// stopping rule (mode 1).
+__device__ void sp2_finish(int mode, const double *idem_part, const double *diag_part, int64_t nb,
+                           Sp2State *st, const Sp2Rule &rule, double *hist, double *sred, bool *s_last)
+{
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) *s_last = atomicAdd(&st->done, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (!*s_last) return;
+    __threadfence();
+    double e2 = block_sum_fixed(idem_part, nb * nb, sred);
+    double tn = block_sum_fixed(diag_part, nb, sred);
+    if (threadIdx.x == 0) {
+        st->tn = tn;
+        st->done = 0;
+        if (mode == 1) {
+            const double e = sqrt(e2);
+            st->e = e;
+            const int it = st->iter + 1;
+            double *row = hist + (int64_t)(it - 1) * SP2_H_COLS;
+            row[SP2_H_TR] = st->t1;
+            row[SP2_H_TR2] = st->t2;
+            row[SP2_H_IDEM] = e;
+            row[SP2_H_BRANCH] = st->branch ? 1.0 : 0.0;
+            row[SP2_H_TASKS] = (double)st->tasks;
+            row[SP2_H_TRNEW] = tn;
+            st->ehist[0] = st->ehist[1];
+            st->ehist[1] = st->ehist[2];
+            st->ehist[2] = e;
+            st->iter = it;
+            if (rule.fixed_iters > 0) {
+                if (it >= rule.fixed_iters) {
+                    st->stopped = 1;
+                    st->reason = SP2_STOP_FIXED;
+                }
+            } else if (fabs(tn - rule.Ne) < rule.trace_tol && e < rule.idem_tol) {
+                st->stopped = 1;
+                st->reason = SP2_STOP_CONVERGED;
+            } else if (it >= 3 && e < 1e-3 && e > 0.5 * st->ehist[0]) {
+                st->stopped = 1;
+                st->reason = SP2_STOP_STAGNATED;
+            } else if (it >= rule.max_iter) {
+                st->stopped = 1;
+                st->reason = SP2_STOP_MAXITER;
+            }
+        }
+    }
+}
+
+
 // Elementwise pass over all leaves of X, one warp per leaf.
 //   mode 0: X <- (emax I - F) / (emax - emin)          (src = F)
 //   mode 1: X <- X2 if branch else 2 X - X2            (src = X2)
@@ -218,51 +270,9 @@ k_sp2_elementwise(int mode, double *__restrict__ X, const double *__restrict__ s
             if (diag) diag_part[I] = dsum;
         }
     }
-    // last block reduces
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(&st->done, 1) == (int)gridDim.x - 1;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    double e2 = block_sum_fixed(idem_part, nb * nb, sred);
-    double tn = block_sum_fixed(diag_part, nb, sred);
-    if (threadIdx.x == 0) {
-        st->tn = tn;
-        st->done = 0;
-        if (mode == 1) {
-            const double e = sqrt(e2);
-            st->e = e;
-            const int it = st->iter + 1;
-            double *row = hist + (int64_t)(it - 1) * SP2_H_COLS;
-            row[SP2_H_TR] = st->t1;
-            row[SP2_H_TR2] = st->t2;
-            row[SP2_H_IDEM] = e;
-            row[SP2_H_BRANCH] = st->branch ? 1.0 : 0.0;
-            row[SP2_H_TASKS] = (double)st->tasks;
-            row[SP2_H_TRNEW] = tn;
-            st->ehist[0] = st->ehist[1];
-            st->ehist[1] = st->ehist[2];
-            st->ehist[2] = e;
-            st->iter = it;
-            if (rule.fixed_iters > 0) {
-                if (it >= rule.fixed_iters) {
-                    st->stopped = 1;
-                    st->reason = SP2_STOP_FIXED;
-                }
-            } else if (fabs(tn - rule.Ne) < rule.trace_tol && e < rule.idem_tol) {
-                st->stopped = 1;
-                st->reason = SP2_STOP_CONVERGED;
-            } else if (it >= 3 && e < 1e-3 && e > 0.5 * st->ehist[0]) {
-                st->stopped = 1;
-                st->reason = SP2_STOP_STAGNATED;
-            } else if (it >= rule.max_iter) {
-                st->stopped = 1;
-                st->reason = SP2_STOP_MAXITER;
-            }
-        }
-    }
+    sp2_finish(mode, idem_part, diag_part, nb, st, rule, hist, sred, &s_last);
 }
+
 
 __global__ void __launch_bounds__(kRedThreads)
 k_sp2_decide(const double *__restrict__ tr_part, int64_t nb, const int64_t *__restrict__ off_end,
@@ -363,6 +373,7 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
     mo.leaf = F->b;
     mo.prec = o.prec;
     mo.slices = o.slices;
+    mo.flags = kFlagUnitScale;  // iterates satisfy |x_ij| <= ||X||_2 < 2
     const int limit = o.fixed_iters > 0 ? o.fixed_iters : o.max_iter;
     unsigned ew_blocks = (unsigned)((G + kWarps - 1) / kWarps);
 
@@ -395,6 +406,9 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
     SP2_TRY(spamm_alloc((void **)&sc.hist, sizeof(double) * SP2_H_COLS * limit, s));
     SP2_CUDA(cudaMallocHost((void **)&sc.host, sizeof(Sp2State)));
     SP2_CUDA(cudaMemsetAsync(sc.st, 0, sizeof(Sp2State), s));
+    SP2_CUDA(cudaMemsetAsync(sc.flag, 0, sizeof(int32_t) * 4, s));
+    if (X->scale)  // clear the slicing overflow flag left by an earlier solve into P
+        SP2_CUDA(cudaMemsetAsync(reinterpret_cast<char *>(X->scale) + 12, 0, sizeof(int32_t), s));
     SP2_CUDA(cudaEventCreate(&ev0));
     SP2_CUDA(cudaEventCreate(&ev1));
     if (timing)
@@ -476,6 +490,18 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
     SP2_TRY(launch_pyramid(X, s));
     SP2_CUDA(cudaEventRecord(ev1, s));
     SP2_CUDA(cudaEventSynchronize(ev1));
+    if (o.prec == SPAMM_OZAKI_BF16 && X->scale) {
+        // the unit scale needs |x| < 2 in every iterate (spectrum in [0, 1])
+        int32_t ovf = 0;
+        SP2_CUDA(cudaMemcpy(&ovf, reinterpret_cast<const char *>(X->scale) + 12, sizeof(int32_t),
+                            cudaMemcpyDeviceToHost));
+        if (ovf) {
+            spamm_set_error("sp2_solve: an iterate left the slicing range |x| < 2");
+            rc = SPAMM_E_INVAL;
+            goto done;
+        }
+    }
+
     if (report) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ev0, ev1);
