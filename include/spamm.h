@@ -54,7 +54,13 @@ typedef enum {
      * accumulation in tensor memory (exact for integers below 2^24) and
      * combined in FP64.  Error-free splitting after Ozaki, Ogita, Oishi and
      * Rump (2012). */
-    SPAMM_OZAKI_BF16 = 1
+    SPAMM_OZAKI_BF16 = 1,
+    /* One BF16 term per operand (x rounded to BF16), FP32 accumulation on the
+     * tensor cores: the plain low-precision product of the precision study. */
+    SPAMM_BF16 = 2,
+    /* Split-BF16, 3 terms: hi = bf16(x), lo = bf16(x - hi);
+     * hi*hi + hi*lo + lo*hi with FP32 accumulation, combined in FP64. */
+    SPAMM_BF16X3 = 3
 } spamm_prec_t;
 
 /* ---- options ---------------------------------------------------------- */

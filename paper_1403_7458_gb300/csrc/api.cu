@@ -366,22 +366,23 @@ int spamm_multiply_into(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t C,
         ws->task_total = ws->off + A->nb * A->nb;
         if (ev) SPAMM_CK(cudaEventRecord(ev[1], s));
         rc = launch_gemm_fp64(A, B, C, ws, tr_part, s);
-    } else if (prec == SPAMM_OZAKI_BF16) {
-        const int sl = opts && opts->slices ? opts->slices : 7;
+    } else if (prec_is_tc(prec)) {
+        const int sl = prec_slices(prec, opts ? opts->slices : 0);
+        const bool fsplit = prec_float_split(prec);
         const int symm = (sym && A == B) ? 1 : 0;
         const bool unit = opts && (opts->flags & kFlagUnitScale);
         // slices first: the tile cull reads each leaf's leading zero slices
         if (slices_ready) {
             // the caller (SP2's fused update) already wrote A's slices
         } else if (A == B) {
-            if ((rc = launch_slices(A, sl, true, true, !symm, s, ws->stop, unit))) return rc;
+            if ((rc = launch_slices(A, sl, true, true, !symm, s, ws->stop, unit, fsplit))) return rc;
         } else {
-            if ((rc = launch_slices(A, sl, true, false, false, s, ws->stop, unit))) return rc;
-            if ((rc = launch_slices(B, sl, false, true, true, s, ws->stop, unit))) return rc;
+            if ((rc = launch_slices(A, sl, true, false, false, s, ws->stop, unit, fsplit))) return rc;
+            if ((rc = launch_slices(B, sl, false, true, true, s, ws->stop, unit, fsplit))) return rc;
         }
         if ((rc = tc_tile_cull(A, B, tau, ws, symm, sl, s))) return rc;
         if (ev) SPAMM_CK(cudaEventRecord(ev[1], s));
-        rc = launch_gemm_tc(A, B, C, ws, tr_part, sl, s);
+        rc = launch_gemm_tc(A, B, C, ws, tr_part, sl, s, fsplit);
         if (rc) return rc;
         const int64_t T = ((A->nb + 3) / 4) * A->nb;
         ws->task_total = ws->toff + T + 1;
@@ -420,13 +421,13 @@ extern "C" int spamm_multiply(spamm_mat_t A, spamm_mat_t B, double tau, spamm_ma
     int rc = check_tau(tau);
     if (rc) return rc;
     int prec = opts ? opts->prec : SPAMM_FP64;
-    if (prec != SPAMM_FP64 && prec != SPAMM_OZAKI_BF16) {
+    if (prec != SPAMM_FP64 && !prec_is_tc(prec)) {
         spamm_set_error("spamm_multiply: unknown precision mode %d", prec);
         return SPAMM_E_NOTSUP;
     }
-    if (prec == SPAMM_OZAKI_BF16 &&
-        (A->b != 32 || !tc_slices_ok(opts && opts->slices ? opts->slices : 7))) {
-        spamm_set_error("spamm_multiply: the tensor-core path needs leaf 32 and slices in 3..7");
+    if (prec_is_tc(prec) &&
+        (A->b != 32 || (prec == SPAMM_OZAKI_BF16 && !tc_slices_ok(opts && opts->slices ? opts->slices : 7)))) {
+        spamm_set_error("spamm_multiply: the tensor-core path needs leaf 32 (and 3..7 exact slices)");
         return SPAMM_E_NOTSUP;
     }
     cudaStream_t s = (cudaStream_t)stream;
@@ -459,9 +460,7 @@ extern "C" int spamm_multiply(spamm_mat_t A, spamm_mat_t B, double tau, spamm_ma
         stats->candidates = nb * nb * nb;
         stats->flops_useful = 2.0 * b3 * double(total);
         stats->flops_issued = stats->flops_useful;
-        if (prec == SPAMM_OZAKI_BF16) {
-            const int sl = opts && opts->slices ? opts->slices : 7;
-            (void)sl;
+        if (prec_is_tc(prec)) {
             stats->flops_issued = 2.0 * 128 * 32 * 32 * double((*C)->ws.last_pairs);
         }
         stats->ms_cull = stats->ms_gemm = stats->ms_norm = 0.f;

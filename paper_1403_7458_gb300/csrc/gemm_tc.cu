@@ -394,6 +394,7 @@ struct TcArgs {
     int64_t T;             // tiles in the order list
     int sym;               // symmetric product: upper block triangle + mirror
     const int32_t *stop;   // set once an SP2 loop has stopped: nothing to do
+    int float_split;       // slices are a float split: C = sum_d S_d in FP64, no scaling
 };
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
@@ -735,18 +736,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcArgs g)
             const uint32_t tbase = tmem + acc * kAccStride + lane_off;
 #pragma unroll
             for (int h = 0; h < 2; h++) {
-                long long cint[16];
+                long long cint[16];   // exact slices: integer combination
+                double cflt[16];      // float split: FP64 sum of the FP32 diagonals
 #pragma unroll
-                for (int c = 0; c < 16; c++) cint[c] = 0;
+                for (int c = 0; c < 16; c++) {
+                    cint[c] = 0;
+                    cflt[c] = 0.0;
+                }
                 if (has_work) {
 #pragma unroll
                     for (int d = 0; d < S; d++) {
                         uint32_t v[16];
                         tmem_ld16(tbase + 32 * d + 16 * h, v);
                         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                        if (g.float_split) {
 #pragma unroll
-                        for (int c = 0; c < 16; c++)
-                            cint[c] += (long long)__float2ll_rn(__uint_as_float(v[c])) * (1ll << (7 * (S - 1 - d)));
+                            for (int c = 0; c < 16; c++) cflt[c] += (double)__uint_as_float(v[c]);
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < 16; c++)
+                                cint[c] += (long long)__float2ll_rn(__uint_as_float(v[c])) * (1ll << (7 * (S - 1 - d)));
+                        }
                         tmem_zero16(tbase + 32 * d + 16 * h);
                     }
                 }
@@ -755,8 +765,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcArgs g)
                     for (int c = 0; c < 16; c += 2) {
                         const int col = 16 * h + c;
                         double2 v;
-                        v.x = i64_scaled(cint[c], kexp);
-                        v.y = i64_scaled(cint[c + 1], kexp);
+                        v.x = g.float_split ? cflt[c] : i64_scaled(cint[c], kexp);
+                        v.y = g.float_split ? cflt[c + 1] : i64_scaled(cint[c + 1], kexp);
                         if (col == (r & ~1)) diag = (r & 1) ? v.y : v.x;
                         reinterpret_cast<double2 *>(dst)[col >> 1] = v;
                         if (mir) {
@@ -886,9 +896,9 @@ int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, i
 }
 
 int launch_gemm_tc(spamm_mat_t A, spamm_mat_t B, spamm_mat_t C, SpammWorkspace *ws,
-                   double *tr_part, int slices, cudaStream_t s)
+                   double *tr_part, int slices, cudaStream_t s, bool float_split)
 {
-    if (A->b != 32 || !tc_slices_ok(slices)) {
+    if (A->b != 32 || !(float_split ? (slices == 1 || slices == 2) : tc_slices_ok(slices) != 0)) {
         spamm_set_error("tensor-core path: leaf must be 32 and slices in 3..7 (leaf %d, slices %d)", A->b,
                         slices);
         return SPAMM_E_NOTSUP;
@@ -914,8 +924,11 @@ int launch_gemm_tc(spamm_mat_t A, spamm_mat_t B, spamm_mat_t C, SpammWorkspace *
     a.sym = ws->tsym;
     a.stop = ws->stop;
     a.next_tile = ws->counter + 10;
+    a.float_split = float_split ? 1 : 0;
     SPAMM_CK(cudaMemsetAsync(a.next_tile, 0, sizeof(int32_t), s));
     switch (slices) {
+    case 1: return launch_tc_s<1>(a, s);
+    case 2: return launch_tc_s<2>(a, s);
     case 3: return launch_tc_s<3>(a, s);
     case 4: return launch_tc_s<4>(a, s);
     case 5: return launch_tc_s<5>(a, s);

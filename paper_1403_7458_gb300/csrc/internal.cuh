@@ -126,7 +126,19 @@ int64_t spamm_launch_count();
 
 // Tensor-core path (slice.cu, gemm_tc.cu)
 int launch_slices(spamm_mat_t m, int s, bool tile_a, bool per_leaf, bool transposed, cudaStream_t st,
-                  const int32_t *stop = nullptr, bool unit_scale = false);
+                  const int32_t *stop = nullptr, bool unit_scale = false, bool float_split = false);
+
+// Tensor-core precision modes: slices per operand and whether the slices are
+// exact integer digits (Ozaki) or a float split.
+static inline bool prec_is_tc(int prec)
+{
+    return prec == SPAMM_OZAKI_BF16 || prec == SPAMM_BF16 || prec == SPAMM_BF16X3;
+}
+static inline int prec_slices(int prec, int slices)
+{
+    return prec == SPAMM_BF16 ? 1 : prec == SPAMM_BF16X3 ? 2 : (slices ? slices : 7);
+}
+static inline bool prec_float_split(int prec) { return prec == SPAMM_BF16 || prec == SPAMM_BF16X3; }
 
 // Internal flag of spamm_opts_t.flags: slice with the fixed scale sigma = 1
 // (the caller guarantees |x| < 2, as SP2 does for its iterates).
@@ -135,8 +147,8 @@ int slices_alloc(spamm_mat_t m, int s, bool tile_a, bool per_leaf, cudaStream_t 
 int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, int sym, int slices,
                  cudaStream_t s);
 int launch_gemm_tc(spamm_mat_t A, spamm_mat_t B, spamm_mat_t C, SpammWorkspace *ws,
-                   double *tr_part, int slices, cudaStream_t s);
-int tc_slices_ok(int s);
+                   double *tr_part, int slices, cudaStream_t s, bool float_split = false);
+int tc_slices_ok(int s);  // exact slices: 3..7; float splits use 1 or 2
 
 // Leaf products (gemm_fp64.cu)
 int launch_gemm_fp64(spamm_mat_t A, spamm_mat_t B, spamm_mat_t C, SpammWorkspace *ws,

@@ -21,6 +21,8 @@
 // is 0) is recorded: slice pairs touching them contribute exactly nothing.
 //
 // Roofline: HBM-bound; per element 8 B read, 4s B written (both roles).
+#include <cuda_bf16.h>
+
 #include "internal.cuh"
 
 namespace {
@@ -67,7 +69,7 @@ k_slice(const int32_t *__restrict__ stop, const double *__restrict__ leaf, const
         int64_t nb, int64_t rows,
         const unsigned long long *__restrict__ maxbits, int32_t *__restrict__ sigma_out,
         uint16_t *__restrict__ tileA, uint16_t *__restrict__ perleaf, int perleaf_transposed,
-        uint8_t *__restrict__ zlead, int32_t *__restrict__ overflow)
+        uint8_t *__restrict__ zlead, int32_t *__restrict__ overflow, int float_split)
 {
     constexpr int B = 32;
     __shared__ __align__(16) uint16_t sa[S * 1024];
@@ -86,14 +88,22 @@ k_slice(const int32_t *__restrict__ stop, const double *__restrict__ leaf, const
         for (int q = threadIdx.x; q < B * B; q += blockDim.x) {
             const int r = q / B, l = q % B;
             const double x = sl >= 0 ? src[q] : 0.0;
-            const uint64_t X = slice_int(x, sigma, S);
+            const uint64_t X = float_split ? 0 : slice_int(x, sigma, S);
             const bool neg = x < 0.0;
             xmax = X > xmax ? X : xmax;
             // outside |x| < 2^sigma (possible only with a caller-fixed scale)
-            if (X > (1ull << (7 * S)) || !(fabs(x) <= 1e300)) atomicExch(overflow, 1);
+            if (!float_split && (X > (1ull << (7 * S)) || !(fabs(x) <= 1e300))) atomicExch(overflow, 1);
+            double rest = x;  // float split: s_p = bf16(x - s_0 - ... - s_{p-1})
 #pragma unroll
             for (int p = 0; p < S; p++) {
-                const uint16_t h = slice_digit_bf16(X, neg, p, S);
+                uint16_t h;
+                if (float_split) {
+                    const __nv_bfloat16 t = __double2bfloat16(rest);
+                    h = __bfloat16_as_ushort(t);
+                    rest -= (double)__bfloat162float(t);
+                } else {
+                    h = slice_digit_bf16(X, neg, p, S);
+                }
                 // [p][g][cc][8 x 8]; transposed: element (r, l) stored as (l, r)
                 if (!perleaf_transposed || !perleaf)
                     sa[p * 1024 + slice_offset(r, l)] = h;
@@ -108,10 +118,11 @@ k_slice(const int32_t *__restrict__ stop, const double *__restrict__ leaf, const
         if ((threadIdx.x & 31) == 0 && xmax) atomicMax(&s_xmax, xmax);
         __syncthreads();
         if (threadIdx.x == 0 && zlead && sl >= 0) {
-            // leading zero slices: X < 2^(7 (S - z)) for every element
+            // leading zero slices: X < 2^(7 (S - z)) for every element (float
+            // splits have none)
             const unsigned long long xm = s_xmax;
             const int bits = xm ? 64 - __clzll((long long)xm) : 0;
-            const int z = S - (bits + 6) / 7;
+            const int z = float_split ? 0 : S - (bits + 6) / 7;
             zlead[sl] = (uint8_t)(z < 0 ? 0 : z);
         }
         const uint4 *ss = reinterpret_cast<const uint4 *>(sa);
@@ -170,7 +181,7 @@ int slices_alloc(spamm_mat_t m, int s, bool tile_a, bool per_leaf, cudaStream_t 
 // and the transposed per-leaf array; a symmetric product uses the untransposed
 // per-leaf array of the transpose leaf as its B operand.
 int launch_slices(spamm_mat_t m, int s, bool tile_a, bool per_leaf, bool transposed, cudaStream_t st,
-                  const int32_t *stop, bool unit_scale)
+                  const int32_t *stop, bool unit_scale, bool float_split)
 {
     if (m->b != 32) {
         spamm_set_error("tensor-core path is built for leaf 32 (got %d)", m->b);
@@ -201,9 +212,11 @@ int launch_slices(spamm_mat_t m, int s, bool tile_a, bool per_leaf, bool transpo
 #define SPAMM_SLICE_CASE(SS)                                                                          \
     case SS:                                                                                          \
         k_slice<SS><<<grid, 256, 0, st>>>(stop, m->leaf, m->slot, m->nb, rows, mx, sig, ta, pl, tr, zl,    \
-                                          sig + 1);                                                    \
+                                          sig + 1, float_split ? 1 : 0);                               \
         break;
         switch (s) {
+            SPAMM_SLICE_CASE(1)
+            SPAMM_SLICE_CASE(2)
             SPAMM_SLICE_CASE(3)
             SPAMM_SLICE_CASE(4)
             SPAMM_SLICE_CASE(5)

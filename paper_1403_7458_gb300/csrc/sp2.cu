@@ -334,7 +334,8 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
         return SPAMM_E_INVAL;
     }
     if (o.prec != SPAMM_FP64 &&
-        !(o.prec == SPAMM_OZAKI_BF16 && F->b == 32 && tc_slices_ok(o.slices ? o.slices : 7))) {
+        !(prec_is_tc(o.prec) && F->b == 32 &&
+          (o.prec != SPAMM_OZAKI_BF16 || tc_slices_ok(o.slices ? o.slices : 7)))) {
         spamm_set_error("sp2_solve: precision mode %d (leaf %d, slices %d) not built", o.prec, F->b,
                         o.slices);
         return SPAMM_E_NOTSUP;
@@ -415,7 +416,7 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
         for (int q = 0; q < 5 * kBatch; q++) SP2_CUDA(cudaEventCreate(&evs[q]));
     SP2_CUDA(cudaEventRecord(ev0, s));
 
-    if (o.prec == SPAMM_OZAKI_BF16 && !(o.flags & SPAMM_F_NOSYM)) {
+    if (prec_is_tc(o.prec) && !(o.flags & SPAMM_F_NOSYM)) {
         SP2_CUDA(cudaMemsetAsync(sc.flag, 0, sizeof(int32_t), s));
         k_symmetry<<<(unsigned)((G + 7) / 8), 256, 0, s>>>(F->leaf, F->slot, nb, F->b, sc.flag);
         SP2_LAUNCHED();

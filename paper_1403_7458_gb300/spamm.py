@@ -24,7 +24,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libspamm.so")
 
 OK, E_INVAL, E_NOMEM, E_CUDA, E_CAPACITY, E_TIMEOUT, E_NOCONV, E_NOTSUP = 0, -1, -2, -3, -4, -5, -6, -7
-FP64, OZAKI_BF16 = 0, 1
+FP64, OZAKI_BF16, BF16, BF16X3 = 0, 1, 2, 3
 F_TIMING = 1
 F_NOSYM = 2
 RULE_TRACE_DISTANCE, RULE_TRACE_ABOVE = 0, 1

@@ -174,3 +174,64 @@ def test_mixed_sp2_asymmetric_input_uses_full_product(cuda_lib):
     F = cuda_lib.tree_build(_dev(h), leaf=32)
     P, r = cuda_lib.sp2_solve(F, n / 2, 1e-8, prec=cuda_lib.OZAKI_BF16, fixed_iters=4)
     assert r["symmetric"] == 0
+
+
+def _kept_abs_product(a, b, leaf, tasks):
+    """sum over kept leaf products of |A_ik| |B_kj| (elementwise) and the
+    number of terms K per output element."""
+    n = a.shape[0]
+    nb = -(-n // leaf)
+    npad = nb * leaf
+    pa = np.pad(np.abs(a), ((0, npad - n),) * 2)
+    pb = np.pad(np.abs(b), ((0, npad - n),) * 2)
+    acc = np.zeros((npad, npad))
+    kcnt = np.zeros((nb, nb))
+    for i, k, j in tasks:
+        acc[i * leaf:(i + 1) * leaf, j * leaf:(j + 1) * leaf] += (
+            pa[i * leaf:(i + 1) * leaf, k * leaf:(k + 1) * leaf] @ pb[k * leaf:(k + 1) * leaf, j * leaf:(j + 1) * leaf])
+        kcnt[i, j] += leaf
+    K = np.kron(kcnt, np.ones((leaf, leaf)))
+    return acc[:n, :n], K[:n, :n]
+
+
+@pytest.mark.parametrize("prec_name,n,tau", [("BF16", 384, 1e-6), ("BF16X3", 384, 1e-6),
+                                             ("BF16X3", 256, 0.0)])
+def test_float_split_modes_within_rounding_bounds(cuda_lib, prec_name, n, tau):
+    """BF16 (p = 8, u_b = 2^-8) operands, exact products, FP32 accumulation of
+    K terms (u_f = 2^-24; the bound takes 2K u_f for the accumulator):
+      one term : |dC| <= (2 u_b + u_b^2 + 2 K u_f (1 + u_b)^2) sum |a||b|
+      3 terms  : |dC| <= (5 u_b^2 + 3 K u_f) sum |a||b|   (dropped lo*lo and
+                 residuals below u_b^2 |x|)."""
+    prec = getattr(cuda_lib, prec_name)
+    a = synth.decaying_matrix(n, 13)
+    b = synth.decaying_matrix(n, 14, decay=1.3)
+    A = cuda_lib.tree_build(_dev(a), leaf=32)
+    B = cuda_lib.tree_build(_dev(b), leaf=32)
+    C, st = cuda_lib.multiply(A, B, tau, prec=prec, stats=True)
+    got = cuda_lib.to_dense(C).cpu().numpy()
+    ref, tasks = oracle.spamm(a, b, 32, tau, want_tasks=True)
+    assert st["tasks"] == len(tasks)
+    absab, K = _kept_abs_product(a, b, 32, tasks)
+    ub, uf = 2.0 ** -8, 2.0 ** -24
+    if prec_name == "BF16":
+        coef = 2 * ub + ub * ub + 2 * K * uf * (1 + ub) ** 2
+    else:
+        coef = 5 * ub * ub + 3 * K * uf
+    bound = coef * absab + 2.0 ** -52 * np.abs(ref)
+    assert np.all(np.abs(got - ref) <= bound)
+    if prec_name == "BF16X3":
+        # and clearly better than one term somewhere
+        assert np.abs(got - ref).max() < (2 * ub) * absab.max()
+
+
+def test_float_split_sp2_misses_target_that_exact_slices_meet(cuda_lib):
+    n = 1024
+    h = synth.tb_hamiltonian(n, 1)
+    F = cuda_lib.tree_build(_dev(h), leaf=32)
+    P64, r64 = cuda_lib.sp2_solve(F, n / 2, 1e-8)
+    p64 = cuda_lib.to_dense(P64).cpu().numpy()
+    errs = {}
+    for name in ("BF16X3", "OZAKI_BF16"):
+        P, r = cuda_lib.sp2_solve(F, n / 2, 1e-8, prec=getattr(cuda_lib, name), fixed_iters=r64["iters"])
+        errs[name] = np.linalg.norm(cuda_lib.to_dense(P).cpu().numpy() - p64)
+    assert errs["OZAKI_BF16"] <= 1e-6 < errs["BF16X3"] < 1e-1
