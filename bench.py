@@ -181,7 +181,7 @@ def run_ours(args):
     # ---- device-timed region: inputs resident in HBM ----
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    flops = gemm_ms = 0.0
+    flops = tflops = gemm_ms = 0.0
     iters = launches = 0
     step_ms = []
     with ClockSampler(local) as clk:
@@ -198,6 +198,7 @@ def run_ours(args):
             step_ms.append(ms)
             total_ms += ms
             flops += rep["flops_useful"]
+            tflops += rep["flops_tensor"]
             gemm_ms += rep["ms_gemm"]
             iters += rep["iters"]
             launches += rep["launches"]
@@ -261,8 +262,9 @@ def run_ours(args):
         bound = "tensor"
         kern = "k_gemm_tc<%d>" % slices
         peak_note = "bf16 tensor, sustained, %s (MEASURED_PEAKS.json)" % peak_src
-        # tensor work of the surviving products: every kept slice pair
-        alg_flops = flops * slices * (slices + 1) / 2
+        # tensor work of the surviving products: each slice pair that is not
+        # identically zero, on the tiles actually formed (symmetric half)
+        alg_flops = tflops
     achieved = alg_flops / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else None
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": None,
@@ -317,6 +319,49 @@ def cpu_baseline(h=None, iters=1):
                       "X0^2 by recursive SpAMM)" % iters}
 
 
+def run_precision_study(args):
+    """SP2 on the tight-binding Hamiltonian (N = args.n, default 16384) for
+    each tau, with FP64 leaf products as the reference and each mixed mode at
+    the reference's iteration count: ||P - P_FP64||_F, idempotency, trace,
+    Tr[F (P - P_FP64)] and solve time.  One JSON line per (tau, mode)."""
+    import torch
+    from paper_1403_7458_gb300 import spamm, synth
+    spamm.load()
+    torch.cuda.set_device(0)
+    n = args.n
+    h = synth.tb_hamiltonian(n, seed=0)
+    hd = torch.from_numpy(h).cuda()
+    F = spamm.tree_build(hd, leaf=32)
+    ne = n // 2
+    modes = [("bf16", spamm.BF16, 0), ("bf16x3", spamm.BF16X3, 0), ("ozaki5", spamm.OZAKI_BF16, 5),
+             ("ozaki6", spamm.OZAKI_BF16, 6), ("ozaki7", spamm.OZAKI_BF16, 7)]
+    for tau in args.taus:
+        spamm.sp2_solve(F, ne, tau)                       # warm-up
+        P64, r64 = spamm.sp2_solve(F, ne, tau)
+        p64 = spamm.to_dense(P64)
+        base = {"study": "precision", "n": n, "tau": tau, "ne": ne}
+        print(json.dumps(dict(base, mode="fp64", solve_ms=r64["ms_total"], iters=r64["iters"],
+                              stop=r64["stop_reason"], idem=r64["idem_err"], trace_err=r64["trace_err"],
+                              dP=0.0, dE=0.0, tasks=r64["tasks_total"])), flush=True)
+        for name, prec, sl in modes:
+            spamm.sp2_solve(F, ne, tau, prec=prec, slices=sl, fixed_iters=r64["iters"])
+            P, r = spamm.sp2_solve(F, ne, tau, prec=prec, slices=sl, fixed_iters=r64["iters"])
+            p = spamm.to_dense(P)
+            d = p - p64
+            line = dict(base, mode=name, solve_ms=r["ms_total"], iters=r["iters"], stop=r["stop_reason"],
+                        idem=r["idem_err"], trace_err=r["trace_err"], dP=torch.linalg.norm(d).item(),
+                        dE=float((hd * d.T).sum().item()), tasks=r["tasks_total"],
+                        speedup_vs_fp64=r64["ms_total"] / r["ms_total"])
+            # the same mode with its own stopping rule (time to solution)
+            P2, r2 = spamm.sp2_solve(F, ne, tau, prec=prec, slices=sl)
+            line.update(own_stop_ms=r2["ms_total"], own_stop_iters=r2["iters"],
+                        own_stop_reason=r2["stop_reason"])
+            print(json.dumps(line), flush=True)
+            del P, P2, p, d
+        del P64, p64
+        torch.cuda.empty_cache()
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -358,10 +403,15 @@ def main(argv=None):
     ap.add_argument("--cpu-iters", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-leg", action="store_true")
+    ap.add_argument("--study", choices=["none", "precision"], default="none")
+    ap.add_argument("--n", type=int, default=16384)
+    ap.add_argument("--taus", type=float, nargs="+", default=[1e-4, 1e-6, 1e-8, 1e-10])
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
-    if args.impl == "reference":
+    if args.study == "precision":
+        run_precision_study(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -165,6 +165,7 @@ static void ws_free(SpammWorkspace *ws, cudaStream_t s)
     spamm_release(ws->tcounts, s);
     spamm_release(ws->ttasks, s);
     spamm_release(ws->tpairs, s);
+    spamm_release(ws->tuseful, s);
     spamm_release(ws->toff, s);
     spamm_release(ws->torder, s);
     spamm_release(ws->tbins, s);
@@ -364,6 +365,7 @@ int spamm_multiply_into(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t C,
         rc = spamm_cull(A, B, tau, ws, A->nb, A->P, s, need_total, &total);
         if (rc) return rc;
         ws->task_total = ws->off + A->nb * A->nb;
+        ws->pair_units = nullptr;
         if (ev) SPAMM_CK(cudaEventRecord(ev[1], s));
         rc = launch_gemm_fp64(A, B, C, ws, tr_part, s);
     } else if (prec_is_tc(prec)) {
@@ -386,6 +388,7 @@ int spamm_multiply_into(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t C,
         if (rc) return rc;
         const int64_t T = ((A->nb + 3) / 4) * A->nb;
         ws->task_total = ws->toff + T + 1;
+        ws->pair_units = ws->toff + T + 3;
         if (need_total) {
             int64_t both[3];
             SPAMM_CK(cudaMemcpyAsync(both, ws->toff + T, sizeof(int64_t) * 3, cudaMemcpyDeviceToHost, s));

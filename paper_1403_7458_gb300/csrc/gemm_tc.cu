@@ -74,8 +74,10 @@ struct CullArgs {
 };
 
 // Work item of tile (I, j) at k: k | mask << 15 | zA << 19 | zB << 22, or 0
-// when no kept leaf has a nonzero product.  *ntask += surviving triples.
-__device__ __forceinline__ uint32_t tile_item(const CullArgs &c, int64_t I, int64_t j, int64_t k, int &ntask)
+// when no kept leaf has a nonzero product.  *ntask += surviving triples;
+// *npair += slice pairs those triples need (p >= zA_i, q >= zB, p + q < S).
+__device__ __forceinline__ uint32_t tile_item(const CullArgs &c, int64_t I, int64_t j, int64_t k, int &ntask,
+                                              int &npair)
 {
     if (k >= c.nb) return 0;
     const double b = __ldg(c.n2BT + j * c.P + k);
@@ -90,6 +92,8 @@ __device__ __forceinline__ uint32_t tile_item(const CullArgs &c, int64_t I, int6
             ntask++;
             const int zr = c.zA[c.slotA[i * c.nb + k]];
             if (zr + zb < c.S) {
+                const int mr = c.S - zr - zb;
+                npair += mr * (mr + 1) / 2;
                 mask |= 1u << r;
                 za = zr < za ? zr : za;
             }
@@ -107,7 +111,7 @@ __device__ __forceinline__ int item_pairs(uint32_t w, int S)
 
 __global__ void __launch_bounds__(kWarps * 32)
 k_tile_count(CullArgs c, int32_t *__restrict__ counts, int32_t *__restrict__ tasks,
-             int32_t *__restrict__ pairs)
+             int32_t *__restrict__ pairs, int32_t *__restrict__ useful)
 {
     if (c.stop && *c.stop) return;
     const int64_t t = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
@@ -115,20 +119,22 @@ k_tile_count(CullArgs c, int32_t *__restrict__ counts, int32_t *__restrict__ tas
     if (t >= c.nI * c.nb) return;
     const int64_t I = t / c.nb, j = t % c.nb;
     const bool active = !c.sym || j >= 4 * I;
-    int cnt = 0, ntask = 0, npair = 0;
+    int cnt = 0, ntask = 0, npair = 0, nuse = 0;
     for (int64_t k0 = 0; k0 < c.nb; k0 += 32) {
-        const uint32_t w = tile_item(c, I, j, k0 + lane, ntask);
+        const uint32_t w = tile_item(c, I, j, k0 + lane, ntask, nuse);
         cnt += __popc(__ballot_sync(0xffffffffu, w != 0));
         if (w) npair += item_pairs(w, c.S);
     }
     for (int o = 16; o > 0; o >>= 1) {
         ntask += __shfl_xor_sync(0xffffffffu, ntask, o);
         npair += __shfl_xor_sync(0xffffffffu, npair, o);
+        nuse += __shfl_xor_sync(0xffffffffu, nuse, o);
     }
     if (lane == 0) {
         counts[t] = active ? cnt : 0;
         tasks[t] = ntask;
         pairs[t] = active ? npair : 0;
+        useful[t] = active ? nuse : 0;
     }
 }
 
@@ -148,9 +154,9 @@ k_tile_emit(CullArgs c, const int64_t *__restrict__ off, uint32_t *__restrict__ 
     }
     int64_t base = off[t];
     const unsigned lt = (1u << lane) - 1u;
-    int dummy = 0;
+    int dummy = 0, dummy2 = 0;
     for (int64_t k0 = 0; k0 < c.nb; k0 += 32) {
-        const uint32_t w = tile_item(c, I, j, k0 + lane, dummy);
+        const uint32_t w = tile_item(c, I, j, k0 + lane, dummy, dummy2);
         const unsigned bal = __ballot_sync(0xffffffffu, w != 0);
         if (w) list[base + __popc(bal & lt)] = w;
         base += __popc(bal);
@@ -162,25 +168,29 @@ constexpr int kScanThreads = 1024;
 // exclusive scan of counts -> off (one block), plus the total of `tasks`
 __global__ void __launch_bounds__(kScanThreads)
 k_tile_scan(const int32_t *__restrict__ stop, const int32_t *__restrict__ counts, const int32_t *__restrict__ tasks,
-            const int32_t *__restrict__ pairs, int64_t G, int64_t *__restrict__ off,
-            int64_t *__restrict__ task_total, int64_t *__restrict__ pair_total)
+            const int32_t *__restrict__ pairs, const int32_t *__restrict__ useful, int64_t G,
+            int64_t *__restrict__ off, int64_t *__restrict__ task_total, int64_t *__restrict__ pair_total,
+            int64_t *__restrict__ useful_total)
 {
     __shared__ int64_t part[kScanThreads];
     __shared__ int64_t tpart[kScanThreads];
     __shared__ int64_t ppart[kScanThreads];
+    __shared__ int64_t upart[kScanThreads];
     if (stop && *stop) return;  // the SP2 loop has already stopped
     const int t = threadIdx.x;
     const int64_t chunk = (G + kScanThreads - 1) / kScanThreads;
     const int64_t lo = t * chunk, hi = lo + chunk < G ? lo + chunk : G;
-    int64_t s = 0, ts = 0, ps = 0;
+    int64_t s = 0, ts = 0, ps = 0, us = 0;
     for (int64_t q = lo; q < hi; q++) {
         s += counts[q];
         ts += tasks[q];
         ps += pairs[q];
+        us += useful[q];
     }
     part[t] = s;
     tpart[t] = ts;
     ppart[t] = ps;
+    upart[t] = us;
     __syncthreads();
     for (int o = 1; o < kScanThreads; o <<= 1) {
         const int64_t v = t >= o ? part[t - o] : 0;
@@ -192,6 +202,7 @@ k_tile_scan(const int32_t *__restrict__ stop, const int32_t *__restrict__ counts
         if (t < o) {
             tpart[t] += tpart[t + o];
             ppart[t] += ppart[t + o];
+            upart[t] += upart[t + o];
         }
         __syncthreads();
     }
@@ -204,6 +215,7 @@ k_tile_scan(const int32_t *__restrict__ stop, const int32_t *__restrict__ counts
     if (t == 0) {
         *task_total = tpart[0];
         *pair_total = ppart[0];
+        *useful_total = upart[0];
     }
 }
 
@@ -835,13 +847,15 @@ int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, i
         spamm_release(ws->toff, s);
         spamm_release(ws->torder, s);
         spamm_release(ws->tbins, s);
-        ws->tcounts = ws->ttasks = ws->tpairs = ws->torder = ws->tbins = nullptr;
+        spamm_release(ws->tuseful, s);
+        ws->tcounts = ws->ttasks = ws->tpairs = ws->tuseful = ws->torder = ws->tbins = nullptr;
         ws->toff = nullptr;
         ws->tile_cap = 0;
         if ((rc = spamm_alloc((void **)&ws->tcounts, sizeof(int32_t) * T, s))) return rc;
         if ((rc = spamm_alloc((void **)&ws->ttasks, sizeof(int32_t) * T, s))) return rc;
         if ((rc = spamm_alloc((void **)&ws->tpairs, sizeof(int32_t) * T, s))) return rc;
-        if ((rc = spamm_alloc((void **)&ws->toff, sizeof(int64_t) * (T + 3), s))) return rc;
+        if ((rc = spamm_alloc((void **)&ws->tuseful, sizeof(int32_t) * T, s))) return rc;
+        if ((rc = spamm_alloc((void **)&ws->toff, sizeof(int64_t) * (T + 4), s))) return rc;
         if ((rc = spamm_alloc((void **)&ws->torder, sizeof(int32_t) * T, s))) return rc;
         if ((rc = spamm_alloc((void **)&ws->tbins, sizeof(int32_t) * (nb + 1), s))) return rc;
         ws->tile_cap = T;
@@ -861,11 +875,12 @@ int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, i
     c.S = slices;
     c.stop = ws->stop;
     const unsigned blocks = (unsigned)((T + kWarps - 1) / kWarps);
-    k_tile_count<<<blocks, kWarps * 32, 0, s>>>(c, ws->tcounts, ws->ttasks, ws->tpairs);
+    k_tile_count<<<blocks, kWarps * 32, 0, s>>>(c, ws->tcounts, ws->ttasks, ws->tpairs, ws->tuseful);
     SPAMM_CK_LAUNCH();
-    // toff[0..T] offsets, toff[T+1] surviving triples, toff[T+2] slice-pair work
-    k_tile_scan<<<1, kScanThreads, 0, s>>>(ws->stop, ws->tcounts, ws->ttasks, ws->tpairs, T, ws->toff, ws->toff + T + 1,
-                                           ws->toff + T + 2);
+    // toff[0..T] offsets, toff[T+1] surviving triples, toff[T+2] issued slice-pair
+    // work, toff[T+3] slice pairs the surviving triples need
+    k_tile_scan<<<1, kScanThreads, 0, s>>>(ws->stop, ws->tcounts, ws->ttasks, ws->tpairs, ws->tuseful, T,
+                                           ws->toff, ws->toff + T + 1, ws->toff + T + 2, ws->toff + T + 3);
     SPAMM_CK_LAUNCH();
     const int64_t worst = T * nb;
     if (ws->tlist_cap < worst) {

@@ -34,12 +34,14 @@ struct SpammWorkspace {
     int32_t *tcounts = nullptr;  // work items per tile
     int32_t *ttasks = nullptr;   // surviving triples per tile
     int32_t *tpairs = nullptr;   // slice-pair work per tile (sum of m(m+1)/2)
+    int32_t *tuseful = nullptr;  // slice pairs the tile's surviving triples need
     int64_t *toff = nullptr;     // T + 2: offsets, then the triple total
     int32_t *torder = nullptr;   // heaviest-first tile order
     int32_t *tbins = nullptr;    // nb + 1 histogram bins
     uint32_t *tlist = nullptr;   // k | mask << 24
     int64_t tile_cap = 0, tlist_cap = 0;
     const int64_t *task_total = nullptr;  // device: surviving triples of the last cull
+    const int64_t *pair_units = nullptr;  // device: slice pairs needed (tensor path), else null
     int64_t last_items = 0;               // host copy: tile work items of the last product
     int64_t last_pairs = 0;               // host copy: slice-pair MMA work (units of 128x32x32)
     int64_t tactive = 0;                  // tiles in the order list of the last tile cull

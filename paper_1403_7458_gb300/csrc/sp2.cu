@@ -44,6 +44,7 @@ struct Sp2State {
     int32_t iter;    // iterations completed
     int32_t pad;
     double ehist[3]; // e of the last three iterations
+    int64_t units;   // tensor path: slice pairs of surviving triples, summed
 };
 
 // Stopping rule parameters (same rule as the host-side description in spamm.h)
@@ -276,7 +277,7 @@ k_sp2_elementwise(int mode, double *__restrict__ X, const double *__restrict__ s
 
 __global__ void __launch_bounds__(kRedThreads)
 k_sp2_decide(const double *__restrict__ tr_part, int64_t nb, const int64_t *__restrict__ off_end,
-             double Ne, int rule, Sp2State *st)
+             const int64_t *__restrict__ units, double Ne, int rule, Sp2State *st)
 {
     __shared__ double sred[kRedThreads];
     if (*(volatile int32_t *)&st->stopped) return;
@@ -290,6 +291,7 @@ k_sp2_decide(const double *__restrict__ tr_part, int64_t nb, const int64_t *__re
         st->t2 = t2;
         st->branch = take;
         st->tasks = *off_end;
+        if (units) st->units += *units;
     }
 }
 
@@ -448,7 +450,8 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
                 cudaEvent_t *ev = timing ? evs + 5 * q : nullptr;
                 SP2_TRY(spamm_multiply_into(X, X, tau, X2, &mo, sc.tr_part, s, false, nullptr, false, ev,
                                             sym ? 1 : 0));
-                k_sp2_decide<<<1, kRedThreads, 0, s>>>(sc.tr_part, nb, X2->ws.task_total, Ne, o.rule, sc.st);
+                k_sp2_decide<<<1, kRedThreads, 0, s>>>(sc.tr_part, nb, X2->ws.task_total, X2->ws.pair_units, Ne,
+                                                       o.rule, sc.st);
                 SP2_LAUNCHED();
                 k_sp2_elementwise<<<ew_blocks, kWarps * 32, 0, s>>>(
                     1, X->leaf, X2->leaf, X->slot, F->n, nb, X->P, X->b, X->n2 + tier_offset(X->depth),
@@ -514,6 +517,8 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
         report->emax = h.emax;
         report->tasks_total = tasks_total;
         report->flops_useful = 2.0 * double(F->b) * F->b * F->b * double(tasks_total);
+        report->flops_tensor = prec_is_tc(o.prec) ? 2.0 * double(F->b) * F->b * F->b * double(h.units)
+                                                  : report->flops_useful;
         report->ms_total = ms;
         report->ms_cull = ms_cull;
         report->ms_gemm = ms_gemm;

@@ -66,6 +66,7 @@ class _Sp2Report(ctypes.Structure):
                 ("trace_err", ctypes.c_double), ("idem_err", ctypes.c_double),
                 ("emin", ctypes.c_double), ("emax", ctypes.c_double),
                 ("tasks_total", ctypes.c_int64), ("flops_useful", ctypes.c_double),
+                ("flops_tensor", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("ms_cull", ctypes.c_double),
                 ("ms_gemm", ctypes.c_double), ("ms_update", ctypes.c_double),
                 ("launches", ctypes.c_int64), ("symmetric", ctypes.c_int32),
