@@ -60,7 +60,13 @@ typedef enum {
     SPAMM_BF16 = 2,
     /* Split-BF16, 3 terms: hi = bf16(x), lo = bf16(x - hi);
      * hi*hi + hi*lo + lo*hi with FP32 accumulation, combined in FP64. */
-    SPAMM_BF16X3 = 3
+    SPAMM_BF16X3 = 3,
+    /* One TF32 term per operand (x rounded to nearest TF32, 10 fraction
+     * bits), FP32 accumulation on the tensor cores (tcgen05 kind::tf32). */
+    SPAMM_TF32 = 4,
+    /* Split-TF32, 3 terms: hi = tf32(x), lo = tf32(x - hi);
+     * hi*hi + hi*lo + lo*hi with FP32 accumulation, combined in FP64. */
+    SPAMM_TF32X3 = 5
 } spamm_prec_t;
 
 /* ---- options ---------------------------------------------------------- */
@@ -115,13 +121,44 @@ int spamm_tree_build(const double *a, int64_t n, int64_t lda,
  * tau    : >= 0 and finite.
  * C      : *C == NULL creates a new handle; otherwise *C must have A's shape
  *          and is overwritten.  C may not alias A or B.
- * opts   : precision (SPAMM_FP64 or SPAMM_OZAKI_BF16), slices, flags.
+ * opts   : precision (spamm_prec_t), slices, flags.  The tensor-core modes
+ *          take leaf 16, 32 or 64 with slices x leaf <= 256 (so leaf 64
+ *          allows at most 4 exact slices).
  * stats  : optional; when given the call waits for the stream and fills it.
  * Errors: E_INVAL, E_NOTSUP, E_NOMEM, E_CUDA, E_CAPACITY (internal list
  *         overflow, never expected).
  */
 int spamm_multiply(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t *C,
                    const spamm_opts_t *opts, spamm_stats_t *stats, void *stream);
+
+/*
+ * Many independent products C[m] = SpAMM(A[m], B[m], tau[m]), m < count, of
+ * any sizes (each as in spamm_multiply, Eq. 4 and Algorithm 1), with the leaf
+ * products of all of them in ONE persistent kernel launch (per group of at
+ * most 64 products): tiles of every product are handed out from one device
+ * counter, larger products first, each product's tiles heaviest first.  The
+ * paper has no batched form; this is the deployment batching of many small
+ * SpAMMs onto one GPU.
+ * A, B   : count handles each; A[m] and B[m] of equal n; one leaf size for
+ *          all (the kernel is compiled per leaf size).
+ * tau    : count thresholds (>= 0, finite).
+ * C      : count handle slots; NULL entries are created (A[m]'s shape),
+ *          others reused (must match A[m] and alias neither A[m] nor B[m];
+ *          two slots may not share a handle).
+ * opts   : one precision / slices / flags for the whole batch.
+ * stats  : optional, ONE struct: totals over the batch (tasks, candidates,
+ *          flops); the call then waits for the stream.  With SPAMM_F_TIMING,
+ *          ms_cull covers slicing and culling of all products, ms_gemm the
+ *          batched leaf-product launch(es), ms_norm the output norms.
+ * Graph capture: without stats the call never waits for the stream.  Once a
+ * batch has run with given handles, a repeat of it allocates nothing, so the
+ * repeat may be captured into a CUDA graph on `stream`.
+ * Errors: E_INVAL (count < 0, NULL arrays, shapes, aliasing, tau), E_NOTSUP,
+ *         E_NOMEM, E_CUDA, E_CAPACITY.
+ */
+int spamm_multiply_batched(int32_t count, const spamm_mat_t *A, const spamm_mat_t *B,
+                           const double *tau, spamm_mat_t *C, const spamm_opts_t *opts,
+                           spamm_stats_t *stats, void *stream);
 
 /*
  * Write the matrix to dense row-major storage (host or device), n x n with

@@ -4,6 +4,9 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "internal.cuh"
 
 // ---------------------------------------------------------------------------
@@ -350,6 +353,37 @@ int ws_reserve_groups(SpammWorkspace *ws, int64_t groups, int64_t nb, cudaStream
     return SPAMM_OK;
 }
 
+// Slices of the operands of A x B (tensor-core path): A's tile-major array
+// and B's per-leaf array (B-role layout; for a symmetric product A == B, the
+// A-role layout of the transpose).
+static int slice_operands(spamm_mat_t A, spamm_mat_t B, int sl, int el, int symm, cudaStream_t s,
+                          const int32_t *stop, bool unit, bool fsplit)
+{
+    if (A == B) return launch_slices(A, sl, el, true, true, !symm, s, stop, unit, fsplit);
+    int rc = launch_slices(A, sl, el, true, false, false, s, stop, unit, fsplit);
+    if (rc) return rc;
+    return launch_slices(B, sl, el, false, true, true, s, stop, unit, fsplit);
+}
+
+// Device-side error words of a product's workspace (blocking read): list
+// overflow of the cull (counter 8) and a bounded wait that gave up in the
+// tensor-core kernel (counter 9).  Both are cleared after reading.
+int ws_check_errors(SpammWorkspace *ws, cudaStream_t s)
+{
+    if (!ws->counter) return SPAMM_OK;
+    int32_t w[2] = {0, 0};
+    SPAMM_CK(cudaMemcpyAsync(w, ws->counter + 8, sizeof(w), cudaMemcpyDeviceToHost, s));
+    SPAMM_CK(cudaStreamSynchronize(s));
+    if (!w[0] && !w[1]) return SPAMM_OK;
+    SPAMM_CK(cudaMemsetAsync(ws->counter + 8, 0, sizeof(w), s));
+    if (w[1]) {
+        spamm_set_error("tensor-core leaf products: a device-side wait timed out");
+        return SPAMM_E_TIMEOUT;
+    }
+    spamm_set_error("task list overflow in the cull");
+    return SPAMM_E_CAPACITY;
+}
+
 int spamm_multiply_into(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t C,
                         const spamm_opts_t *opts, double *tr_part, cudaStream_t s,
                         bool need_total, int64_t *tasks_out, bool build_pyramid,
@@ -370,23 +404,22 @@ int spamm_multiply_into(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t C,
         rc = launch_gemm_fp64(A, B, C, ws, tr_part, s);
     } else if (prec_is_tc(prec)) {
         const int sl = prec_slices(prec, opts ? opts->slices : 0);
+        const int el = prec_elem(prec);
         const bool fsplit = prec_float_split(prec);
         const int symm = (sym && A == B) ? 1 : 0;
         const bool unit = opts && (opts->flags & kFlagUnitScale);
         // slices first: the tile cull reads each leaf's leading zero slices
         if (slices_ready) {
-            // the caller (SP2's fused update) already wrote A's slices
-        } else if (A == B) {
-            if ((rc = launch_slices(A, sl, true, true, !symm, s, ws->stop, unit, fsplit))) return rc;
-        } else {
-            if ((rc = launch_slices(A, sl, true, false, false, s, ws->stop, unit, fsplit))) return rc;
-            if ((rc = launch_slices(B, sl, false, true, true, s, ws->stop, unit, fsplit))) return rc;
+            // the caller already wrote A's slices
+        } else if ((rc = slice_operands(A, B, sl, el, symm, s, ws->stop, unit, fsplit))) {
+            return rc;
         }
         if ((rc = tc_tile_cull(A, B, tau, ws, symm, sl, s))) return rc;
         if (ev) SPAMM_CK(cudaEventRecord(ev[1], s));
-        rc = launch_gemm_tc(A, B, C, ws, tr_part, sl, s, fsplit);
+        rc = launch_gemm_tc(A, B, C, ws, tr_part, sl, el, s, fsplit);
         if (rc) return rc;
-        const int64_t T = ((A->nb + 3) / 4) * A->nb;
+        const int64_t R = 128 / A->b;
+        const int64_t T = ((A->nb + R - 1) / R) * A->nb;
         ws->task_total = ws->toff + T + 1;
         ws->pair_units = ws->toff + T + 3;
         if (need_total) {
@@ -428,9 +461,10 @@ extern "C" int spamm_multiply(spamm_mat_t A, spamm_mat_t B, double tau, spamm_ma
         spamm_set_error("spamm_multiply: unknown precision mode %d", prec);
         return SPAMM_E_NOTSUP;
     }
-    if (prec_is_tc(prec) &&
-        (A->b != 32 || (prec == SPAMM_OZAKI_BF16 && !tc_slices_ok(opts && opts->slices ? opts->slices : 7)))) {
-        spamm_set_error("spamm_multiply: the tensor-core path needs leaf 32 (and 3..7 exact slices)");
+    if (prec_is_tc(prec) && !tc_mode_ok(prec, opts ? opts->slices : 0, A->b)) {
+        spamm_set_error("spamm_multiply: tensor-core mode %d with %d slices at leaf %d not built (exact "
+                        "slices 3..7, slices x leaf <= 256)",
+                        prec, opts ? opts->slices : 0, A->b);
         return SPAMM_E_NOTSUP;
     }
     cudaStream_t s = (cudaStream_t)stream;
@@ -464,10 +498,11 @@ extern "C" int spamm_multiply(spamm_mat_t A, spamm_mat_t B, double tau, spamm_ma
         stats->flops_useful = 2.0 * b3 * double(total);
         stats->flops_issued = stats->flops_useful;
         if (prec_is_tc(prec)) {
-            stats->flops_issued = 2.0 * 128 * 32 * 32 * double((*C)->ws.last_pairs);
+            stats->flops_issued = 2.0 * 128 * double(A->b) * A->b * double((*C)->ws.last_pairs);
         }
         stats->ms_cull = stats->ms_gemm = stats->ms_norm = 0.f;
-        if (timing) {
+        rc = ws_check_errors(&(*C)->ws, s);
+        if (timing && rc == SPAMM_OK) {
             cudaError_t e = cudaEventSynchronize(ev[3]);
             if (e != cudaSuccess) rc = spamm_cuda_fail(e, "cudaEventSynchronize", __FILE__, __LINE__);
             cudaEventElapsedTime(&stats->ms_cull, ev[0], ev[1]);
@@ -480,6 +515,150 @@ extern "C" int spamm_multiply(spamm_mat_t A, spamm_mat_t B, double tau, spamm_ma
     if (rc && created) {
         spamm_free(*C);
         *C = nullptr;
+    }
+    return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Batched products: per product slicing / cull, then ONE leaf-product launch
+// per group of at most kMaxBatch products, then per product output norms.
+// ---------------------------------------------------------------------------
+extern "C" int spamm_multiply_batched(int32_t count, const spamm_mat_t *A, const spamm_mat_t *B,
+                                      const double *tau, spamm_mat_t *C, const spamm_opts_t *opts,
+                                      spamm_stats_t *stats, void *stream)
+{
+    if (count < 0 || (count > 0 && (!A || !B || !tau || !C))) {
+        spamm_set_error("spamm_multiply_batched: bad arguments");
+        return SPAMM_E_INVAL;
+    }
+    if (stats) memset(stats, 0, sizeof(*stats));
+    if (count == 0) return SPAMM_OK;
+    const int prec = opts ? opts->prec : SPAMM_FP64;
+    const int leaf = A[0] ? A[0]->b : 0;
+    int rc;
+    for (int m = 0; m < count; m++) {
+        if (!A[m] || !B[m] || !spamm_mat_same_shape(A[m], B[m]) || A[m]->b != leaf) {
+            spamm_set_error("spamm_multiply_batched: product %d: NULL handle, shape mismatch or a leaf size "
+                            "other than the batch's",
+                            m);
+            return SPAMM_E_INVAL;
+        }
+        if ((rc = check_tau(tau[m]))) return rc;
+        if (C[m] && (!spamm_mat_same_shape(C[m], A[m]) || C[m] == A[m] || C[m] == B[m])) {
+            spamm_set_error("spamm_multiply_batched: C[%d] must match A[%d]'s shape and not alias A or B", m, m);
+            return SPAMM_E_INVAL;
+        }
+        for (int q = 0; q < count && C[m]; q++) {
+            if (q != m && (C[q] == C[m] || A[q] == C[m] || B[q] == C[m])) {
+                spamm_set_error("spamm_multiply_batched: C[%d] is also another product's input or output", m);
+                return SPAMM_E_INVAL;
+            }
+        }
+    }
+    if (prec != SPAMM_FP64 && !tc_mode_ok(prec, opts ? opts->slices : 0, leaf)) {
+        spamm_set_error("spamm_multiply_batched: precision mode %d (leaf %d, slices %d) not built", prec, leaf,
+                        opts ? opts->slices : 0);
+        return SPAMM_E_NOTSUP;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<char> created(count, 0);
+    for (int m = 0; m < count && rc == SPAMM_OK; m++) {
+        if (C[m]) continue;
+        spamm_mat_t c = new spamm_mat();
+        if ((rc = spamm_mat_alloc(c, A[m]->n, leaf, s))) {
+            spamm_free(c);
+            break;
+        }
+        C[m] = c;
+        created[m] = 1;
+    }
+    // larger products first: with tiles handed out dynamically this is
+    // longest-processing-time-first scheduling across the batch
+    std::vector<int> ord(count);
+    for (int m = 0; m < count; m++) ord[m] = m;
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return A[x]->nb > A[y]->nb; });
+    const bool timing = stats && opts && (opts->flags & SPAMM_F_TIMING);
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    if (timing)
+        for (int q = 0; q < 4 && rc == SPAMM_OK; q++)
+            if (cudaEventCreate(&ev[q]) != cudaSuccess) rc = SPAMM_E_CUDA;
+    const bool tcp = prec != SPAMM_FP64;
+    const int sl = tcp ? prec_slices(prec, opts ? opts->slices : 0) : 0;
+    const int el = tcp ? prec_elem(prec) : 0;
+    const bool fsplit = tcp && prec_float_split(prec);
+    const bool unit = opts && (opts->flags & kFlagUnitScale);
+    std::vector<spamm_mat_t> a(count), b(count), c(count);
+    std::vector<SpammWorkspace *> w(count);
+    for (int q = 0; q < count; q++) {
+        a[q] = A[ord[q]];
+        b[q] = B[ord[q]];
+        c[q] = C[ord[q]];
+        w[q] = &C[ord[q]]->ws;
+    }
+    if (rc == SPAMM_OK && timing && cudaEventRecord(ev[0], s) != cudaSuccess) rc = SPAMM_E_CUDA;
+    for (int q = 0; q < count && rc == SPAMM_OK; q++) {
+        const int64_t nb = a[q]->nb;
+        if ((rc = ws_reserve_groups(w[q], nb * nb, nb, s))) break;
+        if (!tcp) {
+            rc = spamm_cull(a[q], b[q], tau[ord[q]], w[q], nb, a[q]->P, s, false, nullptr, true);
+            w[q]->task_total = w[q]->off + nb * nb;
+            w[q]->pair_units = nullptr;
+        } else {
+            rc = slice_operands(a[q], b[q], sl, el, 0, s, nullptr, unit, fsplit);
+            if (rc == SPAMM_OK) rc = tc_tile_cull(a[q], b[q], tau[ord[q]], w[q], 0, sl, s);
+        }
+    }
+    if (rc == SPAMM_OK && timing && cudaEventRecord(ev[1], s) != cudaSuccess) rc = SPAMM_E_CUDA;
+    for (int q0 = 0; q0 < count && rc == SPAMM_OK; q0 += kMaxBatch) {
+        const int k = count - q0 < kMaxBatch ? count - q0 : kMaxBatch;
+        int32_t *ctr = w[q0]->counter;
+        rc = tcp ? launch_gemm_tc_batched(k, &a[q0], &b[q0], &c[q0], &w[q0], sl, el, s, fsplit, ctr)
+                 : launch_gemm_fp64_batched(k, &a[q0], &b[q0], &c[q0], &w[q0], s, ctr);
+    }
+    if (rc == SPAMM_OK && timing && cudaEventRecord(ev[2], s) != cudaSuccess) rc = SPAMM_E_CUDA;
+    for (int q = 0; q < count && rc == SPAMM_OK; q++)
+        rc = tcp ? launch_leaf_norms(c[q], s) : launch_pyramid(c[q], s);
+    if (rc == SPAMM_OK && timing && cudaEventRecord(ev[3], s) != cudaSuccess) rc = SPAMM_E_CUDA;
+    if (rc == SPAMM_OK && stats) {
+        // totals (one blocking read per product) and the device error words
+        for (int q = 0; q < count && rc == SPAMM_OK; q++) {
+            const int64_t nb = a[q]->nb;
+            int64_t v[4] = {0, 0, 0, 0};
+            cudaError_t e;
+            if (tcp) {
+                const int64_t R = 128 / leaf, T = ((nb + R - 1) / R) * nb;
+                e = cudaMemcpyAsync(v, w[q]->toff + T, sizeof(int64_t) * 4, cudaMemcpyDeviceToHost, s);
+            } else {
+                e = cudaMemcpyAsync(v + 1, w[q]->off + nb * nb, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+            }
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) {
+                rc = spamm_cuda_fail(e, "batched totals", __FILE__, __LINE__);
+                break;
+            }
+            const double b3 = double(leaf) * leaf * leaf;
+            stats->tasks += v[1];
+            stats->candidates += nb * nb * nb;
+            stats->flops_useful += 2.0 * b3 * double(v[1]);
+            stats->flops_issued += tcp ? 2.0 * 128 * double(leaf) * leaf * double(v[2]) : 2.0 * b3 * double(v[1]);
+            rc = ws_check_errors(w[q], s);
+        }
+        if (rc == SPAMM_OK && timing) {
+            cudaError_t e = cudaEventSynchronize(ev[3]);
+            if (e != cudaSuccess) rc = spamm_cuda_fail(e, "cudaEventSynchronize", __FILE__, __LINE__);
+            cudaEventElapsedTime(&stats->ms_cull, ev[0], ev[1]);
+            cudaEventElapsedTime(&stats->ms_gemm, ev[1], ev[2]);
+            cudaEventElapsedTime(&stats->ms_norm, ev[2], ev[3]);
+        }
+    }
+    for (int q = 0; q < 4; q++)
+        if (ev[q]) cudaEventDestroy(ev[q]);
+    if (rc) {
+        for (int m = 0; m < count; m++)
+            if (created[m]) {
+                spamm_free(C[m]);
+                C[m] = nullptr;
+            }
     }
     return rc;
 }

@@ -106,7 +106,7 @@ k_cull_emit(const int32_t *__restrict__ stop, const double *__restrict__ n2A,
 static const int64_t kEagerListBytes = int64_t(512) << 20;
 
 int spamm_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, int64_t nb,
-               int64_t P, cudaStream_t s, bool need_total, int64_t *total_host)
+               int64_t P, cudaStream_t s, bool need_total, int64_t *total_host, bool worst_case)
 {
     int64_t G = nb * nb;
     double tau2 = tau * tau;
@@ -118,14 +118,14 @@ int spamm_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, int
     SPAMM_CK_LAUNCH();
     int64_t worst = G * nb;
     int64_t total = -1;
-    if (need_total || (ws->klist_cap < worst && worst * 4 > kEagerListBytes)) {
+    if (need_total || (!worst_case && ws->klist_cap < worst && worst * 4 > kEagerListBytes)) {
         SPAMM_CK(cudaMemcpyAsync(&total, ws->off + G, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         SPAMM_CK(cudaStreamSynchronize(s));
     }
     int64_t want = total >= 0 ? total : worst;
     if (ws->klist_cap < want) {
         int64_t cap = want;
-        if (total >= 0 && worst * 4 <= kEagerListBytes) cap = worst;
+        if (worst_case || (total >= 0 && worst * 4 <= kEagerListBytes)) cap = worst;
         else if (total >= 0) cap = want + want / 4 < worst ? want + want / 4 : worst;
         spamm_release(ws->klist, s);
         ws->klist = nullptr;

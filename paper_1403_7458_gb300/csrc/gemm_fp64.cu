@@ -10,6 +10,10 @@
 // writes C_ij, its exact squared norm (leaf tier of C's quadtree), and for
 // diagonal leaves the partial trace used by SP2.
 //
+// A launch serves a table of up to kMaxBatch independent products: output
+// leaves of all of them are numbered consecutively (product by product) and
+// pulled from the one counter.
+//
 // Roofline: FP64 pipe bound (2 b^3 FLOP per task; operands 16 b^2 bytes per
 // task, mostly served from L2).
 #include "internal.cuh"
@@ -26,7 +30,7 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
-struct GemmArgs {
+struct FpProb {
     const double *leafA;
     const int32_t *slotA;
     const double *leafB;
@@ -37,12 +41,30 @@ struct GemmArgs {
     int64_t P;
     const int64_t *off;
     const uint32_t *klist;
-    int32_t *counter;
     double *n2C;
     double *n2CT;
     double *tr_part;
+    int64_t g0;  // first output-leaf number of this product
+};
+
+struct GemmArgs {
+    FpProb p[kMaxBatch];
+    int64_t G;            // output leaves over all products
+    int32_t nprob;
+    int32_t *counter;
     const int32_t *stop;  // set once an SP2 loop has stopped: nothing to do
 };
+
+__device__ __forceinline__ int find_prob(const GemmArgs &g, int64_t x)
+{
+    int lo = 0, hi = g.nprob - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (g.p[mid].g0 <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
 
 template <int B>
 struct Tile {
@@ -60,7 +82,7 @@ __device__ __forceinline__ void stage_leaf(double *dst, const double *src, int t
 }
 
 template <int B>
-__global__ void __launch_bounds__(kThreads) k_gemm_fp64(GemmArgs g)
+__global__ void __launch_bounds__(kThreads) k_gemm_fp64(const __grid_constant__ GemmArgs g)
 {
     using T = Tile<B>;
     extern __shared__ __align__(16) double smem[];
@@ -74,15 +96,17 @@ __global__ void __launch_bounds__(kThreads) k_gemm_fp64(GemmArgs g)
     const int tid = threadIdx.x;
     const int r0 = (tid / T::COLT) * T::TR;
     const int c0 = (tid % T::COLT) * T::TC;
-    const int64_t G = g.nb * g.nb;
+    const int64_t G = g.G;
 
     for (;;) {
         if (tid == 0) s_group = atomicAdd(g.counter, 1);
         __syncthreads();
-        const int64_t grp = s_group;
-        if (grp >= G) break;
-        const int64_t i = grp / g.nb, j = grp % g.nb;
-        const int64_t t0 = g.off[grp], t1 = g.off[grp + 1];
+        const int64_t gg = s_group;
+        if (gg >= G) break;
+        const FpProb &P = g.p[find_prob(g, gg)];
+        const int64_t grp = gg - P.g0;
+        const int64_t i = grp / P.nb, j = grp % P.nb;
+        const int64_t t0 = P.off[grp], t1 = P.off[grp + 1];
 
         double acc[T::TR][T::TC];
 #pragma unroll
@@ -92,19 +116,19 @@ __global__ void __launch_bounds__(kThreads) k_gemm_fp64(GemmArgs g)
 
         if (t1 > t0) {
             {
-                uint32_t k = g.klist[t0];
-                stage_leaf<B>(As, g.leafA + (int64_t)g.slotA[i * g.nb + k] * B * B, tid);
-                stage_leaf<B>(Bs, g.leafB + (int64_t)g.slotB[(int64_t)k * g.nb + j] * B * B, tid);
+                uint32_t k = P.klist[t0];
+                stage_leaf<B>(As, P.leafA + (int64_t)P.slotA[i * P.nb + k] * B * B, tid);
+                stage_leaf<B>(Bs, P.leafB + (int64_t)P.slotB[(int64_t)k * P.nb + j] * B * B, tid);
                 cp_async_commit();
             }
             for (int64_t t = t0; t < t1; t++) {
                 const int st = (int)((t - t0) & 1);
                 if (t + 1 < t1) {
-                    uint32_t k = g.klist[t + 1];
+                    uint32_t k = P.klist[t + 1];
                     stage_leaf<B>(As + (st ^ 1) * B * B,
-                                  g.leafA + (int64_t)g.slotA[i * g.nb + k] * B * B, tid);
+                                  P.leafA + (int64_t)P.slotA[i * P.nb + k] * B * B, tid);
                     stage_leaf<B>(Bs + (st ^ 1) * B * B,
-                                  g.leafB + (int64_t)g.slotB[(int64_t)k * g.nb + j] * B * B, tid);
+                                  P.leafB + (int64_t)P.slotB[(int64_t)k * P.nb + j] * B * B, tid);
                 }
                 cp_async_commit();
                 cp_async_wait1();
@@ -134,7 +158,7 @@ __global__ void __launch_bounds__(kThreads) k_gemm_fp64(GemmArgs g)
 #pragma unroll
             for (int b = 0; b < T::TC; b++) Cs[(r0 + a) * B + c0 + b] = acc[a][b];
         __syncthreads();
-        double *dst = g.leafC + (int64_t)g.slotC[grp] * B * B;
+        double *dst = P.leafC + (int64_t)P.slotC[grp] * B * B;
         int emax = 0;
         for (int q = tid; q < B * B / 2; q += kThreads) {
             double2 v = reinterpret_cast<const double2 *>(Cs)[q];
@@ -157,12 +181,12 @@ __global__ void __launch_bounds__(kThreads) k_gemm_fp64(GemmArgs g)
             u128 tot = 0;
             for (int w = 0; w < kThreads / 32; w++) tot += s_red_u[w];
             double r = emax > 0 ? sq_sum_round(tot, emax) : 0.0;
-            g.n2C[i * g.P + j] = r;
-            g.n2CT[j * g.P + i] = r;
-            if (i == j && g.tr_part) {
+            P.n2C[i * P.P + j] = r;
+            P.n2CT[j * P.P + i] = r;
+            if (i == j && P.tr_part) {
                 double tr = 0.0;
                 for (int q = 0; q < B; q++) tr += Cs[q * B + q];
-                g.tr_part[i] = tr;
+                P.tr_part[i] = tr;
             }
         }
         __syncthreads();
@@ -182,9 +206,9 @@ int launch_b(const GemmArgs &args, cudaStream_t s)
     int per_sm = 0;
     SPAMM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gemm_fp64<B>, kThreads, smem));
     if (per_sm < 1) per_sm = 1;
-    int64_t G = args.nb * args.nb;
     int64_t grid = (int64_t)spamm_num_sms() * per_sm;
-    if (grid > G) grid = G;
+    if (grid > args.G) grid = args.G;
+    if (grid < 1) grid = 1;
     k_gemm_fp64<B><<<(unsigned)grid, kThreads, smem, s>>>(args);
     SPAMM_CK_LAUNCH();
     return SPAMM_OK;
@@ -192,32 +216,63 @@ int launch_b(const GemmArgs &args, cudaStream_t s)
 
 }  // namespace
 
-int launch_gemm_fp64(spamm_mat_t A, spamm_mat_t B, spamm_mat_t C, SpammWorkspace *ws,
-                     double *tr_part, cudaStream_t s)
+static void fill_prob(FpProb &p, spamm_mat_t A, spamm_mat_t B, spamm_mat_t C, SpammWorkspace *ws,
+                      double *tr_part, int64_t g0)
 {
-    GemmArgs g;
-    g.leafA = A->leaf;
-    g.slotA = A->slot;
-    g.leafB = B->leaf;
-    g.slotB = B->slot;
-    g.leafC = C->leaf;
-    g.slotC = C->slot;
-    g.nb = A->nb;
-    g.P = A->P;
-    g.off = ws->off;
-    g.klist = ws->klist;
-    g.counter = ws->counter;
-    g.n2C = C->n2 + tier_offset(C->depth);
-    g.n2CT = C->n2T;
-    g.tr_part = tr_part;
-    g.stop = ws->stop;
-    SPAMM_CK(cudaMemsetAsync(ws->counter, 0, sizeof(int32_t), s));
-    switch (A->b) {
+    p.leafA = A->leaf;
+    p.slotA = A->slot;
+    p.leafB = B->leaf;
+    p.slotB = B->slot;
+    p.leafC = C->leaf;
+    p.slotC = C->slot;
+    p.nb = A->nb;
+    p.P = A->P;
+    p.off = ws->off;
+    p.klist = ws->klist;
+    p.n2C = C->n2 + tier_offset(C->depth);
+    p.n2CT = C->n2T;
+    p.tr_part = tr_part;
+    p.g0 = g0;
+}
+
+static int launch_args(GemmArgs &g, int leaf, cudaStream_t s)
+{
+    SPAMM_CK(cudaMemsetAsync(g.counter, 0, sizeof(int32_t), s));
+    switch (leaf) {
     case 16: return launch_b<16>(g, s);
     case 32: return launch_b<32>(g, s);
     case 64: return launch_b<64>(g, s);
     default:
-        spamm_set_error("leaf size %d not built", A->b);
+        spamm_set_error("leaf size %d not built", leaf);
         return SPAMM_E_NOTSUP;
     }
+}
+
+int launch_gemm_fp64(spamm_mat_t A, spamm_mat_t B, spamm_mat_t C, SpammWorkspace *ws,
+                     double *tr_part, cudaStream_t s)
+{
+    thread_local GemmArgs g;  // large (one table entry used); host-side staging only
+    fill_prob(g.p[0], A, B, C, ws, tr_part, 0);
+    g.nprob = 1;
+    g.G = A->nb * A->nb;
+    g.counter = ws->counter;
+    g.stop = ws->stop;
+    return launch_args(g, A->b, s);
+}
+
+int launch_gemm_fp64_batched(int count, const spamm_mat_t *A, const spamm_mat_t *B, const spamm_mat_t *C,
+                             SpammWorkspace *const *ws, cudaStream_t s, int32_t *counter)
+{
+    if (count < 1 || count > kMaxBatch) return SPAMM_E_INVAL;
+    thread_local GemmArgs g;
+    int64_t g0 = 0;
+    for (int m = 0; m < count; m++) {
+        fill_prob(g.p[m], A[m], B[m], C[m], ws[m], nullptr, g0);
+        g0 += A[m]->nb * A[m]->nb;
+    }
+    g.nprob = count;
+    g.G = g0;
+    g.counter = counter;
+    g.stop = nullptr;
+    return launch_args(g, A[0]->b, s);
 }

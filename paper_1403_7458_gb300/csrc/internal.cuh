@@ -30,7 +30,7 @@ struct SpammWorkspace {
     int32_t *counter = nullptr;  // work counters and error flags (16 ints)
     double *tr_part = nullptr;   // per leaf row partial traces (nb)
     int64_t tr_cap = 0;
-    // tensor-core path: tile work lists (tile t = I * nb + j, I = i / 4)
+    // tensor-core path: tile work lists (tile t = I * nb + j, I = i / R)
     int32_t *tcounts = nullptr;  // work items per tile
     int32_t *ttasks = nullptr;   // surviving triples per tile
     int32_t *tpairs = nullptr;   // slice-pair work per tile (sum of m(m+1)/2)
@@ -38,12 +38,12 @@ struct SpammWorkspace {
     int64_t *toff = nullptr;     // T + 2: offsets, then the triple total
     int32_t *torder = nullptr;   // heaviest-first tile order
     int32_t *tbins = nullptr;    // nb + 1 histogram bins
-    uint32_t *tlist = nullptr;   // k | mask << 24
+    uint32_t *tlist = nullptr;   // k | mask << 15 | zA << 23 | zB << 26
     int64_t tile_cap = 0, tlist_cap = 0;
     const int64_t *task_total = nullptr;  // device: surviving triples of the last cull
     const int64_t *pair_units = nullptr;  // device: slice pairs needed (tensor path), else null
     int64_t last_items = 0;               // host copy: tile work items of the last product
-    int64_t last_pairs = 0;               // host copy: slice-pair MMA work (units of 128x32x32)
+    int64_t last_pairs = 0;               // host copy: slice-pair MMA work (units of 128 x b x b)
     int64_t tactive = 0;                  // tiles in the order list of the last tile cull
     const int32_t *stop = nullptr;        // device flag: when set, the product's kernels return at once
     int tsym = 0;                         // last tile cull was symmetric
@@ -62,12 +62,14 @@ struct spamm_mat {
     double *n2T = nullptr;
     cudaStream_t stream = nullptr;
     int device = 0;
-    // exact BF16 slices for the tensor-core path (slice.cu)
-    uint16_t *slA = nullptr;          // A operand, tile-major [I][k][p][L] (4 leaf rows per block)
-    uint16_t *slB = nullptr;          // per-leaf [p][..] array (B operand)
+    // slices for the tensor-core path (slice.cu): BF16 (2-byte) or TF32
+    // (4-byte) elements; R = 128 / b leaf rows per tile
+    uint8_t *slA = nullptr;           // A operand, tile-major [I][k][p][L] (R leaf rows per block)
+    uint8_t *slB = nullptr;           // per-leaf [p][..] array (B operand)
     int slB_transposed = -1;          // layout of slB: 1 = B-role (transposed), 0 = A-role
     uint8_t *zlead = nullptr;         // leading all-zero slices per slot
     int sl_s = 0;
+    int sl_e = 0;                     // bytes per slice element
     unsigned long long *scale = nullptr;  // [0] max |x| bits, [1] int32 sigma, int32 overflow flag
     SpammWorkspace ws;  // used when this handle is the output of a product
 };
@@ -108,8 +110,11 @@ int launch_pyramid(spamm_mat_t m, cudaStream_t s);
 // Cull (cull.cu): fills ws.off / ws.klist for SpAMM(A, B, tau) into C's workspace.
 // On return *total_host is the number of tasks when `need_total` is set (blocking),
 // otherwise -1.
+// worst_case: reserve room for every candidate instead of asking the device
+// for the count (never waits for the stream; for graph capture).
 int spamm_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws,
-               int64_t nb, int64_t P, cudaStream_t s, bool need_total, int64_t *total_host);
+               int64_t nb, int64_t P, cudaStream_t s, bool need_total, int64_t *total_host,
+               bool worst_case = false);
 int ws_reserve_groups(SpammWorkspace *ws, int64_t groups, int64_t nb, cudaStream_t s);
 
 // C = SpAMM(A, B, tau) into an existing handle (api.cu).  ev (optional, 4
@@ -122,35 +127,55 @@ int spamm_multiply_into(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t C,
                         bool need_total, int64_t *tasks_out, bool build_pyramid,
                         cudaEvent_t *ev, int sym = 0, bool slices_ready = false);
 
+// Read and clear the device-side error words of a product (blocking).
+int ws_check_errors(SpammWorkspace *ws, cudaStream_t s);
+
 // Count of kernels this library launched (for reports).
 void spamm_note_launches(int64_t k);
 int64_t spamm_launch_count();
 
-// Tensor-core path (slice.cu, gemm_tc.cu)
-int launch_slices(spamm_mat_t m, int s, bool tile_a, bool per_leaf, bool transposed, cudaStream_t st,
+// Tensor-core path (slice.cu, gemm_tc*.cu).  e = bytes per slice element:
+// 2 (BF16, tcgen05 kind::f16) or 4 (TF32, kind::tf32).
+int launch_slices(spamm_mat_t m, int s, int e, bool tile_a, bool per_leaf, bool transposed, cudaStream_t st,
                   const int32_t *stop = nullptr, bool unit_scale = false, bool float_split = false);
 
-// Tensor-core precision modes: slices per operand and whether the slices are
-// exact integer digits (Ozaki) or a float split.
+// Tensor-core precision modes: slices per operand, element size, and whether
+// the slices are exact integer digits (Ozaki) or a float split.
 static inline bool prec_is_tc(int prec)
 {
-    return prec == SPAMM_OZAKI_BF16 || prec == SPAMM_BF16 || prec == SPAMM_BF16X3;
+    return prec == SPAMM_OZAKI_BF16 || prec == SPAMM_BF16 || prec == SPAMM_BF16X3 || prec == SPAMM_TF32 ||
+           prec == SPAMM_TF32X3;
 }
 static inline int prec_slices(int prec, int slices)
 {
-    return prec == SPAMM_BF16 ? 1 : prec == SPAMM_BF16X3 ? 2 : (slices ? slices : 7);
+    return (prec == SPAMM_BF16 || prec == SPAMM_TF32) ? 1
+           : (prec == SPAMM_BF16X3 || prec == SPAMM_TF32X3) ? 2
+                                                             : (slices ? slices : 7);
 }
-static inline bool prec_float_split(int prec) { return prec == SPAMM_BF16 || prec == SPAMM_BF16X3; }
+static inline bool prec_float_split(int prec) { return prec != SPAMM_OZAKI_BF16; }
+static inline int prec_elem(int prec) { return (prec == SPAMM_TF32 || prec == SPAMM_TF32X3) ? 4 : 2; }
 
 // Internal flag of spamm_opts_t.flags: slice with the fixed scale sigma = 1
 // (the caller guarantees |x| < 2, as SP2 does for its iterates).
 constexpr int32_t kFlagUnitScale = 1 << 30;
-int slices_alloc(spamm_mat_t m, int s, bool tile_a, bool per_leaf, cudaStream_t st);
+int slices_alloc(spamm_mat_t m, int s, int e, bool tile_a, bool per_leaf, cudaStream_t st);
 int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, int sym, int slices,
                  cudaStream_t s);
 int launch_gemm_tc(spamm_mat_t A, spamm_mat_t B, spamm_mat_t C, SpammWorkspace *ws,
-                   double *tr_part, int slices, cudaStream_t s, bool float_split = false);
-int tc_slices_ok(int s);  // exact slices: 3..7; float splits use 1 or 2
+                   double *tr_part, int slices, int e, cudaStream_t s, bool float_split = false);
+// One launch over the products m < count (count <= kMaxBatch) whose tile
+// lists are in ws[m]; products are taken in the given order.
+constexpr int kMaxBatch = 64;
+int launch_gemm_tc_batched(int count, const spamm_mat_t *A, const spamm_mat_t *B, const spamm_mat_t *C,
+                           SpammWorkspace *const *ws, int slices, int e, cudaStream_t s, bool float_split,
+                           int32_t *counters);
+// A tensor-core mode is built for (prec, slices, leaf): exact slices 3..7
+// (BF16), float splits 1 or 2 terms; slices x leaf <= 256 TMEM columns.
+int tc_mode_ok(int prec, int slices, int leaf);
+
+// FP64 leaf products of count independent products in one launch (gemm_fp64.cu)
+int launch_gemm_fp64_batched(int count, const spamm_mat_t *A, const spamm_mat_t *B, const spamm_mat_t *C,
+                             SpammWorkspace *const *ws, cudaStream_t s, int32_t *counter);
 
 // Leaf products (gemm_fp64.cu)
 int launch_gemm_fp64(spamm_mat_t A, spamm_mat_t B, spamm_mat_t C, SpammWorkspace *ws,
@@ -300,11 +325,14 @@ __device__ __forceinline__ uint16_t slice_digit_bf16(uint64_t X, bool neg, int p
     return (uint16_t)(__float_as_uint(f) >> 16);
 }
 
-// Offset (BF16 elements) of leaf element (r, c) inside one slice of the
-// A-role core-matrix layout [g = r/8][cc = c/8][r%8][c%8].
+// Offset (elements) of leaf element (r, c) inside one slice of the A-role
+// core-matrix layout of a B x B leaf with E-byte elements:
+// [g = r/8][cc = c/ce][r%8][c%ce], ce = 16/E elements per 16-byte row.
+template <int B, int E>
 __device__ __forceinline__ int slice_offset(int r, int c)
 {
-    return (r >> 3) * 256 + (c >> 3) * 64 + (r & 7) * 8 + (c & 7);
+    constexpr int ce = 16 / E;
+    return (r >> 3) * (8 * B) + (c / ce) * (8 * ce) + (r & 7) * ce + (c % ce);
 }
 
 // The culling predicate of Eq. 4 on squared norms, n2a * n2b > tau2, decided

@@ -9,19 +9,27 @@
 // sums of such products stay exact while they are below 2^24.
 // (Error-free splitting after Ozaki, Ogita, Oishi and Rump, 2012.)
 //
-// Two layouts per leaf (b = 32, 2s KB each), both slice-major and made of
-// 8 x 8 "core matrices" of BF16 (16-byte rows) as the tcgen05 K-major
-// operand wants; slice p occupies bytes [2048 p, 2048 (p + 1)):
-//   A role : [p][g = r/8][cc = l/8][8 x 8]   rows r of the leaf, K = columns l
-//   B role : [q][g = c/8][cc = l/8][8 x 8]   N = columns c, K = rows l
+// Float splits instead store s_0 = round(x), s_1 = round(x - s_0), ... in
+// BF16 or TF32 (round to nearest), for the low-precision modes.
+//
+// Two layouts per b x b leaf (b = 16, 32, 64), both slice-major and made of
+// "core matrices" of 8 rows x 16 bytes (8 x 8 BF16 or 8 x 4 TF32) as the
+// tcgen05 K-major operand wants; slice p occupies bytes [p b^2 e, (p+1) b^2 e)
+// for e-byte elements, ce = 16 / e elements per core-matrix row:
+//   A role : [p][g = r/8][cc = l/ce][8 x ce]   rows r of the leaf, K = columns l
+//   B role : [q][g = c/8][cc = l/ce][8 x ce]   N = columns c, K = rows l
 // The B-role image of leaf (k, j) equals the A-role image of its transpose,
-// so for a symmetric matrix the A-role array serves both operands.
+// so for a symmetric matrix the A-role array serves both operands.  The
+// tile-major A array puts the R = 128 / b leaves (i, k), i = R I .. R I + R-1,
+// of one tile next to each other per slice: [I][k][p][L][slice].
 //
 // Per leaf the number z of leading all-zero slices (every digit d_p, p < z,
 // is 0) is recorded: slice pairs touching them contribute exactly nothing.
 //
-// Roofline: HBM-bound; per element 8 B read, 4s B written (both roles).
+// Roofline: HBM-bound; per element 8 B read, 2 e s B written (both roles).
 #include <cuda_bf16.h>
+
+#include <type_traits>
 
 #include "internal.cuh"
 
@@ -63,21 +71,52 @@ __device__ __forceinline__ int sigma_of(unsigned long long maxbits)
     return E - 1022;
 }
 
-template <int S>
+// Round to the nearest TF32 (10 fraction bits, ties away from zero): the
+// bit pattern of an FP32 value whose low 13 bits are zero.
+__device__ __forceinline__ uint32_t to_tf32(float f)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(f));
+    return r;
+}
+
+// Slice p of element x as the stored element: exact digit (BF16) or the next
+// term of a float split (BF16 or TF32); `rest` carries the unsplit remainder.
+template <int E>
+__device__ __forceinline__ uint32_t slice_elem(uint64_t X, bool neg, int p, int S, bool float_split, double &rest)
+{
+    if (E == 4) {
+        const uint32_t t = to_tf32((float)rest);
+        rest -= (double)__uint_as_float(t);
+        return t;
+    }
+    if (float_split) {
+        const __nv_bfloat16 t = __double2bfloat16(rest);
+        rest -= (double)__bfloat162float(t);
+        return __bfloat16_as_ushort(t);
+    }
+    return slice_digit_bf16(X, neg, p, S);
+}
+
+// One block per leaf position (i, k) of the rows = R * ceil(nb / R) padded
+// leaf rows (R = 128 / B): slices of the leaf staged in shared memory in the
+// core-matrix layout, then copied to the per-leaf and/or tile-major arrays.
+template <int S, int E, int B>
 __global__ void __launch_bounds__(256)
 k_slice(const int32_t *__restrict__ stop, const double *__restrict__ leaf, const int32_t *__restrict__ slot,
         int64_t nb, int64_t rows,
         const unsigned long long *__restrict__ maxbits, int32_t *__restrict__ sigma_out,
-        uint16_t *__restrict__ tileA, uint16_t *__restrict__ perleaf, int perleaf_transposed,
+        uint8_t *__restrict__ tileA, uint8_t *__restrict__ perleaf, int perleaf_transposed,
         uint8_t *__restrict__ zlead, int32_t *__restrict__ overflow, int float_split)
 {
-    constexpr int B = 32;
-    __shared__ __align__(16) uint16_t sa[S * 1024];
+    using W = typename std::conditional<E == 4, uint32_t, uint16_t>::type;
+    constexpr int R = 128 / B;               // leaf rows per tile
+    constexpr int kU4 = B * B * E / 16;      // 16-byte chunks per slice
+    __shared__ __align__(16) W sa[S * B * B];
     __shared__ unsigned long long s_xmax;
     if (stop && *stop) return;  // the SP2 loop has already stopped
     const int sigma = sigma_of(*maxbits);
     if (blockIdx.x == 0 && threadIdx.x == 0 && sigma_out) *sigma_out = sigma;
-    // positions (i, k) over rows = 4 * ceil(nb / 4) padded leaf rows
     for (int64_t pos = blockIdx.x; pos < rows * nb; pos += gridDim.x) {
         const int64_t i = pos / nb, k = pos % nb;
         const int32_t sl = i < nb ? slot[i * nb + k] : -1;
@@ -93,23 +132,11 @@ k_slice(const int32_t *__restrict__ stop, const double *__restrict__ leaf, const
             xmax = X > xmax ? X : xmax;
             // outside |x| < 2^sigma (possible only with a caller-fixed scale)
             if (!float_split && (X > (1ull << (7 * S)) || !(fabs(x) <= 1e300))) atomicExch(overflow, 1);
-            double rest = x;  // float split: s_p = bf16(x - s_0 - ... - s_{p-1})
+            double rest = x;  // float split: s_p = round(x - s_0 - ... - s_{p-1})
+            // [p][g][cc][8 x ce]; transposed: element (r, l) stored as (l, r)
+            const int o = (perleaf_transposed && perleaf) ? slice_offset<B, E>(l, r) : slice_offset<B, E>(r, l);
 #pragma unroll
-            for (int p = 0; p < S; p++) {
-                uint16_t h;
-                if (float_split) {
-                    const __nv_bfloat16 t = __double2bfloat16(rest);
-                    h = __bfloat16_as_ushort(t);
-                    rest -= (double)__bfloat162float(t);
-                } else {
-                    h = slice_digit_bf16(X, neg, p, S);
-                }
-                // [p][g][cc][8 x 8]; transposed: element (r, l) stored as (l, r)
-                if (!perleaf_transposed || !perleaf)
-                    sa[p * 1024 + slice_offset(r, l)] = h;
-                else
-                    sa[p * 1024 + slice_offset(l, r)] = h;
-            }
+            for (int p = 0; p < S; p++) sa[p * B * B + o] = (W)slice_elem<E>(X, neg, p, S, float_split, rest);
         }
         for (int o = 16; o > 0; o >>= 1) {
             const unsigned long long v = __shfl_xor_sync(0xffffffffu, xmax, o);
@@ -127,14 +154,14 @@ k_slice(const int32_t *__restrict__ stop, const double *__restrict__ leaf, const
         }
         const uint4 *ss = reinterpret_cast<const uint4 *>(sa);
         if (perleaf && sl >= 0) {
-            uint4 *d = reinterpret_cast<uint4 *>(perleaf + (int64_t)sl * (S * 1024));
-            for (int q = threadIdx.x; q < S * 128; q += blockDim.x) d[q] = ss[q];
+            uint4 *d = reinterpret_cast<uint4 *>(perleaf + (int64_t)sl * (S * B * B * E));
+            for (int q = threadIdx.x; q < S * kU4; q += blockDim.x) d[q] = ss[q];
         }
         if (tileA && !perleaf_transposed) {
-            // tile-major: block (I, k) holds [p][L][2 KB] for its four rows
-            const int64_t I = i >> 2, L = i & 3;
-            uint4 *d = reinterpret_cast<uint4 *>(tileA + ((I * nb + k) * S * 4 + L) * 1024);
-            for (int q = threadIdx.x; q < S * 128; q += blockDim.x) d[(q >> 7) * 512 + (q & 127)] = ss[q];
+            // tile-major: block (I, k) holds [p][L][slice] for its R rows
+            const int64_t I = i / R, L = i % R;
+            uint4 *d = reinterpret_cast<uint4 *>(tileA + ((I * nb + k) * S * R + L) * (int64_t)(B * B * E));
+            for (int q = threadIdx.x; q < S * kU4; q += blockDim.x) d[(q / kU4) * (R * kU4) + (q % kU4)] = ss[q];
         }
         __syncthreads();
     }
@@ -142,23 +169,26 @@ k_slice(const int32_t *__restrict__ stop, const double *__restrict__ leaf, const
 
 }  // namespace
 
-// Storage for the slices of matrix m (kept across calls while s is unchanged).
-int slices_alloc(spamm_mat_t m, int s, bool tile_a, bool per_leaf, cudaStream_t st)
+// Storage for the slices of matrix m (kept across calls while s and e are
+// unchanged).
+int slices_alloc(spamm_mat_t m, int s, int e, bool tile_a, bool per_leaf, cudaStream_t st)
 {
-    if (m->b != 32) {
-        spamm_set_error("tensor-core path is built for leaf 32 (got %d)", m->b);
+    if (m->b != 16 && m->b != 32 && m->b != 64) {
+        spamm_set_error("tensor-core path: leaf must be 16, 32 or 64 (got %d)", m->b);
         return SPAMM_E_NOTSUP;
     }
     int rc;
-    const size_t per = (size_t)s * 1024;  // BF16 elements per leaf
-    const int64_t rows = ((m->nb + 3) / 4) * 4;
-    if (m->sl_s != s) {
+    const size_t per = (size_t)s * m->b * m->b * e;  // bytes per leaf
+    const int64_t R = 128 / m->b;
+    const int64_t rows = ((m->nb + R - 1) / R) * R;
+    if (m->sl_s != s || m->sl_e != e) {
         spamm_release(m->slA, st);
         spamm_release(m->slB, st);
         spamm_release(m->zlead, st);
         m->slA = m->slB = nullptr;
         m->zlead = nullptr;
         m->sl_s = s;
+        m->sl_e = e;
         m->slB_transposed = -1;
     }
     if (!m->zlead && (rc = spamm_alloc((void **)&m->zlead, m->nslots, st))) return rc;
@@ -167,31 +197,68 @@ int slices_alloc(spamm_mat_t m, int s, bool tile_a, bool per_leaf, cudaStream_t 
         SPAMM_CK(cudaMemsetAsync(m->scale, 0, 16, st));  // max bits, sigma, overflow flag
     }
     if (tile_a && !m->slA) {
-        if ((rc = spamm_alloc((void **)&m->slA, sizeof(uint16_t) * per * rows * m->nb, st))) return rc;
+        if ((rc = spamm_alloc((void **)&m->slA, per * rows * m->nb, st))) return rc;
     }
     if (per_leaf && !m->slB) {
-        if ((rc = spamm_alloc((void **)&m->slB, sizeof(uint16_t) * per * m->nslots, st))) return rc;
+        if ((rc = spamm_alloc((void **)&m->slB, per * m->nslots, st))) return rc;
     }
     return SPAMM_OK;
 }
+
+namespace {
+
+template <int S, int E, int B>
+void slice_launch(unsigned grid, cudaStream_t st, const int32_t *stop, spamm_mat_t m, int64_t rows,
+                  unsigned long long *mx, int32_t *sig, uint8_t *ta, uint8_t *pl, int tr, uint8_t *zl,
+                  int float_split)
+{
+    k_slice<S, E, B><<<grid, 256, 0, st>>>(stop, m->leaf, m->slot, m->nb, rows, mx, sig, ta, pl, tr, zl, sig + 1,
+                                           float_split);
+}
+
+template <int B>
+bool slice_dispatch_b(int s, int e, unsigned grid, cudaStream_t st, const int32_t *stop, spamm_mat_t m,
+                      int64_t rows, unsigned long long *mx, int32_t *sig, uint8_t *ta, uint8_t *pl, int tr,
+                      uint8_t *zl, int fs)
+{
+#define SPAMM_SLICE_CASE(SS, EE)                                              \
+    if (s == SS && e == EE && SS * B <= 256) {                                \
+        slice_launch<SS, EE, B>(grid, st, stop, m, rows, mx, sig, ta, pl, tr, zl, fs); \
+        return true;                                                          \
+    }
+    SPAMM_SLICE_CASE(1, 2)
+    SPAMM_SLICE_CASE(2, 2)
+    SPAMM_SLICE_CASE(3, 2)
+    SPAMM_SLICE_CASE(4, 2)
+    SPAMM_SLICE_CASE(5, 2)
+    SPAMM_SLICE_CASE(6, 2)
+    SPAMM_SLICE_CASE(7, 2)
+    SPAMM_SLICE_CASE(1, 4)
+    SPAMM_SLICE_CASE(2, 4)
+#undef SPAMM_SLICE_CASE
+    return false;
+}
+
+}  // namespace
 
 // Slices of matrix m: `tile_a` asks for the tile-major A-operand array,
 // `per_leaf` for the per-leaf array (transposed = B-operand layout).  A matrix
 // that serves as both operands of a non-symmetric product needs the A array
 // and the transposed per-leaf array; a symmetric product uses the untransposed
 // per-leaf array of the transpose leaf as its B operand.
-int launch_slices(spamm_mat_t m, int s, bool tile_a, bool per_leaf, bool transposed, cudaStream_t st,
+int launch_slices(spamm_mat_t m, int s, int e, bool tile_a, bool per_leaf, bool transposed, cudaStream_t st,
                   const int32_t *stop, bool unit_scale, bool float_split)
 {
-    if (m->b != 32) {
-        spamm_set_error("tensor-core path is built for leaf 32 (got %d)", m->b);
+    int rc = slices_alloc(m, s, e, tile_a, per_leaf, st);
+    if (rc) return rc;
+    if (e == 4 && !float_split) {
+        spamm_set_error("TF32 slices are float splits only");
         return SPAMM_E_NOTSUP;
     }
-    int rc = slices_alloc(m, s, tile_a, per_leaf, st);
-    if (rc) return rc;
-    const int64_t rows = ((m->nb + 3) / 4) * 4;
+    const int64_t R = 128 / m->b;
+    const int64_t rows = ((m->nb + R - 1) / R) * R;
     SPAMM_CK(cudaMemsetAsync(m->scale, 0, sizeof(unsigned long long), st));  // max bits
-    const int64_t count = m->nslots * 1024;
+    const int64_t count = m->nslots * m->b * m->b;
     const int blocks = spamm_num_sms() * 8;
     if (unit_scale)
         k_unit_scale<<<1, 1, 0, st>>>(stop, reinterpret_cast<unsigned long long *>(m->scale));
@@ -205,28 +272,21 @@ int launch_slices(spamm_mat_t m, int s, bool tile_a, bool per_leaf, bool transpo
     // the tile-major array and a transposed per-leaf array need two passes
     const int passes = (tile_a && per_leaf && transposed) ? 2 : 1;
     for (int pass = 0; pass < passes; pass++) {
-        uint16_t *ta = (tile_a && pass == 0) ? m->slA : nullptr;
-        uint16_t *pl = (per_leaf && (passes == 1 || pass == 1)) ? m->slB : nullptr;
+        uint8_t *ta = (tile_a && pass == 0) ? m->slA : nullptr;
+        uint8_t *pl = (per_leaf && (passes == 1 || pass == 1)) ? m->slB : nullptr;
         const int tr = pl && transposed ? 1 : 0;
         uint8_t *zl = pass == 0 ? m->zlead : nullptr;
-#define SPAMM_SLICE_CASE(SS)                                                                          \
-    case SS:                                                                                          \
-        k_slice<SS><<<grid, 256, 0, st>>>(stop, m->leaf, m->slot, m->nb, rows, mx, sig, ta, pl, tr, zl,    \
-                                          sig + 1, float_split ? 1 : 0);                               \
-        break;
-        switch (s) {
-            SPAMM_SLICE_CASE(1)
-            SPAMM_SLICE_CASE(2)
-            SPAMM_SLICE_CASE(3)
-            SPAMM_SLICE_CASE(4)
-            SPAMM_SLICE_CASE(5)
-            SPAMM_SLICE_CASE(6)
-            SPAMM_SLICE_CASE(7)
-        default:
-            spamm_set_error("slices must be in 3..7 (got %d)", s);
-            return SPAMM_E_INVAL;
+        const int fs = float_split ? 1 : 0;
+        bool ok = false;
+        switch (m->b) {
+        case 16: ok = slice_dispatch_b<16>(s, e, grid, st, stop, m, rows, mx, sig, ta, pl, tr, zl, fs); break;
+        case 32: ok = slice_dispatch_b<32>(s, e, grid, st, stop, m, rows, mx, sig, ta, pl, tr, zl, fs); break;
+        case 64: ok = slice_dispatch_b<64>(s, e, grid, st, stop, m, rows, mx, sig, ta, pl, tr, zl, fs); break;
         }
-#undef SPAMM_SLICE_CASE
+        if (!ok) {
+            spamm_set_error("slices: %d slices of %d-byte elements at leaf %d not built", s, e, m->b);
+            return SPAMM_E_NOTSUP;
+        }
         SPAMM_CK_LAUNCH();
     }
     if (per_leaf) m->slB_transposed = transposed ? 1 : 0;

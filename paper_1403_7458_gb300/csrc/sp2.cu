@@ -335,9 +335,7 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
         spamm_set_error("sp2_solve: opts.leaf (%d) differs from F's leaf size (%d)", o.leaf, F->b);
         return SPAMM_E_INVAL;
     }
-    if (o.prec != SPAMM_FP64 &&
-        !(prec_is_tc(o.prec) && F->b == 32 &&
-          (o.prec != SPAMM_OZAKI_BF16 || tc_slices_ok(o.slices ? o.slices : 7)))) {
+    if (o.prec != SPAMM_FP64 && !(tc_mode_ok(o.prec, o.slices, F->b) && F->b <= 32)) {
         spamm_set_error("sp2_solve: precision mode %d (leaf %d, slices %d) not built", o.prec, F->b,
                         o.slices);
         return SPAMM_E_NOTSUP;
@@ -491,6 +489,7 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
             memcpy(report->history, hrows.data(), sizeof(double) * rows * SP2_H_COLS);
         }
     }
+    SP2_TRY(ws_check_errors(&X2->ws, s));
     SP2_TRY(launch_pyramid(X, s));
     SP2_CUDA(cudaEventRecord(ev1, s));
     SP2_CUDA(cudaEventSynchronize(ev1));

@@ -1,0 +1,708 @@
+// tc_kernel.cuh -- grouped leaf products on the tcgen05 tensor cores (the
+// mixed-precision form of Algorithm 1's leaf branch), shared by the
+// translation units that instantiate it per leaf size.
+//
+// Tiles.  A tile is R = 128 / b consecutive output leaf rows i = R I ..
+// R I + R - 1 and one output leaf column j (M = 128 rows, N = b columns).
+// Its work list holds every k for which at least one of the R triples
+// (i, k, j) survives the culling test of Eq. 4, with an R-bit mask of the
+// survivors; leaves of culled triples are replaced by zeros, so each output
+// leaf receives exactly the products of its own task list (no extra
+// products, no missing ones).
+//
+// Slices.  With s slices per operand (see slice.cu), the MMAs for A slice p
+// multiply the 128 x b A slab by B slices q = zB..s-1-p (N = b (s - p - zB))
+// and accumulate into TMEM columns [b (p + zB), b s): column block d then
+// holds S_d = sum_{p+q=d} sum_k sum_l dA_p dB_q.  Pairs with p + q >= s are
+// never formed, nor pairs with p < zA or q < zB, where zA (the least over
+// the item's kept A leaves) and zB count leading slices that are zero in
+// every element: those products are exactly zero.  An item whose kept leaves
+// all have zA + zB >= s contributes exactly nothing and is not listed.  For
+// exact (Ozaki) slices the S_d are integers and the epilogue forms
+//     C = 2^(sigmaA + sigmaB - 7s - 7) * sum_d S_d 128^(s-1-d)
+// with integer arithmetic and one rounding to FP64; for float splits (BF16
+// or TF32 terms) it forms C = sum_d S_d in FP64.  It then zeroes the
+// accumulator for the next tile.
+//
+// Element types.  BF16 slices use tcgen05.mma kind::f16 (K = 16 per
+// instruction), TF32 slices kind::tf32 (K = 8); either way one instruction
+// covers 32 bytes of K, so a b-wide leaf takes b e / 32 instructions per
+// slice pair for e-byte elements.
+//
+// Batches.  The kernel parameters carry a table of up to kMaxBatch products
+// (pointers, leaf grid, tile order); tiles of all of them are handed out
+// from one device counter over the concatenated orders, so one persistent
+// launch serves many independent SpAMMs.
+//
+// Kernel roles (192 threads, one CTA per SM, persistent):
+//   warp 0     : producer; two bulk copies (cp.async.bulk) per work item:
+//                the needed slices of the R A leaves (one contiguous block of
+//                the tile-major array, stage layout [p][leaf][slice]) and of
+//                the B leaf, into a shared-memory byte ring, completion on
+//                the item's mbarrier;
+//   warp 1     : allocates 512 TMEM columns; once an item lands, the warp
+//                zeroes the leaves of culled triples in it, then lane 0
+//                issues the tcgen05.mma of the item and commits to the
+//                item's "empty" barrier and, at the end of a tile, to the
+//                accumulator's "full" barrier;
+//   warps 2-5  : epilogue; tcgen05.ld of the s diagonal blocks of the row the
+//                thread owns, combine, FP64 store, diagonal traces.
+// Two accumulators (TMEM columns 0 and 256) let the epilogue of one tile run
+// under the MMAs of the next.  Every wait is bounded (SM cycle counter); on
+// timeout the kernel records the error, drains and frees TMEM, and returns.
+//
+// Roofline: tensor pipe.  Useful work 2 b^3 per surviving triple; issued
+// tensor work 2 * 128 * b * b per slice pair of a work item.
+#pragma once
+
+#include <type_traits>
+
+#include "internal.cuh"
+
+namespace tc {
+
+// Shared-memory byte ring for work items: an item needing m slices per
+// operand takes exactly m (R + 1) b^2 e bytes, so small items (many leading
+// zero slices) leave room for more items in flight.
+constexpr uint32_t kRingBytes = 216 * 1024;
+constexpr int kSlots = 16;  // work items in flight at most
+constexpr int kThreads = 192;
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kAccStride = 256;
+constexpr long long kTimeoutCycles = 8000000000ll;  // about 4 s at 2 GHz per wait
+constexpr int kTileRing = 4;  // tiles handed from the producer to the other roles
+
+// Work item of tile (I, j) at k: k | mask << 15 | zA << 23 | zB << 26.
+__host__ __device__ constexpr uint32_t item_k(uint32_t w) { return w & 0x7FFF; }
+__host__ __device__ constexpr uint32_t item_mask(uint32_t w) { return (w >> 15) & 0xFF; }
+__host__ __device__ constexpr int item_za(uint32_t w) { return (int)((w >> 23) & 7); }
+__host__ __device__ constexpr int item_zb(uint32_t w) { return (int)((w >> 26) & 7); }
+__host__ __device__ constexpr uint32_t item_make(uint32_t k, uint32_t mask, int za, int zb)
+{
+    return k | (mask << 15) | ((uint32_t)za << 23) | ((uint32_t)zb << 26);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: false after about kTimeoutCycles SM cycles (or as soon as
+// another role has failed).  The SM cycle counter is read, not the global
+// timer, which is far slower to read and would sit on every handoff.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag)
+{
+    if (mbar_try(bar, parity)) return true;
+    const long long t0 = clock64();
+    for (uint32_t it = 1;; it++) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 255) == 0) {
+            if (*abort_flag) return false;
+            if (clock64() - t0 > kTimeoutCycles) return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+// tcgen05 shared-memory descriptor: no swizzle, K-major core matrices.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// instruction descriptor: FP32 accumulator (bit 4), A and B types (bits 7
+// and 10: BF16 = 1 under kind::f16, TF32 = 2 under kind::tf32), both
+// K-major, N / 8 at bit 17, M / 16 at bit 24.
+template <int E>
+__device__ __forceinline__ uint32_t mma_idesc(int M, int N)
+{
+    constexpr uint32_t ab = E == 4 ? 2u : 1u;
+    return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// D (TMEM) += A (smem) x B (smem); BF16 (E = 2, K = 16) or TF32 (E = 4,
+// K = 8): 32 bytes of K per instruction either way.
+template <int E>
+__device__ __forceinline__ void mma_issue(uint32_t dtmem, uint64_t da, uint64_t db, uint32_t idesc)
+{
+    if (E == 4)
+        asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;" ::"r"(dtmem), "l"(da), "l"(db),
+                     "r"(idesc)
+                     : "memory");
+    else
+        asm volatile("tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, 1;" ::"r"(dtmem), "l"(da), "l"(db),
+                     "r"(idesc)
+                     : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+// RN(v * 2^k) for a signed 64-bit integer v, by integer operations only.
+__device__ __forceinline__ double i64_scaled(long long v, int k)
+{
+    if (v == 0) return 0.0;
+    const uint64_t sign = v < 0 ? (1ull << 63) : 0ull;
+    uint64_t u = v < 0 ? (uint64_t)(-v) : (uint64_t)v;
+    const int msb = 63 - __clzll((long long)u);
+    uint64_t mant;
+    if (msb <= 52) {
+        mant = u << (52 - msb);
+    } else {
+        const int sh = msb - 52;
+        mant = u >> sh;
+        const uint64_t rem = u & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+        if (rem > half || (rem == half && (mant & 1))) mant++;
+        if (mant == (1ull << 53)) {
+            mant >>= 1;
+            k++;
+        }
+    }
+    const int be = msb + k + 1023;
+    if (be >= 1 && be <= 2046)
+        return __longlong_as_double((long long)(sign | ((uint64_t)be << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+    const double r = ldexp((double)(mant >> 0), msb - 52 + k);  // rare: subnormal / overflow
+    return sign ? -r : r;
+}
+
+// One product of a launch.
+struct TcProb {
+    const uint8_t *slA;    // A operand: tile-major [I][k][p][L][slice]
+    const uint8_t *slB;    // B operand: per slot [q][slice] (symmetric: A-role of the transpose)
+    const int32_t *slotA;  // nb*nb
+    const int32_t *slotB;
+    const int32_t *slotC;
+    double *leafC;
+    const int64_t *off;    // tile work-list offsets
+    const uint32_t *list;  // work items
+    const int32_t *order;  // tile order (tile ids of this product)
+    const int32_t *sigA;   // sigma of A
+    const int32_t *sigB;
+    double *tr_part;       // diagonal-leaf traces (may be null; b = 32 only)
+    int64_t nb;
+    int64_t pos0;          // first hand-out position of this product
+    int32_t sym;           // symmetric product: upper block triangle + mirror
+    int32_t pad_;
+};
+
+struct TcArgs {
+    TcProb p[kMaxBatch];
+    int64_t T;             // hand-out positions over all products
+    int32_t *err;          // error word (timeout)
+    int32_t *next_tile;    // dynamic scheduler: next position (zeroed per launch)
+    const int32_t *stop;   // set once an SP2 loop has stopped: nothing to do
+    int32_t nprob;
+    int32_t float_split;   // slices are a float split: C = sum_d S_d in FP64, no scaling
+};
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_zero16(uint32_t taddr)
+{
+    const uint32_t z = 0;
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr),
+        "r"(z)
+        : "memory");
+}
+
+// The product owning hand-out position pos (products sorted by pos0).
+__device__ __forceinline__ int find_prob(const TcArgs &g, int64_t pos)
+{
+    int lo = 0, hi = g.nprob - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (g.p[mid].pos0 <= pos) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int S, int E, int B>
+__global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__ TcArgs g)
+{
+    constexpr int R = 128 / B;                  // leaf rows per tile
+    constexpr uint32_t kSlice = B * B * E;      // one slice of one leaf (bytes)
+    constexpr uint32_t kSBO = 8 * B * E;        // 8-row core-matrix group stride
+    constexpr int kMmaK = B * E / 32;           // instructions per slice pair
+    constexpr uint32_t kFull = (1u << R) - 1;
+    static_assert(S * B <= (int)kAccStride, "accumulator exceeds its TMEM columns");
+    static_assert((uint32_t)S * (R + 1) * kSlice <= kRingBytes, "work item exceeds the ring");
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ __align__(8) uint64_t full_bar[kSlots], empty_bar[kSlots];
+    __shared__ __align__(8) uint64_t accf_bar[2], acce_bar[2], done_bar;
+    __shared__ uint32_t slot_off[kSlots];  // ring byte offset of each in-flight item
+    __shared__ uint32_t slot_w[kSlots];    // its work-list entry
+    __shared__ int32_t tile_q[kTileRing];  // tiles handed out (product << 24 | tile), -1 = no more
+    __shared__ __align__(8) uint64_t tfull_bar[kTileRing], tempty_bar[kTileRing];
+    __shared__ uint32_t tmem_holder;
+    __shared__ int abort_flag;
+
+    if (g.stop && *g.stop) return;  // before any barrier or TMEM is touched
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t T = g.T;
+
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < kSlots; q++) {
+            mbar_init(smem_u32(&full_bar[q]), 1);
+            mbar_init(smem_u32(&empty_bar[q]), 1);
+        }
+        for (int q = 0; q < 2; q++) {
+            mbar_init(smem_u32(&accf_bar[q]), 1);
+            mbar_init(smem_u32(&acce_bar[q]), 4);
+        }
+        mbar_init(smem_u32(&done_bar), 1);
+        for (int q = 0; q < kTileRing; q++) {
+            mbar_init(smem_u32(&tfull_bar[q]), 1);
+            mbar_init(smem_u32(&tempty_bar[q]), 5);  // MMA warp + four epilogue warps
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_holder)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_holder;
+    const uint32_t sbase = smem_u32(smem);
+    volatile int *abort_v = &abort_flag;
+
+    if (warp == 0) {
+        // ------------------------------ producer ------------------------------
+        // The warp loads 32 work entries (and their B slots) at a time; lane 0
+        // then allocates ring space and issues the copies item by item.
+        // cumulative byte pointers (allocation incl. wrap padding, release)
+        unsigned long long alloc_ptr = 0, free_ptr = 0;
+        unsigned long long end_ptr[kSlots];
+        uint32_t issued = 0, released = 0;
+        bool ok = true;
+        uint32_t tq = 0, tph = 0;
+        for (;;) {
+            // take the next tile and hand it to the MMA and epilogue warps
+            int32_t tt = -1;
+            int tgood = 1;
+            if (lane == 0) {
+                if (!mbar_wait(smem_u32(&tempty_bar[tq]), tph ^ 1, abort_v)) {
+                    tgood = 0;
+                } else {
+                    const int32_t pos = atomicAdd(g.next_tile, 1);
+                    if (pos < T) {
+                        const int mp = find_prob(g, pos);
+                        tt = (mp << 24) | g.p[mp].order[pos - g.p[mp].pos0];
+                    }
+                    tile_q[tq] = tt;
+                    mbar_arrive(smem_u32(&tfull_bar[tq]));
+                }
+            }
+            tt = __shfl_sync(0xffffffffu, tt, 0);
+            if (!__shfl_sync(0xffffffffu, tgood, 0)) {
+                ok = false;
+                break;
+            }
+            if (++tq == kTileRing) {
+                tq = 0;
+                tph ^= 1;
+            }
+            if (tt < 0) break;
+            const TcProb &P = g.p[tt >> 24];
+            const int64_t t = tt & 0xFFFFFF;
+            const int64_t nb = P.nb;
+            const int64_t I = t / nb, j = t % nb;
+            const int64_t e0 = P.off[t], e1 = P.off[t + 1];
+            for (int64_t base = e0; base < e1 && ok; base += 32) {
+                const int cnt = (int)(e1 - base < 32 ? e1 - base : 32);
+                uint32_t wl = 0;
+                int64_t bl = 0;
+                if (lane < cnt) {
+                    wl = P.list[base + lane];
+                    const int64_t kk = item_k(wl);
+                    bl = P.sym ? P.slotA[j * nb + kk] : P.slotB[kk * nb + j];
+                }
+                for (int q = 0; q < cnt; q++) {
+                    const uint32_t w = __shfl_sync(0xffffffffu, wl, q);
+                    const int64_t bslot = __shfl_sync(0xffffffffu, bl, q);
+                    int good = 1;
+                    if (lane == 0) {
+                        const int64_t k = item_k(w);
+                        const int za = item_za(w), zb = item_zb(w);
+                        const int m = S - za - zb;  // slices needed from each operand
+                        const uint32_t need = (uint32_t)m * (R + 1) * kSlice;
+                        uint32_t pos = (uint32_t)(alloc_ptr % kRingBytes);
+                        if (pos + need > kRingBytes) {
+                            alloc_ptr += kRingBytes - pos;
+                            pos = 0;
+                        }
+                        const unsigned long long new_end = alloc_ptr + need;
+                        // wait (in order) for released items until the region and a slot are free
+                        while (new_end - free_ptr > kRingBytes || issued - released >= (uint32_t)kSlots) {
+                            const uint32_t rs = released % kSlots;
+                            if (!mbar_wait(smem_u32(&empty_bar[rs]), (released / kSlots) & 1, abort_v)) {
+                                good = 0;
+                                break;
+                            }
+                            free_ptr = end_ptr[rs];
+                            released++;
+                        }
+                        if (good) {
+                            const uint32_t sl = issued % kSlots;
+                            slot_off[sl] = pos;
+                            slot_w[sl] = w;
+                            end_ptr[sl] = new_end;
+                            alloc_ptr = new_end;
+                            const uint32_t fb = smem_u32(&full_bar[sl]);
+                            const uint32_t dst = sbase + pos;
+                            mbar_expect_tx(fb, need);
+                            // A: slices za..za+m-1 of the R rows' leaves, one contiguous block
+                            bulk_g2s(dst, P.slA + ((I * nb + k) * S + za) * (int64_t)(R * kSlice),
+                                     (uint32_t)m * R * kSlice, fb);
+                            // B: slices zb..zb+m-1 of leaf (k, j) (symmetric: leaf (j, k))
+                            bulk_g2s(dst + (uint32_t)m * R * kSlice,
+                                     P.slB + bslot * (int64_t)(S * kSlice) + zb * kSlice, (uint32_t)m * kSlice, fb);
+                            issued++;
+                        }
+                    }
+                    if (!__shfl_sync(0xffffffffu, good, 0)) {
+                        ok = false;
+                        break;
+                    }
+                }
+            }
+        }
+        if (lane == 0) {
+            if (!ok) {
+                atomicExch(g.err, 1);
+                abort_flag = 1;
+            }
+            // drain: every issued item is consumed (and so landed) before exit
+            while (released < issued) {
+                if (!mbar_wait(smem_u32(&empty_bar[released % kSlots]), (released / kSlots) & 1, abort_v)) break;
+                released++;
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ------------------------------ MMA issuer ------------------------------
+        // Lane 0 issues; the whole warp zeroes the leaves of culled triples in
+        // a landed item before the MMAs read it.
+        uint32_t consumed = 0, acc = 0, aph = 0;
+        bool ok = true;
+        uint32_t tq = 0, tph = 0;
+        for (;;) {
+            int32_t tt = -1;
+            int tgood = 1;
+            if (lane == 0) {
+                tgood = mbar_wait(smem_u32(&tfull_bar[tq]), tph, abort_v);
+                if (tgood) {
+                    tt = tile_q[tq];
+                    mbar_arrive(smem_u32(&tempty_bar[tq]));
+                }
+            }
+            tt = __shfl_sync(0xffffffffu, tt, 0);
+            if (!__shfl_sync(0xffffffffu, tgood, 0)) {
+                ok = false;
+                break;
+            }
+            if (++tq == kTileRing) {
+                tq = 0;
+                tph ^= 1;
+            }
+            if (tt < 0) break;
+            const TcProb &P = g.p[tt >> 24];
+            const int64_t t = tt & 0xFFFFFF;
+            // the accumulator was zeroed by the epilogue (phase u of its barrier)
+            int good = 1;
+            if (lane == 0) good = mbar_wait(smem_u32(&acce_bar[acc]), aph, abort_v);
+            if (!__shfl_sync(0xffffffffu, good, 0)) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t dacc = tmem + acc * kAccStride;
+            const int64_t e1 = P.off[t + 1];
+            for (int64_t e = P.off[t]; e < e1; e++) {
+                const uint32_t sl = consumed % kSlots;
+                good = 1;
+                if (lane == 0) good = mbar_wait(smem_u32(&full_bar[sl]), (consumed / kSlots) & 1, abort_v);
+                if (!__shfl_sync(0xffffffffu, good, 0)) {
+                    ok = false;
+                    break;
+                }
+                // lane 0 observed the landed data (and the slot's metadata);
+                // hand both to the other lanes
+                __syncwarp();
+                const uint32_t w = __shfl_sync(0xffffffffu, lane == 0 ? slot_w[sl] : 0u, 0);
+                const uint32_t pos = __shfl_sync(0xffffffffu, lane == 0 ? slot_off[sl] : 0u, 0);
+                const uint32_t mask = item_mask(w);
+                const int za = item_za(w), zb = item_zb(w);
+                const int m = S - za - zb;
+                if (mask != kFull) {
+                    const uint4 zero4 = make_uint4(0, 0, 0, 0);
+                    for (int L = 0; L < R; L++) {
+                        if (mask & (1u << L)) continue;
+                        for (int pp = 0; pp < m; pp++) {
+                            uint4 *z = reinterpret_cast<uint4 *>(smem + pos + (pp * R + L) * kSlice);
+#pragma unroll
+                            for (int q = 0; q < (int)(kSlice / 512); q++) z[q * 32 + lane] = zero4;
+                        }
+                    }
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t sa = sbase + pos;                        // A slice za
+                    const uint32_t sb = sa + (uint32_t)m * R * kSlice;      // B slice zb
+                    // descriptors advance by adding (bytes >> 4) to the address field
+                    // (shared addresses stay below 256 KB, so the field never carries)
+                    const uint64_t da0 = smem_desc(sa, 128, kSBO);
+                    const uint64_t db0 = smem_desc(sb, 128, kSBO);
+                    uint32_t idesc = mma_idesc<E>(128, B * m);
+                    uint32_t dcol = dacc + B * (za + zb);
+                    for (int pp = 0; pp < m; pp++) {
+                        const uint64_t da = da0 + (uint64_t)(pp * (R * kSlice / 16));
+#pragma unroll
+                        for (int h = 0; h < kMmaK; h++)  // 32 bytes of K each: +256 B (two core matrices)
+                            mma_issue<E>(dcol, da + 16 * h, db0 + 16 * h, idesc);
+                        idesc -= (uint32_t)(B >> 3) << 17;  // N shrinks by b
+                        dcol += B;
+                    }
+                    mma_commit(smem_u32(&empty_bar[sl]));
+                }
+                __syncwarp();
+                consumed++;
+            }
+            if (lane == 0) mma_commit(smem_u32(&accf_bar[acc]));
+            if (++acc == 2) {
+                acc = 0;
+                aph ^= 1;
+            }
+        }
+        if (lane == 0) {
+            if (!ok) {
+                atomicExch(g.err, 1);
+                abort_flag = 1;
+            }
+            // all MMAs issued by this thread complete before TMEM is freed
+            mma_commit(smem_u32(&done_bar));
+            mbar_wait(smem_u32(&done_bar), 0, abort_v);
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------ epilogue ------------------------------
+        const int quad = warp & 3;             // TMEM lane quadrant of this warp
+        const int row = quad * 32 + lane;      // tile row 0..127
+        const int L = row / B, r = row % B;    // leaf within tile, row within leaf
+        const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
+        // both accumulators start at zero (first phase of their "empty" barriers)
+        for (int b = 0; b < 2; b++) {
+            for (int d = 0; d < S; d++)
+                for (int h = 0; h < B / 16; h++) tmem_zero16(tmem + b * kAccStride + lane_off + B * d + 16 * h);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+            mbar_arrive(smem_u32(&acce_bar[0]));
+            mbar_arrive(smem_u32(&acce_bar[1]));
+        }
+        uint32_t acc = 0, aph = 0;
+        uint32_t tq = 0, tph = 0;
+        for (;;) {
+            int32_t tt = -1;
+            int tgood = 1;
+            if (lane == 0) {
+                tgood = mbar_wait(smem_u32(&tfull_bar[tq]), tph, abort_v);
+                if (tgood) {
+                    tt = tile_q[tq];
+                    mbar_arrive(smem_u32(&tempty_bar[tq]));
+                }
+            }
+            tt = __shfl_sync(0xffffffffu, tt, 0);
+            if (!__shfl_sync(0xffffffffu, tgood, 0)) {
+                if (lane == 0) atomicExch(g.err, 1);
+                abort_flag = 1;
+                break;
+            }
+            if (++tq == kTileRing) {
+                tq = 0;
+                tph ^= 1;
+            }
+            if (tt < 0) break;
+            const TcProb &P = g.p[tt >> 24];
+            const int64_t t = tt & 0xFFFFFF;
+            const int64_t nb = P.nb;
+            const int64_t I = t / nb, j = t % nb;
+            const bool has_work = P.off[t + 1] > P.off[t];
+            if (!mbar_wait(smem_u32(&accf_bar[acc]), aph, abort_v)) {
+                if (lane == 0) atomicExch(g.err, 1);
+                abort_flag = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int64_t i = (int64_t)R * I + L;
+            // symmetric mode: leaf (i, j) is written only for i <= j, and for
+            // i < j its transpose goes to leaf (j, i)
+            const bool store = i < nb && (!P.sym || i <= j);
+            const int kexp = g.float_split ? 0 : *P.sigA + *P.sigB - 7 * S - 7;
+            double *dst = store ? P.leafC + (int64_t)P.slotC[i * nb + j] * (B * B) + r * B : nullptr;
+            double *mir = (store && P.sym && i < j) ? P.leafC + (int64_t)P.slotC[j * nb + i] * (B * B) + r : nullptr;
+            double diag = 0.0;
+            const uint32_t tbase = tmem + acc * kAccStride + lane_off;
+#pragma unroll
+            for (int h = 0; h < B / 16; h++) {
+                long long cint[16];   // exact slices: integer combination
+                double cflt[16];      // float split: FP64 sum of the FP32 diagonals
+#pragma unroll
+                for (int c = 0; c < 16; c++) {
+                    cint[c] = 0;
+                    cflt[c] = 0.0;
+                }
+                if (has_work) {
+#pragma unroll
+                    for (int d = 0; d < S; d++) {
+                        uint32_t v[16];
+                        tmem_ld16(tbase + B * d + 16 * h, v);
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                        if (g.float_split) {
+#pragma unroll
+                            for (int c = 0; c < 16; c++) cflt[c] += (double)__uint_as_float(v[c]);
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < 16; c++)
+                                cint[c] += (long long)__float2ll_rn(__uint_as_float(v[c])) * (1ll << (7 * (S - 1 - d)));
+                        }
+                        tmem_zero16(tbase + B * d + 16 * h);
+                    }
+                }
+                if (store) {
+#pragma unroll
+                    for (int c = 0; c < 16; c += 2) {
+                        const int col = 16 * h + c;
+                        double2 v;
+                        v.x = g.float_split ? cflt[c] : i64_scaled(cint[c], kexp);
+                        v.y = g.float_split ? cflt[c + 1] : i64_scaled(cint[c + 1], kexp);
+                        if (col == (r & ~1)) diag = (r & 1) ? v.y : v.x;
+                        reinterpret_cast<double2 *>(dst)[col >> 1] = v;
+                        if (mir) {
+                            mir[col * B] = v.x;
+                            mir[(col + 1) * B] = v.y;
+                        }
+                    }
+                }
+            }
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&acce_bar[acc]));
+            if (++acc == 2) {
+                acc = 0;
+                aph ^= 1;
+            }
+            if (B <= 32 && P.tr_part) {
+                // fixed butterfly over the B rows of a diagonal leaf (a warp
+                // holds 32 / B whole leaves; the condition is warp-uniform)
+                for (int o = B / 2; o > 0; o >>= 1) diag += __shfl_xor_sync(0xffffffffu, diag, o);
+                if (r == 0 && store && i == j) P.tr_part[i] = diag;
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
+                     : "memory");
+}
+
+template <int S, int E, int B>
+int launch_k(const TcArgs &a, cudaStream_t s)
+{
+    const size_t smem = kRingBytes;
+    static int configured = 0;
+    if (!configured) {
+        SPAMM_CK(cudaFuncSetAttribute(k_gemm_tc<S, E, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        configured = 1;
+    }
+    int64_t grid = spamm_num_sms();
+    if (grid > a.T) grid = a.T;
+    if (grid < 1) grid = 1;
+    k_gemm_tc<S, E, B><<<(unsigned)grid, kThreads, smem, s>>>(a);
+    SPAMM_CK_LAUNCH();
+    return SPAMM_OK;
+}
+
+// Launch for leaf B with S slices of E-byte elements; E_NOTSUP if that
+// combination is not instantiated.
+template <int B>
+int launch_leaf(const TcArgs &a, int S, int E, cudaStream_t s)
+{
+#define SPAMM_TC_CASE(SS, EE)                                            \
+    if constexpr (SS * B <= (int)kAccStride)                             \
+        if (S == SS && E == EE) return launch_k<SS, EE, B>(a, s);
+    SPAMM_TC_CASE(1, 2)
+    SPAMM_TC_CASE(2, 2)
+    SPAMM_TC_CASE(3, 2)
+    SPAMM_TC_CASE(4, 2)
+    SPAMM_TC_CASE(5, 2)
+    SPAMM_TC_CASE(6, 2)
+    SPAMM_TC_CASE(7, 2)
+    SPAMM_TC_CASE(1, 4)
+    SPAMM_TC_CASE(2, 4)
+#undef SPAMM_TC_CASE
+    spamm_set_error("tensor-core kernel: %d slices of %d-byte elements at leaf %d not built", S, E, B);
+    return SPAMM_E_NOTSUP;
+}
+
+}  // namespace tc
+
+// Per-leaf launchers (gemm_tc_b16.cu, gemm_tc.cu, gemm_tc_b64.cu).
+int tc_launch_b16(const tc::TcArgs &a, int S, int E, cudaStream_t s);
+int tc_launch_b32(const tc::TcArgs &a, int S, int E, cudaStream_t s);
+int tc_launch_b64(const tc::TcArgs &a, int S, int E, cudaStream_t s);

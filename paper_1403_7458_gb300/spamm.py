@@ -24,7 +24,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libspamm.so")
 
 OK, E_INVAL, E_NOMEM, E_CUDA, E_CAPACITY, E_TIMEOUT, E_NOCONV, E_NOTSUP = 0, -1, -2, -3, -4, -5, -6, -7
-FP64, OZAKI_BF16, BF16, BF16X3 = 0, 1, 2, 3
+FP64, OZAKI_BF16, BF16, BF16X3, TF32, TF32X3 = 0, 1, 2, 3, 4, 5
 F_TIMING = 1
 F_NOSYM = 2
 RULE_TRACE_DISTANCE, RULE_TRACE_ABOVE = 0, 1
@@ -86,6 +86,7 @@ def load():
     H = ctypes.POINTER(ctypes.c_void_p)
     lib.spamm_tree_build.argtypes = [P, i64, i64, ctypes.POINTER(_Opts), P, H]
     lib.spamm_multiply.argtypes = [P, P, dbl, H, ctypes.POINTER(_Opts), ctypes.POINTER(_Stats), P]
+    lib.spamm_multiply_batched.argtypes = [i32, P, P, P, P, ctypes.POINTER(_Opts), ctypes.POINTER(_Stats), P]
     lib.spamm_to_dense.argtypes = [P, P, i64, P]
     lib.spamm_norms.argtypes = [P, i32, P, P]
     lib.spamm_info.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i64),
@@ -100,7 +101,7 @@ def load():
     lib.spamm_last_error.restype = ctypes.c_char_p
     lib.sp2_solve.argtypes = [P, dbl, dbl, ctypes.POINTER(_Sp2Opts), H,
                               ctypes.POINTER(_Sp2Report), P]
-    for name in ("spamm_tree_build", "spamm_multiply", "spamm_to_dense", "spamm_norms",
+    for name in ("spamm_tree_build", "spamm_multiply", "spamm_multiply_batched", "spamm_to_dense", "spamm_norms",
                  "spamm_info", "spamm_task_list", "sp2_solve", "spamm_cull_noalloc"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -188,6 +189,38 @@ def multiply(A: Matrix, B: Matrix, tau: float, C: Matrix | None = None, prec: in
                                  ctypes.byref(opts), ctypes.byref(st) if want else None,
                                  _stream(stream)), "spamm_multiply")
     out = C if C is not None else Matrix(h.value)
+    info = None
+    if want:
+        info = {k: getattr(st, k) for k, _ in _Stats._fields_ if k != "reserved"}
+    return out, info
+
+
+def multiply_batched(A, B, tau, C=None, prec: int = FP64, slices: int = 0, timing: bool = False,
+                     stats: bool = False, stream=None):
+    """C[m] = SpAMM(A[m], B[m], tau[m]) for every m, leaf products of the whole
+    batch in one launch.  `tau` is a float or a sequence; `C` None or a list
+    whose None entries are created.  Returns (list of C, stats dict or None:
+    totals over the batch)."""
+    count = len(A)
+    if len(B) != count:
+        raise ValueError("A and B differ in length")
+    taus = [float(tau)] * count if np.isscalar(tau) else [float(t) for t in tau]
+    if len(taus) != count:
+        raise ValueError("tau has the wrong length")
+    Cs = list(C) if C is not None else [None] * count
+    if len(Cs) != count:
+        raise ValueError("C has the wrong length")
+    ha = (ctypes.c_void_p * max(count, 1))(*[a.handle.value for a in A])
+    hb = (ctypes.c_void_p * max(count, 1))(*[b.handle.value for b in B])
+    hc = (ctypes.c_void_p * max(count, 1))(*[c.handle.value if c is not None else None for c in Cs])
+    ht = (ctypes.c_double * max(count, 1))(*taus)
+    opts = _Opts(A[0].leaf if count else 32, prec, slices, F_TIMING if timing else 0)
+    st = _Stats()
+    want = stats or timing
+    _check(load().spamm_multiply_batched(count, ha, hb, ht, hc, ctypes.byref(opts),
+                                         ctypes.byref(st) if want else None, _stream(stream)),
+           "spamm_multiply_batched")
+    out = [Cs[m] if Cs[m] is not None else Matrix(hc[m]) for m in range(count)]
     info = None
     if want:
         info = {k: getattr(st, k) for k, _ in _Stats._fields_ if k != "reserved"}

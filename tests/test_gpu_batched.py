@@ -1,0 +1,144 @@
+"""Batched SpAMM (one leaf-product launch over many products) vs single calls
+and the oracle.
+
+Each product of a batch runs the same per-tile (tensor path) or per-output-
+leaf (FP64 path) arithmetic as a single spamm_multiply call, in the same
+order, so batched results must be bit-identical to single calls; task
+totals must equal the oracle's task counts (Eq. 4), summed.  A repeat of a
+batch allocates nothing and never waits for the stream, so it can be
+captured into a CUDA graph; the replayed graph must recompute the products.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1403_7458_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _batch(sizes, leaf, seed0=0):
+    mats = []
+    for q, n in enumerate(sizes):
+        a = synth.decaying_matrix(n, seed0 + q, decay=1.0 + (q % 5) * 0.25)
+        b = synth.decaying_matrix(n, seed0 + 100 + q, decay=1.5)
+        mats.append((a, b))
+    return mats
+
+
+@pytest.mark.parametrize("prec_name,leaf,slices", [("FP64", 32, 0), ("OZAKI_BF16", 32, 7), ("TF32", 64, 0),
+                                                   ("BF16X3", 16, 0), ("TF32X3", 32, 0), ("FP64", 16, 0)])
+def test_batched_bit_identical_to_single_calls(cuda_lib, prec_name, leaf, slices):
+    prec = getattr(cuda_lib, prec_name)
+    sizes = [96, 300, 64, 517, 128, 33, 250]  # uneven, ragged, smaller than one tile
+    taus = [1e-6, 1e-4, 0.0, 1e-6, 1e-8, 1e-6, 1e-3]
+    mats = _batch(sizes, leaf)
+    A = [cuda_lib.tree_build(_dev(a), leaf=leaf) for a, _ in mats]
+    B = [cuda_lib.tree_build(_dev(b), leaf=leaf) for _, b in mats]
+    C, st = cuda_lib.multiply_batched(A, B, taus, prec=prec, slices=slices, stats=True)
+    tasks = 0
+    for q, (a, b) in enumerate(mats):
+        Cs, sq = cuda_lib.multiply(A[q], B[q], taus[q], prec=prec, slices=slices, stats=True)
+        got = cuda_lib.to_dense(C[q]).cpu().numpy()
+        want = cuda_lib.to_dense(Cs).cpu().numpy()
+        assert np.array_equal(got, want), (q, np.abs(got - want).max())
+        # output norm quadtree identical too
+        assert np.array_equal(cuda_lib.norms(C[q], C[q].depth), cuda_lib.norms(Cs, Cs.depth))
+        tasks += sq["tasks"]
+    assert st["tasks"] == tasks
+    # the task totals are the oracle's (Eq. 4 on the same norms)
+    want_tasks = sum(len(oracle.spamm(a, b, leaf, t, want_tasks=True)[1]) for (a, b), t in zip(mats, taus))
+    assert st["tasks"] == want_tasks
+
+
+def test_batched_values_match_oracle_fp64(cuda_lib):
+    sizes = [200, 64, 150]
+    mats = _batch(sizes, 32, seed0=7)
+    A = [cuda_lib.tree_build(_dev(a), leaf=32) for a, _ in mats]
+    B = [cuda_lib.tree_build(_dev(b), leaf=32) for _, b in mats]
+    C, _ = cuda_lib.multiply_batched(A, B, 1e-6)
+    for q, (a, b) in enumerate(mats):
+        ref = oracle.spamm(a, b, 32, 1e-6)
+        got = cuda_lib.to_dense(C[q]).cpu().numpy()
+        n = a.shape[0]
+        # same task set; each element within gamma_K of the oracle's (K = n)
+        g = n * 2.0 ** -53 / (1 - n * 2.0 ** -53)
+        bound = 2 * g * (np.abs(a) @ np.abs(b)) + 1e-300
+        assert np.all(np.abs(got - ref) <= bound)
+
+
+def test_batched_more_than_one_launch_group(cuda_lib):
+    """70 products: two launches of at most 64."""
+    sizes = [32 + 16 * (q % 7) for q in range(70)]
+    mats = _batch(sizes, 16, seed0=3)
+    A = [cuda_lib.tree_build(_dev(a), leaf=16) for a, _ in mats]
+    B = [cuda_lib.tree_build(_dev(b), leaf=16) for _, b in mats]
+    C, st = cuda_lib.multiply_batched(A, B, 1e-6, prec=cuda_lib.TF32, stats=True)
+    tasks = 0
+    for q in range(70):
+        Cs, sq = cuda_lib.multiply(A[q], B[q], 1e-6, prec=cuda_lib.TF32, stats=True)
+        assert np.array_equal(cuda_lib.to_dense(C[q]).cpu().numpy(), cuda_lib.to_dense(Cs).cpu().numpy())
+        tasks += sq["tasks"]
+    assert st["tasks"] == tasks
+
+
+def test_batched_reuses_outputs_and_captures_into_a_graph(cuda_lib):
+    import torch
+    sizes = [256, 96, 160]
+    mats = _batch(sizes, 32, seed0=11)
+    A = [cuda_lib.tree_build(_dev(a), leaf=32) for a, _ in mats]
+    B = [cuda_lib.tree_build(_dev(b), leaf=32) for _, b in mats]
+    prec = cuda_lib.OZAKI_BF16
+    C, _ = cuda_lib.multiply_batched(A, B, 1e-6, prec=prec)
+    torch.cuda.synchronize()
+    want = [cuda_lib.to_dense(c).cpu().numpy() for c in C]
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        cuda_lib.multiply_batched(A, B, 1e-6, C=C, prec=prec, stream=s.cuda_stream)  # warm repeat
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        cuda_lib.multiply_batched(A, B, 1e-6, C=C, prec=prec,
+                                  stream=torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    # overwrite C with a different product (tau huge: every triple culled, C = 0)
+    cuda_lib.multiply_batched(A, B, 1e300, C=C, prec=prec)
+    torch.cuda.synchronize()
+    assert all(not np.any(cuda_lib.to_dense(c).cpu().numpy()) for c in C)
+    g.replay()
+    torch.cuda.synchronize()
+    for c, w in zip(C, want):
+        assert np.array_equal(cuda_lib.to_dense(c).cpu().numpy(), w)
+
+
+def test_batched_bad_arguments(cuda_lib):
+    a = synth.decaying_matrix(64, 0)
+    A32 = cuda_lib.tree_build(_dev(a), leaf=32)
+    A16 = cuda_lib.tree_build(_dev(a), leaf=16)
+    b = synth.decaying_matrix(96, 1)
+    B32 = cuda_lib.tree_build(_dev(b), leaf=32)
+    with pytest.raises(cuda_lib.SpammError) as ei:  # mixed leaf sizes
+        cuda_lib.multiply_batched([A32, A16], [A32, A16], 1e-6)
+    assert ei.value.status == cuda_lib.E_INVAL
+    with pytest.raises(cuda_lib.SpammError) as ei:  # shape mismatch within a product
+        cuda_lib.multiply_batched([A32], [B32], 1e-6)
+    assert ei.value.status == cuda_lib.E_INVAL
+    with pytest.raises(cuda_lib.SpammError) as ei:  # negative tau
+        cuda_lib.multiply_batched([A32], [A32], -1.0)
+    assert ei.value.status == cuda_lib.E_INVAL
+    C, _ = cuda_lib.multiply_batched([A32], [A32], 1e-6)
+    with pytest.raises(cuda_lib.SpammError) as ei:  # one output handle for two products
+        cuda_lib.multiply_batched([A32, A32], [A32, A32], 1e-6, C=[C[0], C[0]])
+    assert ei.value.status == cuda_lib.E_INVAL
+    with pytest.raises(cuda_lib.SpammError) as ei:  # output aliases an input
+        cuda_lib.multiply_batched([A32], [A32], 1e-6, C=[A32])
+    assert ei.value.status == cuda_lib.E_INVAL
+    out, st = cuda_lib.multiply_batched([], [], 1e-6, stats=True)
+    assert out == [] and st["tasks"] == 0

@@ -76,16 +76,18 @@ def _model(a, b, leaf, tau, s):
     return c[:n, :n], tasks, sa, sb
 
 
-@pytest.mark.parametrize("n,tau,s,seed", [(256, 1e-6, 5, 0), (200, 1e-4, 4, 1), (320, 1e-8, 6, 2),
-                                          (130, 0.0, 3, 3), (256, 1e-6, 7, 4)])
-def test_mixed_spamm_bit_exact_vs_integer_model(cuda_lib, n, tau, s, seed):
+@pytest.mark.parametrize("n,tau,s,seed,leaf", [(256, 1e-6, 5, 0, 32), (200, 1e-4, 4, 1, 32), (320, 1e-8, 6, 2, 32),
+                                               (130, 0.0, 3, 3, 32), (256, 1e-6, 7, 4, 32),
+                                               (200, 1e-6, 7, 5, 16), (136, 1e-4, 3, 6, 16),
+                                               (300, 1e-6, 4, 7, 64), (192, 0.0, 3, 8, 64)])
+def test_mixed_spamm_bit_exact_vs_integer_model(cuda_lib, n, tau, s, seed, leaf):
     a = synth.decaying_matrix(n, seed)
     b = synth.decaying_matrix(n, seed + 50, decay=1.3)
-    A = cuda_lib.tree_build(_dev(a), leaf=32)
-    B = cuda_lib.tree_build(_dev(b), leaf=32)
+    A = cuda_lib.tree_build(_dev(a), leaf=leaf)
+    B = cuda_lib.tree_build(_dev(b), leaf=leaf)
     C, st = cuda_lib.multiply(A, B, tau, prec=cuda_lib.OZAKI_BF16, slices=s, stats=True)
     got = cuda_lib.to_dense(C).cpu().numpy()
-    want, tasks, _, _ = _model(a, b, 32, tau, s)
+    want, tasks, _, _ = _model(a, b, leaf, tau, s)
     assert st["tasks"] == len(tasks)
     assert np.array_equal(got, want), np.abs(got - want).max()
 
@@ -121,14 +123,25 @@ def test_mixed_spamm_within_slicing_bound_of_fp64(cuda_lib, n, tau, s):
 
 
 def test_mixed_rejects_unsupported(cuda_lib):
-    a = synth.decaying_matrix(64, 0)
-    A16 = cuda_lib.tree_build(_dev(a), leaf=16)
+    a = synth.decaying_matrix(128, 0)
+    A64 = cuda_lib.tree_build(_dev(a), leaf=64)
+    # 7 slices x leaf 64 = 448 accumulator columns > 256
     with pytest.raises(cuda_lib.SpammError) as ei:
-        cuda_lib.multiply(A16, A16, 1e-6, prec=cuda_lib.OZAKI_BF16)
+        cuda_lib.multiply(A64, A64, 1e-6, prec=cuda_lib.OZAKI_BF16)
     assert ei.value.status == cuda_lib.E_NOTSUP
     A = cuda_lib.tree_build(_dev(a), leaf=32)
-    with pytest.raises(cuda_lib.SpammError):
-        cuda_lib.multiply(A, A, 1e-6, prec=cuda_lib.OZAKI_BF16, slices=9)
+    for bad in (9, 2):
+        with pytest.raises(cuda_lib.SpammError) as ei:
+            cuda_lib.multiply(A, A, 1e-6, prec=cuda_lib.OZAKI_BF16, slices=bad)
+        assert ei.value.status == cuda_lib.E_NOTSUP
+    with pytest.raises(cuda_lib.SpammError) as ei:
+        cuda_lib.multiply(A, A, 1e-6, prec=17)
+    assert ei.value.status == cuda_lib.E_NOTSUP
+    # SP2 on the tensor path needs the diagonal traces: leaf 16 or 32
+    F64 = cuda_lib.tree_build(_dev(synth.tb_hamiltonian(128, 0)), leaf=64)
+    with pytest.raises(cuda_lib.SpammError) as ei:
+        cuda_lib.sp2_solve(F64, 64, 1e-8, prec=cuda_lib.TF32)
+    assert ei.value.status == cuda_lib.E_NOTSUP
 
 
 @pytest.mark.parametrize("n,s", [(1024, 6), (1024, 7), (4096, 7)])
@@ -194,34 +207,43 @@ def _kept_abs_product(a, b, leaf, tasks):
     return acc[:n, :n], K[:n, :n]
 
 
-@pytest.mark.parametrize("prec_name,n,tau", [("BF16", 384, 1e-6), ("BF16X3", 384, 1e-6),
-                                             ("BF16X3", 256, 0.0)])
-def test_float_split_modes_within_rounding_bounds(cuda_lib, prec_name, n, tau):
-    """BF16 (p = 8, u_b = 2^-8) operands, exact products, FP32 accumulation of
+@pytest.mark.parametrize("prec_name,n,tau,leaf", [("BF16", 384, 1e-6, 32), ("BF16X3", 384, 1e-6, 32),
+                                                  ("BF16X3", 256, 0.0, 32), ("TF32", 384, 1e-6, 32),
+                                                  ("TF32X3", 384, 1e-6, 32), ("TF32", 200, 1e-6, 16),
+                                                  ("TF32X3", 320, 1e-6, 64), ("BF16X3", 300, 1e-6, 64),
+                                                  ("BF16", 200, 1e-4, 16), ("TF32X3", 136, 0.0, 16)])
+def test_float_split_modes_within_rounding_bounds(cuda_lib, prec_name, n, tau, leaf):
+    """Operands rounded to nearest in BF16 (u = 2^-8) or TF32 (u = 2^-11, plus
+    2^-24 for the FP32 step on the way), exact products, FP32 accumulation of
     K terms (u_f = 2^-24; the bound takes 2K u_f for the accumulator):
-      one term : |dC| <= (2 u_b + u_b^2 + 2 K u_f (1 + u_b)^2) sum |a||b|
-      3 terms  : |dC| <= (5 u_b^2 + 3 K u_f) sum |a||b|   (dropped lo*lo and
-                 residuals below u_b^2 |x|)."""
+      one term : |dC| <= (2 u + u^2 + 2 K u_f (1 + u)^2) sum |a||b|
+      3 terms  : |dC| <= (5 u^2 + 3 K u_f) sum |a||b|   (dropped lo*lo and
+                 residuals below u^2 |x|)."""
     prec = getattr(cuda_lib, prec_name)
     a = synth.decaying_matrix(n, 13)
     b = synth.decaying_matrix(n, 14, decay=1.3)
-    A = cuda_lib.tree_build(_dev(a), leaf=32)
-    B = cuda_lib.tree_build(_dev(b), leaf=32)
+    A = cuda_lib.tree_build(_dev(a), leaf=leaf)
+    B = cuda_lib.tree_build(_dev(b), leaf=leaf)
     C, st = cuda_lib.multiply(A, B, tau, prec=prec, stats=True)
     got = cuda_lib.to_dense(C).cpu().numpy()
-    ref, tasks = oracle.spamm(a, b, 32, tau, want_tasks=True)
+    ref, tasks = oracle.spamm(a, b, leaf, tau, want_tasks=True)
     assert st["tasks"] == len(tasks)
-    absab, K = _kept_abs_product(a, b, 32, tasks)
-    ub, uf = 2.0 ** -8, 2.0 ** -24
-    if prec_name == "BF16":
-        coef = 2 * ub + ub * ub + 2 * K * uf * (1 + ub) ** 2
+    absab, K = _kept_abs_product(a, b, leaf, tasks)
+    u = 2.0 ** -8 if prec_name.startswith("BF16") else 2.0 ** -11 + 2.0 ** -24
+    uf = 2.0 ** -24
+    if not prec_name.endswith("X3"):
+        coef = 2 * u + u * u + 2 * K * uf * (1 + u) ** 2
     else:
-        coef = 5 * ub * ub + 3 * K * uf
+        coef = 5 * u * u + 3 * K * uf
     bound = coef * absab + 2.0 ** -52 * np.abs(ref)
-    assert np.all(np.abs(got - ref) <= bound)
-    if prec_name == "BF16X3":
-        # and clearly better than one term somewhere
-        assert np.abs(got - ref).max() < (2 * ub) * absab.max()
+    err = np.abs(got - ref)
+    assert np.all(err <= bound), (err / np.maximum(absab, 1e-300)).max()
+    # and not far below the one-term rounding of its own type (the operands
+    # really were rounded: a wrong element type would show up here)
+    if not prec_name.endswith("X3"):
+        assert err.max() > 0.01 * u * absab.max()
+    else:
+        assert err.max() < (2 * u) * absab.max()
 
 
 def test_float_split_sp2_misses_target_that_exact_slices_meet(cuda_lib):
