@@ -17,6 +17,8 @@ products, and the line reports that solve time, the speedup and
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--prec ozaki|fp64] [--slices S]
   python bench.py --impl reference ...   (the FP64 CPU oracle, bounded sample)
+  python bench.py --study precision [--n 16384] [--taus ...]   (modes vs FP64 SP2)
+  python bench.py --study batch [--batch 64] [--batch-prec tf32] (many SpAMMs, one launch)
 
 N > 1 runs independent replicas (one solve per GPU, launched with torchrun);
 value = all ranks' useful FLOPs / the slowest rank's time.
@@ -333,7 +335,8 @@ def run_precision_study(args):
     hd = torch.from_numpy(h).cuda()
     F = spamm.tree_build(hd, leaf=32)
     ne = n // 2
-    modes = [("bf16", spamm.BF16, 0), ("bf16x3", spamm.BF16X3, 0), ("ozaki5", spamm.OZAKI_BF16, 5),
+    modes = [("bf16", spamm.BF16, 0), ("bf16x3", spamm.BF16X3, 0), ("tf32", spamm.TF32, 0),
+             ("tf32x3", spamm.TF32X3, 0), ("ozaki5", spamm.OZAKI_BF16, 5),
              ("ozaki6", spamm.OZAKI_BF16, 6), ("ozaki7", spamm.OZAKI_BF16, 7)]
     for tau in args.taus:
         spamm.sp2_solve(F, ne, tau)                       # warm-up
@@ -360,6 +363,126 @@ def run_precision_study(args):
             del P, P2, p, d
         del P64, p64
         torch.cuda.empty_cache()
+
+
+def run_batch_study(args):
+    """Many independent SpAMMs in one persistent launch: `args.batch` products
+    C_m = A_m A_m of sizes log-uniform in [512, 8192] (multiples of 32, seeds
+    0..count-1, decay length uniform in [1, 2] A, the decaying-matrix
+    generator), tau = 1e-6, TF32 leaves with FP32 accumulation.  The leaf size
+    and tile schedule come from the library's autotuner; the batched call is
+    captured into a CUDA graph and replayed.  Compared with the same products
+    as sequential spamm_multiply calls (plain and graph-captured) and with the
+    FP64 batched form.  One JSON line."""
+    import torch
+    from paper_1403_7458_gb300 import spamm, synth
+    spamm.load()
+    torch.cuda.set_device(0)
+    prec = {"tf32": spamm.TF32, "tf32x3": spamm.TF32X3, "bf16x3": spamm.BF16X3,
+            "ozaki": spamm.OZAKI_BF16}[args.batch_prec]
+    slices = 7 if prec == spamm.OZAKI_BF16 else 0
+    tau = args.batch_tau
+    sizes, decays = synth.batch_sizes(args.batch, seed=0)
+    t0 = time.perf_counter()
+    mats = [torch.from_numpy(synth.decaying_matrix(n, seed=q, decay=d)).cuda()
+            for q, (n, d) in enumerate(zip(sizes, decays))]
+    gen_s = time.perf_counter() - t0
+    tune = spamm.autotune_batched(mats, mats, tau, prec=prec, slices=slices, reps=3)
+    leaf, flags = tune["leaf"], tune["flags"]
+    A = [spamm.tree_build(m, leaf=leaf) for m in mats]
+    C, st = spamm.multiply_batched(A, A, tau, prec=prec, slices=slices, flags=flags, stats=True)
+    _, stt = spamm.multiply_batched(A, A, tau, C=C, prec=prec, slices=slices, flags=flags, timing=True)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def timed(fn, steps):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        out = []
+        for _ in range(steps):
+            flush.zero_()
+            ev0.record()
+            fn()
+            ev1.record()
+            ev1.synchronize()
+            out.append(ev0.elapsed_time(ev1))
+        out.sort()
+        return out[len(out) // 2]
+
+    def capture(fn):
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            fn(side.cuda_stream)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn(torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        return g
+
+    def batched(stream=None):
+        spamm.multiply_batched(A, A, tau, C=C, prec=prec, slices=slices, flags=flags, stream=stream)
+
+    Cs = [None] * len(A)
+
+    def sequential(stream=None):
+        for q in range(len(A)):
+            Cs[q], _ = spamm.multiply(A[q], A[q], tau, C=Cs[q], prec=prec, slices=slices, flags=flags,
+                                      stream=stream)
+
+    steps = max(args.steps, 3)
+    for _ in range(args.warmup):
+        batched()
+        sequential()
+    torch.cuda.synchronize()
+    ms_batched = timed(batched, steps)
+    ms_seq = timed(sequential, steps)
+    gb = capture(batched)
+    ms_batched_graph = timed(gb.replay, steps)
+    gs = capture(sequential)
+    ms_seq_graph = timed(gs.replay, steps)
+    # FP64 batched at the same leaf size: reference values (same task set)
+    C64, st64 = spamm.multiply_batched(A, A, tau, stats=True)
+    rel = 0.0
+    for q in range(len(A)):
+        x = spamm.to_dense(C[q])
+        y = spamm.to_dense(C64[q])
+        rel = max(rel, (torch.linalg.norm(x - y) / torch.linalg.norm(y)).item())
+        del x, y
+    del C64
+    # FP64 batched at its own tuned leaf size: the plain form's best time
+    tune64 = spamm.autotune_batched(mats, mats, tau, reps=1)
+    A64 = [spamm.tree_build(m, leaf=tune64["leaf"]) for m in mats]
+    D64, sd64 = spamm.multiply_batched(A64, A64, tau, stats=True)
+    ms_fp64 = timed(lambda: spamm.multiply_batched(A64, A64, tau, C=D64), max(2, steps // 2))
+    peaks, peak_src = _peaks()
+    # nominal dense TF32 : BF16 = 1.1 : 2.25 PFLOP/s applied to the measured BF16 peak
+    tf32_peak = peaks.get("bf16_tflops_sustained", 1700.0) * (1.1 / 2.25)
+    line = {
+        "study": "batch", "products": len(A), "prec": args.batch_prec, "tau": tau,
+        "sizes": {"min": min(sizes), "max": max(sizes), "median": sorted(sizes)[len(sizes) // 2],
+                  "sum_n2": int(sum(n * n for n in sizes))},
+        "autotune": tune, "autotune_fp64": tune64, "tasks": st["tasks"], "candidates": st["candidates"],
+        "useful_tflop_per_batch": st["flops_useful"] / 1e12,
+        "ms": {"batched_graph": ms_batched_graph, "batched": ms_batched,
+               "sequential": ms_seq, "sequential_graph": ms_seq_graph, "fp64_batched": ms_fp64,
+               "split_cull_gemm_norm": [stt["ms_cull"], stt["ms_gemm"], stt["ms_norm"]]},
+        "value_tflops": st["flops_useful"] / (ms_batched_graph * 1e-3) / 1e12,
+        "speedup_vs_sequential": ms_seq / ms_batched_graph,
+        "speedup_vs_sequential_graph": ms_seq_graph / ms_batched_graph,
+        "speedup_vs_fp64_batched": ms_fp64 / ms_batched_graph,
+        "fp64_batched_tflops": sd64["flops_useful"] / (ms_fp64 * 1e-3) / 1e12,
+        "roofline": {"bound": "tensor", "kernel": "k_gemm_tc (one batched launch)",
+                     "achieved": st["flops_issued"] / (stt["ms_gemm"] * 1e-3) / 1e12,
+                     "peak": tf32_peak, "unit": "TFLOP/s",
+                     "frac": st["flops_issued"] / (stt["ms_gemm"] * 1e-3) / 1e12 / tf32_peak,
+                     "peak_source": "TF32 = 1.1/2.25 x the %s sustained BF16 peak (nominal ratio)" % peak_src,
+                     "note": "issued tensor work (tiles of 128 rows, culled leaves zero-filled)"},
+        "max_rel_err_vs_fp64": rel,
+        "generation_s": gen_s,
+        "l2": "flushed between steps",
+    }
+    print(json.dumps(line), flush=True)
 
 
 def run_reference(args):
@@ -403,7 +526,10 @@ def main(argv=None):
     ap.add_argument("--cpu-iters", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-leg", action="store_true")
-    ap.add_argument("--study", choices=["none", "precision"], default="none")
+    ap.add_argument("--study", choices=["none", "precision", "batch"], default="none")
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--batch-prec", choices=["tf32", "tf32x3", "bf16x3", "ozaki"], default="tf32")
+    ap.add_argument("--batch-tau", type=float, default=1e-6)
     ap.add_argument("--n", type=int, default=16384)
     ap.add_argument("--taus", type=float, nargs="+", default=[1e-4, 1e-6, 1e-8, 1e-10])
     args = ap.parse_args(argv)
@@ -411,6 +537,8 @@ def main(argv=None):
         args.warmup = 3
     if args.study == "precision":
         run_precision_study(args)
+    elif args.study == "batch":
+        run_batch_study(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

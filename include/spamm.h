@@ -72,6 +72,8 @@ typedef enum {
 /* ---- options ---------------------------------------------------------- */
 #define SPAMM_F_TIMING 1 /* record per-stage device times into spamm_stats_t */
 #define SPAMM_F_NOSYM 2  /* SP2: form every leaf of X^2 even when F is symmetric */
+#define SPAMM_F_ROWMAJOR 4 /* tensor path: hand tiles out row-major instead of
+                              heaviest first (a schedule the autotuner tries) */
 
 typedef struct {
     int32_t leaf;   /* leaf edge b: 16, 32 or 64; 0 selects 32            */
@@ -159,6 +161,41 @@ int spamm_multiply(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t *C,
 int spamm_multiply_batched(int32_t count, const spamm_mat_t *A, const spamm_mat_t *B,
                            const double *tau, spamm_mat_t *C, const spamm_opts_t *opts,
                            spamm_stats_t *stats, void *stream);
+
+/* ---- autotuner --------------------------------------------------------- */
+#define SPAMM_TUNE_MAX 6
+
+typedef struct {
+    int32_t leaf;                      /* chosen leaf edge                      */
+    int32_t flags;                     /* chosen schedule (0 or SPAMM_F_ROWMAJOR) */
+    float ms;                          /* its device time for the batch          */
+    int32_t tried;                     /* candidates timed                       */
+    int32_t cand_leaf[SPAMM_TUNE_MAX];
+    int32_t cand_flags[SPAMM_TUNE_MAX];
+    float cand_ms[SPAMM_TUNE_MAX];     /* median over reps; -1 = mode not built  */
+    int64_t cand_tasks[SPAMM_TUNE_MAX]; /* surviving triples at that leaf       */
+} spamm_tune_t;
+
+/*
+ * Pick the leaf size (16, 32, 64) and the tile schedule (heaviest first or
+ * row-major) for a batch of products C[m] = SpAMM(A[m], B[m], tau[m]) by
+ * timing spamm_multiply_batched on the caller's own data.  The paper's task
+ * granularity is fixed (Sec. 3); this is the GPU's counterpart of choosing
+ * it.  For each leaf size the precision mode supports, handles are built
+ * from the dense inputs, the batch is run once to warm up and then `reps`
+ * times per schedule (CUDA events on `stream`); the smallest median wins.
+ * a, b   : count dense n[m] x n[m] FP64 row-major matrices (host or device),
+ *          leading dimension n[m].
+ * tau    : count thresholds.  opts: precision and slices (leaf ignored).
+ * reps   : timed runs per candidate (>= 1).
+ * out    : receives the choice and every candidate's time.
+ * Blocking.  Allocates and frees its trial handles.
+ * Errors: E_INVAL, E_NOTSUP (no leaf size supports the mode), E_NOMEM,
+ *         E_CUDA.
+ */
+int spamm_autotune_batched(int32_t count, const double *const *a, const double *const *b,
+                           const int64_t *n, const double *tau, const spamm_opts_t *opts,
+                           int32_t reps, spamm_tune_t *out, void *stream);
 
 /*
  * Write the matrix to dense row-major storage (host or device), n x n with

@@ -414,7 +414,8 @@ int spamm_multiply_into(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t C,
         } else if ((rc = slice_operands(A, B, sl, el, symm, s, ws->stop, unit, fsplit))) {
             return rc;
         }
-        if ((rc = tc_tile_cull(A, B, tau, ws, symm, sl, s))) return rc;
+        const bool heavy = !(opts && (opts->flags & SPAMM_F_ROWMAJOR));
+        if ((rc = tc_tile_cull(A, B, tau, ws, symm, sl, s, heavy))) return rc;
         if (ev) SPAMM_CK(cudaEventRecord(ev[1], s));
         rc = launch_gemm_tc(A, B, C, ws, tr_part, sl, el, s, fsplit);
         if (rc) return rc;
@@ -605,7 +606,9 @@ extern "C" int spamm_multiply_batched(int32_t count, const spamm_mat_t *A, const
             w[q]->pair_units = nullptr;
         } else {
             rc = slice_operands(a[q], b[q], sl, el, 0, s, nullptr, unit, fsplit);
-            if (rc == SPAMM_OK) rc = tc_tile_cull(a[q], b[q], tau[ord[q]], w[q], 0, sl, s);
+            if (rc == SPAMM_OK)
+                rc = tc_tile_cull(a[q], b[q], tau[ord[q]], w[q], 0, sl, s,
+                                  !(opts && (opts->flags & SPAMM_F_ROWMAJOR)));
         }
     }
     if (rc == SPAMM_OK && timing && cudaEventRecord(ev[1], s) != cudaSuccess) rc = SPAMM_E_CUDA;

@@ -6,10 +6,6 @@
 
 namespace {
 
-// Tile order: true = heaviest first (tiles are handed out dynamically, so
-// this is longest-processing-time-first scheduling); false = row-major.
-constexpr bool kHeaviestFirst = true;
-
 // ---------------------------------------------------------------------------
 // tile cull: work lists of items (k, mask, zA, zB), grouped by tile t = I * nb + j
 // ---------------------------------------------------------------------------
@@ -229,10 +225,12 @@ int tc_mode_ok(int prec, int slices, int leaf)
     return s * leaf <= (int)tc::kAccStride;
 }
 
-// Tile cull for the tensor-core path into ws (tile lists + heaviest-first
-// order); toff[T + 1] receives the number of surviving triples.
+// Tile cull for the tensor-core path into ws: tile lists and the order in
+// which tiles are handed out, heaviest first (tiles are taken dynamically,
+// so this is longest-processing-time-first scheduling) or row-major;
+// toff[T + 1] receives the number of surviving triples.
 int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, int sym, int slices,
-                 cudaStream_t s)
+                 cudaStream_t s, bool heaviest_first)
 {
     const int R = 128 / A->b;
     const int64_t nb = A->nb, P = A->P, nI = (nb + R - 1) / R, T = nI * nb;
@@ -296,7 +294,7 @@ int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, i
     SPAMM_CK_LAUNCH();
     ws->tsym = sym;
     ws->tactive = sym ? nI * nb - (int64_t)R * nI * (nI - 1) / 2 : T;
-    if (kHeaviestFirst) {
+    if (heaviest_first) {
         SPAMM_CK(cudaMemsetAsync(ws->tbins, 0, sizeof(int32_t) * (nb + 1), s));
         k_tile_hist<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(ws->stop, ws->tcounts, nb, T, sym, R, ws->tbins);
         SPAMM_CK_LAUNCH();

@@ -160,7 +160,7 @@ static inline int prec_elem(int prec) { return (prec == SPAMM_TF32 || prec == SP
 constexpr int32_t kFlagUnitScale = 1 << 30;
 int slices_alloc(spamm_mat_t m, int s, int e, bool tile_a, bool per_leaf, cudaStream_t st);
 int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, int sym, int slices,
-                 cudaStream_t s);
+                 cudaStream_t s, bool heaviest_first = true);
 int launch_gemm_tc(spamm_mat_t A, spamm_mat_t B, spamm_mat_t C, SpammWorkspace *ws,
                    double *tr_part, int slices, int e, cudaStream_t s, bool float_split = false);
 // One launch over the products m < count (count <= kMaxBatch) whose tile

@@ -27,6 +27,8 @@ OK, E_INVAL, E_NOMEM, E_CUDA, E_CAPACITY, E_TIMEOUT, E_NOCONV, E_NOTSUP = 0, -1,
 FP64, OZAKI_BF16, BF16, BF16X3, TF32, TF32X3 = 0, 1, 2, 3, 4, 5
 F_TIMING = 1
 F_NOSYM = 2
+F_ROWMAJOR = 4
+TUNE_MAX = 6
 RULE_TRACE_DISTANCE, RULE_TRACE_ABOVE = 0, 1
 STOP_CONVERGED, STOP_STAGNATED, STOP_FIXED, STOP_MAXITER = 0, 1, 2, 3
 H_COLS = 6
@@ -51,6 +53,13 @@ class _Stats(ctypes.Structure):
                 ("flops_useful", ctypes.c_double), ("flops_issued", ctypes.c_double),
                 ("ms_cull", ctypes.c_float), ("ms_gemm", ctypes.c_float),
                 ("ms_norm", ctypes.c_float), ("reserved", ctypes.c_float)]
+
+
+class _Tune(ctypes.Structure):
+    _fields_ = [("leaf", ctypes.c_int32), ("flags", ctypes.c_int32), ("ms", ctypes.c_float),
+                ("tried", ctypes.c_int32), ("cand_leaf", ctypes.c_int32 * TUNE_MAX),
+                ("cand_flags", ctypes.c_int32 * TUNE_MAX), ("cand_ms", ctypes.c_float * TUNE_MAX),
+                ("cand_tasks", ctypes.c_int64 * TUNE_MAX)]
 
 
 class _Sp2Opts(ctypes.Structure):
@@ -87,6 +96,8 @@ def load():
     lib.spamm_tree_build.argtypes = [P, i64, i64, ctypes.POINTER(_Opts), P, H]
     lib.spamm_multiply.argtypes = [P, P, dbl, H, ctypes.POINTER(_Opts), ctypes.POINTER(_Stats), P]
     lib.spamm_multiply_batched.argtypes = [i32, P, P, P, P, ctypes.POINTER(_Opts), ctypes.POINTER(_Stats), P]
+    lib.spamm_autotune_batched.argtypes = [i32, P, P, P, P, ctypes.POINTER(_Opts), i32,
+                                           ctypes.POINTER(_Tune), P]
     lib.spamm_to_dense.argtypes = [P, P, i64, P]
     lib.spamm_norms.argtypes = [P, i32, P, P]
     lib.spamm_info.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i64),
@@ -101,7 +112,8 @@ def load():
     lib.spamm_last_error.restype = ctypes.c_char_p
     lib.sp2_solve.argtypes = [P, dbl, dbl, ctypes.POINTER(_Sp2Opts), H,
                               ctypes.POINTER(_Sp2Report), P]
-    for name in ("spamm_tree_build", "spamm_multiply", "spamm_multiply_batched", "spamm_to_dense", "spamm_norms",
+    for name in ("spamm_tree_build", "spamm_multiply", "spamm_multiply_batched", "spamm_autotune_batched",
+                 "spamm_to_dense", "spamm_norms",
                  "spamm_info", "spamm_task_list", "sp2_solve", "spamm_cull_noalloc"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -179,10 +191,10 @@ def tree_build(a, leaf: int = 32, stream=None) -> Matrix:
 
 
 def multiply(A: Matrix, B: Matrix, tau: float, C: Matrix | None = None, prec: int = FP64,
-             slices: int = 0, timing: bool = False, stats: bool = False, stream=None):
+             slices: int = 0, timing: bool = False, stats: bool = False, stream=None, flags: int = 0):
     """C = SpAMM(A, B, tau).  Returns (C, stats dict or None)."""
     h = ctypes.c_void_p(C.handle.value if C is not None else None)
-    opts = _Opts(A.leaf, prec, slices, F_TIMING if timing else 0)
+    opts = _Opts(A.leaf, prec, slices, flags | (F_TIMING if timing else 0))
     st = _Stats()
     want = stats or timing
     _check(load().spamm_multiply(A.handle, B.handle, float(tau), ctypes.byref(h),
@@ -196,7 +208,7 @@ def multiply(A: Matrix, B: Matrix, tau: float, C: Matrix | None = None, prec: in
 
 
 def multiply_batched(A, B, tau, C=None, prec: int = FP64, slices: int = 0, timing: bool = False,
-                     stats: bool = False, stream=None):
+                     stats: bool = False, stream=None, flags: int = 0):
     """C[m] = SpAMM(A[m], B[m], tau[m]) for every m, leaf products of the whole
     batch in one launch.  `tau` is a float or a sequence; `C` None or a list
     whose None entries are created.  Returns (list of C, stats dict or None:
@@ -214,7 +226,7 @@ def multiply_batched(A, B, tau, C=None, prec: int = FP64, slices: int = 0, timin
     hb = (ctypes.c_void_p * max(count, 1))(*[b.handle.value for b in B])
     hc = (ctypes.c_void_p * max(count, 1))(*[c.handle.value if c is not None else None for c in Cs])
     ht = (ctypes.c_double * max(count, 1))(*taus)
-    opts = _Opts(A[0].leaf if count else 32, prec, slices, F_TIMING if timing else 0)
+    opts = _Opts(A[0].leaf if count else 32, prec, slices, flags | (F_TIMING if timing else 0))
     st = _Stats()
     want = stats or timing
     _check(load().spamm_multiply_batched(count, ha, hb, ht, hc, ctypes.byref(opts),
@@ -225,6 +237,42 @@ def multiply_batched(A, B, tau, C=None, prec: int = FP64, slices: int = 0, timin
     if want:
         info = {k: getattr(st, k) for k, _ in _Stats._fields_ if k != "reserved"}
     return out, info
+
+
+def autotune_batched(a, b, tau, prec: int = FP64, slices: int = 0, reps: int = 3, stream=None):
+    """Leaf size and tile schedule for a batch of products a[m] x b[m] (dense
+    FP64 square matrices, host arrays or CUDA tensors) chosen by timing.
+    Returns {"leaf", "flags", "ms", "candidates": [(leaf, flags, ms, tasks)]}."""
+    count = len(a)
+    if len(b) != count or count < 1:
+        raise ValueError("a and b must be equal, non-empty lists")
+    keep, pa, pb, ns = [], [], [], []
+    for x, y in zip(a, b):
+        px, nx, ldx, kx = _data(x)
+        if y is x:
+            py, ky = px, kx
+        else:
+            py, ny, ldy, ky = _data(y)
+            if ny != nx or ldy != ny:
+                raise ValueError("a[m] and b[m] must be contiguous and of equal size")
+        if ldx != nx:
+            raise ValueError("contiguous matrices expected")
+        keep += [kx, ky]
+        pa.append(px.value)
+        pb.append(py.value)
+        ns.append(nx)
+    taus = [float(tau)] * count if np.isscalar(tau) else [float(t) for t in tau]
+    ha = (ctypes.c_void_p * count)(*pa)
+    hb = (ctypes.c_void_p * count)(*pb)
+    hn = (ctypes.c_int64 * count)(*ns)
+    ht = (ctypes.c_double * count)(*taus)
+    opts = _Opts(0, prec, slices, 0)
+    out = _Tune()
+    _check(load().spamm_autotune_batched(count, ha, hb, hn, ht, ctypes.byref(opts), reps,
+                                         ctypes.byref(out), _stream(stream)), "spamm_autotune_batched")
+    del keep
+    cands = [(out.cand_leaf[q], out.cand_flags[q], out.cand_ms[q], out.cand_tasks[q]) for q in range(out.tried)]
+    return {"leaf": out.leaf, "flags": out.flags, "ms": out.ms, "candidates": cands}
 
 
 def to_dense(M: Matrix, out=None, stream=None):

@@ -142,3 +142,41 @@ def test_batched_bad_arguments(cuda_lib):
     assert ei.value.status == cuda_lib.E_INVAL
     out, st = cuda_lib.multiply_batched([], [], 1e-6, stats=True)
     assert out == [] and st["tasks"] == 0
+
+
+def test_row_major_schedule_gives_identical_results(cuda_lib):
+    """The tile schedule changes only the order in which tiles are handed
+    out, never the arithmetic of a tile."""
+    mats = _batch([300, 200], 32, seed0=21)
+    A = [cuda_lib.tree_build(_dev(a), leaf=32) for a, _ in mats]
+    B = [cuda_lib.tree_build(_dev(b), leaf=32) for _, b in mats]
+    for prec in (cuda_lib.OZAKI_BF16, cuda_lib.TF32):
+        C1, _ = cuda_lib.multiply_batched(A, B, 1e-6, prec=prec)
+        C2, _ = cuda_lib.multiply_batched(A, B, 1e-6, prec=prec, flags=cuda_lib.F_ROWMAJOR)
+        for x, y in zip(C1, C2):
+            assert np.array_equal(cuda_lib.to_dense(x).cpu().numpy(), cuda_lib.to_dense(y).cpu().numpy())
+
+
+def test_autotuner_reports_every_candidate_and_picks_the_fastest(cuda_lib):
+    import torch
+    sizes = [256, 200, 320]
+    dense = [torch.from_numpy(synth.decaying_matrix(n, q, decay=1.2)).cuda() for q, n in enumerate(sizes)]
+    res = cuda_lib.autotune_batched(dense, dense, 1e-6, prec=cuda_lib.TF32, reps=2)
+    cands = res["candidates"]
+    assert [c[0] for c in cands] == [16, 16, 32, 32, 64, 64]
+    assert all(c[2] > 0 for c in cands)
+    best = min(cands, key=lambda c: c[2])
+    assert (res["leaf"], res["flags"], res["ms"]) == (best[0], best[1], best[2])
+    # the task counts the tuner saw are the oracle's at each leaf size
+    for leaf in (16, 32, 64):
+        want = sum(len(oracle.spamm(d.cpu().numpy(), d.cpu().numpy(), leaf, 1e-6, want_tasks=True)[1])
+                   for d in dense)
+        assert all(c[3] == want for c in cands if c[0] == leaf)
+    # exact slices at leaf 64 allow at most 4 slices: with 7 the candidates
+    # at 64 are reported as not built
+    res7 = cuda_lib.autotune_batched(dense[:1], dense[:1], 1e-6, prec=cuda_lib.OZAKI_BF16, slices=7, reps=1)
+    assert [c[2] for c in res7["candidates"] if c[0] == 64] == [-1.0, -1.0]
+    assert res7["leaf"] in (16, 32)
+    # FP64: one schedule per leaf
+    res64 = cuda_lib.autotune_batched(dense[:2], dense[:2], 1e-6, reps=1)
+    assert [c[0] for c in res64["candidates"]] == [16, 32, 64]
