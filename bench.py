@@ -19,6 +19,7 @@ products, and the line reports that solve time, the speedup and
   python bench.py --impl reference ...   (the FP64 CPU oracle, bounded sample)
   python bench.py --study precision [--n 16384] [--taus ...]   (modes vs FP64 SP2)
   python bench.py --study batch [--batch 64] [--batch-prec tf32] (many SpAMMs, one launch)
+  python bench.py --study large [--n-large 65536]   (one large SP2, mixed vs FP64)
 
 N > 1 runs independent replicas (one solve per GPU, launched with torchrun);
 value = all ranks' useful FLOPs / the slowest rank's time.
@@ -485,6 +486,86 @@ def run_batch_study(args):
     print(json.dumps(line), flush=True)
 
 
+def run_large_study(args):
+    """SP2 at N = args.n_large (default 65536) on the tight-binding
+    Hamiltonian with decay length 1.0 A, tau = 1e-8, leaf 32, Ne = N/2: FP64
+    leaf products with their own stopping rule, then exact BF16 slices (7)
+    at the same iteration count (||P - P_FP64||_F, Tr[F (P - P_FP64)]) and
+    with their own stopping rule (time to solution).  The Hamiltonian is
+    generated on the device.  One JSON line."""
+    import torch
+    from paper_1403_7458_gb300 import spamm, synth
+    spamm.load()
+    torch.cuda.set_device(0)
+    n, leaf, tau = args.n_large, 32, 1e-8
+    ne = n // 2
+    gib = lambda b: b / 2.0 ** 30
+    mem = {"total_gib": gib(torch.cuda.mem_get_info()[1])}
+    t0 = time.perf_counter()
+    h = synth.tb_hamiltonian_torch(n, seed=0, decay=1.0)
+    F = spamm.tree_build(h, leaf=leaf)
+    torch.cuda.synchronize()
+    del h
+    torch.cuda.empty_cache()
+    gen_s = time.perf_counter() - t0
+    nb = F.nb
+    fill = lambda M: float((spamm.norms(M, M.depth)[:nb, :nb] > 1e-24).mean())
+    fill_h = fill(F)
+
+    P64, r64 = spamm.sp2_solve(F, ne, tau, timing=True)
+    fill_p = fill(P64)
+    mem["free_after_fp64_gib"] = gib(torch.cuda.mem_get_info()[0])
+    p64 = spamm.to_dense(P64)
+    P64.free()
+    torch.cuda.synchronize()
+
+    P, r = spamm.sp2_solve(F, ne, tau, prec=spamm.OZAKI_BF16, slices=7, fixed_iters=r64["iters"], timing=True)
+    mem["free_with_mixed_scratch_gib"] = gib(torch.cuda.mem_get_info()[0])
+    spamm.release_scratch(P)
+    torch.cuda.synchronize()
+    d = spamm.to_dense(P)
+    d.sub_(p64)                                  # P_mixed - P_FP64, in place
+    dP = torch.linalg.norm(d).item()
+    del p64
+    torch.cuda.empty_cache()
+    hh = synth.tb_hamiltonian_torch(n, seed=0, decay=1.0)
+    dE = 0.0
+    for r0 in range(0, n, 4096):                 # Tr[F dP] = sum_ij F_ij dP_ji
+        dE += float((hh[r0:r0 + 4096] * d[:, r0:r0 + 4096].T).sum().item())
+    del hh, d
+    torch.cuda.empty_cache()
+
+    P2, r2 = spamm.sp2_solve(F, ne, tau, P=P, prec=spamm.OZAKI_BF16, slices=7, timing=True)
+    peaks, peak_src = _peaks()
+    bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
+    keys = ("iters", "stop_reason", "ms_total", "ms_cull", "ms_gemm", "ms_update", "tasks_total",
+            "flops_useful", "flops_tensor", "idem_err", "trace_err", "launches", "symmetric")
+    line = {
+        "study": "large", "n": n, "leaf": leaf, "tau": tau, "ne": ne, "decay_A": 1.0,
+        "storage": "dense leaf grid (zero leaves never multiplied)",
+        "leaf_fill": {"H_n2_gt_1e-24": fill_h, "P_n2_gt_1e-24": fill_p},
+        "fp64": {k: r64[k] for k in keys},
+        "mixed_same_iters": {k: r[k] for k in keys},
+        "mixed_own_stop": {k: r2[k] for k in keys},
+        "dP_fro": dP, "dE_trF": dE,
+        "speedup_same_iters": r64["ms_total"] / r["ms_total"],
+        "speedup_time_to_solution": r64["ms_total"] / r2["ms_total"],
+        "useful_tflops": {"fp64": r64["flops_useful"] / (r64["ms_total"] * 1e-3) / 1e12,
+                          "mixed": r["flops_useful"] / (r["ms_total"] * 1e-3) / 1e12},
+        "roofline": {"fp64": {"bound": "alu", "kernel": "k_gemm_fp64<32>", "unit": "TFLOP/s",
+                              "achieved": r64["flops_useful"] / (r64["ms_gemm"] * 1e-3) / 1e12,
+                              "peak": fp64_peak_tflops()},
+                     "mixed": {"bound": "tensor", "kernel": "k_gemm_tc<7,2,32>", "unit": "TFLOP/s",
+                               "achieved": r["flops_tensor"] / (r["ms_gemm"] * 1e-3) / 1e12,
+                               "peak": bf16, "peak_source": "bf16 sustained, %s" % peak_src}},
+        "memory": mem, "generation_s": gen_s,
+    }
+    for k in ("fp64", "mixed"):
+        rf = line["roofline"][k]
+        rf["frac"] = rf["achieved"] / rf["peak"]
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -526,7 +607,8 @@ def main(argv=None):
     ap.add_argument("--cpu-iters", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-leg", action="store_true")
-    ap.add_argument("--study", choices=["none", "precision", "batch"], default="none")
+    ap.add_argument("--study", choices=["none", "precision", "batch", "large"], default="none")
+    ap.add_argument("--n-large", type=int, default=65536)
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--batch-prec", choices=["tf32", "tf32x3", "bf16x3", "ozaki"], default="tf32")
     ap.add_argument("--batch-tau", type=float, default=1e-6)
@@ -539,6 +621,8 @@ def main(argv=None):
         run_precision_study(args)
     elif args.study == "batch":
         run_batch_study(args)
+    elif args.study == "large":
+        run_large_study(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

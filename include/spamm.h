@@ -254,6 +254,16 @@ int spamm_cull_noalloc(const double *n2A, int64_t lda, const double *n2B, int64_
 /* Release a handle (its device memory is freed in stream order). */
 void spamm_free(spamm_mat_t M);
 
+/*
+ * Free the scratch a handle keeps for later products: its tensor-core slices
+ * (the largest buffers of the mixed path: 2 e s bytes per stored element
+ * for s slices of e-byte elements, in two layouts) and the task lists of the
+ * product it was the output of.  The matrix, its norms and its shape are
+ * untouched; the next product that needs the scratch allocates it again.
+ * Stream-ordered on `stream`.  No-op for NULL.
+ */
+void spamm_release_scratch(spamm_mat_t M, void *stream);
+
 /* Static text for a status code. */
 const char *spamm_strerror(int status);
 

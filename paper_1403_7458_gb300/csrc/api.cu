@@ -197,6 +197,22 @@ extern "C" void spamm_free(spamm_mat_t m)
     delete m;
 }
 
+extern "C" void spamm_release_scratch(spamm_mat_t m, void *stream)
+{
+    if (!m) return;
+    cudaStream_t s = (cudaStream_t)stream;
+    spamm_release(m->slA, s);
+    spamm_release(m->slB, s);
+    spamm_release(m->zlead, s);
+    m->slA = m->slB = nullptr;
+    m->zlead = nullptr;
+    m->sl_s = m->sl_e = 0;
+    m->slB_transposed = -1;
+    const int32_t *stop = m->ws.stop;
+    ws_free(&m->ws, s);
+    m->ws.stop = stop;
+}
+
 extern "C" int spamm_tree_build(const double *a, int64_t n, int64_t lda, const spamm_opts_t *opts,
                                 void *stream, spamm_mat_t *out)
 {
@@ -437,6 +453,7 @@ int spamm_multiply_into(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t C,
     }
     if (rc) return rc;
     if (ev) SPAMM_CK(cudaEventRecord(ev[2], s));
+    C->tiers_ok = build_pyramid;
     if (build_pyramid) {
         // the FP64 epilogue already wrote C's leaf norms; the tensor-core
         // epilogue does not, so they are formed from the stored leaves

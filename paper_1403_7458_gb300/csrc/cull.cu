@@ -9,7 +9,12 @@
 //
 // Three launches:
 //   count : one warp per group; lanes walk k in steps of 32 and count the
-//           passing candidates with a ballot + popcount;
+//           passing candidates with a ballot + popcount; a step is skipped
+//           whole when the quadtree tier whose blocks are 32 x 32 leaves
+//           already fails the test for the block row of i and the block
+//           column of j (Algorithm 1's early occlusion: a parent's squared
+//           norm is never below a child's, so no leaf triple under a failing
+//           parent pair can pass);
 //   scan  : exclusive prefix sum of the counts (one block);
 //   emit  : the warps re-test and write each passing k at its ballot rank.
 // Roofline: ALU/latency bound on the candidate tests; HBM/L2 traffic is the
@@ -20,9 +25,23 @@ namespace {
 
 constexpr int kWarps = 8;
 
+// Squared norms of the tier whose blocks are 32 x 32 leaves (W x W grid),
+// for the early skip; null when the quadtree has fewer than 5 tiers below
+// the root.
+struct Coarse {
+    const double *a, *b;
+    int64_t W;
+};
+
+__device__ __forceinline__ bool coarse_pass(const Coarse &c, int64_t i, int64_t k0, int64_t j, double tau2)
+{
+    return !c.a || keep_product(__ldg(c.a + (i >> 5) * c.W + (k0 >> 5)), __ldg(c.b + (k0 >> 5) * c.W + (j >> 5)),
+                                tau2);
+}
+
 __global__ void __launch_bounds__(kWarps * 32)
 k_cull_count(const int32_t *__restrict__ stop, const double *__restrict__ n2A,
-             const double *__restrict__ n2BT, int64_t nb, int64_t P, double tau2,
+             const double *__restrict__ n2BT, int64_t nb, int64_t P, double tau2, Coarse co,
              int32_t *__restrict__ counts)
 {
     if (stop && *stop) return;  // the SP2 loop has already stopped
@@ -34,6 +53,7 @@ k_cull_count(const int32_t *__restrict__ stop, const double *__restrict__ n2A,
     const double *rb = n2BT + j * P;
     int cnt = 0;
     for (int64_t k0 = 0; k0 < nb; k0 += 32) {
+        if (!coarse_pass(co, i, k0, j, tau2)) continue;  // warp-uniform
         int64_t k = k0 + lane;
         bool p = k < nb && keep_product(__ldg(ra + k), __ldg(rb + k), tau2);
         cnt += __popc(__ballot_sync(0xffffffffu, p));
@@ -73,7 +93,7 @@ k_scan(const int32_t *__restrict__ stop, const int32_t *__restrict__ counts, int
 
 __global__ void __launch_bounds__(kWarps * 32)
 k_cull_emit(const int32_t *__restrict__ stop, const double *__restrict__ n2A,
-            const double *__restrict__ n2BT, int64_t nb, int64_t P, double tau2,
+            const double *__restrict__ n2BT, int64_t nb, int64_t P, double tau2, Coarse co,
             const int64_t *__restrict__ off, uint32_t *__restrict__ klist, int64_t cap,
             int32_t *__restrict__ err)
 {
@@ -91,12 +111,24 @@ k_cull_emit(const int32_t *__restrict__ stop, const double *__restrict__ n2A,
     }
     unsigned lt = (1u << lane) - 1u;
     for (int64_t k0 = 0; k0 < nb; k0 += 32) {
+        if (!coarse_pass(co, i, k0, j, tau2)) continue;  // warp-uniform
         int64_t k = k0 + lane;
         bool p = k < nb && keep_product(__ldg(ra + k), __ldg(rb + k), tau2);
         unsigned m = __ballot_sync(0xffffffffu, p);
         if (p) klist[base + __popc(m & lt)] = (uint32_t)k;
         base += __popc(m);
     }
+}
+
+Coarse coarse_tier(spamm_mat_t A, spamm_mat_t B)
+{
+    Coarse c{nullptr, nullptr, 0};
+    if (A->depth >= 5 && A->tiers_ok && B->tiers_ok) {
+        c.a = A->n2 + tier_offset(A->depth - 5);
+        c.b = B->n2 + tier_offset(B->depth - 5);
+        c.W = int64_t(1) << (A->depth - 5);
+    }
+    return c;
 }
 
 }  // namespace
@@ -111,7 +143,8 @@ int spamm_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, int
     int64_t G = nb * nb;
     double tau2 = tau * tau;
     unsigned blocks = (unsigned)((G + kWarps - 1) / kWarps);
-    k_cull_count<<<blocks, kWarps * 32, 0, s>>>(ws->stop, A->n2 + tier_offset(A->depth), B->n2T, nb, P, tau2,
+    const Coarse co = coarse_tier(A, B);
+    k_cull_count<<<blocks, kWarps * 32, 0, s>>>(ws->stop, A->n2 + tier_offset(A->depth), B->n2T, nb, P, tau2, co,
                                                 ws->counts);
     SPAMM_CK_LAUNCH();
     k_scan<<<1, kScanThreads, 0, s>>>(ws->stop, ws->counts, G, ws->off);
@@ -134,7 +167,7 @@ int spamm_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, int
         if (rc) return rc;
         ws->klist_cap = cap;
     }
-    k_cull_emit<<<blocks, kWarps * 32, 0, s>>>(ws->stop, A->n2 + tier_offset(A->depth), B->n2T, nb, P, tau2,
+    k_cull_emit<<<blocks, kWarps * 32, 0, s>>>(ws->stop, A->n2 + tier_offset(A->depth), B->n2T, nb, P, tau2, co,
                                                ws->off, ws->klist, ws->klist_cap, ws->counter + 8);
     SPAMM_CK_LAUNCH();
     if (total_host) *total_host = total;

@@ -13,6 +13,10 @@ constexpr int kWarps = 8;
 
 struct CullArgs {
     const double *n2A, *n2BT;
+    // tier whose blocks are 32 x 32 leaves (W x W), for skipping a 32-wide
+    // step of k at once (null when the quadtree is shallower)
+    const double *cA, *cB;
+    int64_t cW;
     const uint8_t *zA, *zB;        // leading zero slices per slot
     const int32_t *slotA, *slotB;  // slot maps (B: of the matrix whose slices serve as B)
     int64_t nb, P, nI;
@@ -22,7 +26,8 @@ struct CullArgs {
 };
 
 // Work item of tile (I, j) at k (tc::item_make), or 0 when no kept leaf has a
-// nonzero product.  *ntask += surviving triples;
+// nonzero product.  *ntask += surviving triples (symmetric mode: of the whole
+// product, see below);
 // *npair += slice pairs those triples need (p >= zA_i, q >= zB, p + q < S).
 __device__ __forceinline__ uint32_t tile_item(const CullArgs &c, int64_t I, int64_t j, int64_t k, int &ntask,
                                               int &npair)
@@ -37,7 +42,10 @@ __device__ __forceinline__ uint32_t tile_item(const CullArgs &c, int64_t I, int6
     for (int r = 0; r < 8; r++) {
         const int64_t i = (int64_t)c.R * I + r;
         if (r < c.R && i < c.nb && keep_product(__ldg(c.n2A + i * c.P + k), b, c.tau2)) {
-            ntask++;
+            // symmetric mode counts the whole product's triples from the
+            // active tiles alone: (i, k, j) survives iff (j, k, i) does, so
+            // a leaf above the diagonal stands for itself and its mirror
+            ntask += !c.sym ? 1 : (i < j ? 2 : (i == j ? 1 : 0));
             const int zr = c.zA[c.slotA[i * c.nb + k]];
             if (zr + zb < c.S) {
                 const int mr = c.S - zr - zb;
@@ -49,6 +57,17 @@ __device__ __forceinline__ uint32_t tile_item(const CullArgs &c, int64_t I, int6
     }
     if (!mask) return 0;
     return tc::item_make((uint32_t)k, mask, za, zb);
+}
+
+// Early occlusion (Algorithm 1): the R rows of tile I lie in one block row
+// of the 32 x 32-leaf tier (R divides 32), so when that block row of A and
+// the block of B holding (k0 .. k0+31, j) fail the test, every triple of the
+// step fails (a parent's squared norm is never below a child's).
+__device__ __forceinline__ bool coarse_pass(const CullArgs &c, int64_t I, int64_t k0, int64_t j)
+{
+    const int64_t i = (int64_t)c.R * I;
+    return !c.cA || keep_product(__ldg(c.cA + (i >> 5) * c.cW + (k0 >> 5)),
+                                 __ldg(c.cB + (k0 >> 5) * c.cW + (j >> 5)), c.tau2);
 }
 
 __device__ __forceinline__ int item_pairs(uint32_t w, int S)
@@ -68,7 +87,12 @@ k_tile_count(CullArgs c, int32_t *__restrict__ counts, int32_t *__restrict__ tas
     const int64_t I = t / c.nb, j = t % c.nb;
     const bool active = !c.sym || j >= (int64_t)c.R * I;
     int cnt = 0, ntask = 0, npair = 0, nuse = 0;
+    if (!active) {  // symmetric mode: a lower-triangle tile is formed as a mirror
+        if (lane == 0) counts[t] = tasks[t] = pairs[t] = useful[t] = 0;
+        return;
+    }
     for (int64_t k0 = 0; k0 < c.nb; k0 += 32) {
+        if (!coarse_pass(c, I, k0, j)) continue;  // warp-uniform
         const uint32_t w = tile_item(c, I, j, k0 + lane, ntask, nuse);
         cnt += __popc(__ballot_sync(0xffffffffu, w != 0));
         if (w) npair += item_pairs(w, c.S);
@@ -104,6 +128,7 @@ k_tile_emit(CullArgs c, const int64_t *__restrict__ off, uint32_t *__restrict__ 
     const unsigned lt = (1u << lane) - 1u;
     int dummy = 0, dummy2 = 0;
     for (int64_t k0 = 0; k0 < c.nb; k0 += 32) {
+        if (!coarse_pass(c, I, k0, j)) continue;  // warp-uniform
         const uint32_t w = tile_item(c, I, j, k0 + lane, dummy, dummy2);
         const unsigned bal = __ballot_sync(0xffffffffu, w != 0);
         if (w) list[base + __popc(bal & lt)] = w;
@@ -274,6 +299,13 @@ int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, i
     c.S = slices;
     c.R = R;
     c.stop = ws->stop;
+    c.cA = c.cB = nullptr;
+    c.cW = 0;
+    if (A->depth >= 5 && A->tiers_ok && B->tiers_ok) {
+        c.cA = A->n2 + tier_offset(A->depth - 5);
+        c.cB = B->n2 + tier_offset(B->depth - 5);
+        c.cW = int64_t(1) << (A->depth - 5);
+    }
     const unsigned blocks = (unsigned)((T + kWarps - 1) / kWarps);
     k_tile_count<<<blocks, kWarps * 32, 0, s>>>(c, ws->tcounts, ws->ttasks, ws->tpairs, ws->tuseful);
     SPAMM_CK_LAUNCH();

@@ -71,6 +71,7 @@ struct spamm_mat {
     int sl_s = 0;
     int sl_e = 0;                     // bytes per slice element
     unsigned long long *scale = nullptr;  // [0] max |x| bits, [1] int32 sigma, int32 overflow flag
+    bool tiers_ok = true;  // upper norm tiers match the leaf tier (the cull's early skip reads them)
     SpammWorkspace ws;  // used when this handle is the output of a product
 };
 
@@ -102,6 +103,10 @@ static inline int64_t tier_offset(int t) { return ((int64_t(1) << (2 * t)) - 1) 
 int spamm_num_sms();
 int spamm_mat_alloc(spamm_mat_t m, int64_t n, int b, cudaStream_t s);
 int spamm_mat_same_shape(spamm_mat_t a, spamm_mat_t b);
+
+// The early skip of the cull (32 x 32-leaf tier) pays from this many leaf
+// rows on; SP2 rebuilds its iterate's upper tiers only then.
+constexpr int64_t kCoarseMinNb = 256;
 
 // Norms (norms.cu)
 int launch_leaf_norms(spamm_mat_t m, cudaStream_t s);

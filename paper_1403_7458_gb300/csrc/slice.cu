@@ -23,6 +23,7 @@
 // tile-major A array puts the R = 128 / b leaves (i, k), i = R I .. R I + R-1,
 // of one tile next to each other per slice: [I][k][p][L][slice].
 //
+// Leaves of squared norm 0 are skipped (no product reads their slices).
 // Per leaf the number z of leading all-zero slices (every digit d_p, p < z,
 // is 0) is recorded: slice pairs touching them contribute exactly nothing.
 //
@@ -104,7 +105,7 @@ __device__ __forceinline__ uint32_t slice_elem(uint64_t X, bool neg, int p, int 
 template <int S, int E, int B>
 __global__ void __launch_bounds__(256)
 k_slice(const int32_t *__restrict__ stop, const double *__restrict__ leaf, const int32_t *__restrict__ slot,
-        int64_t nb, int64_t rows,
+        const double *__restrict__ n2, int64_t P, int64_t nb, int64_t rows,
         const unsigned long long *__restrict__ maxbits, int32_t *__restrict__ sigma_out,
         uint8_t *__restrict__ tileA, uint8_t *__restrict__ perleaf, int perleaf_transposed,
         uint8_t *__restrict__ zlead, int32_t *__restrict__ overflow, int float_split)
@@ -120,13 +121,17 @@ k_slice(const int32_t *__restrict__ stop, const double *__restrict__ leaf, const
     for (int64_t pos = blockIdx.x; pos < rows * nb; pos += gridDim.x) {
         const int64_t i = pos / nb, k = pos % nb;
         const int32_t sl = i < nb ? slot[i * nb + k] : -1;
+        // a leaf of squared norm 0 (and a padding position) takes part in no
+        // product: it is never in a work item's mask (A) and never a listed
+        // B leaf, so its slices are never read unmasked; skip it
+        if (sl < 0 || n2[i * P + k] == 0.0) continue;  // block-uniform
         if (threadIdx.x == 0) s_xmax = 0;
         __syncthreads();
         unsigned long long xmax = 0;
-        const double *src = leaf + (int64_t)(sl < 0 ? 0 : sl) * (B * B);
+        const double *src = leaf + (int64_t)sl * (B * B);
         for (int q = threadIdx.x; q < B * B; q += blockDim.x) {
             const int r = q / B, l = q % B;
-            const double x = sl >= 0 ? src[q] : 0.0;
+            const double x = src[q];
             const uint64_t X = float_split ? 0 : slice_int(x, sigma, S);
             const bool neg = x < 0.0;
             xmax = X > xmax ? X : xmax;
@@ -144,7 +149,7 @@ k_slice(const int32_t *__restrict__ stop, const double *__restrict__ leaf, const
         }
         if ((threadIdx.x & 31) == 0 && xmax) atomicMax(&s_xmax, xmax);
         __syncthreads();
-        if (threadIdx.x == 0 && zlead && sl >= 0) {
+        if (threadIdx.x == 0 && zlead) {
             // leading zero slices: X < 2^(7 (S - z)) for every element (float
             // splits have none)
             const unsigned long long xm = s_xmax;
@@ -153,7 +158,7 @@ k_slice(const int32_t *__restrict__ stop, const double *__restrict__ leaf, const
             zlead[sl] = (uint8_t)(z < 0 ? 0 : z);
         }
         const uint4 *ss = reinterpret_cast<const uint4 *>(sa);
-        if (perleaf && sl >= 0) {
+        if (perleaf) {
             uint4 *d = reinterpret_cast<uint4 *>(perleaf + (int64_t)sl * (S * B * B * E));
             for (int q = threadIdx.x; q < S * kU4; q += blockDim.x) d[q] = ss[q];
         }
@@ -212,8 +217,8 @@ void slice_launch(unsigned grid, cudaStream_t st, const int32_t *stop, spamm_mat
                   unsigned long long *mx, int32_t *sig, uint8_t *ta, uint8_t *pl, int tr, uint8_t *zl,
                   int float_split)
 {
-    k_slice<S, E, B><<<grid, 256, 0, st>>>(stop, m->leaf, m->slot, m->nb, rows, mx, sig, ta, pl, tr, zl, sig + 1,
-                                           float_split);
+    k_slice<S, E, B><<<grid, 256, 0, st>>>(stop, m->leaf, m->slot, m->n2 + tier_offset(m->depth), m->P, m->nb,
+                                           rows, mx, sig, ta, pl, tr, zl, sig + 1, float_split);
 }
 
 template <int B>

@@ -376,6 +376,7 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
     mo.slices = o.slices;
     mo.flags = kFlagUnitScale;  // iterates satisfy |x_ij| <= ||X||_2 < 2
     const int limit = o.fixed_iters > 0 ? o.fixed_iters : o.max_iter;
+    const bool coarse = nb >= kCoarseMinNb;
     unsigned ew_blocks = (unsigned)((G + kWarps - 1) / kWarps);
 
 #define SP2_TRY(x)                 \
@@ -435,6 +436,10 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
                                                         sc.idem_part, sc.diag_part, sc.st,
                                                         Sp2Rule{Ne, 0, 0, 0, 1}, sc.hist);
     SP2_LAUNCHED();
+    // upper tiers of the iterate: the cull's early skip reads them (rebuilt
+    // only where the skip pays; otherwise marked stale and not used)
+    if (coarse) SP2_TRY(launch_pyramid(X, s));
+    X->tiers_ok = coarse;
 
     // X2's product kernels return at once when the device rule has stopped
     X2->ws.stop = reinterpret_cast<const int32_t *>(reinterpret_cast<const char *>(sc.st) +
@@ -455,6 +460,7 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
                     1, X->leaf, X2->leaf, X->slot, F->n, nb, X->P, X->b, X->n2 + tier_offset(X->depth),
                     X->n2T, sc.idem_part, sc.diag_part, sc.st, rule, sc.hist);
                 SP2_LAUNCHED();
+                if (coarse) SP2_TRY(launch_pyramid(X, s));
                 if (timing) SP2_CUDA(cudaEventRecord(ev[4], s));
             }
             enq += batch;
@@ -491,6 +497,7 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
     }
     SP2_TRY(ws_check_errors(&X2->ws, s));
     SP2_TRY(launch_pyramid(X, s));
+    X->tiers_ok = true;
     SP2_CUDA(cudaEventRecord(ev1, s));
     SP2_CUDA(cudaEventSynchronize(ev1));
     if (o.prec == SPAMM_OZAKI_BF16 && X->scale) {

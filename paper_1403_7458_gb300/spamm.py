@@ -106,6 +106,8 @@ def load():
     lib.spamm_cull_noalloc.argtypes = [P, i64, P, i64, i64, dbl, P, P, i64, P]
     lib.spamm_free.argtypes = [P]
     lib.spamm_free.restype = None
+    lib.spamm_release_scratch.argtypes = [P, P]
+    lib.spamm_release_scratch.restype = None
     lib.spamm_strerror.argtypes = [ctypes.c_int]
     lib.spamm_strerror.restype = ctypes.c_char_p
     lib.spamm_last_error.argtypes = []
@@ -273,6 +275,11 @@ def autotune_batched(a, b, tau, prec: int = FP64, slices: int = 0, reps: int = 3
     del keep
     cands = [(out.cand_leaf[q], out.cand_flags[q], out.cand_ms[q], out.cand_tasks[q]) for q in range(out.tried)]
     return {"leaf": out.leaf, "flags": out.flags, "ms": out.ms, "candidates": cands}
+
+
+def release_scratch(M: Matrix, stream=None):
+    """Free the slices and task lists a handle keeps for later products."""
+    load().spamm_release_scratch(M.handle, _stream(stream))
 
 
 def to_dense(M: Matrix, out=None, stream=None):

@@ -27,7 +27,7 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = ["water_sites", "morton3", "distances", "decaying_matrix",
-           "tb_hamiltonian", "batch_sizes"]
+           "tb_hamiltonian", "tb_hamiltonian_torch", "batch_sizes"]
 
 _MORTON_BITS = 21
 
@@ -114,6 +114,28 @@ def tb_hamiltonian(n: int, seed: int, decay: float = 1.2, onsite: float = 2.0,
         blk[np.abs(blk) < cut] = 0.0
         h[r0:r0 + step] = blk
     np.fill_diagonal(h, np.where(gen % 2 == 0, -onsite, onsite))
+    return h
+
+
+def tb_hamiltonian_torch(n: int, seed: int, decay: float = 1.2, onsite: float = 2.0,
+                         cut: float = 1e-12, device="cuda", rows_per_block: int = 1024):
+    """`tb_hamiltonian` built in a torch tensor on `device` (same sites, same
+    formula; exp may differ from numpy's in the last bit), for sizes whose
+    dense host copy would not fit in host memory."""
+    import torch
+    rng = np.random.default_rng(seed)
+    pos, gen = water_sites(n, rng)
+    p = torch.from_numpy(pos).to(device)
+    h = torch.empty((n, n), dtype=torch.float64, device=device)
+    for r0 in range(0, n, rows_per_block):
+        d = p[r0:r0 + rows_per_block, None, :] - p[None, :, :]
+        blk = -torch.exp(-torch.sqrt((d * d).sum(dim=2)) / decay)
+        del d
+        blk[blk.abs() < cut] = 0.0
+        h[r0:r0 + rows_per_block] = blk
+        del blk
+    diag = torch.from_numpy(np.where(gen % 2 == 0, -onsite, onsite)).to(device)
+    h.diagonal().copy_(diag)
     return h
 
 

@@ -257,3 +257,23 @@ def test_float_split_sp2_misses_target_that_exact_slices_meet(cuda_lib):
         P, r = cuda_lib.sp2_solve(F, n / 2, 1e-8, prec=getattr(cuda_lib, name), fixed_iters=r64["iters"])
         errs[name] = np.linalg.norm(cuda_lib.to_dense(P).cpu().numpy() - p64)
     assert errs["OZAKI_BF16"] <= 1e-6 < errs["BF16X3"] < 1e-1
+
+
+@pytest.mark.parametrize("prec_name,leaf,slices", [("OZAKI_BF16", 32, 7), ("TF32", 16, 0), ("BF16X3", 64, 0),
+                                                   ("OZAKI_BF16", 64, 4)])
+def test_tile_cull_counts_match_oracle_with_early_skip(cuda_lib, prec_name, leaf, slices):
+    """Surviving triples of the tile cull (deep quadtree, sparse matrix: the
+    32-leaf early skip fires) equal the oracle's flat enumeration."""
+    n, tau = 4096, 1e-8
+    h = synth.tb_hamiltonian(n, 5, decay=1.0)
+    g = synth.decaying_matrix(n, 6, decay=1.1)
+    A = cuda_lib.tree_build(_dev(h), leaf=leaf)
+    B = cuda_lib.tree_build(_dev(g), leaf=leaf)
+    nb = A.nb
+    want_ab = len(oracle.flat_tasks(oracle.leaf_norms2(h, leaf), oracle.leaf_norms2(g, leaf), nb, tau))
+    want_aa = len(oracle.flat_tasks(oracle.leaf_norms2(h, leaf), oracle.leaf_norms2(h, leaf), nb, tau))
+    prec = getattr(cuda_lib, prec_name)
+    _, st = cuda_lib.multiply(A, B, tau, prec=prec, slices=slices, stats=True)
+    assert st["tasks"] == want_ab
+    _, st = cuda_lib.multiply(A, A, tau, prec=prec, slices=slices, stats=True)
+    assert st["tasks"] == want_aa

@@ -69,10 +69,14 @@ def test_tree_build_from_host_memory(cuda_lib):
     assert np.array_equal(cuda_lib.norms(A, A.depth), oracle.leaf_norms2(a, 16))
 
 
-@pytest.mark.parametrize("n,b,tau", [(1024, 32, 1e-6), (1000, 16, 1e-6), (512, 64, 1e-8),
-                                     (384, 32, 0.0), (384, 32, 1e-2), (256, 32, 1e300)])
-def test_task_list_bit_exact(cuda_lib, n, b, tau):
-    a = synth.decaying_matrix(n, 7)
+@pytest.mark.parametrize("n,b,tau,kind", [(1024, 32, 1e-6, "dec"), (1000, 16, 1e-6, "dec"), (512, 64, 1e-8, "dec"),
+                                          (384, 32, 0.0, "dec"), (384, 32, 1e-2, "dec"), (256, 32, 1e300, "dec"),
+                                          (3000, 16, 1e-6, "dec"), (4096, 32, 1e-8, "tb"), (4100, 64, 1e-6, "tb")])
+def test_task_list_bit_exact(cuda_lib, n, b, tau, kind):
+    """Flat enumeration of Eq. 4 by the oracle vs the GPU's list; the larger
+    cases have quadtrees deep enough for the early skip of whole 32-leaf
+    steps of k (and sparse enough, "tb": decay 1.0, for it to fire)."""
+    a = synth.decaying_matrix(n, 7) if kind == "dec" else synth.tb_hamiltonian(n, 7, decay=1.0)
     A = cuda_lib.tree_build(_dev(a), leaf=b)
     off, k = cuda_lib.task_list(A, A, tau)
     nb = A.nb

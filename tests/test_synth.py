@@ -2,6 +2,7 @@
 Fockians): site counts, Morton order, symmetry, decay and the gapped
 on-site pattern."""
 import numpy as np
+import pytest
 
 from paper_1403_7458_gb300 import synth
 
@@ -52,3 +53,15 @@ def test_batch_sizes():
     n, lam = synth.batch_sizes(64, 0)
     assert len(n) == 64 and all(512 <= x <= 8192 and x % 32 == 0 for x in n)
     assert all(1.0 <= x <= 2.0 for x in lam)
+
+
+def test_hamiltonian_torch_matches_numpy_generator():
+    torch = pytest.importorskip("torch")
+    for n, decay in ((300, 1.2), (1100, 1.0)):
+        h = synth.tb_hamiltonian(n, 3, decay=decay)
+        ht = synth.tb_hamiltonian_torch(n, 3, decay=decay, device="cpu", rows_per_block=256).numpy()
+        # same sites, same cut pattern; values equal up to the rounding of
+        # r / decay (an ulp of an argument up to ~28 moves exp by ~28 ulp)
+        assert np.array_equal(h == 0, ht == 0)
+        assert np.array_equal(np.diag(h), np.diag(ht))
+        assert np.allclose(h, ht, rtol=1e-14, atol=0)
