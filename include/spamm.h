@@ -72,8 +72,9 @@ typedef enum {
 /* ---- options ---------------------------------------------------------- */
 #define SPAMM_F_TIMING 1 /* record per-stage device times into spamm_stats_t */
 #define SPAMM_F_NOSYM 2  /* SP2: form every leaf of X^2 even when F is symmetric */
-#define SPAMM_F_ROWMAJOR 4 /* tensor path: hand tiles out row-major instead of
-                              heaviest first (a schedule the autotuner tries) */
+#define SPAMM_F_HEAVIEST 4 /* tensor path: hand tiles out heaviest first
+                              (longest-processing-time order) instead of
+                              row-major (a schedule the autotuner tries) */
 
 typedef struct {
     int32_t leaf;   /* leaf edge b: 16, 32 or 64; 0 selects 32            */
@@ -138,7 +139,8 @@ int spamm_multiply(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t *C,
  * any sizes (each as in spamm_multiply, Eq. 4 and Algorithm 1), with the leaf
  * products of all of them in ONE persistent kernel launch (per group of at
  * most 64 products): tiles of every product are handed out from one device
- * counter, larger products first, each product's tiles heaviest first.  The
+ * counter, larger products first, each product's tiles in row-major order
+ * (SPAMM_F_HEAVIEST: heaviest first).  The
  * paper has no batched form; this is the deployment batching of many small
  * SpAMMs onto one GPU.
  * A, B   : count handles each; A[m] and B[m] of equal n; one leaf size for
@@ -167,7 +169,7 @@ int spamm_multiply_batched(int32_t count, const spamm_mat_t *A, const spamm_mat_
 
 typedef struct {
     int32_t leaf;                      /* chosen leaf edge                      */
-    int32_t flags;                     /* chosen schedule (0 or SPAMM_F_ROWMAJOR) */
+    int32_t flags;                     /* chosen schedule (0 or SPAMM_F_HEAVIEST) */
     float ms;                          /* its device time for the batch          */
     int32_t tried;                     /* candidates timed                       */
     int32_t cand_leaf[SPAMM_TUNE_MAX];
@@ -288,7 +290,8 @@ typedef struct {
     int32_t leaf;        /* 0 selects 32                                     */
     int32_t prec;        /* spamm_prec_t of the X^2 products                 */
     int32_t slices;      /* for SPAMM_OZAKI_BF16 (0 = 7)                     */
-    int32_t flags;       /* SPAMM_F_TIMING: per-stage device times           */
+    int32_t flags;       /* SPAMM_F_TIMING: per-stage device times;
+                            SPAMM_F_NOSYM, SPAMM_F_HEAVIEST as for products */
     int32_t reserved;
 } sp2_opts_t;
 

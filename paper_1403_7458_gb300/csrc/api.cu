@@ -171,6 +171,7 @@ static void ws_free(SpammWorkspace *ws, cudaStream_t s)
     spamm_release(ws->tuseful, s);
     spamm_release(ws->toff, s);
     spamm_release(ws->torder, s);
+    spamm_release(ws->tnz, s);
     spamm_release(ws->tbins, s);
     spamm_release(ws->tlist, s);
     spamm_release(ws->counts, s);
@@ -403,7 +404,7 @@ int ws_check_errors(SpammWorkspace *ws, cudaStream_t s)
 int spamm_multiply_into(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t C,
                         const spamm_opts_t *opts, double *tr_part, cudaStream_t s,
                         bool need_total, int64_t *tasks_out, bool build_pyramid,
-                        cudaEvent_t *ev, int sym, bool slices_ready)
+                        cudaEvent_t *ev, int sym, bool slices_ready, bool zero_empty)
 {
     int prec = opts ? opts->prec : SPAMM_FP64;
     if (ev) SPAMM_CK(cudaEventRecord(ev[0], s));
@@ -430,8 +431,9 @@ int spamm_multiply_into(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t C,
         } else if ((rc = slice_operands(A, B, sl, el, symm, s, ws->stop, unit, fsplit))) {
             return rc;
         }
-        const bool heavy = !(opts && (opts->flags & SPAMM_F_ROWMAJOR));
+        const bool heavy = opts && (opts->flags & SPAMM_F_HEAVIEST);
         if ((rc = tc_tile_cull(A, B, tau, ws, symm, sl, s, heavy))) return rc;
+        if (zero_empty && (rc = tc_zero_empty_tiles(C, ws, s))) return rc;
         if (ev) SPAMM_CK(cudaEventRecord(ev[1], s));
         rc = launch_gemm_tc(A, B, C, ws, tr_part, sl, el, s, fsplit);
         if (rc) return rc;
@@ -625,7 +627,8 @@ extern "C" int spamm_multiply_batched(int32_t count, const spamm_mat_t *A, const
             rc = slice_operands(a[q], b[q], sl, el, 0, s, nullptr, unit, fsplit);
             if (rc == SPAMM_OK)
                 rc = tc_tile_cull(a[q], b[q], tau[ord[q]], w[q], 0, sl, s,
-                                  !(opts && (opts->flags & SPAMM_F_ROWMAJOR)));
+                                  opts && (opts->flags & SPAMM_F_HEAVIEST));
+            if (rc == SPAMM_OK) rc = tc_zero_empty_tiles(c[q], w[q], s);
         }
     }
     if (rc == SPAMM_OK && timing && cudaEventRecord(ev[1], s) != cudaSuccess) rc = SPAMM_E_CUDA;

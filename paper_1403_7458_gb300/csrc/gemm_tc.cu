@@ -138,14 +138,16 @@ k_tile_emit(CullArgs c, const int64_t *__restrict__ off, uint32_t *__restrict__ 
 
 constexpr int kScanThreads = 1024;
 
-// exclusive scan of counts -> off (one block), plus the total of `tasks`
+// exclusive scan of counts -> off (one block), the rank of every tile among
+// the tiles with work -> nz, plus the totals of tasks / pairs / useful pairs
 __global__ void __launch_bounds__(kScanThreads)
 k_tile_scan(const int32_t *__restrict__ stop, const int32_t *__restrict__ counts, const int32_t *__restrict__ tasks,
             const int32_t *__restrict__ pairs, const int32_t *__restrict__ useful, int64_t G,
-            int64_t *__restrict__ off, int64_t *__restrict__ task_total, int64_t *__restrict__ pair_total,
-            int64_t *__restrict__ useful_total)
+            int64_t *__restrict__ off, int32_t *__restrict__ nz, int64_t *__restrict__ task_total,
+            int64_t *__restrict__ pair_total, int64_t *__restrict__ useful_total)
 {
     __shared__ int64_t part[kScanThreads];
+    __shared__ int32_t zpart[kScanThreads];
     __shared__ int64_t tpart[kScanThreads];
     __shared__ int64_t ppart[kScanThreads];
     __shared__ int64_t upart[kScanThreads];
@@ -154,21 +156,26 @@ k_tile_scan(const int32_t *__restrict__ stop, const int32_t *__restrict__ counts
     const int64_t chunk = (G + kScanThreads - 1) / kScanThreads;
     const int64_t lo = t * chunk, hi = lo + chunk < G ? lo + chunk : G;
     int64_t s = 0, ts = 0, ps = 0, us = 0;
+    int32_t zs = 0;
     for (int64_t q = lo; q < hi; q++) {
         s += counts[q];
+        zs += counts[q] > 0;
         ts += tasks[q];
         ps += pairs[q];
         us += useful[q];
     }
     part[t] = s;
+    zpart[t] = zs;
     tpart[t] = ts;
     ppart[t] = ps;
     upart[t] = us;
     __syncthreads();
     for (int o = 1; o < kScanThreads; o <<= 1) {
         const int64_t v = t >= o ? part[t - o] : 0;
+        const int32_t z = t >= o ? zpart[t - o] : 0;
         __syncthreads();
         part[t] += v;
+        zpart[t] += z;
         __syncthreads();
     }
     for (int o = kScanThreads / 2; o > 0; o >>= 1) {
@@ -180,9 +187,12 @@ k_tile_scan(const int32_t *__restrict__ stop, const int32_t *__restrict__ counts
         __syncthreads();
     }
     int64_t run = part[t] - s;
+    int32_t zrun = zpart[t] - zs;
     for (int64_t q = lo; q < hi; q++) {
         off[q] = run;
+        nz[q] = zrun;
         run += counts[q];
+        zrun += counts[q] > 0;
     }
     if (t == kScanThreads - 1) off[G] = part[t];
     if (t == 0) {
@@ -192,14 +202,16 @@ k_tile_scan(const int32_t *__restrict__ stop, const int32_t *__restrict__ counts
     }
 }
 
-// Heaviest-first tile order (counting sort on the work-list length):
+// Hand-out orders list only the tiles with work (the rest of the order array
+// holds -1); tiles without work are never handed out.
+// Heaviest-first order (counting sort on the work-list length):
 // hist -> descending exclusive scan -> scatter.
 __global__ void k_tile_hist(const int32_t *__restrict__ stop, const int32_t *__restrict__ counts, int64_t nb,
                             int64_t G, int sym, int R, int32_t *__restrict__ bins)
 {
     if (stop && *stop) return;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < G && !(sym && t % nb < R * (t / nb))) atomicAdd(bins + counts[t], 1);
+    if (t < G && counts[t] > 0) atomicAdd(bins + counts[t], 1);
 }
 
 __global__ void k_tile_bins_scan(const int32_t *__restrict__ stop, int32_t *__restrict__ bins, int64_t nbins)
@@ -215,17 +227,35 @@ __global__ void k_tile_bins_scan(const int32_t *__restrict__ stop, int32_t *__re
     }
 }
 
-// Row-major order of the active tiles: all tiles, or in symmetric mode the
-// tiles with j >= R I (row I holds nb - R I of them).
-__global__ void k_tile_natural(int64_t nb, int64_t nI, int sym, int R, int32_t *__restrict__ order)
+// Row-major order of the tiles with work (their rank from the scan).
+__global__ void k_tile_natural(const int32_t *__restrict__ stop, const int32_t *__restrict__ counts,
+                               const int32_t *__restrict__ nz, int64_t G, int32_t *__restrict__ order)
 {
+    if (stop && *stop) return;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nI * nb) return;
-    const int64_t I = t / nb, j = t % nb;
-    if (!sym) {
-        order[t] = (int32_t)t;
-    } else if (j >= R * I) {
-        order[I * nb - R * I * (I - 1) / 2 + (j - R * I)] = (int32_t)t;
+    if (t < G && counts[t] > 0) order[nz[t]] = (int32_t)t;
+}
+
+// Zeroes the output leaves of tiles without work (they are never handed
+// out): one warp per (tile, leaf row); in symmetric mode leaf (i, j), i < j,
+// and its mirror (j, i).
+__global__ void __launch_bounds__(kWarps * 32)
+k_tile_zero(const int32_t *__restrict__ stop, const int32_t *__restrict__ counts, int64_t nb, int64_t nI, int R,
+            int sym, int b, const int32_t *__restrict__ slotC, double *__restrict__ leafC)
+{
+    if (stop && *stop) return;
+    const int64_t w = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (w >= nI * nb * R) return;
+    const int64_t t = w / R, L = w % R;
+    const int64_t I = t / nb, j = t % nb, i = (int64_t)R * I + L;
+    if (counts[t] > 0 || i >= nb || (sym && (j < (int64_t)R * I || i > j))) return;
+    const double2 z = make_double2(0.0, 0.0);
+    double2 *d = reinterpret_cast<double2 *>(leafC + (int64_t)slotC[i * nb + j] * b * b);
+    for (int q = lane; q < b * b / 2; q += 32) d[q] = z;
+    if (sym && i < j) {
+        d = reinterpret_cast<double2 *>(leafC + (int64_t)slotC[j * nb + i] * b * b);
+        for (int q = lane; q < b * b / 2; q += 32) d[q] = z;
     }
 }
 
@@ -234,7 +264,7 @@ __global__ void k_tile_scatter(const int32_t *__restrict__ stop, const int32_t *
 {
     if (stop && *stop) return;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < G && !(sym && t % nb < R * (t / nb))) order[atomicAdd(bins + counts[t], 1)] = (int32_t)t;
+    if (t < G && counts[t] > 0) order[atomicAdd(bins + counts[t], 1)] = (int32_t)t;
 }
 
 
@@ -251,8 +281,9 @@ int tc_mode_ok(int prec, int slices, int leaf)
 }
 
 // Tile cull for the tensor-core path into ws: tile lists and the order in
-// which tiles are handed out, heaviest first (tiles are taken dynamically,
-// so this is longest-processing-time-first scheduling) or row-major;
+// which tiles are handed out: row-major (consecutive tiles share their row
+// of A leaves, which then stays in L2) or heaviest first (tiles are taken
+// dynamically, so this is longest-processing-time-first scheduling);
 // toff[T + 1] receives the number of surviving triples.
 int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, int sym, int slices,
                  cudaStream_t s, bool heaviest_first)
@@ -272,7 +303,8 @@ int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, i
         spamm_release(ws->torder, s);
         spamm_release(ws->tbins, s);
         spamm_release(ws->tuseful, s);
-        ws->tcounts = ws->ttasks = ws->tpairs = ws->tuseful = ws->torder = ws->tbins = nullptr;
+        spamm_release(ws->tnz, s);
+        ws->tcounts = ws->ttasks = ws->tpairs = ws->tuseful = ws->torder = ws->tbins = ws->tnz = nullptr;
         ws->toff = nullptr;
         ws->tile_cap = 0;
         if ((rc = spamm_alloc((void **)&ws->tcounts, sizeof(int32_t) * T, s))) return rc;
@@ -281,6 +313,7 @@ int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, i
         if ((rc = spamm_alloc((void **)&ws->tuseful, sizeof(int32_t) * T, s))) return rc;
         if ((rc = spamm_alloc((void **)&ws->toff, sizeof(int64_t) * (T + 4), s))) return rc;
         if ((rc = spamm_alloc((void **)&ws->torder, sizeof(int32_t) * T, s))) return rc;
+        if ((rc = spamm_alloc((void **)&ws->tnz, sizeof(int32_t) * T, s))) return rc;
         if ((rc = spamm_alloc((void **)&ws->tbins, sizeof(int32_t) * (nb + 1), s))) return rc;
         ws->tile_cap = T;
     }
@@ -312,7 +345,7 @@ int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, i
     // toff[0..T] offsets, toff[T+1] surviving triples, toff[T+2] issued slice-pair
     // work, toff[T+3] slice pairs the surviving triples need
     k_tile_scan<<<1, kScanThreads, 0, s>>>(ws->stop, ws->tcounts, ws->ttasks, ws->tpairs, ws->tuseful, T,
-                                           ws->toff, ws->toff + T + 1, ws->toff + T + 2, ws->toff + T + 3);
+                                           ws->toff, ws->tnz, ws->toff + T + 1, ws->toff + T + 2, ws->toff + T + 3);
     SPAMM_CK_LAUNCH();
     const int64_t worst = T * nb;
     if (ws->tlist_cap < worst) {
@@ -326,6 +359,7 @@ int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, i
     SPAMM_CK_LAUNCH();
     ws->tsym = sym;
     ws->tactive = sym ? nI * nb - (int64_t)R * nI * (nI - 1) / 2 : T;
+    SPAMM_CK(cudaMemsetAsync(ws->torder, 0xFF, sizeof(int32_t) * ws->tactive, s));  // -1: no tile
     if (heaviest_first) {
         SPAMM_CK(cudaMemsetAsync(ws->tbins, 0, sizeof(int32_t) * (nb + 1), s));
         k_tile_hist<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(ws->stop, ws->tcounts, nb, T, sym, R, ws->tbins);
@@ -336,9 +370,20 @@ int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, i
                                                                      ws->torder);
         SPAMM_CK_LAUNCH();
     } else {
-        k_tile_natural<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(nb, nI, sym, R, ws->torder);
+        k_tile_natural<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(ws->stop, ws->tcounts, ws->tnz, T, ws->torder);
         SPAMM_CK_LAUNCH();
     }
+    return SPAMM_OK;
+}
+
+int tc_zero_empty_tiles(spamm_mat_t C, SpammWorkspace *ws, cudaStream_t s)
+{
+    const int R = 128 / C->b;
+    const int64_t nb = C->nb, nI = (nb + R - 1) / R;
+    const int64_t warps = nI * nb * R;
+    k_tile_zero<<<(unsigned)((warps + kWarps - 1) / kWarps), kWarps * 32, 0, s>>>(ws->stop, ws->tcounts, nb, nI, R,
+                                                                                ws->tsym, C->b, C->slot, C->leaf);
+    SPAMM_CK_LAUNCH();
     return SPAMM_OK;
 }
 
@@ -381,6 +426,9 @@ int launch_gemm_tc(spamm_mat_t A, spamm_mat_t B, spamm_mat_t C, SpammWorkspace *
         spamm_set_error("tensor-core path: diagonal traces need leaf 16 or 32 (got %d)", A->b);
         return SPAMM_E_NOTSUP;
     }
+    // diagonal leaves of tiles without work are never handed out: their
+    // traces are 0
+    if (tr_part) SPAMM_CK(cudaMemsetAsync(tr_part, 0, sizeof(double) * A->nb, s));
     thread_local tc::TcArgs a;  // large (one table entry used); host-side staging only
     fill_prob(a.p[0], A, B, C, ws, tr_part, 0);
     a.nprob = 1;

@@ -36,7 +36,8 @@ struct SpammWorkspace {
     int32_t *tpairs = nullptr;   // slice-pair work per tile (sum of m(m+1)/2)
     int32_t *tuseful = nullptr;  // slice pairs the tile's surviving triples need
     int64_t *toff = nullptr;     // T + 2: offsets, then the triple total
-    int32_t *torder = nullptr;   // heaviest-first tile order
+    int32_t *torder = nullptr;   // tile hand-out order (row-major or heaviest first), tiles with work only, then -1
+    int32_t *tnz = nullptr;      // rank of each tile among the tiles with work
     int32_t *tbins = nullptr;    // nb + 1 histogram bins
     uint32_t *tlist = nullptr;   // k | mask << 15 | zA << 23 | zB << 26
     int64_t tile_cap = 0, tlist_cap = 0;
@@ -127,10 +128,12 @@ int ws_reserve_groups(SpammWorkspace *ws, int64_t groups, int64_t nb, cudaStream
 // C's upper norm tiers.
 // sym: A == B is exactly symmetric; the tensor-core path then forms only the
 // upper block triangle of C and mirrors it (bit-identical, half the work).
+// zero_empty = false (tensor path): leaves of tiles without work are left
+// unwritten; the caller treats them as zero through ws->toff (SP2 does).
 int spamm_multiply_into(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t C,
                         const spamm_opts_t *opts, double *tr_part, cudaStream_t s,
                         bool need_total, int64_t *tasks_out, bool build_pyramid,
-                        cudaEvent_t *ev, int sym = 0, bool slices_ready = false);
+                        cudaEvent_t *ev, int sym = 0, bool slices_ready = false, bool zero_empty = true);
 
 // Read and clear the device-side error words of a product (blocking).
 int ws_check_errors(SpammWorkspace *ws, cudaStream_t s);
@@ -165,7 +168,9 @@ static inline int prec_elem(int prec) { return (prec == SPAMM_TF32 || prec == SP
 constexpr int32_t kFlagUnitScale = 1 << 30;
 int slices_alloc(spamm_mat_t m, int s, int e, bool tile_a, bool per_leaf, cudaStream_t st);
 int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, int sym, int slices,
-                 cudaStream_t s, bool heaviest_first = true);
+                 cudaStream_t s, bool heaviest_first = false);
+// Zero the output leaves of tiles without work (never handed out).
+int tc_zero_empty_tiles(spamm_mat_t C, SpammWorkspace *ws, cudaStream_t s);
 int launch_gemm_tc(spamm_mat_t A, spamm_mat_t B, spamm_mat_t C, SpammWorkspace *ws,
                    double *tr_part, int slices, int e, cudaStream_t s, bool float_split = false);
 // One launch over the products m < count (count <= kMaxBatch) whose tile

@@ -210,6 +210,10 @@ __device__ void sp2_finish(int mode, const double *idem_part, const double *diag
 // Elementwise pass over all leaves of X, one warp per leaf.
 //   mode 0: X <- (emax I - F) / (emax - emin)          (src = F)
 //   mode 1: X <- X2 if branch else 2 X - X2            (src = X2)
+// In mode 1 with x2off (the tensor path's tile offsets of X2's product, R
+// leaf rows per tile, symmetric or not), a leaf of X2 whose tile had no work
+// is zero and was not written: it is not read, and a leaf that is zero in
+// both X (squared norm 0) and X2 stays zero without being touched.
 // Writes the leaf's squared norm (exact, once rounded), its partial
 // ||X2 - X||^2 (mode 1) and, for diagonal leaves, its trace.  The last block
 // reduces the partials and stores e and the new trace in the state.
@@ -217,7 +221,8 @@ __global__ void __launch_bounds__(kWarps * 32)
 k_sp2_elementwise(int mode, double *__restrict__ X, const double *__restrict__ src,
                   const int32_t *__restrict__ slot, int64_t n, int64_t nb, int64_t P, int b,
                   double *__restrict__ n2, double *__restrict__ n2T, double *__restrict__ idem_part,
-                  double *__restrict__ diag_part, Sp2State *st, Sp2Rule rule, double *__restrict__ hist)
+                  double *__restrict__ diag_part, Sp2State *st, Sp2Rule rule, double *__restrict__ hist,
+                  const int64_t *__restrict__ x2off, int R, int sym)
 {
     __shared__ double sred[kWarps * 32];
     __shared__ bool s_last;
@@ -233,10 +238,23 @@ k_sp2_elementwise(int mode, double *__restrict__ X, const double *__restrict__ s
         double *x = X + base;
         const double *y = src + base;
         const bool diag = I == K;
+        bool y0 = false;  // X2 leaf known to be zero
+        if (mode == 1 && x2off) {
+            const int64_t a = (sym && I > K) ? K : I, c = (sym && I > K) ? I : K;
+            const int64_t t = (a / R) * nb + c;
+            y0 = x2off[t + 1] == x2off[t];
+        }
+        // X_new = X2 or 2X - X2 = 0 with X = 0 = X2: nothing to read or write
+        const bool untouched = y0 && n2[I * P + K] == 0.0;
+        if (untouched && lane == 0) {
+            idem_part[w] = 0.0;
+            if (diag) diag_part[I] = 0.0;
+        }
+        if (!untouched) {
         double idem = 0.0;
         int ek = 0;
         for (int q = lane; q < bb; q += 32) {
-            double yv = y[q], nv;
+            double yv = y0 ? 0.0 : y[q], nv;
             if (mode == 0) {
                 const int r = q / b;
                 nv = ((diag && r == q % b && I * b + r < n) ? emax : 0.0) - yv;
@@ -270,6 +288,7 @@ k_sp2_elementwise(int mode, double *__restrict__ X, const double *__restrict__ s
             idem_part[w] = idem;
             if (diag) diag_part[I] = dsum;
         }
+        }  // !untouched
     }
     sp2_finish(mode, idem_part, diag_part, nb, st, rule, hist, sred, &s_last);
 }
@@ -374,9 +393,10 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
     mo.leaf = F->b;
     mo.prec = o.prec;
     mo.slices = o.slices;
-    mo.flags = kFlagUnitScale;  // iterates satisfy |x_ij| <= ||X||_2 < 2
+    mo.flags = kFlagUnitScale | (o.flags & SPAMM_F_HEAVIEST);  // iterates satisfy |x_ij| <= ||X||_2 < 2
     const int limit = o.fixed_iters > 0 ? o.fixed_iters : o.max_iter;
     const bool coarse = nb >= kCoarseMinNb;
+    const bool tcpath = prec_is_tc(o.prec);  // X2's tiles without work are left unwritten
     unsigned ew_blocks = (unsigned)((G + kWarps - 1) / kWarps);
 
 #define SP2_TRY(x)                 \
@@ -434,7 +454,7 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
     k_sp2_elementwise<<<ew_blocks, kWarps * 32, 0, s>>>(0, X->leaf, F->leaf, X->slot, F->n, nb, X->P, X->b,
                                                         X->n2 + tier_offset(X->depth), X->n2T,
                                                         sc.idem_part, sc.diag_part, sc.st,
-                                                        Sp2Rule{Ne, 0, 0, 0, 1}, sc.hist);
+                                                        Sp2Rule{Ne, 0, 0, 0, 1}, sc.hist, nullptr, 1, 0);
     SP2_LAUNCHED();
     // upper tiers of the iterate: the cull's early skip reads them (rebuilt
     // only where the skip pays; otherwise marked stale and not used)
@@ -452,13 +472,14 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
             for (int q = 0; q < batch; q++) {
                 cudaEvent_t *ev = timing ? evs + 5 * q : nullptr;
                 SP2_TRY(spamm_multiply_into(X, X, tau, X2, &mo, sc.tr_part, s, false, nullptr, false, ev,
-                                            sym ? 1 : 0));
+                                            sym ? 1 : 0, false, !tcpath));
+                const int64_t *x2off = tcpath ? X2->ws.toff : nullptr;
                 k_sp2_decide<<<1, kRedThreads, 0, s>>>(sc.tr_part, nb, X2->ws.task_total, X2->ws.pair_units, Ne,
                                                        o.rule, sc.st);
                 SP2_LAUNCHED();
                 k_sp2_elementwise<<<ew_blocks, kWarps * 32, 0, s>>>(
                     1, X->leaf, X2->leaf, X->slot, F->n, nb, X->P, X->b, X->n2 + tier_offset(X->depth),
-                    X->n2T, sc.idem_part, sc.diag_part, sc.st, rule, sc.hist);
+                    X->n2T, sc.idem_part, sc.diag_part, sc.st, rule, sc.hist, x2off, 128 / X->b, sym ? 1 : 0);
                 SP2_LAUNCHED();
                 if (coarse) SP2_TRY(launch_pyramid(X, s));
                 if (timing) SP2_CUDA(cudaEventRecord(ev[4], s));

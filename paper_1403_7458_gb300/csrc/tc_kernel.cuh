@@ -209,7 +209,7 @@ struct TcProb {
     double *leafC;
     const int64_t *off;    // tile work-list offsets
     const uint32_t *list;  // work items
-    const int32_t *order;  // tile order (tile ids of this product)
+    const int32_t *order;  // tile order (tile ids of this product; -1 after the tiles with work)
     const int32_t *sigA;   // sigma of A
     const int32_t *sigB;
     double *tr_part;       // diagonal-leaf traces (may be null; b = 32 only)
@@ -332,10 +332,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                 if (!mbar_wait(smem_u32(&tempty_bar[tq]), tph ^ 1, abort_v)) {
                     tgood = 0;
                 } else {
-                    const int32_t pos = atomicAdd(g.next_tile, 1);
-                    if (pos < T) {
+                    for (;;) {
+                        const int32_t pos = atomicAdd(g.next_tile, 1);
+                        if (pos >= T) break;
                         const int mp = find_prob(g, pos);
-                        tt = (mp << 24) | g.p[mp].order[pos - g.p[mp].pos0];
+                        const int32_t o = g.p[mp].order[pos - g.p[mp].pos0];
+                        if (o >= 0) {
+                            tt = (mp << 24) | o;
+                            break;
+                        }
+                        // the rest of this product's order holds no tile with
+                        // work: move the counter past it (positions only grow)
+                        atomicMax(g.next_tile, (int32_t)(mp + 1 < g.nprob ? g.p[mp + 1].pos0 : T));
                     }
                     tile_q[tq] = tt;
                     mbar_arrive(smem_u32(&tfull_bar[tq]));

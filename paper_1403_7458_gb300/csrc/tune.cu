@@ -46,7 +46,7 @@ extern "C" int spamm_autotune_batched(int32_t count, const double *const *a, con
     memset(&o, 0, sizeof(o));
     if (opts) o = *opts;
     const int prec = o.prec;
-    const int base_flags = o.flags & ~(SPAMM_F_TIMING | SPAMM_F_ROWMAJOR);
+    const int base_flags = o.flags & ~(SPAMM_F_TIMING | SPAMM_F_HEAVIEST);
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -64,7 +64,7 @@ extern "C" int spamm_autotune_batched(int32_t count, const double *const *a, con
         if (!built) {
             for (int sc = 0; sc < nsched && out->tried < SPAMM_TUNE_MAX; sc++) {
                 out->cand_leaf[out->tried] = leaf;
-                out->cand_flags[out->tried] = sc ? SPAMM_F_ROWMAJOR : 0;
+                out->cand_flags[out->tried] = sc ? SPAMM_F_HEAVIEST : 0;
                 out->cand_ms[out->tried] = -1.f;
                 out->tried++;
             }
@@ -81,7 +81,7 @@ extern "C" int spamm_autotune_batched(int32_t count, const double *const *a, con
             }
         }
         for (int sc = 0; sc < nsched && rc == SPAMM_OK; sc++) {
-            bo.flags = base_flags | (sc ? SPAMM_F_ROWMAJOR : 0);
+            bo.flags = base_flags | (sc ? SPAMM_F_HEAVIEST : 0);
             spamm_stats_t st;
             rc = spamm_multiply_batched(count, h.A.data(), h.B.data(), tau, h.C.data(), &bo, &st, stream);
             std::vector<float> ts;
@@ -101,7 +101,7 @@ extern "C" int spamm_autotune_batched(int32_t count, const double *const *a, con
             const float med = ts[ts.size() / 2];
             if (out->tried < SPAMM_TUNE_MAX) {
                 out->cand_leaf[out->tried] = leaf;
-                out->cand_flags[out->tried] = bo.flags & SPAMM_F_ROWMAJOR;
+                out->cand_flags[out->tried] = bo.flags & SPAMM_F_HEAVIEST;
                 out->cand_ms[out->tried] = med;
                 out->cand_tasks[out->tried] = st.tasks;
                 out->tried++;
@@ -109,7 +109,7 @@ extern "C" int spamm_autotune_batched(int32_t count, const double *const *a, con
             if (med < best) {
                 best = med;
                 out->leaf = leaf;
-                out->flags = bo.flags & SPAMM_F_ROWMAJOR;
+                out->flags = bo.flags & SPAMM_F_HEAVIEST;
                 out->ms = med;
             }
         }

@@ -27,7 +27,7 @@ OK, E_INVAL, E_NOMEM, E_CUDA, E_CAPACITY, E_TIMEOUT, E_NOCONV, E_NOTSUP = 0, -1,
 FP64, OZAKI_BF16, BF16, BF16X3, TF32, TF32X3 = 0, 1, 2, 3, 4, 5
 F_TIMING = 1
 F_NOSYM = 2
-F_ROWMAJOR = 4
+F_HEAVIEST = 4
 TUNE_MAX = 6
 RULE_TRACE_DISTANCE, RULE_TRACE_ABOVE = 0, 1
 STOP_CONVERGED, STOP_STAGNATED, STOP_FIXED, STOP_MAXITER = 0, 1, 2, 3
@@ -333,10 +333,10 @@ def cull_noalloc(n2a, n2b, nb: int, tau: float, off, klist, stream=None):
 def sp2_solve(F: Matrix, ne: float, tau: float, P: Matrix | None = None, max_iter: int = 100,
               rule: int = RULE_TRACE_DISTANCE, trace_tol: float = 1e-10, idem_tol: float = 1e-8,
               fixed_iters: int = 0, prec: int = FP64, slices: int = 0, timing: bool = False,
-              symmetric: bool = True, stream=None):
+              symmetric: bool = True, stream=None, flags: int = 0):
     """P = SP2(F, Ne, tau).  Returns (P, report dict with a 'history' array)."""
     opts = _Sp2Opts(max_iter, rule, trace_tol, idem_tol, fixed_iters, F.leaf, prec, slices,
-                    (F_TIMING if timing else 0) | (0 if symmetric else F_NOSYM), 0)
+                    flags | (F_TIMING if timing else 0) | (0 if symmetric else F_NOSYM), 0)
     cap = fixed_iters if fixed_iters > 0 else max_iter
     hist = np.zeros((max(cap, 1), H_COLS))
     rep = _Sp2Report()

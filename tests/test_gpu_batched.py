@@ -144,7 +144,7 @@ def test_batched_bad_arguments(cuda_lib):
     assert out == [] and st["tasks"] == 0
 
 
-def test_row_major_schedule_gives_identical_results(cuda_lib):
+def test_heaviest_first_schedule_gives_identical_results(cuda_lib):
     """The tile schedule changes only the order in which tiles are handed
     out, never the arithmetic of a tile."""
     mats = _batch([300, 200], 32, seed0=21)
@@ -152,7 +152,7 @@ def test_row_major_schedule_gives_identical_results(cuda_lib):
     B = [cuda_lib.tree_build(_dev(b), leaf=32) for _, b in mats]
     for prec in (cuda_lib.OZAKI_BF16, cuda_lib.TF32):
         C1, _ = cuda_lib.multiply_batched(A, B, 1e-6, prec=prec)
-        C2, _ = cuda_lib.multiply_batched(A, B, 1e-6, prec=prec, flags=cuda_lib.F_ROWMAJOR)
+        C2, _ = cuda_lib.multiply_batched(A, B, 1e-6, prec=prec, flags=cuda_lib.F_HEAVIEST)
         for x, y in zip(C1, C2):
             assert np.array_equal(cuda_lib.to_dense(x).cpu().numpy(), cuda_lib.to_dense(y).cpu().numpy())
 

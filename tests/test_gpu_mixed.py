@@ -277,3 +277,29 @@ def test_tile_cull_counts_match_oracle_with_early_skip(cuda_lib, prec_name, leaf
     assert st["tasks"] == want_ab
     _, st = cuda_lib.multiply(A, A, tau, prec=prec, slices=slices, stats=True)
     assert st["tasks"] == want_aa
+
+
+@pytest.mark.parametrize("prec_name,leaf", [("OZAKI_BF16", 32), ("TF32", 64), ("BF16X3", 16)])
+def test_tiles_without_work_are_zero_in_a_reused_output(cuda_lib, prec_name, leaf):
+    """Tiles without work are never handed out; their output leaves are
+    zeroed by a separate pass.  Reuse an output that held a dense product
+    and check that a sparse product overwrites every leaf."""
+    n = 1000
+    h = synth.tb_hamiltonian(n, 8, decay=1.0)
+    A = cuda_lib.tree_build(_dev(h), leaf=leaf)
+    prec = getattr(cuda_lib, prec_name)
+    C, _ = cuda_lib.multiply(A, A, 0.0, prec=prec)               # every tile has work
+    assert np.count_nonzero(cuda_lib.to_dense(C).cpu().numpy()) > 0.5 * n * n
+    C, st = cuda_lib.multiply(A, A, 1e-3, C=C, prec=prec, stats=True)  # most tiles empty
+    got = cuda_lib.to_dense(C).cpu().numpy()
+    ref, tasks = oracle.spamm(h, h, leaf, 1e-3, want_tasks=True)
+    assert st["tasks"] == len(tasks)
+    nb = -(-n // leaf)
+    has = np.zeros((nb, nb), dtype=bool)
+    has[tasks[:, 0], tasks[:, 2]] = True
+    mask = np.kron(has, np.ones((leaf, leaf), dtype=bool))[:n, :n]
+    assert not np.any(got[~mask])                                 # leaves without tasks: exactly 0
+    absab, K = _kept_abs_product(h, h, leaf, tasks)
+    # the rest: the product (loose: each mode's own bound is tested elsewhere;
+    # exact slices err in absolute terms, float splits in relative terms)
+    assert np.all(np.abs(got - ref) <= 0.02 * absab + 1e-9 * absab.max())
