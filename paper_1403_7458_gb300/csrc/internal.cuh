@@ -335,14 +335,28 @@ __device__ __forceinline__ uint16_t slice_digit_bf16(uint64_t X, bool neg, int p
     return (uint16_t)(__float_as_uint(f) >> 16);
 }
 
-// Offset (elements) of leaf element (r, c) inside one slice of the A-role
-// core-matrix layout of a B x B leaf with E-byte elements:
-// [g = r/8][cc = c/ce][r%8][c%ce], ce = 16/E elements per 16-byte row.
+// Layout of one slice of a B x B leaf with E-byte elements, as the tcgen05
+// K-major operand wants it: row r of the leaf (M or N index) holds its
+// B E bytes of K (= columns c); rows come in groups of 8 (stride 8 B E
+// bytes, the descriptor's stride offset); within a group the K bytes are cut
+// into swizzle atoms of AW = min(B E, 128) bytes (8 rows x AW bytes each,
+// atoms along K adjacent), and inside an atom the 16-byte chunk index of row
+// r8 is XOR-permuted by the row bits (the 32-, 64- and 128-byte swizzle
+// modes).  Byte offset of element (r, c):
 template <int B, int E>
-__device__ __forceinline__ int slice_offset(int r, int c)
+__host__ __device__ constexpr int slice_atom_bytes() { return B * E < 128 ? B * E : 128; }
+
+template <int B, int E>
+__device__ __forceinline__ int slice_byte_offset(int r, int c)
 {
-    constexpr int ce = 16 / E;
-    return (r >> 3) * (8 * B) + (c / ce) * (8 * ce) + (r & 7) * ce + (c % ce);
+    constexpr int RB = B * E, AW = slice_atom_bytes<B, E>();
+    const int cb = c * E, katom = cb / AW, inb = cb % AW;
+    const int chunk = inb >> 4, r8 = r & 7;
+    int sw;
+    if (AW == 128) sw = chunk ^ r8;                 // 128-byte swizzle
+    else if (AW == 64) sw = chunk ^ ((r8 >> 1) & 3);  // 64-byte swizzle
+    else sw = chunk ^ ((r8 >> 2) & 1);              // 32-byte swizzle
+    return (r >> 3) * (8 * RB) + katom * (8 * AW) + r8 * AW + sw * 16 + (inb & 15);
 }
 
 // The culling predicate of Eq. 4 on squared norms, n2a * n2b > tau2, decided

@@ -12,12 +12,12 @@
 // Float splits instead store s_0 = round(x), s_1 = round(x - s_0), ... in
 // BF16 or TF32 (round to nearest), for the low-precision modes.
 //
-// Two layouts per b x b leaf (b = 16, 32, 64), both slice-major and made of
-// "core matrices" of 8 rows x 16 bytes (8 x 8 BF16 or 8 x 4 TF32) as the
-// tcgen05 K-major operand wants; slice p occupies bytes [p b^2 e, (p+1) b^2 e)
-// for e-byte elements, ce = 16 / e elements per core-matrix row:
-//   A role : [p][g = r/8][cc = l/ce][8 x ce]   rows r of the leaf, K = columns l
-//   B role : [q][g = c/8][cc = l/ce][8 x ce]   N = columns c, K = rows l
+// Two layouts per b x b leaf (b = 16, 32, 64), both slice-major and each
+// slice in the tcgen05 K-major swizzled layout (slice_byte_offset: 8-row
+// groups, 32/64/128-byte swizzle atoms along K); slice p occupies bytes
+// [p b^2 e, (p+1) b^2 e) for e-byte elements:
+//   A role : rows r of the leaf, K = columns l
+//   B role : rows = columns c of the leaf (N), K = rows l
 // The B-role image of leaf (k, j) equals the A-role image of its transpose,
 // so for a symmetric matrix the A-role array serves both operands.  The
 // tile-major A array puts the R = 128 / b leaves (i, k), i = R I .. R I + R-1,
@@ -139,7 +139,8 @@ k_slice(const int32_t *__restrict__ stop, const double *__restrict__ leaf, const
             if (!float_split && (X > (1ull << (7 * S)) || !(fabs(x) <= 1e300))) atomicExch(overflow, 1);
             double rest = x;  // float split: s_p = round(x - s_0 - ... - s_{p-1})
             // [p][g][cc][8 x ce]; transposed: element (r, l) stored as (l, r)
-            const int o = (perleaf_transposed && perleaf) ? slice_offset<B, E>(l, r) : slice_offset<B, E>(r, l);
+            const int o = ((perleaf_transposed && perleaf) ? slice_byte_offset<B, E>(l, r)
+                                                           : slice_byte_offset<B, E>(r, l)) / E;
 #pragma unroll
             for (int p = 0; p < S; p++) sa[p * B * B + o] = (W)slice_elem<E>(X, neg, p, S, float_split, rest);
         }

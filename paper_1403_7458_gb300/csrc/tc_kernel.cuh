@@ -134,11 +134,17 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
         : "memory");
 }
 
-// tcgen05 shared-memory descriptor: no swizzle, K-major core matrices.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+// tcgen05 shared-memory descriptor of a K-major swizzled operand: start
+// address, leading offset (unused by swizzled K-major layouts: 16 B), stride
+// offset (8-row groups), version 1, swizzle mode for an atom of AW bytes
+// (128 B: 2, 64 B: 4, 32 B: 6).  The atom's base is aligned to its repeat
+// (8 AW bytes), so the base-offset field stays 0.
+template <int AW>
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t sbo)
 {
-    return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+    constexpr uint64_t mode = AW == 128 ? 2 : AW == 64 ? 4 : 6;
+    return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) |
+           ((uint64_t)1 << 46) | (mode << 61);
 }
 
 // instruction descriptor: FP32 accumulator (bit 4), A and B types (bits 7
@@ -264,7 +270,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
 {
     constexpr int R = 128 / B;                  // leaf rows per tile
     constexpr uint32_t kSlice = B * B * E;      // one slice of one leaf (bytes)
-    constexpr uint32_t kSBO = 8 * B * E;        // 8-row core-matrix group stride
+    constexpr uint32_t kSBO = 8 * B * E;        // 8-row group stride
+    constexpr uint32_t kAW = slice_atom_bytes<B, E>();  // swizzle atom width (bytes)
     constexpr int kMmaK = B * E / 32;           // instructions per slice pair
     constexpr uint32_t kFull = (1u << R) - 1;
     static_assert(S * B <= (int)kAccStride, "accumulator exceeds its TMEM columns");
@@ -311,7 +318,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_holder;
-    const uint32_t sbase = smem_u32(smem);
+    // the ring starts on a 1 KB boundary: swizzle atoms (up to 8 rows x 128 B)
+    // must sit at addresses aligned to their repeat
+    const uint32_t sraw = smem_u32(smem);
+    const uint32_t sbase = (sraw + 1023u) & ~1023u;
+    uint8_t *const ring = smem + (sbase - sraw);
     volatile int *abort_v = &abort_flag;
 
     if (warp == 0) {
@@ -495,7 +506,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                     for (int L = 0; L < R; L++) {
                         if (mask & (1u << L)) continue;
                         for (int pp = 0; pp < m; pp++) {
-                            uint4 *z = reinterpret_cast<uint4 *>(smem + pos + (pp * R + L) * kSlice);
+                            uint4 *z = reinterpret_cast<uint4 *>(ring + pos + (pp * R + L) * kSlice);
 #pragma unroll
                             for (int q = 0; q < (int)(kSlice / 512); q++) z[q * 32 + lane] = zero4;
                         }
@@ -509,15 +520,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                     const uint32_t sb = sa + (uint32_t)m * R * kSlice;      // B slice zb
                     // descriptors advance by adding (bytes >> 4) to the address field
                     // (shared addresses stay below 256 KB, so the field never carries)
-                    const uint64_t da0 = smem_desc(sa, 128, kSBO);
-                    const uint64_t db0 = smem_desc(sb, 128, kSBO);
+                    const uint64_t da0 = smem_desc<kAW>(sa, kSBO);
+                    const uint64_t db0 = smem_desc<kAW>(sb, kSBO);
                     uint32_t idesc = mma_idesc<E>(128, B * m);
                     uint32_t dcol = dacc + B * (za + zb);
                     for (int pp = 0; pp < m; pp++) {
                         const uint64_t da = da0 + (uint64_t)(pp * (R * kSlice / 16));
 #pragma unroll
-                        for (int h = 0; h < kMmaK; h++)  // 32 bytes of K each: +256 B (two core matrices)
-                            mma_issue<E>(dcol, da + 16 * h, db0 + 16 * h, idesc);
+                        for (int h = 0; h < kMmaK; h++) {
+                            // 32 bytes of K each: inside a swizzle atom the start
+                            // address moves by 32 B, across atoms by 8 AW bytes
+                            const uint32_t kb = (uint32_t)(32 * h);
+                            const uint64_t adv = ((kb / kAW) * 8 * kAW + kb % kAW) >> 4;
+                            mma_issue<E>(dcol, da + adv, db0 + adv, idesc);
+                        }
                         idesc -= (uint32_t)(B >> 3) << 17;  // N shrinks by b
                         dcol += B;
                     }
@@ -672,7 +688,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
 template <int S, int E, int B>
 int launch_k(const TcArgs &a, cudaStream_t s)
 {
-    const size_t smem = kRingBytes;
+    const size_t smem = kRingBytes + 1024;  // + alignment slack of the ring
     static int configured = 0;
     if (!configured) {
         SPAMM_CK(cudaFuncSetAttribute(k_gemm_tc<S, E, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
