@@ -34,17 +34,19 @@
 // from one device counter over the concatenated orders, so one persistent
 // launch serves many independent SpAMMs.
 //
-// Kernel roles (192 threads, one CTA per SM, persistent):
+// Kernel roles (224 threads, one CTA per SM, persistent):
 //   warp 0     : producer; two bulk copies (cp.async.bulk) per work item:
 //                the needed slices of the R A leaves (one contiguous block of
 //                the tile-major array, stage layout [p][leaf][slice]) and of
 //                the B leaf, into a shared-memory byte ring, completion on
 //                the item's mbarrier;
-//   warp 1     : allocates 512 TMEM columns; once an item lands, the warp
-//                zeroes the leaves of culled triples in it, then lane 0
-//                issues the tcgen05.mma of the item and commits to the
-//                item's "empty" barrier and, at the end of a tile, to the
-//                accumulator's "full" barrier;
+//   warp 6     : prep; once an item lands, zeroes the leaves of culled
+//                triples in it and marks it ready (so the MMA issuer never
+//                stalls on shared-memory stores);
+//   warp 1     : allocates 512 TMEM columns; lane 0 issues the tcgen05.mma
+//                of each ready item and commits to the item's "empty"
+//                barrier and, at the end of a tile, to the accumulator's
+//                "full" barrier;
 //   warps 2-5  : epilogue; tcgen05.ld of the s diagonal blocks of the row the
 //                thread owns, combine, FP64 store, diagonal traces.
 // Two accumulators (TMEM columns 0 and 256) let the epilogue of one tile run
@@ -66,7 +68,7 @@ namespace tc {
 // zero slices) leave room for more items in flight.
 constexpr uint32_t kRingBytes = 216 * 1024;
 constexpr int kSlots = 16;  // work items in flight at most
-constexpr int kThreads = 192;
+constexpr int kThreads = 224;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kAccStride = 256;
 constexpr long long kTimeoutCycles = 8000000000ll;  // about 4 s at 2 GHz per wait
@@ -277,7 +279,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
     static_assert(S * B <= (int)kAccStride, "accumulator exceeds its TMEM columns");
     static_assert((uint32_t)S * (R + 1) * kSlice <= kRingBytes, "work item exceeds the ring");
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ __align__(8) uint64_t full_bar[kSlots], empty_bar[kSlots];
+    __shared__ __align__(8) uint64_t full_bar[kSlots], ready_bar[kSlots], empty_bar[kSlots];
     __shared__ __align__(8) uint64_t accf_bar[2], acce_bar[2], done_bar;
     __shared__ uint32_t slot_off[kSlots];  // ring byte offset of each in-flight item
     __shared__ uint32_t slot_w[kSlots];    // its work-list entry
@@ -293,6 +295,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
     if (threadIdx.x == 0) {
         for (int q = 0; q < kSlots; q++) {
             mbar_init(smem_u32(&full_bar[q]), 1);
+            mbar_init(smem_u32(&ready_bar[q]), 1);
             mbar_init(smem_u32(&empty_bar[q]), 1);
         }
         for (int q = 0; q < 2; q++) {
@@ -302,7 +305,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
         mbar_init(smem_u32(&done_bar), 1);
         for (int q = 0; q < kTileRing; q++) {
             mbar_init(smem_u32(&tfull_bar[q]), 1);
-            mbar_init(smem_u32(&tempty_bar[q]), 5);  // MMA warp + four epilogue warps
+            mbar_init(smem_u32(&tempty_bar[q]), 6);  // MMA, prep and four epilogue warps
         }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -448,9 +451,91 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
         __syncwarp();
     } else if (warp == 1) {
         // ------------------------------ MMA issuer ------------------------------
-        // Lane 0 issues; the whole warp zeroes the leaves of culled triples in
-        // a landed item before the MMAs read it.
-        uint32_t consumed = 0, acc = 0, aph = 0;
+        // Lane 0 alone: waits until the prep warp has made an item ready, then
+        // issues its MMAs and commits them to the item's "empty" barrier and,
+        // at the end of a tile, to the accumulator's "full" barrier.
+        if (lane == 0) {
+            uint32_t consumed = 0, acc = 0, aph = 0;
+            bool ok = true;
+            uint32_t tq = 0, tph = 0;
+            for (;;) {
+                if (!mbar_wait(smem_u32(&tfull_bar[tq]), tph, abort_v)) {
+                    ok = false;
+                    break;
+                }
+                const int32_t tt = tile_q[tq];
+                mbar_arrive(smem_u32(&tempty_bar[tq]));
+                if (++tq == kTileRing) {
+                    tq = 0;
+                    tph ^= 1;
+                }
+                if (tt < 0) break;
+                const TcProb &P = g.p[tt >> 24];
+                const int64_t t = tt & 0xFFFFFF;
+                // the accumulator was zeroed by the epilogue (phase u of its barrier)
+                if (!mbar_wait(smem_u32(&acce_bar[acc]), aph, abort_v)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t dacc = tmem + acc * kAccStride;
+                const int64_t e1 = P.off[t + 1];
+                for (int64_t e = P.off[t]; e < e1; e++) {
+                    const uint32_t sl = consumed % kSlots;
+                    if (!mbar_wait(smem_u32(&ready_bar[sl]), (consumed / kSlots) & 1, abort_v)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t w = slot_w[sl], pos = slot_off[sl];
+                    const int za = item_za(w), zb = item_zb(w);
+                    const int m = S - za - zb;
+                    const uint32_t sa = sbase + pos;                        // A slice za
+                    const uint32_t sb = sa + (uint32_t)m * R * kSlice;      // B slice zb
+                    // descriptors advance by adding (bytes >> 4) to the address field
+                    // (shared addresses stay below 256 KB, so the field never carries)
+                    const uint64_t da0 = smem_desc<kAW>(sa, kSBO);
+                    const uint64_t db0 = smem_desc<kAW>(sb, kSBO);
+                    uint32_t idesc = mma_idesc<E>(128, B * m);
+                    uint32_t dcol = dacc + B * (za + zb);
+                    for (int pp = 0; pp < m; pp++) {
+                        const uint64_t da = da0 + (uint64_t)(pp * (R * kSlice / 16));
+#pragma unroll
+                        for (int h = 0; h < kMmaK; h++) {
+                            // 32 bytes of K each: inside a swizzle atom the start
+                            // address moves by 32 B, across atoms by 8 AW bytes
+                            const uint32_t kb = (uint32_t)(32 * h);
+                            const uint64_t adv = ((kb / kAW) * 8 * kAW + kb % kAW) >> 4;
+                            mma_issue<E>(dcol, da + adv, db0 + adv, idesc);
+                        }
+                        idesc -= (uint32_t)(B >> 3) << 17;  // N shrinks by b
+                        dcol += B;
+                    }
+                    mma_commit(smem_u32(&empty_bar[sl]));
+                    consumed++;
+                }
+                if (!ok) break;
+                mma_commit(smem_u32(&accf_bar[acc]));
+                if (++acc == 2) {
+                    acc = 0;
+                    aph ^= 1;
+                }
+            }
+            if (!ok) {
+                atomicExch(g.err, 1);
+                abort_flag = 1;
+            }
+            // all MMAs issued by this thread complete before TMEM is freed
+            mma_commit(smem_u32(&done_bar));
+            mbar_wait(smem_u32(&done_bar), 0, abort_v);
+        }
+        __syncwarp();
+    } else if (warp == 6) {
+        // ------------------------------ prep ------------------------------
+        // Once an item lands, the warp zeroes the leaves of culled triples in
+        // it (generic-proxy stores made visible to the tensor core's async
+        // proxy by fence.proxy.async) and marks the item ready.
+        uint32_t consumed = 0;
         bool ok = true;
         uint32_t tq = 0, tph = 0;
         for (;;) {
@@ -475,32 +560,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
             if (tt < 0) break;
             const TcProb &P = g.p[tt >> 24];
             const int64_t t = tt & 0xFFFFFF;
-            // the accumulator was zeroed by the epilogue (phase u of its barrier)
-            int good = 1;
-            if (lane == 0) good = mbar_wait(smem_u32(&acce_bar[acc]), aph, abort_v);
-            if (!__shfl_sync(0xffffffffu, good, 0)) {
-                ok = false;
-                break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t dacc = tmem + acc * kAccStride;
             const int64_t e1 = P.off[t + 1];
             for (int64_t e = P.off[t]; e < e1; e++) {
                 const uint32_t sl = consumed % kSlots;
-                good = 1;
+                int good = 1;
                 if (lane == 0) good = mbar_wait(smem_u32(&full_bar[sl]), (consumed / kSlots) & 1, abort_v);
                 if (!__shfl_sync(0xffffffffu, good, 0)) {
                     ok = false;
                     break;
                 }
-                // lane 0 observed the landed data (and the slot's metadata);
-                // hand both to the other lanes
+                // lane 0 observed the landed data and the item's metadata
+                // (written before the arrive that released them); the warp
+                // barrier orders the other lanes' reads after that observation
                 __syncwarp();
-                const uint32_t w = __shfl_sync(0xffffffffu, lane == 0 ? slot_w[sl] : 0u, 0);
-                const uint32_t pos = __shfl_sync(0xffffffffu, lane == 0 ? slot_off[sl] : 0u, 0);
+                const uint32_t w = slot_w[sl], pos = slot_off[sl];
                 const uint32_t mask = item_mask(w);
-                const int za = item_za(w), zb = item_zb(w);
-                const int m = S - za - zb;
+                const int m = S - item_za(w) - item_zb(w);
                 if (mask != kFull) {
                     const uint4 zero4 = make_uint4(0, 0, 0, 0);
                     for (int L = 0; L < R; L++) {
@@ -514,52 +589,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 }
                 __syncwarp();
-                if (lane == 0) {
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t sa = sbase + pos;                        // A slice za
-                    const uint32_t sb = sa + (uint32_t)m * R * kSlice;      // B slice zb
-                    // descriptors advance by adding (bytes >> 4) to the address field
-                    // (shared addresses stay below 256 KB, so the field never carries)
-                    const uint64_t da0 = smem_desc<kAW>(sa, kSBO);
-                    const uint64_t db0 = smem_desc<kAW>(sb, kSBO);
-                    uint32_t idesc = mma_idesc<E>(128, B * m);
-                    uint32_t dcol = dacc + B * (za + zb);
-                    for (int pp = 0; pp < m; pp++) {
-                        const uint64_t da = da0 + (uint64_t)(pp * (R * kSlice / 16));
-#pragma unroll
-                        for (int h = 0; h < kMmaK; h++) {
-                            // 32 bytes of K each: inside a swizzle atom the start
-                            // address moves by 32 B, across atoms by 8 AW bytes
-                            const uint32_t kb = (uint32_t)(32 * h);
-                            const uint64_t adv = ((kb / kAW) * 8 * kAW + kb % kAW) >> 4;
-                            mma_issue<E>(dcol, da + adv, db0 + adv, idesc);
-                        }
-                        idesc -= (uint32_t)(B >> 3) << 17;  // N shrinks by b
-                        dcol += B;
-                    }
-                    mma_commit(smem_u32(&empty_bar[sl]));
-                }
-                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&ready_bar[sl]));
                 consumed++;
             }
-            if (lane == 0) mma_commit(smem_u32(&accf_bar[acc]));
-            if (++acc == 2) {
-                acc = 0;
-                aph ^= 1;
-            }
+            if (!ok) break;
         }
-        if (lane == 0) {
-            if (!ok) {
-                atomicExch(g.err, 1);
-                abort_flag = 1;
-            }
-            // all MMAs issued by this thread complete before TMEM is freed
-            mma_commit(smem_u32(&done_bar));
-            mbar_wait(smem_u32(&done_bar), 0, abort_v);
+        if (!ok) {
+            if (lane == 0) atomicExch(g.err, 1);
+            abort_flag = 1;
         }
-        __syncwarp();
     } else {
-        // ------------------------------ epilogue ------------------------------
+        // ------------------------------ epilogue (warps 2-5) ------------------------------
         const int quad = warp & 3;             // TMEM lane quadrant of this warp
         const int row = quad * 32 + lane;      // tile row 0..127
         const int L = row / B, r = row % B;    // leaf within tile, row within leaf
