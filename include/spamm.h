@@ -72,6 +72,8 @@ typedef enum {
 /* ---- options ---------------------------------------------------------- */
 #define SPAMM_F_TIMING 1 /* record per-stage device times into spamm_stats_t */
 #define SPAMM_F_NOSYM 2  /* SP2: form every leaf of X^2 even when F is symmetric */
+#define SPAMM_F_NOGRAPH 8 /* SP2: enqueue every iteration's launches directly
+                             instead of replaying a captured CUDA graph */
 #define SPAMM_F_HEAVIEST 4 /* tensor path: hand tiles out heaviest first
                               (longest-processing-time order) instead of
                               row-major (a schedule the autotuner tries) */
@@ -322,7 +324,7 @@ typedef struct {
     double ms_update;     /*   ... of the SP2 decide + update passes        */
     int64_t launches;     /* kernels the solve launched                     */
     int32_t symmetric;    /* 1: upper block triangle of X^2 formed + mirrored */
-    int32_t reserved2;
+    int32_t graphed;      /* iterations run by replaying a captured CUDA graph */
     double *history;      /* in: optional host buffer of history_cap rows  */
     int32_t history_cap;  /* in: rows available in history                 */
     int32_t reserved;
@@ -341,7 +343,12 @@ typedef struct {
  * F      : symmetric handle; Ne in (0, n) is the trace of the projector.
  * P      : *P == NULL creates a new handle; otherwise reused (F's shape).
  * report : optional; filled when given.
- * Blocking: waits for the stream once per iteration to read four scalars.
+ * Iterations are enqueued four at a time and the state is read once per
+ * four (blocking).  After the first four, the launches of four iterations
+ * are captured once into a CUDA graph (on an internal stream) and replayed
+ * for the rest of the solve, unless SPAMM_F_NOGRAPH is set or a product
+ * could need to wait for a task count (FP64 lists above 512 MB); the results
+ * are the same either way.
  * Errors: E_INVAL, E_NOTSUP, E_NOMEM, E_CUDA; E_NOCONV when max_iter is
  *         reached (P holds the last iterate).
  */

@@ -72,6 +72,17 @@ void spamm_release(void *p, cudaStream_t s)
     if (p) cudaFreeAsync(p, s);
 }
 
+// Record an event on s; inside a stream capture as an external event node
+// (a plain record there only orders the captured work and is never timed).
+cudaError_t spamm_event_record(cudaEvent_t e, cudaStream_t s)
+{
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    cudaError_t err = cudaStreamIsCapturing(s, &st);
+    if (err != cudaSuccess) return err;
+    return st == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal)
+                                               : cudaEventRecord(e, s);
+}
+
 int spamm_num_sms()
 {
     int dev = 0, sms = 0;
@@ -407,7 +418,7 @@ int spamm_multiply_into(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t C,
                         cudaEvent_t *ev, int sym, bool slices_ready, bool zero_empty)
 {
     int prec = opts ? opts->prec : SPAMM_FP64;
-    if (ev) SPAMM_CK(cudaEventRecord(ev[0], s));
+    if (ev) SPAMM_CK(spamm_event_record(ev[0], s));
     SpammWorkspace *ws = &C->ws;
     int rc = ws_reserve_groups(ws, A->nb * A->nb, A->nb, s);
     if (rc) return rc;
@@ -417,7 +428,7 @@ int spamm_multiply_into(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t C,
         if (rc) return rc;
         ws->task_total = ws->off + A->nb * A->nb;
         ws->pair_units = nullptr;
-        if (ev) SPAMM_CK(cudaEventRecord(ev[1], s));
+        if (ev) SPAMM_CK(spamm_event_record(ev[1], s));
         rc = launch_gemm_fp64(A, B, C, ws, tr_part, s);
     } else if (prec_is_tc(prec)) {
         const int sl = prec_slices(prec, opts ? opts->slices : 0);
@@ -434,7 +445,7 @@ int spamm_multiply_into(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t C,
         const bool heavy = opts && (opts->flags & SPAMM_F_HEAVIEST);
         if ((rc = tc_tile_cull(A, B, tau, ws, symm, sl, s, heavy))) return rc;
         if (zero_empty && (rc = tc_zero_empty_tiles(C, ws, s))) return rc;
-        if (ev) SPAMM_CK(cudaEventRecord(ev[1], s));
+        if (ev) SPAMM_CK(spamm_event_record(ev[1], s));
         rc = launch_gemm_tc(A, B, C, ws, tr_part, sl, el, s, fsplit);
         if (rc) return rc;
         const int64_t R = 128 / A->b;
@@ -454,7 +465,7 @@ int spamm_multiply_into(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t C,
         rc = SPAMM_E_NOTSUP;
     }
     if (rc) return rc;
-    if (ev) SPAMM_CK(cudaEventRecord(ev[2], s));
+    if (ev) SPAMM_CK(spamm_event_record(ev[2], s));
     C->tiers_ok = build_pyramid;
     if (build_pyramid) {
         // the FP64 epilogue already wrote C's leaf norms; the tensor-core
@@ -462,7 +473,7 @@ int spamm_multiply_into(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t C,
         rc = prec == SPAMM_FP64 ? launch_pyramid(C, s) : launch_leaf_norms(C, s);
         if (rc) return rc;
     }
-    if (ev) SPAMM_CK(cudaEventRecord(ev[3], s));
+    if (ev) SPAMM_CK(spamm_event_record(ev[3], s));
     if (tasks_out) *tasks_out = total;
     return SPAMM_OK;
 }
@@ -615,7 +626,7 @@ extern "C" int spamm_multiply_batched(int32_t count, const spamm_mat_t *A, const
         c[q] = C[ord[q]];
         w[q] = &C[ord[q]]->ws;
     }
-    if (rc == SPAMM_OK && timing && cudaEventRecord(ev[0], s) != cudaSuccess) rc = SPAMM_E_CUDA;
+    if (rc == SPAMM_OK && timing && spamm_event_record(ev[0], s) != cudaSuccess) rc = SPAMM_E_CUDA;
     for (int q = 0; q < count && rc == SPAMM_OK; q++) {
         const int64_t nb = a[q]->nb;
         if ((rc = ws_reserve_groups(w[q], nb * nb, nb, s))) break;
@@ -631,17 +642,17 @@ extern "C" int spamm_multiply_batched(int32_t count, const spamm_mat_t *A, const
             if (rc == SPAMM_OK) rc = tc_zero_empty_tiles(c[q], w[q], s);
         }
     }
-    if (rc == SPAMM_OK && timing && cudaEventRecord(ev[1], s) != cudaSuccess) rc = SPAMM_E_CUDA;
+    if (rc == SPAMM_OK && timing && spamm_event_record(ev[1], s) != cudaSuccess) rc = SPAMM_E_CUDA;
     for (int q0 = 0; q0 < count && rc == SPAMM_OK; q0 += kMaxBatch) {
         const int k = count - q0 < kMaxBatch ? count - q0 : kMaxBatch;
         int32_t *ctr = w[q0]->counter;
         rc = tcp ? launch_gemm_tc_batched(k, &a[q0], &b[q0], &c[q0], &w[q0], sl, el, s, fsplit, ctr)
                  : launch_gemm_fp64_batched(k, &a[q0], &b[q0], &c[q0], &w[q0], s, ctr);
     }
-    if (rc == SPAMM_OK && timing && cudaEventRecord(ev[2], s) != cudaSuccess) rc = SPAMM_E_CUDA;
+    if (rc == SPAMM_OK && timing && spamm_event_record(ev[2], s) != cudaSuccess) rc = SPAMM_E_CUDA;
     for (int q = 0; q < count && rc == SPAMM_OK; q++)
         rc = tcp ? launch_leaf_norms(c[q], s) : launch_pyramid(c[q], s);
-    if (rc == SPAMM_OK && timing && cudaEventRecord(ev[3], s) != cudaSuccess) rc = SPAMM_E_CUDA;
+    if (rc == SPAMM_OK && timing && spamm_event_record(ev[3], s) != cudaSuccess) rc = SPAMM_E_CUDA;
     if (rc == SPAMM_OK && stats) {
         // totals (one blocking read per product) and the device error words
         for (int q = 0; q < count && rc == SPAMM_OK; q++) {

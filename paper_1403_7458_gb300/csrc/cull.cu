@@ -137,6 +137,8 @@ Coarse coarse_tier(spamm_mat_t A, spamm_mat_t B)
 // device for the exact count.
 static const int64_t kEagerListBytes = int64_t(512) << 20;
 
+bool spamm_cull_never_waits(int64_t nb) { return nb * nb * nb * 4 <= kEagerListBytes; }
+
 int spamm_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, int64_t nb,
                int64_t P, cudaStream_t s, bool need_total, int64_t *total_host, bool worst_case)
 {

@@ -102,6 +102,7 @@ __host__ __device__
 static inline int64_t tier_offset(int t) { return ((int64_t(1) << (2 * t)) - 1) / 3; }
 
 int spamm_num_sms();
+cudaError_t spamm_event_record(cudaEvent_t e, cudaStream_t s);
 int spamm_mat_alloc(spamm_mat_t m, int64_t n, int b, cudaStream_t s);
 int spamm_mat_same_shape(spamm_mat_t a, spamm_mat_t b);
 
@@ -122,6 +123,9 @@ int spamm_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws,
                int64_t nb, int64_t P, cudaStream_t s, bool need_total, int64_t *total_host,
                bool worst_case = false);
 int ws_reserve_groups(SpammWorkspace *ws, int64_t groups, int64_t nb, cudaStream_t s);
+// The FP64 cull of an nb x nb leaf grid reserves its worst-case list (and so
+// never waits for the stream once reserved).
+bool spamm_cull_never_waits(int64_t nb);
 
 // C = SpAMM(A, B, tau) into an existing handle (api.cu).  ev (optional, 4
 // events) is recorded before the cull, before the products, before and after

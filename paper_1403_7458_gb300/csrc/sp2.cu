@@ -397,6 +397,11 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
     const int limit = o.fixed_iters > 0 ? o.fixed_iters : o.max_iter;
     const bool coarse = nb >= kCoarseMinNb;
     const bool tcpath = prec_is_tc(o.prec);  // X2's tiles without work are left unwritten
+    bool use_graph = !(o.flags & SPAMM_F_NOGRAPH) && (tcpath || spamm_cull_never_waits(nb));
+    cudaStream_t cs = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int64_t graph_launches = 0;
+    int graphed = 0;  // iterations run by graph replays
     unsigned ew_blocks = (unsigned)((G + kWarps - 1) / kWarps);
 
 #define SP2_TRY(x)                 \
@@ -466,29 +471,66 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
                                                     offsetof(Sp2State, stopped));
     {
         const Sp2Rule rule{Ne, o.trace_tol, o.idem_tol, o.fixed_iters, o.max_iter};
+        // the launches of `batch` iterations on stream st
+        auto enqueue = [&](cudaStream_t st, int batch) -> int {
+            for (int q = 0; q < batch; q++) {
+                cudaEvent_t *ev = timing ? evs + 5 * q : nullptr;
+                int r = spamm_multiply_into(X, X, tau, X2, &mo, sc.tr_part, st, false, nullptr, false, ev,
+                                            sym ? 1 : 0, false, !tcpath);
+                if (r) return r;
+                const int64_t *x2off = tcpath ? X2->ws.toff : nullptr;
+                k_sp2_decide<<<1, kRedThreads, 0, st>>>(sc.tr_part, nb, X2->ws.task_total, X2->ws.pair_units, Ne,
+                                                        o.rule, sc.st);
+                SPAMM_CK_LAUNCH();
+                k_sp2_elementwise<<<ew_blocks, kWarps * 32, 0, st>>>(
+                    1, X->leaf, X2->leaf, X->slot, F->n, nb, X->P, X->b, X->n2 + tier_offset(X->depth),
+                    X->n2T, sc.idem_part, sc.diag_part, sc.st, rule, sc.hist, x2off, 128 / X->b, sym ? 1 : 0);
+                SPAMM_CK_LAUNCH();
+                if (coarse && (r = launch_pyramid(X, st))) return r;
+                if (timing) SPAMM_CK(spamm_event_record(ev[4], st));
+            }
+            return SPAMM_OK;
+        };
         int enq = 0;
         while (enq < limit) {
             const int batch = limit - enq < kBatch ? limit - enq : kBatch;
-            for (int q = 0; q < batch; q++) {
-                cudaEvent_t *ev = timing ? evs + 5 * q : nullptr;
-                SP2_TRY(spamm_multiply_into(X, X, tau, X2, &mo, sc.tr_part, s, false, nullptr, false, ev,
-                                            sym ? 1 : 0, false, !tcpath));
-                const int64_t *x2off = tcpath ? X2->ws.toff : nullptr;
-                k_sp2_decide<<<1, kRedThreads, 0, s>>>(sc.tr_part, nb, X2->ws.task_total, X2->ws.pair_units, Ne,
-                                                       o.rule, sc.st);
-                SP2_LAUNCHED();
-                k_sp2_elementwise<<<ew_blocks, kWarps * 32, 0, s>>>(
-                    1, X->leaf, X2->leaf, X->slot, F->n, nb, X->P, X->b, X->n2 + tier_offset(X->depth),
-                    X->n2T, sc.idem_part, sc.diag_part, sc.st, rule, sc.hist, x2off, 128 / X->b, sym ? 1 : 0);
-                SP2_LAUNCHED();
-                if (coarse) SP2_TRY(launch_pyramid(X, s));
-                if (timing) SP2_CUDA(cudaEventRecord(ev[4], s));
+            bool replayed = false;
+            if (use_graph && batch == kBatch && enq > 0) {
+                // the first batch ran directly (it allocated every workspace);
+                // capture one batch on an internal stream, then replay it
+                if (!gexec) {
+                    cudaGraph_t gr = nullptr;
+                    const int64_t l0 = spamm_launch_count();
+                    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+                    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+                    if (e == cudaSuccess) {
+                        const int r = enqueue(cs, kBatch);
+                        e = cudaStreamEndCapture(cs, &gr);
+                        if (r == SPAMM_OK && e == cudaSuccess) e = cudaGraphInstantiate(&gexec, gr, 0);
+                        else if (e == cudaSuccess) e = cudaErrorUnknown;
+                    }
+                    if (gr) cudaGraphDestroy(gr);
+                    graph_launches = spamm_launch_count() - l0;
+                    spamm_note_launches(-graph_launches);  // counted per replay instead
+                    if (e != cudaSuccess || !gexec) {
+                        cudaGetLastError();  // fall back to direct launches
+                        use_graph = false;
+                        gexec = nullptr;
+                    }
+                }
+                if (gexec) {
+                    SP2_CUDA(cudaGraphLaunch(gexec, s));
+                    spamm_note_launches(graph_launches);
+                    replayed = true;
+                }
             }
+            if (!replayed) SP2_TRY(enqueue(s, batch));
             enq += batch;
             const int before = h.iter;
             SP2_CUDA(cudaMemcpyAsync(sc.host, sc.st, sizeof(Sp2State), cudaMemcpyDeviceToHost, s));
             SP2_CUDA(cudaStreamSynchronize(s));
             h = *sc.host;
+            if (replayed) graphed += h.iter - before;
             if (timing) {
                 for (int q = 0; q < h.iter - before && q < batch; q++) {
                     float a = 0.f, b = 0.f, c = 0.f;
@@ -552,10 +594,13 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
         report->ms_update = ms_update;
         report->launches = spamm_launch_count() - launches0;
         report->symmetric = sym ? 1 : 0;
+        report->graphed = graphed;
     }
     rc = reason == SP2_STOP_MAXITER ? SPAMM_E_NOCONV : SPAMM_OK;
     if (rc == SPAMM_E_NOCONV) spamm_set_error("sp2_solve: %d iterations without convergence", it);
 done:
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (cs) cudaStreamDestroy(cs);
     for (int q = 0; q < 5 * kBatch; q++)
         if (evs[q]) cudaEventDestroy(evs[q]);
     if (ev0) cudaEventDestroy(ev0);

@@ -28,6 +28,7 @@ FP64, OZAKI_BF16, BF16, BF16X3, TF32, TF32X3 = 0, 1, 2, 3, 4, 5
 F_TIMING = 1
 F_NOSYM = 2
 F_HEAVIEST = 4
+F_NOGRAPH = 8
 TUNE_MAX = 6
 RULE_TRACE_DISTANCE, RULE_TRACE_ABOVE = 0, 1
 STOP_CONVERGED, STOP_STAGNATED, STOP_FIXED, STOP_MAXITER = 0, 1, 2, 3
@@ -79,7 +80,7 @@ class _Sp2Report(ctypes.Structure):
                 ("ms_total", ctypes.c_double), ("ms_cull", ctypes.c_double),
                 ("ms_gemm", ctypes.c_double), ("ms_update", ctypes.c_double),
                 ("launches", ctypes.c_int64), ("symmetric", ctypes.c_int32),
-                ("reserved2", ctypes.c_int32), ("history", ctypes.POINTER(ctypes.c_double)),
+                ("graphed", ctypes.c_int32), ("history", ctypes.POINTER(ctypes.c_double)),
                 ("history_cap", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
@@ -348,7 +349,7 @@ def sp2_solve(F: Matrix, ne: float, tau: float, P: Matrix | None = None, max_ite
     _check(rc, "sp2_solve", allow=(E_NOCONV,))
     out = P if P is not None else Matrix(h.value)
     report = {k: getattr(rep, k) for k, _ in _Sp2Report._fields_
-              if k not in ("history", "history_cap", "reserved", "reserved2")}
+              if k not in ("history", "history_cap", "reserved")}
     report["history"] = hist[:rep.iters].copy()
     report["converged"] = rc == OK
     return out, report

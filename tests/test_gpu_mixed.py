@@ -303,3 +303,23 @@ def test_tiles_without_work_are_zero_in_a_reused_output(cuda_lib, prec_name, lea
     # the rest: the product (loose: each mode's own bound is tested elsewhere;
     # exact slices err in absolute terms, float splits in relative terms)
     assert np.all(np.abs(got - ref) <= 0.02 * absab + 1e-9 * absab.max())
+
+
+@pytest.mark.parametrize("prec_name", ["FP64", "OZAKI_BF16", "TF32X3"])
+def test_sp2_graph_replay_matches_direct_launches(cuda_lib, prec_name):
+    """After the first four iterations SP2 replays a captured CUDA graph of
+    four iterations; the result must equal enqueuing every launch directly."""
+    n = 1024
+    h = synth.tb_hamiltonian(n, 2)
+    F = cuda_lib.tree_build(_dev(h), leaf=32)
+    prec = getattr(cuda_lib, prec_name)
+    Pg, rg = cuda_lib.sp2_solve(F, n / 2, 1e-8, prec=prec, timing=True)
+    Pd, rd = cuda_lib.sp2_solve(F, n / 2, 1e-8, prec=prec, timing=True, flags=cuda_lib.F_NOGRAPH)
+    assert rd["graphed"] == 0
+    assert rg["iters"] > 8 and rg["graphed"] >= 4
+    assert rg["iters"] == rd["iters"] and rg["stop_reason"] == rd["stop_reason"]
+    assert np.array_equal(rg["history"], rd["history"])
+    assert np.array_equal(cuda_lib.to_dense(Pg).cpu().numpy(), cuda_lib.to_dense(Pd).cpu().numpy())
+    # launches of replayed iterations are still counted
+    assert abs(rg["launches"] - rd["launches"]) <= 4
+    assert rg["ms_gemm"] > 0
