@@ -44,6 +44,11 @@ WORKLOAD = {"workload": "sp2_tb_hamiltonian", "n": 4096, "leaf": 32, "tau": 1e-8
 METRIC = "SpAMM leaf TFLOP/s over the SP2 solve (useful FLOPs of surviving products)"
 UNIT = "TFLOP/s"
 L2_BYTES = 129 * 1024 * 1024
+# DRAM bytes (read + write) per launch of the tensor-core leaf-product kernel
+# of this workload (mean over the 24 launches of one solve), from an ncu
+# capture of the kernel as it stands (k_gemm_tc<7, 2, 32>: swizzled operands,
+# prep warp, row-major tiles); set to None when the kernel changes.
+TC_TRAFFIC_BYTES_PER_LAUNCH = 487.7e6
 
 
 def _peaks():
@@ -263,14 +268,15 @@ def run_ours(args):
     else:
         peak = peaks.get("bf16_tflops_sustained", 1700.0)
         bound = "tensor"
-        kern = "k_gemm_tc<%d>" % slices
+        kern = "k_gemm_tc<%d, 2, 32>" % slices
         peak_note = "bf16 tensor, sustained, %s (MEASURED_PEAKS.json)" % peak_src
         # tensor work of the surviving products: each slice pair that is not
         # identically zero, on the tiles actually formed (symmetric half)
         alg_flops = tflops
     achieved = alg_flops / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else None
+    traffic = TC_TRAFFIC_BYTES_PER_LAUNCH if (prec == spamm.OZAKI_BF16 and slices == 7) else None
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                 "kernel": kern, "peak_source": peak_note,
                 "useful_leaf_tflops_in_kernel": flops / (gemm_ms * 1e-3) / 1e12 if gemm_ms else None,
                 "kernel_share_of_step": gemm_ms / total_ms if total_ms else None}
