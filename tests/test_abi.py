@@ -24,8 +24,9 @@ def _declared():
 
 def test_header_declares_the_boundary():
     names = _declared()
-    for must in ("spamm_tree_build", "spamm_multiply", "sp2_solve", "spamm_task_list",
-                 "spamm_to_dense", "spamm_norms", "spamm_free", "spamm_strerror"):
+    for must in ("spamm_tree_build", "spamm_multiply", "spamm_multiply_batched", "sp2_solve",
+                 "spamm_task_list", "spamm_to_dense", "spamm_norms", "spamm_free", "spamm_strerror",
+                 "spamm_autotune_batched", "spamm_release_scratch", "spamm_cull_noalloc"):
         assert must in names
 
 
@@ -43,3 +44,31 @@ def test_strerror_without_gpu():
     assert lib.spamm_strerror(0) == b"ok"
     assert lib.spamm_strerror(-6).startswith(b"SP2")
     assert lib.spamm_strerror(-99) == b"unknown status"
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Sizes and field offsets of the ctypes mirrors equal the C structs of
+    include/spamm.h (compiled here with the host C compiler)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no host C compiler")
+    from paper_1403_7458_gb300 import spamm
+    structs = {"spamm_opts_t": spamm._Opts, "spamm_stats_t": spamm._Stats, "sp2_opts_t": spamm._Sp2Opts,
+               "sp2_report_t": spamm._Sp2Report, "spamm_tune_t": spamm._Tune}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "spamm.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f, _ in cls._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, f))
+    lines += ["return 0; }"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = dict(line.rsplit(" ", 1) for line in out if line)
+    for cname, cls in structs.items():
+        assert int(got["%s size" % cname]) == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert int(got["%s.%s" % (cname, f)]) == getattr(cls, f).offset, (cname, f)
