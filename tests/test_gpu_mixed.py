@@ -323,3 +323,29 @@ def test_sp2_graph_replay_matches_direct_launches(cuda_lib, prec_name):
     # launches of replayed iterations are still counted
     assert abs(rg["launches"] - rd["launches"]) <= 4
     assert rg["ms_gemm"] > 0
+
+
+def test_mixed_sp2_leaf16_matches_fp64(cuda_lib):
+    """Leaf 16 on the tensor path (tiles of 8 leaf rows; diagonal traces
+    reduced over 16-lane halves of a warp)."""
+    n = 1024
+    h = synth.tb_hamiltonian(n, 4)
+    F = cuda_lib.tree_build(_dev(h), leaf=16)
+    P64, r64 = cuda_lib.sp2_solve(F, n / 2, 1e-8)
+    P, r = cuda_lib.sp2_solve(F, n / 2, 1e-8, prec=cuda_lib.OZAKI_BF16, slices=7, fixed_iters=r64["iters"])
+    assert r["symmetric"] == 1
+    assert np.array_equal(r["history"][:, 4], r64["history"][:, 4])      # task counts
+    d = cuda_lib.to_dense(P).cpu().numpy() - cuda_lib.to_dense(P64).cpu().numpy()
+    assert np.linalg.norm(d) <= 1e-6
+
+
+def test_release_scratch_then_reuse(cuda_lib):
+    n = 512
+    a = synth.decaying_matrix(n, 3)
+    A = cuda_lib.tree_build(_dev(a), leaf=32)
+    C1, _ = cuda_lib.multiply(A, A, 1e-6, prec=cuda_lib.OZAKI_BF16)
+    want = cuda_lib.to_dense(C1).cpu().numpy()
+    cuda_lib.release_scratch(A)
+    cuda_lib.release_scratch(C1)
+    C2, _ = cuda_lib.multiply(A, A, 1e-6, C=C1, prec=cuda_lib.OZAKI_BF16)
+    assert np.array_equal(cuda_lib.to_dense(C2).cpu().numpy(), want)
