@@ -263,13 +263,15 @@ int launch_slices(spamm_mat_t m, int s, int e, bool tile_a, bool per_leaf, bool 
     }
     const int64_t R = 128 / m->b;
     const int64_t rows = ((m->nb + R - 1) / R) * R;
-    SPAMM_CK(cudaMemsetAsync(m->scale, 0, sizeof(unsigned long long), st));  // max bits
     const int64_t count = m->nslots * m->b * m->b;
     const int blocks = spamm_num_sms() * 8;
-    if (unit_scale)
+    // the scale matters to exact slices only: float splits take no maximum
+    if (unit_scale || float_split) {
         k_unit_scale<<<1, 1, 0, st>>>(stop, reinterpret_cast<unsigned long long *>(m->scale));
-    else
+    } else {
+        SPAMM_CK(cudaMemsetAsync(m->scale, 0, sizeof(unsigned long long), st));  // max bits
         k_absmax<<<blocks, 256, 0, st>>>(stop, m->leaf, count, reinterpret_cast<unsigned long long *>(m->scale));
+    }
     SPAMM_CK_LAUNCH();
     unsigned long long *mx = reinterpret_cast<unsigned long long *>(m->scale);
     int32_t *sig = reinterpret_cast<int32_t *>(m->scale + 1);

@@ -15,6 +15,8 @@ Bars:
   idempotency error: once X stalls at the SpAMM error floor, each further
   iteration moves X by O(e) and either side may take the other branch.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -212,3 +214,50 @@ def test_bad_arguments_raise(cuda_lib):
         cuda_lib.tree_build(_dev(a), leaf=24)
     with pytest.raises(cuda_lib.SpammError):
         cuda_lib.sp2_solve(A, 64.0, 1e-8)     # Ne must be < n
+
+
+def test_spamm_sampled_leaves_at_n16384(cuda_lib):
+    """A product at the precision-study size (N = 16384, tight-binding
+    Hamiltonian, tau = 1e-8): 24 output leaves recomputed one by one from the
+    definition (Eq. 4 on the oracle's leaf norms, k increasing) and compared
+    with the FP64 path (within 2 gamma_K) and the 7-slice path (within the
+    slicing bound)."""
+    n, b, tau = 16384, 32, 1e-8
+    h = synth.tb_hamiltonian(n, 3)
+    F = cuda_lib.tree_build(_dev(h), leaf=b)
+    n2 = oracle.leaf_norms2(h, b)
+    nb = n // b
+    C64, st = cuda_lib.multiply(F, F, tau, stats=True)
+    Cx, stx = cuda_lib.multiply(F, F, tau, prec=cuda_lib.OZAKI_BF16, slices=7, stats=True)
+    assert st["tasks"] == stx["tasks"]
+    torch = _torch()
+    rng = np.random.default_rng(5)
+    picks = [(i, min(nb - 1, max(0, i + d))) for i, d in zip(rng.integers(0, nb, 24), rng.integers(-6, 7, 24))]
+    d64 = cuda_lib.to_dense(C64)
+    dx = cuda_lib.to_dense(Cx)
+    sig = math.frexp(np.abs(h).max())[1]
+    for i, j in picks:
+        ks = [k for k in range(nb) if n2[i, k] * n2[k, j] > tau * tau]
+        ref = np.zeros((b, b))
+        absref = np.zeros((b, b))
+        rowsum = np.zeros(b)
+        colsum = np.zeros(b)
+        for k in ks:
+            a_ik = h[i * b:(i + 1) * b, k * b:(k + 1) * b]
+            b_kj = h[k * b:(k + 1) * b, j * b:(j + 1) * b]
+            ref += a_ik @ b_kj
+            absref += np.abs(a_ik) @ np.abs(b_kj)
+            rowsum += np.abs(a_ik).sum(axis=1)
+            colsum += np.abs(b_kj).sum(axis=0)
+        got64 = d64[i * b:(i + 1) * b, j * b:(j + 1) * b].cpu().numpy()
+        gotx = dx[i * b:(i + 1) * b, j * b:(j + 1) * b].cpu().numpy()
+        K = max(1, len(ks) * b)
+        g = K * 2.0 ** -53 / (1 - K * 2.0 ** -53)
+        assert np.all(np.abs(got64 - ref) <= 2 * g * absref + 1e-300), (i, j)
+        # rounding of every element to 7 slices (e each) and the dropped
+        # slice pairs p + q >= 7, as in the mixed-precision tests
+        e = 2.0 ** (sig - 7 * 7 - 1)
+        slack = rowsum[:, None] * e + e * colsum[None, :] + K * (e * e + 6 * 2.0 ** (2 * sig - 49))
+        assert np.all(np.abs(gotx - ref) <= slack + 2 * g * absref + 1e-300), (i, j)
+    del d64, dx
+    torch.cuda.empty_cache()
