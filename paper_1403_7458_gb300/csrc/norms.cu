@@ -28,6 +28,7 @@ k_leaf_norms(const double *__restrict__ leaf, const int32_t *__restrict__ slot, 
         const double2 *src = reinterpret_cast<const double2 *>(leaf + (int64_t)s * bb);
         int nv = bb >> 1;
         int emax = 0;
+#pragma unroll 4
         for (int q = lane; q < nv; q += 32) {
             double2 v = __ldg(src + q);
             emax = max(emax, max(exp_key(v.x), exp_key(v.y)));
@@ -35,6 +36,7 @@ k_leaf_norms(const double *__restrict__ leaf, const int32_t *__restrict__ slot, 
         emax = warp_max_int(emax);
         u128 acc = 0;
         if (emax > 0) {
+#pragma unroll 4
             for (int q = lane; q < nv; q += 32) {
                 double2 v = __ldg(src + q);
                 acc += sq_term(v.x, emax) + sq_term(v.y, emax);
