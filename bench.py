@@ -20,6 +20,7 @@ products, and the line reports that solve time, the speedup and
   python bench.py --study precision [--n 16384] [--taus ...]   (modes vs FP64 SP2)
   python bench.py --study batch [--batch 64] [--batch-prec tf32] (many SpAMMs, one launch)
   python bench.py --study large [--n-large 65536]   (one large SP2, mixed vs FP64)
+  python bench.py --study spamm [--spamm-n 1024]     (single products, time per product)
 
 N > 1 runs independent replicas (one solve per GPU, launched with torchrun);
 value = all ranks' useful FLOPs / the slowest rank's time.
@@ -572,6 +573,58 @@ def run_large_study(args):
     print(json.dumps(line), flush=True)
 
 
+def run_spamm_study(args):
+    """Single SpAMM products of the decaying matrix (N = 1024, leaf 32, tau =
+    1e-6; a_ij = u_ij exp(-r_ij / 1.5 A), seed 0): device time per product
+    (plain launches and graph-captured), FP64 and mixed precision, with the
+    task count.  One JSON line."""
+    import torch
+    from paper_1403_7458_gb300 import spamm, synth
+    spamm.load()
+    torch.cuda.set_device(0)
+    n, tau = args.spamm_n, 1e-6
+    a = torch.from_numpy(synth.decaying_matrix(n, 0)).cuda()
+    A = spamm.tree_build(a, leaf=32)
+    out = {"study": "spamm", "n": n, "leaf": 32, "tau": tau}
+    for name, prec, sl in (("fp64", spamm.FP64, 0), ("ozaki7", spamm.OZAKI_BF16, 7), ("tf32", spamm.TF32, 0)):
+        C, st = spamm.multiply(A, A, tau, prec=prec, slices=sl, stats=True, timing=True)
+
+        def one(stream=None):
+            spamm.multiply(A, A, tau, C=C, prec=prec, slices=sl, stream=stream)
+
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 50
+        for _ in range(5):
+            one()
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(reps):
+            one()
+        ev1.record()
+        ev1.synchronize()
+        plain_us = ev0.elapsed_time(ev1) / reps * 1e3
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            one(side.cuda_stream)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            one(torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(reps):
+            g.replay()
+        ev1.record()
+        ev1.synchronize()
+        graph_us = ev0.elapsed_time(ev1) / reps * 1e3
+        out[name] = {"tasks": st["tasks"], "candidates": st["candidates"], "us_per_product": plain_us,
+                     "us_per_product_graph": graph_us, "ms_cull": st["ms_cull"], "ms_gemm": st["ms_gemm"],
+                     "ms_norm": st["ms_norm"], "useful_tflops_graph": st["flops_useful"] / (graph_us * 1e-6) / 1e12}
+    print(json.dumps(out), flush=True)
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -613,7 +666,8 @@ def main(argv=None):
     ap.add_argument("--cpu-iters", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-leg", action="store_true")
-    ap.add_argument("--study", choices=["none", "precision", "batch", "large"], default="none")
+    ap.add_argument("--study", choices=["none", "precision", "batch", "large", "spamm"], default="none")
+    ap.add_argument("--spamm-n", type=int, default=1024)
     ap.add_argument("--n-large", type=int, default=65536)
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--batch-prec", choices=["tf32", "tf32x3", "bf16x3", "ozaki"], default="tf32")
@@ -629,6 +683,8 @@ def main(argv=None):
         run_batch_study(args)
     elif args.study == "large":
         run_large_study(args)
+    elif args.study == "spamm":
+        run_spamm_study(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
