@@ -197,12 +197,8 @@ template <int B>
 int launch_b(const GemmArgs &args, cudaStream_t s)
 {
     size_t smem = sizeof(double) * 4 * B * B;
-    static int configured = 0;
-    if (!configured) {
-        SPAMM_CK(cudaFuncSetAttribute(k_gemm_fp64<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
-        configured = 1;
-    }
+    static unsigned long long configured = 0;
+    if (int rc = spamm_smem_attr(k_gemm_fp64<B>, smem, configured)) return rc;
     int per_sm = 0;
     SPAMM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gemm_fp64<B>, kThreads, smem));
     if (per_sm < 1) per_sm = 1;

@@ -102,6 +102,21 @@ __host__ __device__
 static inline int64_t tier_offset(int t) { return ((int64_t(1) << (2 * t)) - 1) / 3; }
 
 int spamm_num_sms();
+
+// Raise a kernel's dynamic shared-memory limit once per device (the
+// attribute belongs to the device the call is made on).
+template <class Kernel>
+int spamm_smem_attr(Kernel kernel, size_t bytes, unsigned long long &done_mask)
+{
+    int dev = 0;
+    SPAMM_CK(cudaGetDevice(&dev));
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(__atomic_load_n(&done_mask, __ATOMIC_ACQUIRE) & bit)) {
+        SPAMM_CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        __atomic_fetch_or(&done_mask, bit, __ATOMIC_RELEASE);
+    }
+    return SPAMM_OK;
+}
 cudaError_t spamm_event_record(cudaEvent_t e, cudaStream_t s);
 int spamm_mat_alloc(spamm_mat_t m, int64_t n, int b, cudaStream_t s);
 int spamm_mat_same_shape(spamm_mat_t a, spamm_mat_t b);

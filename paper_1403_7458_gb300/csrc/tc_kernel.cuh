@@ -729,11 +729,8 @@ template <int S, int E, int B>
 int launch_k(const TcArgs &a, cudaStream_t s)
 {
     const size_t smem = kRingBytes + 1024;  // + alignment slack of the ring
-    static int configured = 0;
-    if (!configured) {
-        SPAMM_CK(cudaFuncSetAttribute(k_gemm_tc<S, E, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        configured = 1;
-    }
+    static unsigned long long configured = 0;
+    if (int rc = spamm_smem_attr(k_gemm_tc<S, E, B>, smem, configured)) return rc;
     int64_t grid = spamm_num_sms();
     if (grid > a.T) grid = a.T;
     if (grid < 1) grid = 1;

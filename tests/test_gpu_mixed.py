@@ -349,3 +349,22 @@ def test_release_scratch_then_reuse(cuda_lib):
     cuda_lib.release_scratch(C1)
     C2, _ = cuda_lib.multiply(A, A, 1e-6, C=C1, prec=cuda_lib.OZAKI_BF16)
     assert np.array_equal(cuda_lib.to_dense(C2).cpu().numpy(), want)
+
+
+@pytest.mark.parametrize("n", [1, 17, 33, 129])
+@pytest.mark.parametrize("prec_name,leaf", [("OZAKI_BF16", 32), ("TF32", 16), ("BF16X3", 64), ("FP64", 16)])
+def test_tiny_and_ragged_sizes(cuda_lib, n, prec_name, leaf):
+    """Sizes below one leaf, one tile and ragged edges: the task set equals
+    the oracle's, padding leaves stay zero, values match the FP64 product."""
+    a = synth.decaying_matrix(n, 11) if n > 1 else np.array([[0.75]])
+    A = cuda_lib.tree_build(_dev(a), leaf=leaf)
+    prec = getattr(cuda_lib, prec_name)
+    for tau in (0.0, 1e-6, 1e300):
+        C, st = cuda_lib.multiply(A, A, tau, prec=prec, stats=True)
+        ref, tasks = oracle.spamm(a, a, leaf, tau, want_tasks=True)
+        assert st["tasks"] == len(tasks)
+        got = cuda_lib.to_dense(C).cpu().numpy()
+        tol = 1e-12 if prec_name in ("FP64", "OZAKI_BF16") else 1e-2
+        assert np.all(np.abs(got - ref) <= tol * (np.abs(a) @ np.abs(a)) + 1e-300)
+        if tau == 1e300:
+            assert not np.any(got)
