@@ -510,7 +510,8 @@ def run_large_study(args):
     mem = {"total_gib": gib(torch.cuda.mem_get_info()[1])}
     t0 = time.perf_counter()
     h = synth.tb_hamiltonian_torch(n, seed=0, decay=1.0)
-    F = spamm.tree_build(h, leaf=leaf)
+    # sparse leaf storage: leaves with ||leaf||_F <= 1e-12 are not stored
+    F = spamm.tree_build(h, leaf=leaf, drop=1e-12)
     torch.cuda.synchronize()
     del h
     torch.cuda.empty_cache()
@@ -549,7 +550,7 @@ def run_large_study(args):
             "flops_useful", "flops_tensor", "idem_err", "trace_err", "launches", "symmetric")
     line = {
         "study": "large", "n": n, "leaf": leaf, "tau": tau, "ne": ne, "decay_A": 1.0,
-        "storage": "dense leaf grid (zero leaves never multiplied)",
+        "storage": "F: sparse leaves (norm > 1e-12 stored, %d of %d); X, X^2: dense leaf grid" % (F.stored, nb * nb),
         "leaf_fill": {"H_n2_gt_1e-24": fill_h, "P_n2_gt_1e-24": fill_p},
         "fp64": {k: r64[k] for k in keys},
         "mixed_same_iters": {k: r[k] for k in keys},

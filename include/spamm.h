@@ -105,6 +105,11 @@ typedef struct spamm_mat *spamm_mat_t;
  *   [A^{t+1}_21, A^{t+1}_22]]; Eq. 2: the leaf Frobenius norms; Eq. 3: a
  *   parent's norm from its four children.
  * a      : n x n FP64, row-major, leading dimension lda >= n (host or device).
+ * drop   : sparse storage: leaf (i, k) is stored iff ||A_ik||_F > drop
+ *          (squared norm > drop * drop in FP64); a leaf not stored is zero
+ *          in every later use.  drop = 0 stores the nonzero leaves; drop < 0
+ *          stores every leaf (dense).  Stored leaves are packed in row-major
+ *          leaf order.  Handles with absent leaves serve as inputs only.
  * opts   : leaf size (others ignored here); NULL = defaults.
  * out    : receives the new handle (caller frees it with spamm_free).
  * Squared norms are stored.  Each is the exact sum of the exact squares
@@ -113,7 +118,7 @@ typedef struct spamm_mat *spamm_mat_t;
  * a host `a` is copied before the call returns.
  * Errors: E_INVAL (n < 1, lda < n, bad leaf, NULL a/out), E_NOMEM, E_CUDA.
  */
-int spamm_tree_build(const double *a, int64_t n, int64_t lda,
+int spamm_tree_build(const double *a, int64_t n, int64_t lda, double drop,
                      const spamm_opts_t *opts, void *stream, spamm_mat_t *out);
 
 /*
@@ -125,7 +130,9 @@ int spamm_tree_build(const double *a, int64_t n, int64_t lda,
  * A, B   : handles of equal n and leaf size.
  * tau    : >= 0 and finite.
  * C      : *C == NULL creates a new handle; otherwise *C must have A's shape
- *          and is overwritten.  C may not alias A or B.
+ *          and is overwritten.  C may not alias A or B; a reused C must
+ *          store every leaf (built by this library as an output, or by
+ *          spamm_tree_build with drop < 0).
  * opts   : precision (spamm_prec_t), slices, flags.  The tensor-core modes
  *          take leaf 16, 32 or 64 with slices x leaf <= 256 (so leaf 64
  *          allows at most 4 exact slices).
@@ -214,9 +221,11 @@ int spamm_to_dense(spamm_mat_t M, double *dst, int64_t ld, void *stream);
  */
 int spamm_norms(spamm_mat_t M, int32_t tier, double *dst, void *stream);
 
-/* Shape of a handle: n, leaf edge b, leaf grid nb, quadtree depth d. */
+/* Shape of a handle: n, leaf edge b, leaf grid nb, quadtree depth d, and the
+ * number of stored leaves (nb * nb for dense handles).  Any pointer may be
+ * NULL. */
 int spamm_info(spamm_mat_t M, int64_t *n, int32_t *leaf, int64_t *nb,
-               int32_t *depth);
+               int32_t *depth, int64_t *stored);
 
 /*
  * The culled task list of SpAMM(A, B, tau), grouped by output leaf (Eq. 4):
@@ -341,7 +350,8 @@ typedef struct {
  * of X^2 is formed and mirrored; the result is bit-identical to forming all
  * leaves (SPAMM_F_NOSYM in flags forces the full product).
  * F      : symmetric handle; Ne in (0, n) is the trace of the projector.
- * P      : *P == NULL creates a new handle; otherwise reused (F's shape).
+ * P      : *P == NULL creates a new handle; otherwise reused (F's shape,
+ *          every leaf stored).  F may have absent leaves.
  * report : optional; filled when given.
  * Iterations are enqueued four at a time and the state is read once per
  * four (blocking).  After the first four, the launches of four iterations

@@ -174,6 +174,8 @@ int spamm_mat_same_shape(spamm_mat_t a, spamm_mat_t b)
     return a && b && a->n == b->n && a->b == b->b;
 }
 
+int spamm_mat_dense(spamm_mat_t m) { return m && m->nslots == m->nb * m->nb; }
+
 static void ws_free(SpammWorkspace *ws, cudaStream_t s)
 {
     spamm_release(ws->tcounts, s);
@@ -225,7 +227,93 @@ extern "C" void spamm_release_scratch(spamm_mat_t m, void *stream)
     m->ws.stop = stop;
 }
 
-extern "C" int spamm_tree_build(const double *a, int64_t n, int64_t lda, const spamm_opts_t *opts,
+// Sparse storage: flags of the leaves kept (squared norm > drop2), their
+// exclusive prefix count (one block), the compacted leaf array.
+__global__ void k_keep_scan(const double *__restrict__ n2, int64_t nb, int64_t P, double drop2,
+                            int32_t *__restrict__ slot, int64_t *__restrict__ total)
+{
+    __shared__ int64_t part[1024];
+    const int t = threadIdx.x;
+    const int64_t G = nb * nb, chunk = (G + 1023) / 1024;
+    const int64_t lo = t * chunk, hi = lo + chunk < G ? lo + chunk : G;
+    int64_t c = 0;
+    for (int64_t q = lo; q < hi; q++) c += n2[(q / nb) * P + q % nb] > drop2;
+    part[t] = c;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const int64_t v = t >= o ? part[t - o] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int64_t run = part[t] - c;
+    for (int64_t q = lo; q < hi; q++) slot[q] = n2[(q / nb) * P + q % nb] > drop2 ? (int32_t)run++ : -1;
+    if (t == 1023) *total = part[t];
+}
+
+__global__ void k_gather_leaves(const double *__restrict__ dense, const int32_t *__restrict__ slot, int64_t G,
+                                int bb, double *__restrict__ packed)
+{
+    const int64_t g = blockIdx.x;
+    if (g >= G || slot[g] < 0) return;
+    const double2 *s = reinterpret_cast<const double2 *>(dense + g * bb);
+    double2 *d = reinterpret_cast<double2 *>(packed + (int64_t)slot[g] * bb);
+    for (int q = threadIdx.x; q < bb / 2; q += blockDim.x) d[q] = s[q];
+}
+
+// Keep only the leaves with squared norm > drop2 (dense handle in, sparse
+// out): dropped leaves get norm 0 and the pyramid is rebuilt.
+static int compact_leaves(spamm_mat_t m, double drop2, cudaStream_t s)
+{
+    const int64_t G = m->nb * m->nb;
+    int64_t *total = nullptr;
+    int32_t *slot = nullptr;
+    int rc;
+    if ((rc = spamm_alloc((void **)&total, sizeof(int64_t), s))) return rc;
+    if ((rc = spamm_alloc((void **)&slot, sizeof(int32_t) * G, s))) {
+        spamm_release(total, s);
+        return rc;
+    }
+    k_keep_scan<<<1, 1024, 0, s>>>(m->n2 + tier_offset(m->depth), m->nb, m->P, drop2, slot, total);
+    spamm_note_launches(1);
+    int64_t kept = 0;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&kept, total, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    spamm_release(total, s);
+    if (e != cudaSuccess) {
+        spamm_release(slot, s);
+        return spamm_cuda_fail(e, "sparse leaf count", __FILE__, __LINE__);
+    }
+    if (kept == G) {  // nothing dropped: stay dense
+        spamm_release(slot, s);
+        return SPAMM_OK;
+    }
+    const int bb = m->b * m->b;
+    double *packed = nullptr;
+    if ((rc = spamm_alloc((void **)&packed, sizeof(double) * (kept > 0 ? kept : 1) * bb, s))) {
+        spamm_release(slot, s);
+        return rc;
+    }
+    if (kept > 0) {
+        k_gather_leaves<<<(unsigned)G, 256, 0, s>>>(m->leaf, slot, G, bb, packed);
+        spamm_note_launches(1);
+        if ((e = cudaGetLastError()) != cudaSuccess) {
+            spamm_release(slot, s);
+            spamm_release(packed, s);
+            return spamm_cuda_fail(e, "k_gather_leaves", __FILE__, __LINE__);
+        }
+    }
+    spamm_release(m->leaf, s);
+    spamm_release(m->slot, s);
+    m->leaf = packed;
+    m->slot = slot;
+    m->nslots = kept;
+    // the norms of the matrix as stored: dropped leaves are zero
+    return launch_leaf_norms(m, s);
+}
+
+extern "C" int spamm_tree_build(const double *a, int64_t n, int64_t lda, double drop, const spamm_opts_t *opts,
                                 void *stream, spamm_mat_t *out)
 {
     if (!out) {
@@ -234,7 +322,7 @@ extern "C" int spamm_tree_build(const double *a, int64_t n, int64_t lda, const s
     }
     *out = nullptr;
     int b = opts && opts->leaf ? opts->leaf : 32;
-    if (!a || n < 1 || lda < n || !valid_leaf(b) || (n + b - 1) / b > (int64_t(1) << 15)) {
+    if (!a || n < 1 || lda < n || !valid_leaf(b) || (n + b - 1) / b > (int64_t(1) << 15) || !(drop < 1e300)) {
         spamm_set_error("spamm_tree_build: bad arguments (n=%lld lda=%lld leaf=%d)", (long long)n,
                         (long long)lda, b);
         return SPAMM_E_INVAL;
@@ -273,6 +361,10 @@ extern "C" int spamm_tree_build(const double *a, int64_t n, int64_t lda, const s
         return spamm_cuda_fail(e, "k_pack", __FILE__, __LINE__);
     }
     if ((rc = launch_leaf_norms(m, s))) {
+        spamm_free(m);
+        return rc;
+    }
+    if (drop >= 0.0 && (rc = compact_leaves(m, drop * drop, s))) {
         spamm_free(m);
         return rc;
     }
@@ -329,7 +421,7 @@ extern "C" int spamm_norms(spamm_mat_t m, int32_t tier, double *dst, void *strea
     return SPAMM_OK;
 }
 
-extern "C" int spamm_info(spamm_mat_t m, int64_t *n, int32_t *leaf, int64_t *nb, int32_t *depth)
+extern "C" int spamm_info(spamm_mat_t m, int64_t *n, int32_t *leaf, int64_t *nb, int32_t *depth, int64_t *stored)
 {
     if (!m) {
         spamm_set_error("spamm_info: NULL handle");
@@ -339,6 +431,7 @@ extern "C" int spamm_info(spamm_mat_t m, int64_t *n, int32_t *leaf, int64_t *nb,
     if (leaf) *leaf = m->b;
     if (nb) *nb = m->nb;
     if (depth) *depth = m->depth;
+    if (stored) *stored = m->nslots;
     return SPAMM_OK;
 }
 
@@ -508,8 +601,8 @@ extern "C" int spamm_multiply(spamm_mat_t A, spamm_mat_t B, double tau, spamm_ma
         }
         *C = m;
         created = true;
-    } else if (!spamm_mat_same_shape(*C, A) || *C == A || *C == B) {
-        spamm_set_error("spamm_multiply: C must match A's shape and not alias A or B");
+    } else if (!spamm_mat_same_shape(*C, A) || *C == A || *C == B || !spamm_mat_dense(*C)) {
+        spamm_set_error("spamm_multiply: C must match A's shape, store every leaf and not alias A or B");
         return SPAMM_E_INVAL;
     }
     bool timing = stats && opts && (opts->flags & SPAMM_F_TIMING);
@@ -575,7 +668,7 @@ extern "C" int spamm_multiply_batched(int32_t count, const spamm_mat_t *A, const
             return SPAMM_E_INVAL;
         }
         if ((rc = check_tau(tau[m]))) return rc;
-        if (C[m] && (!spamm_mat_same_shape(C[m], A[m]) || C[m] == A[m] || C[m] == B[m])) {
+        if (C[m] && (!spamm_mat_same_shape(C[m], A[m]) || C[m] == A[m] || C[m] == B[m] || !spamm_mat_dense(C[m]))) {
             spamm_set_error("spamm_multiply_batched: C[%d] must match A[%d]'s shape and not alias A or B", m, m);
             return SPAMM_E_INVAL;
         }

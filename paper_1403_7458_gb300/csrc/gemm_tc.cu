@@ -34,6 +34,7 @@ __device__ __forceinline__ uint32_t tile_item(const CullArgs &c, int64_t I, int6
 {
     if (k >= c.nb) return 0;
     const double b = __ldg(c.n2BT + j * c.P + k);
+    if (b == 0.0) return 0;  // B leaf zero (or not stored): no triple of the step survives
     // B operand leaf (k, j); in symmetric mode its image is leaf (j, k)'s A role
     const int zb = c.sym ? c.zA[c.slotA[j * c.nb + k]] : c.zB[c.slotB[k * c.nb + j]];
     uint32_t mask = 0;

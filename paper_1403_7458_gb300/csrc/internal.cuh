@@ -4,7 +4,8 @@
 //   leaf   : nslots leaves, each b x b FP64 row-major and contiguous
 //            (leaf (i, k) lives at slot[i * nb + k]; dense handles use
 //            slot = i * nb + k, so a block row of leaves is contiguous);
-//   slot   : nb x nb int32 slot map (-1 = absent leaf);
+//   slot   : nb x nb int32 slot map (-1 = absent leaf: a sparse input built
+//            with a drop threshold; outputs store every leaf);
 //   n2     : squared norms of the whole quadtree (Sec. 2, Eqs. 1-3), tiers
 //            t = 0..d concatenated, tier t a 2^t x 2^t row-major grid at
 //            offset (4^t - 1) / 3; the leaf tier is P x P, P = 2^d;
@@ -120,6 +121,8 @@ int spamm_smem_attr(Kernel kernel, size_t bytes, unsigned long long &done_mask)
 cudaError_t spamm_event_record(cudaEvent_t e, cudaStream_t s);
 int spamm_mat_alloc(spamm_mat_t m, int64_t n, int b, cudaStream_t s);
 int spamm_mat_same_shape(spamm_mat_t a, spamm_mat_t b);
+// Every leaf stored, slot = i * nb + k (outputs of products and of SP2).
+int spamm_mat_dense(spamm_mat_t m);
 
 // The early skip of the cull (32 x 32-leaf tier) pays from this many leaf
 // rows on; SP2 rebuilds its iterate's upper tiers only then.

@@ -219,7 +219,8 @@ __device__ void sp2_finish(int mode, const double *idem_part, const double *diag
 // reduces the partials and stores e and the new trace in the state.
 __global__ void __launch_bounds__(kWarps * 32)
 k_sp2_elementwise(int mode, double *__restrict__ X, const double *__restrict__ src,
-                  const int32_t *__restrict__ slot, int64_t n, int64_t nb, int64_t P, int b,
+                  const int32_t *__restrict__ slot, const int32_t *__restrict__ src_slot, int64_t n, int64_t nb,
+                  int64_t P, int b,
                   double *__restrict__ n2, double *__restrict__ n2T, double *__restrict__ idem_part,
                   double *__restrict__ diag_part, Sp2State *st, Sp2Rule rule, double *__restrict__ hist,
                   const int64_t *__restrict__ x2off, int R, int sym)
@@ -236,16 +237,19 @@ k_sp2_elementwise(int mode, double *__restrict__ X, const double *__restrict__ s
         const int64_t I = w / nb, K = w % nb;
         const int64_t base = (int64_t)slot[w] * bb;
         double *x = X + base;
-        const double *y = src + base;
+        // the source in mode 0 is F, which may leave zero leaves unstored
+        const int32_t ss = src_slot[w];
+        const double *y = src + (int64_t)(ss < 0 ? 0 : ss) * bb;
         const bool diag = I == K;
-        bool y0 = false;  // X2 leaf known to be zero
+        bool y0 = ss < 0;  // source leaf known to be zero
         if (mode == 1 && x2off) {
             const int64_t a = (sym && I > K) ? K : I, c = (sym && I > K) ? I : K;
             const int64_t t = (a / R) * nb + c;
             y0 = x2off[t + 1] == x2off[t];
         }
         // X_new = X2 or 2X - X2 = 0 with X = 0 = X2: nothing to read or write
-        const bool untouched = y0 && n2[I * P + K] == 0.0;
+        // (mode 0 writes every leaf of X: X0 = (emax I - F) / range)
+        const bool untouched = mode == 1 && y0 && n2[I * P + K] == 0.0;
         if (untouched && lane == 0) {
             idem_part[w] = 0.0;
             if (diag) diag_part[I] = 0.0;
@@ -371,8 +375,8 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
         }
         *Pout = m;
         created = true;
-    } else if (!spamm_mat_same_shape(*Pout, F) || *Pout == F) {
-        spamm_set_error("sp2_solve: P must match F's shape and not alias F");
+    } else if (!spamm_mat_same_shape(*Pout, F) || *Pout == F || !spamm_mat_dense(*Pout)) {
+        spamm_set_error("sp2_solve: P must match F's shape, store every leaf and not alias F");
         return SPAMM_E_INVAL;
     }
     spamm_mat_t X = *Pout;
@@ -456,7 +460,7 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
     SP2_LAUNCHED();
     k_gershgorin_bounds<<<1, kRedThreads, 0, s>>>(sc.lo, sc.hi, F->n, sc.st);
     SP2_LAUNCHED();
-    k_sp2_elementwise<<<ew_blocks, kWarps * 32, 0, s>>>(0, X->leaf, F->leaf, X->slot, F->n, nb, X->P, X->b,
+    k_sp2_elementwise<<<ew_blocks, kWarps * 32, 0, s>>>(0, X->leaf, F->leaf, X->slot, F->slot, F->n, nb, X->P, X->b,
                                                         X->n2 + tier_offset(X->depth), X->n2T,
                                                         sc.idem_part, sc.diag_part, sc.st,
                                                         Sp2Rule{Ne, 0, 0, 0, 1}, sc.hist, nullptr, 1, 0);
@@ -483,7 +487,7 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
                                                         o.rule, sc.st);
                 SPAMM_CK_LAUNCH();
                 k_sp2_elementwise<<<ew_blocks, kWarps * 32, 0, st>>>(
-                    1, X->leaf, X2->leaf, X->slot, F->n, nb, X->P, X->b, X->n2 + tier_offset(X->depth),
+                    1, X->leaf, X2->leaf, X->slot, X2->slot, F->n, nb, X->P, X->b, X->n2 + tier_offset(X->depth),
                     X->n2T, sc.idem_part, sc.diag_part, sc.st, rule, sc.hist, x2off, 128 / X->b, sym ? 1 : 0);
                 SPAMM_CK_LAUNCH();
                 if (coarse && (r = launch_pyramid(X, st))) return r;

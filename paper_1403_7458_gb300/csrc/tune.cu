@@ -74,10 +74,10 @@ extern "C" int spamm_autotune_batched(int32_t count, const double *const *a, con
         spamm_opts_t bo = o;
         bo.leaf = leaf;
         for (int m = 0; m < count && rc == SPAMM_OK; m++) {
-            rc = spamm_tree_build(a[m], n[m], n[m], &bo, stream, &h.A[m]);
+            rc = spamm_tree_build(a[m], n[m], n[m], 0.0, &bo, stream, &h.A[m]);
             if (rc == SPAMM_OK) {
                 if (b[m] == a[m]) h.B[m] = h.A[m];
-                else rc = spamm_tree_build(b[m], n[m], n[m], &bo, stream, &h.B[m]);
+                else rc = spamm_tree_build(b[m], n[m], n[m], 0.0, &bo, stream, &h.B[m]);
             }
         }
         for (int sc = 0; sc < nsched && rc == SPAMM_OK; sc++) {

@@ -94,7 +94,7 @@ def load():
     lib = ctypes.CDLL(LIB_PATH)
     P, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
     H = ctypes.POINTER(ctypes.c_void_p)
-    lib.spamm_tree_build.argtypes = [P, i64, i64, ctypes.POINTER(_Opts), P, H]
+    lib.spamm_tree_build.argtypes = [P, i64, i64, dbl, ctypes.POINTER(_Opts), P, H]
     lib.spamm_multiply.argtypes = [P, P, dbl, H, ctypes.POINTER(_Opts), ctypes.POINTER(_Stats), P]
     lib.spamm_multiply_batched.argtypes = [i32, P, P, P, P, ctypes.POINTER(_Opts), ctypes.POINTER(_Stats), P]
     lib.spamm_autotune_batched.argtypes = [i32, P, P, P, P, ctypes.POINTER(_Opts), i32,
@@ -102,7 +102,7 @@ def load():
     lib.spamm_to_dense.argtypes = [P, P, i64, P]
     lib.spamm_norms.argtypes = [P, i32, P, P]
     lib.spamm_info.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i64),
-                               ctypes.POINTER(i32)]
+                               ctypes.POINTER(i32), ctypes.POINTER(i64)]
     lib.spamm_task_list.argtypes = [P, P, dbl, P, P, i64, ctypes.POINTER(i64), P]
     lib.spamm_cull_noalloc.argtypes = [P, i64, P, i64, i64, dbl, P, P, i64, P]
     lib.spamm_free.argtypes = [P]
@@ -162,9 +162,11 @@ class Matrix:
     def __init__(self, handle):
         self._h = ctypes.c_void_p(handle)
         n, leaf, nb, depth = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32()
+        stored = ctypes.c_int64()
         _check(load().spamm_info(self._h, ctypes.byref(n), ctypes.byref(leaf), ctypes.byref(nb),
-                                 ctypes.byref(depth)), "spamm_info")
+                                 ctypes.byref(depth), ctypes.byref(stored)), "spamm_info")
         self.n, self.leaf, self.nb, self.depth = n.value, leaf.value, nb.value, depth.value
+        self.stored = stored.value  # leaves stored (nb * nb when dense)
 
     @property
     def handle(self):
@@ -182,12 +184,13 @@ class Matrix:
             pass
 
 
-def tree_build(a, leaf: int = 32, stream=None) -> Matrix:
-    """Leaf storage + norm quadtree of an n x n FP64 matrix (host or device)."""
+def tree_build(a, leaf: int = 32, drop: float = 0.0, stream=None) -> Matrix:
+    """Leaf storage + norm quadtree of an n x n FP64 matrix (host or device).
+    Leaves with ||leaf||_F <= drop are not stored (drop < 0: store all)."""
     ptr, n, ld, keep = _data(a)
     h = ctypes.c_void_p()
     opts = _Opts(leaf, FP64, 0, 0)
-    _check(load().spamm_tree_build(ptr, n, ld, ctypes.byref(opts), _stream(stream),
+    _check(load().spamm_tree_build(ptr, n, ld, float(drop), ctypes.byref(opts), _stream(stream),
                                    ctypes.byref(h)), "spamm_tree_build")
     del keep
     return Matrix(h.value)

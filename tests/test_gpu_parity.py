@@ -261,3 +261,40 @@ def test_spamm_sampled_leaves_at_n16384(cuda_lib):
         assert np.all(np.abs(gotx - ref) <= slack + 2 * g * absref + 1e-300), (i, j)
     del d64, dx
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("drop", [0.0, 1e-6, 1e-3])
+def test_sparse_leaf_storage_equals_dense_with_dropped_leaves_zeroed(cuda_lib, drop):
+    """spamm_tree_build with a drop threshold stores only the leaves with
+    ||leaf||_F > drop; everything after behaves as the dense matrix with the
+    other leaves set to zero: norms, task lists, FP64 and exact-slice
+    products, and SP2 (F stored sparsely), bit for bit."""
+    n, b = 2048, 32
+    h = synth.tb_hamiltonian(n, 1, decay=1.0)
+    nb = n // b
+    n2 = oracle.leaf_norms2(h, b)[:nb, :nb]
+    keep = n2 > drop * drop
+    hz = h * np.kron(keep, np.ones((b, b)))
+    S = cuda_lib.tree_build(_dev(h), leaf=b, drop=drop)
+    D = cuda_lib.tree_build(_dev(hz), leaf=b, drop=-1.0)
+    assert S.stored == int(keep.sum()) < nb * nb and D.stored == nb * nb
+    assert np.array_equal(cuda_lib.to_dense(S).cpu().numpy(), hz)
+    for t in range(S.depth + 1):
+        assert np.array_equal(cuda_lib.norms(S, t), cuda_lib.norms(D, t))
+    for prec, sl in ((cuda_lib.FP64, 0), (cuda_lib.OZAKI_BF16, 7), (cuda_lib.TF32, 0)):
+        Cs, ss = cuda_lib.multiply(S, S, 1e-8, prec=prec, slices=sl, stats=True)
+        Cd, sd = cuda_lib.multiply(D, D, 1e-8, prec=prec, slices=sl, stats=True)
+        assert ss["tasks"] == sd["tasks"]
+        assert np.array_equal(cuda_lib.to_dense(Cs).cpu().numpy(), cuda_lib.to_dense(Cd).cpu().numpy())
+    for prec, sl in ((cuda_lib.FP64, 0), (cuda_lib.OZAKI_BF16, 7)):
+        Ps, rs = cuda_lib.sp2_solve(S, n / 2, 1e-8, prec=prec, slices=sl)
+        Pd, rd = cuda_lib.sp2_solve(D, n / 2, 1e-8, prec=prec, slices=sl)
+        assert np.array_equal(rs["history"], rd["history"])
+        assert np.array_equal(cuda_lib.to_dense(Ps).cpu().numpy(), cuda_lib.to_dense(Pd).cpu().numpy())
+    # a handle with absent leaves is an input only
+    with pytest.raises(cuda_lib.SpammError) as ei:
+        cuda_lib.multiply(D, D, 1e-8, C=S)
+    assert ei.value.status == cuda_lib.E_INVAL
+    with pytest.raises(cuda_lib.SpammError) as ei:
+        cuda_lib.sp2_solve(D, n / 2, 1e-8, P=S)
+    assert ei.value.status == cuda_lib.E_INVAL
