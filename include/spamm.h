@@ -349,7 +349,9 @@ typedef struct {
  * symmetric (the slice arithmetic is exact), so only the upper block triangle
  * of X^2 is formed and mirrored; the result is bit-identical to forming all
  * leaves (SPAMM_F_NOSYM in flags forces the full product).
- * F      : symmetric handle; Ne in (0, n) is the trace of the projector.
+ * F      : symmetric handle (checked on the leaf norms: mirror leaves whose
+ *          norms differ beyond 1e-12 relative give E_INVAL); Ne in (0, n)
+ *          is the trace of the projector.
  * P      : *P == NULL creates a new handle; otherwise reused (F's shape,
  *          every leaf stored).  F may have absent leaves.
  * report : optional; filled when given.

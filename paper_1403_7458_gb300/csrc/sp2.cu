@@ -107,6 +107,19 @@ __global__ void k_symmetry(const double *__restrict__ leaf, const int32_t *__res
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicExch(asym, 1);
 }
 
+// Cheap symmetry screen on the leaf norms: flags F when some pair of mirror
+// leaves differs in squared norm by more than rel times the larger one.
+__global__ void k_norm_symmetry(const double *__restrict__ n2, int64_t nb, int64_t P, double rel,
+                                int32_t *__restrict__ flag)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nb * nb) return;
+    const int64_t I = g / nb, K = g % nb;
+    if (I >= K) return;
+    const double a = n2[I * P + K], b = n2[K * P + I];
+    if (fabs(a - b) > rel * fmax(a, b)) atomicExch(flag, 1);
+}
+
 __global__ void __launch_bounds__(kRedThreads)
 k_gershgorin_bounds(const double *__restrict__ lo, const double *__restrict__ hi, int64_t n,
                     Sp2State *st)
@@ -446,6 +459,22 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
         for (int q = 0; q < 5 * kBatch; q++) SP2_CUDA(cudaEventCreate(&evs[q]));
     SP2_CUDA(cudaEventRecord(ev0, s));
 
+    {
+        // F must be symmetric: mirror leaves' norms agree to 1e-12 relative
+        // (2e-12 on squared norms)
+        SP2_CUDA(cudaMemsetAsync(sc.flag + 1, 0, sizeof(int32_t), s));
+        k_norm_symmetry<<<(unsigned)((G + 255) / 256), 256, 0, s>>>(F->n2 + tier_offset(F->depth), nb, F->P, 2e-12,
+                                                                   sc.flag + 1);
+        SP2_LAUNCHED();
+        int32_t asym_norms = 0;
+        SP2_CUDA(cudaMemcpyAsync(&asym_norms, sc.flag + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        SP2_CUDA(cudaStreamSynchronize(s));
+        if (asym_norms) {
+            spamm_set_error("sp2_solve: F is not symmetric (mirror leaf norms differ beyond 1e-12 relative)");
+            rc = SPAMM_E_INVAL;
+            goto done;
+        }
+    }
     if (prec_is_tc(o.prec) && !(o.flags & SPAMM_F_NOSYM)) {
         SP2_CUDA(cudaMemsetAsync(sc.flag, 0, sizeof(int32_t), s));
         k_symmetry<<<(unsigned)((G + 7) / 8), 256, 0, s>>>(F->leaf, F->slot, nb, F->b, sc.flag);

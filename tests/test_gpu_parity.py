@@ -298,3 +298,13 @@ def test_sparse_leaf_storage_equals_dense_with_dropped_leaves_zeroed(cuda_lib, d
     with pytest.raises(cuda_lib.SpammError) as ei:
         cuda_lib.sp2_solve(D, n / 2, 1e-8, P=S)
     assert ei.value.status == cuda_lib.E_INVAL
+
+
+def test_sp2_rejects_an_asymmetric_hamiltonian(cuda_lib):
+    n = 256
+    h = synth.tb_hamiltonian(n, 5)
+    h[3, 40] += 1e-3                      # mirror leaves' norms now differ
+    F = cuda_lib.tree_build(_dev(h), leaf=32)
+    with pytest.raises(cuda_lib.SpammError) as ei:
+        cuda_lib.sp2_solve(F, n / 2, 1e-8)
+    assert ei.value.status == cuda_lib.E_INVAL
