@@ -5,6 +5,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "internal.cuh"
@@ -644,6 +646,43 @@ extern "C" int spamm_multiply(spamm_mat_t A, spamm_mat_t B, double tau, spamm_ma
 }
 
 // ---------------------------------------------------------------------------
+// Auxiliary streams of the current device for the per-product preparation of
+// batched products (created once, kept for the life of the process).  The
+// returned lock serialises batched calls on the device while they enqueue.
+// ---------------------------------------------------------------------------
+constexpr int kAuxStreams = 4;
+struct AuxStreams {
+    cudaStream_t st[kAuxStreams];
+    cudaEvent_t fork;
+    cudaEvent_t join[kAuxStreams];
+};
+
+static AuxStreams *aux_streams(std::unique_lock<std::mutex> *lock)
+{
+    static std::mutex mu;
+    static std::map<int, AuxStreams *> sets;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::unique_lock<std::mutex> l(mu);
+    auto it = sets.find(dev);
+    if (it == sets.end()) {
+        AuxStreams *a = new AuxStreams();
+        bool ok = cudaEventCreateWithFlags(&a->fork, cudaEventDisableTiming) == cudaSuccess;
+        for (int i = 0; i < kAuxStreams && ok; i++) {
+            ok = cudaStreamCreateWithFlags(&a->st[i], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&a->join[i], cudaEventDisableTiming) == cudaSuccess;
+        }
+        if (!ok) {
+            spamm_set_error("auxiliary streams: creation failed");
+            return nullptr;  // (what was created stays; only on a failing device)
+        }
+        it = sets.emplace(dev, a).first;
+    }
+    *lock = std::move(l);
+    return it->second;
+}
+
+// ---------------------------------------------------------------------------
 // Batched products: per product slicing / cull, then ONE leaf-product launch
 // per group of at most kMaxBatch products, then per product output norms.
 // ---------------------------------------------------------------------------
@@ -720,19 +759,51 @@ extern "C" int spamm_multiply_batched(int32_t count, const spamm_mat_t *A, const
         w[q] = &C[ord[q]]->ws;
     }
     if (rc == SPAMM_OK && timing && spamm_event_record(ev[0], s) != cudaSuccess) rc = SPAMM_E_CUDA;
+    // per product: slicing and culling, spread over the auxiliary streams
+    // (forked from s and joined back before the leaf products); products that
+    // share an input handle stay on one stream (they write the same slices)
+    std::unique_lock<std::mutex> aux_lock;
+    AuxStreams *aux = rc == SPAMM_OK ? aux_streams(&aux_lock) : nullptr;
+    if (rc == SPAMM_OK && !aux) rc = SPAMM_E_CUDA;
+    std::vector<int> lane_of(count, 0);
+    if (rc == SPAMM_OK) {
+        std::vector<int> root(count), lane_of_root(count, -1);
+        int next = 0;
+        for (int q = 0; q < count; q++) {
+            root[q] = q;
+            for (int p2 = 0; p2 < q; p2++)
+                if (a[q] == a[p2] || a[q] == b[p2] || b[q] == a[p2] || b[q] == b[p2]) {
+                    root[q] = root[p2];
+                    break;
+                }
+            if (lane_of_root[root[q]] < 0) lane_of_root[root[q]] = next++ % kAuxStreams;
+            lane_of[q] = lane_of_root[root[q]];
+        }
+        if (cudaEventRecord(aux->fork, s) != cudaSuccess) rc = SPAMM_E_CUDA;
+        for (int i = 0; i < kAuxStreams && rc == SPAMM_OK; i++)
+            if (cudaStreamWaitEvent(aux->st[i], aux->fork, 0) != cudaSuccess) rc = SPAMM_E_CUDA;
+    }
     for (int q = 0; q < count && rc == SPAMM_OK; q++) {
         const int64_t nb = a[q]->nb;
-        if ((rc = ws_reserve_groups(w[q], nb * nb, nb, s))) break;
+        cudaStream_t sq = aux->st[lane_of[q]];
+        if ((rc = ws_reserve_groups(w[q], nb * nb, nb, sq))) break;
         if (!tcp) {
-            rc = spamm_cull(a[q], b[q], tau[ord[q]], w[q], nb, a[q]->P, s, false, nullptr, true);
+            rc = spamm_cull(a[q], b[q], tau[ord[q]], w[q], nb, a[q]->P, sq, false, nullptr, true);
             w[q]->task_total = w[q]->off + nb * nb;
             w[q]->pair_units = nullptr;
         } else {
-            rc = slice_operands(a[q], b[q], sl, el, 0, s, nullptr, unit, fsplit);
+            rc = slice_operands(a[q], b[q], sl, el, 0, sq, nullptr, unit, fsplit);
             if (rc == SPAMM_OK)
-                rc = tc_tile_cull(a[q], b[q], tau[ord[q]], w[q], 0, sl, s,
+                rc = tc_tile_cull(a[q], b[q], tau[ord[q]], w[q], 0, sl, sq,
                                   opts && (opts->flags & SPAMM_F_HEAVIEST));
-            if (rc == SPAMM_OK) rc = tc_zero_empty_tiles(c[q], w[q], s);
+            if (rc == SPAMM_OK) rc = tc_zero_empty_tiles(c[q], w[q], sq);
+        }
+    }
+    if (aux) {
+        // join (also after a failure, so that no forked stream is left dangling)
+        for (int i = 0; i < kAuxStreams; i++) {
+            cudaEventRecord(aux->join[i], aux->st[i]);
+            cudaStreamWaitEvent(s, aux->join[i], 0);
         }
     }
     if (rc == SPAMM_OK && timing && spamm_event_record(ev[1], s) != cudaSuccess) rc = SPAMM_E_CUDA;
@@ -743,8 +814,20 @@ extern "C" int spamm_multiply_batched(int32_t count, const spamm_mat_t *A, const
                  : launch_gemm_fp64_batched(k, &a[q0], &b[q0], &c[q0], &w[q0], s, ctr);
     }
     if (rc == SPAMM_OK && timing && spamm_event_record(ev[2], s) != cudaSuccess) rc = SPAMM_E_CUDA;
-    for (int q = 0; q < count && rc == SPAMM_OK; q++)
-        rc = tcp ? launch_leaf_norms(c[q], s) : launch_pyramid(c[q], s);
+    // output norms per product, again spread over the auxiliary streams
+    if (rc == SPAMM_OK) {
+        if (cudaEventRecord(aux->fork, s) != cudaSuccess) rc = SPAMM_E_CUDA;
+        for (int i = 0; i < kAuxStreams && rc == SPAMM_OK; i++)
+            if (cudaStreamWaitEvent(aux->st[i], aux->fork, 0) != cudaSuccess) rc = SPAMM_E_CUDA;
+        for (int q = 0; q < count && rc == SPAMM_OK; q++) {
+            cudaStream_t sq = aux->st[lane_of[q]];
+            rc = tcp ? launch_leaf_norms(c[q], sq) : launch_pyramid(c[q], sq);
+        }
+        for (int i = 0; i < kAuxStreams; i++) {
+            cudaEventRecord(aux->join[i], aux->st[i]);
+            cudaStreamWaitEvent(s, aux->join[i], 0);
+        }
+    }
     if (rc == SPAMM_OK && timing && spamm_event_record(ev[3], s) != cudaSuccess) rc = SPAMM_E_CUDA;
     if (rc == SPAMM_OK && stats) {
         // totals (one blocking read per product) and the device error words
