@@ -183,8 +183,8 @@ def run_ours(args):
     def solve(timing=False, p=prec, sl=slices, out=None):
         return spamm.sp2_solve(F, ne, tau, P=out, prec=p, slices=sl, timing=timing)
 
-    for _ in range(args.warmup):
-        P, _ = solve(out=P)
+    for _ in range(args.warmup):  # same settings as the timed steps
+        P, _ = solve(timing=True, out=P)
     torch.cuda.synchronize()
 
     # ---- device-timed region: inputs resident in HBM ----

@@ -140,12 +140,13 @@ k_tile_emit(CullArgs c, const int64_t *__restrict__ off, uint32_t *__restrict__ 
 constexpr int kScanThreads = 1024;
 
 // exclusive scan of counts -> off (one block), the rank of every tile among
-// the tiles with work -> nz, plus the totals of tasks / pairs / useful pairs
+// the tiles with work -> nz (and, when order is given, the row-major order
+// of those tiles), plus the totals of tasks / pairs / useful pairs
 __global__ void __launch_bounds__(kScanThreads)
 k_tile_scan(const int32_t *__restrict__ stop, const int32_t *__restrict__ counts, const int32_t *__restrict__ tasks,
             const int32_t *__restrict__ pairs, const int32_t *__restrict__ useful, int64_t G,
-            int64_t *__restrict__ off, int32_t *__restrict__ nz, int64_t *__restrict__ task_total,
-            int64_t *__restrict__ pair_total, int64_t *__restrict__ useful_total)
+            int64_t *__restrict__ off, int32_t *__restrict__ nz, int32_t *__restrict__ order,
+            int64_t *__restrict__ task_total, int64_t *__restrict__ pair_total, int64_t *__restrict__ useful_total)
 {
     __shared__ int64_t part[kScanThreads];
     __shared__ int32_t zpart[kScanThreads];
@@ -192,6 +193,7 @@ k_tile_scan(const int32_t *__restrict__ stop, const int32_t *__restrict__ counts
     for (int64_t q = lo; q < hi; q++) {
         off[q] = run;
         nz[q] = zrun;
+        if (order && counts[q] > 0) order[zrun] = (int32_t)q;  // row-major hand-out order
         run += counts[q];
         zrun += counts[q] > 0;
     }
@@ -226,15 +228,6 @@ __global__ void k_tile_bins_scan(const int32_t *__restrict__ stop, int32_t *__re
             run += v;
         }
     }
-}
-
-// Row-major order of the tiles with work (their rank from the scan).
-__global__ void k_tile_natural(const int32_t *__restrict__ stop, const int32_t *__restrict__ counts,
-                               const int32_t *__restrict__ nz, int64_t G, int32_t *__restrict__ order)
-{
-    if (stop && *stop) return;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < G && counts[t] > 0) order[nz[t]] = (int32_t)t;
 }
 
 // Zeroes the output leaves of tiles without work (they are never handed
@@ -345,8 +338,12 @@ int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, i
     SPAMM_CK_LAUNCH();
     // toff[0..T] offsets, toff[T+1] surviving triples, toff[T+2] issued slice-pair
     // work, toff[T+3] slice pairs the surviving triples need
+    ws->tsym = sym;
+    ws->tactive = sym ? nI * nb - (int64_t)R * nI * (nI - 1) / 2 : T;
+    SPAMM_CK(cudaMemsetAsync(ws->torder, 0xFF, sizeof(int32_t) * ws->tactive, s));  // -1: no tile
     k_tile_scan<<<1, kScanThreads, 0, s>>>(ws->stop, ws->tcounts, ws->ttasks, ws->tpairs, ws->tuseful, T,
-                                           ws->toff, ws->tnz, ws->toff + T + 1, ws->toff + T + 2, ws->toff + T + 3);
+                                           ws->toff, ws->tnz, heaviest_first ? nullptr : ws->torder,
+                                           ws->toff + T + 1, ws->toff + T + 2, ws->toff + T + 3);
     SPAMM_CK_LAUNCH();
     const int64_t worst = T * nb;
     if (ws->tlist_cap < worst) {
@@ -358,9 +355,6 @@ int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, i
     }
     k_tile_emit<<<blocks, kWarps * 32, 0, s>>>(c, ws->toff, ws->tlist, ws->tlist_cap, ws->counter + 8);
     SPAMM_CK_LAUNCH();
-    ws->tsym = sym;
-    ws->tactive = sym ? nI * nb - (int64_t)R * nI * (nI - 1) / 2 : T;
-    SPAMM_CK(cudaMemsetAsync(ws->torder, 0xFF, sizeof(int32_t) * ws->tactive, s));  // -1: no tile
     if (heaviest_first) {
         SPAMM_CK(cudaMemsetAsync(ws->tbins, 0, sizeof(int32_t) * (nb + 1), s));
         k_tile_hist<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(ws->stop, ws->tcounts, nb, T, sym, R, ws->tbins);
@@ -369,9 +363,6 @@ int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, i
         SPAMM_CK_LAUNCH();
         k_tile_scatter<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(ws->stop, ws->tcounts, nb, T, sym, R, ws->tbins,
                                                                      ws->torder);
-        SPAMM_CK_LAUNCH();
-    } else {
-        k_tile_natural<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(ws->stop, ws->tcounts, ws->tnz, T, ws->torder);
         SPAMM_CK_LAUNCH();
     }
     return SPAMM_OK;

@@ -73,6 +73,7 @@ struct spamm_mat {
     int sl_s = 0;
     int sl_e = 0;                     // bytes per slice element
     unsigned long long *scale = nullptr;  // [0] max |x| bits, [1] int32 sigma, int32 overflow flag
+    bool scale_unit = false;              // scale[0] holds the fixed unit maximum (1.0)
     bool tiers_ok = true;  // upper norm tiers match the leaf tier (the cull's early skip reads them)
     SpammWorkspace ws;  // used when this handle is the output of a product
 };

@@ -265,14 +265,20 @@ int launch_slices(spamm_mat_t m, int s, int e, bool tile_a, bool per_leaf, bool 
     const int64_t rows = ((m->nb + R - 1) / R) * R;
     const int64_t count = m->nslots * m->b * m->b;
     const int blocks = spamm_num_sms() * 8;
-    // the scale matters to exact slices only: float splits take no maximum
+    // the scale matters to exact slices only: float splits take no maximum;
+    // a fixed unit scale is written once and kept while it stays in force
     if (unit_scale || float_split) {
-        k_unit_scale<<<1, 1, 0, st>>>(stop, reinterpret_cast<unsigned long long *>(m->scale));
+        if (!m->scale_unit) {
+            k_unit_scale<<<1, 1, 0, st>>>(nullptr, reinterpret_cast<unsigned long long *>(m->scale));
+            SPAMM_CK_LAUNCH();
+            m->scale_unit = true;
+        }
     } else {
         SPAMM_CK(cudaMemsetAsync(m->scale, 0, sizeof(unsigned long long), st));  // max bits
         k_absmax<<<blocks, 256, 0, st>>>(stop, m->leaf, count, reinterpret_cast<unsigned long long *>(m->scale));
+        SPAMM_CK_LAUNCH();
+        m->scale_unit = false;
     }
-    SPAMM_CK_LAUNCH();
     unsigned long long *mx = reinterpret_cast<unsigned long long *>(m->scale);
     int32_t *sig = reinterpret_cast<int32_t *>(m->scale + 1);
     const int64_t npos = rows * m->nb;
