@@ -277,6 +277,16 @@ void spamm_free(spamm_mat_t M);
  */
 void spamm_release_scratch(spamm_mat_t M, void *stream);
 
+/*
+ * Self-test of the device watchdog that bounds every wait inside the
+ * library's kernels: one GPU thread waits, through the same bounded wait, on
+ * a barrier that nothing completes; after about `ms` milliseconds (1..10000)
+ * the wait gives up and the call returns SPAMM_E_TIMEOUT (the expected
+ * result), with the device context still usable.  Blocking.  No fault, no
+ * trap: the kernel simply returns.  The paper has no counterpart.
+ */
+int spamm_watchdog_selftest(int32_t ms, void *stream);
+
 /* Static text for a status code. */
 const char *spamm_strerror(int status);
 

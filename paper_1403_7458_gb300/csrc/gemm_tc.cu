@@ -266,6 +266,55 @@ __global__ void k_tile_scatter(const int32_t *__restrict__ stop, const int32_t *
 
 int tc_launch_b32(const tc::TcArgs &a, int S, int E, cudaStream_t s) { return tc::launch_leaf<32>(a, S, E, s); }
 
+namespace {
+
+// Watchdog self-test: one thread waits, with the kernels' bounded wait, on an
+// mbarrier that nothing arrives at; the wait gives up after `limit` cycles
+// and the kernel reports it in *err (1 = gave up, 2 = the barrier completed).
+__global__ void k_watchdog(long long limit, int32_t *err)
+{
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x != 0) return;
+    abort_flag = 0;
+    tc::mbar_init(tc::smem_u32(&bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    const bool done = tc::mbar_wait(tc::smem_u32(&bar), 0, &abort_flag, limit);
+    *err = done ? 2 : 1;
+}
+
+}  // namespace
+
+extern "C" int spamm_watchdog_selftest(int32_t ms, void *stream)
+{
+    if (ms < 1 || ms > 10000) {
+        spamm_set_error("spamm_watchdog_selftest: ms must be in 1..10000");
+        return SPAMM_E_INVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0, khz = 0;
+    SPAMM_CK(cudaGetDevice(&dev));
+    SPAMM_CK(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev));
+    if (khz <= 0) khz = 2070000;
+    int32_t *err = nullptr;
+    int rc = spamm_alloc((void **)&err, sizeof(int32_t), s);
+    if (rc) return rc;
+    SPAMM_CK(cudaMemsetAsync(err, 0, sizeof(int32_t), s));
+    k_watchdog<<<1, 32, 0, s>>>((long long)ms * khz, err);
+    SPAMM_CK_LAUNCH();
+    int32_t h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    spamm_release(err, s);
+    if (e != cudaSuccess) return spamm_cuda_fail(e, "watchdog self-test", __FILE__, __LINE__);
+    if (h == 1) {
+        spamm_set_error("watchdog self-test: the wait gave up after %d ms (expected)", ms);
+        return SPAMM_E_TIMEOUT;
+    }
+    spamm_set_error("watchdog self-test: unexpected state %d", h);
+    return SPAMM_E_CUDA;
+}
+
 int tc_mode_ok(int prec, int slices, int leaf)
 {
     if (!prec_is_tc(prec) || (leaf != 16 && leaf != 32 && leaf != 64)) return 0;

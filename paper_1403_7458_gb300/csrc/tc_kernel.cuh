@@ -105,7 +105,8 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
 // Bounded wait: false after about kTimeoutCycles SM cycles (or as soon as
 // another role has failed).  The SM cycle counter is read, not the global
 // timer, which is far slower to read and would sit on every handoff.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                          long long limit = kTimeoutCycles)
 {
     if (mbar_try(bar, parity)) return true;
     const long long t0 = clock64();
@@ -113,7 +114,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
         if (mbar_try(bar, parity)) return true;
         if ((it & 255) == 0) {
             if (*abort_flag) return false;
-            if (clock64() - t0 > kTimeoutCycles) return false;
+            if (clock64() - t0 > limit) return false;
         }
     }
 }

@@ -105,6 +105,7 @@ def load():
                                ctypes.POINTER(i32), ctypes.POINTER(i64)]
     lib.spamm_task_list.argtypes = [P, P, dbl, P, P, i64, ctypes.POINTER(i64), P]
     lib.spamm_cull_noalloc.argtypes = [P, i64, P, i64, i64, dbl, P, P, i64, P]
+    lib.spamm_watchdog_selftest.argtypes = [i32, P]
     lib.spamm_free.argtypes = [P]
     lib.spamm_free.restype = None
     lib.spamm_release_scratch.argtypes = [P, P]
@@ -117,7 +118,7 @@ def load():
                               ctypes.POINTER(_Sp2Report), P]
     for name in ("spamm_tree_build", "spamm_multiply", "spamm_multiply_batched", "spamm_autotune_batched",
                  "spamm_to_dense", "spamm_norms",
-                 "spamm_info", "spamm_task_list", "sp2_solve", "spamm_cull_noalloc"):
+                 "spamm_info", "spamm_task_list", "sp2_solve", "spamm_cull_noalloc", "spamm_watchdog_selftest"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -279,6 +280,12 @@ def autotune_batched(a, b, tau, prec: int = FP64, slices: int = 0, reps: int = 3
     del keep
     cands = [(out.cand_leaf[q], out.cand_flags[q], out.cand_ms[q], out.cand_tasks[q]) for q in range(out.tried)]
     return {"leaf": out.leaf, "flags": out.flags, "ms": out.ms, "candidates": cands}
+
+
+def watchdog_selftest(ms: int = 100, stream=None) -> int:
+    """Status of the watchdog self-test (E_TIMEOUT when the bounded wait gave
+    up as it should)."""
+    return load().spamm_watchdog_selftest(int(ms), _stream(stream))
 
 
 def release_scratch(M: Matrix, stream=None):

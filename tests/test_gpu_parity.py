@@ -308,3 +308,18 @@ def test_sp2_rejects_an_asymmetric_hamiltonian(cuda_lib):
     with pytest.raises(cuda_lib.SpammError) as ei:
         cuda_lib.sp2_solve(F, n / 2, 1e-8)
     assert ei.value.status == cuda_lib.E_INVAL
+
+
+def test_device_watchdog_gives_up_and_the_context_survives(cuda_lib):
+    """Every wait in the library's kernels is bounded; a wait on a barrier that
+    nothing completes gives up and is reported as E_TIMEOUT, after which the
+    device still computes."""
+    import time
+    t0 = time.perf_counter()
+    assert cuda_lib.watchdog_selftest(200) == cuda_lib.E_TIMEOUT
+    assert 0.1 < time.perf_counter() - t0 < 5.0
+    a = synth.decaying_matrix(128, 0)
+    A = cuda_lib.tree_build(_dev(a), leaf=32)
+    C, st = cuda_lib.multiply(A, A, 1e-6, stats=True)
+    ref, tasks = oracle.spamm(a, a, 32, 1e-6, want_tasks=True)
+    assert st["tasks"] == len(tasks)
