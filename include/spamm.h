@@ -323,7 +323,8 @@ typedef struct {
 #define SP2_H_BRANCH 3 /* 1: X <- X^2, 0: X <- 2X - X^2         */
 #define SP2_H_TASKS 4  /* surviving leaf triples of the product */
 #define SP2_H_TRNEW 5  /* tr of the updated X                   */
-#define SP2_H_COLS 6
+#define SP2_H_FILL 6   /* fraction of the updated X's leaves that are nonzero */
+#define SP2_H_COLS 7
 
 typedef struct {
     int32_t iters;        /* iterations run                               */

@@ -45,6 +45,7 @@ struct Sp2State {
     int32_t pad;
     double ehist[3]; // e of the last three iterations
     int64_t units;   // tensor path: slice pairs of surviving triples, summed
+    unsigned long long nonzero;  // leaves of the updated X with nonzero norm
 };
 
 // Stopping rule parameters (same rule as the host-side description in spamm.h)
@@ -196,6 +197,7 @@ __device__ void sp2_finish(int mode, const double *idem_part, const double *diag
             row[SP2_H_BRANCH] = st->branch ? 1.0 : 0.0;
             row[SP2_H_TASKS] = (double)st->tasks;
             row[SP2_H_TRNEW] = tn;
+            row[SP2_H_FILL] = (double)atomicAdd(&st->nonzero, 0ull) / (double)(nb * nb);
             st->ehist[0] = st->ehist[1];
             st->ehist[1] = st->ehist[2];
             st->ehist[2] = e;
@@ -302,6 +304,7 @@ k_sp2_elementwise(int mode, double *__restrict__ X, const double *__restrict__ s
             double r = ek > 0 ? sq_sum_round(acc, ek) : 0.0;
             n2[I * P + K] = r;
             n2T[K * P + I] = r;
+            if (r > 0.0) atomicAdd(&st->nonzero, 1ull);  // fill statistics
             idem_part[w] = idem;
             if (diag) diag_part[I] = dsum;
         }
@@ -327,6 +330,7 @@ k_sp2_decide(const double *__restrict__ tr_part, int64_t nb, const int64_t *__re
         st->t2 = t2;
         st->branch = take;
         st->tasks = *off_end;
+        st->nonzero = 0;  // counted again by this iteration's update
         if (units) st->units += *units;
     }
 }

@@ -32,7 +32,7 @@ F_NOGRAPH = 8
 TUNE_MAX = 6
 RULE_TRACE_DISTANCE, RULE_TRACE_ABOVE = 0, 1
 STOP_CONVERGED, STOP_STAGNATED, STOP_FIXED, STOP_MAXITER = 0, 1, 2, 3
-H_COLS = 6
+H_FILL, H_COLS = 6, 7
 
 _lib = None
 

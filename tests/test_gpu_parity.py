@@ -323,3 +323,17 @@ def test_device_watchdog_gives_up_and_the_context_survives(cuda_lib):
     C, st = cuda_lib.multiply(A, A, 1e-6, stats=True)
     ref, tasks = oracle.spamm(a, a, 32, 1e-6, want_tasks=True)
     assert st["tasks"] == len(tasks)
+
+
+def test_sp2_history_records_leaf_fill(cuda_lib):
+    n, b = 2048, 32
+    h = synth.tb_hamiltonian(n, 2, decay=1.0)
+    F = cuda_lib.tree_build(_dev(h), leaf=b)
+    for prec in (cuda_lib.FP64, cuda_lib.OZAKI_BF16):
+        P, rep = cuda_lib.sp2_solve(F, n / 2, 1e-8, prec=prec)
+        nb = n // b
+        fill = float((cuda_lib.norms(P, P.depth)[:nb, :nb] > 0).mean())
+        hist = rep["history"]
+        assert hist.shape[1] == cuda_lib.H_COLS
+        assert hist[-1, cuda_lib.H_FILL] == pytest.approx(fill, abs=0.5 / (nb * nb))
+        assert np.all((hist[:, cuda_lib.H_FILL] > 0) & (hist[:, cuda_lib.H_FILL] <= 1))
