@@ -7,7 +7,8 @@
 namespace {
 
 // ---------------------------------------------------------------------------
-// tile cull: work lists of items (k, mask, zA, zB), grouped by tile t = I * nb + j
+// tile cull: work lists of items (k, mask, zA, zB); tile t = I * nb + j owns
+// the list segment [t nb, t nb + count[t])
 // ---------------------------------------------------------------------------
 constexpr int kWarps = 8;
 
@@ -77,9 +78,12 @@ __device__ __forceinline__ int item_pairs(uint32_t w, int S)
     return m * (m + 1) / 2;
 }
 
+// One warp per tile: tests the candidates k (ballot), writes the tile's work
+// items into its own segment of the list, [t nb, t nb + count), and counts
+// them, the surviving triples and the slice pairs.
 __global__ void __launch_bounds__(kWarps * 32)
 k_tile_count(CullArgs c, int32_t *__restrict__ counts, int32_t *__restrict__ tasks,
-             int32_t *__restrict__ pairs, int32_t *__restrict__ useful)
+             int32_t *__restrict__ pairs, int32_t *__restrict__ useful, uint32_t *__restrict__ list)
 {
     if (c.stop && *c.stop) return;
     const int64_t t = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
@@ -92,11 +96,17 @@ k_tile_count(CullArgs c, int32_t *__restrict__ counts, int32_t *__restrict__ tas
         if (lane == 0) counts[t] = tasks[t] = pairs[t] = useful[t] = 0;
         return;
     }
+    uint32_t *seg = list + t * c.nb;
+    const unsigned lt = (1u << lane) - 1u;
     for (int64_t k0 = 0; k0 < c.nb; k0 += 32) {
         if (!coarse_pass(c, I, k0, j)) continue;  // warp-uniform
         const uint32_t w = tile_item(c, I, j, k0 + lane, ntask, nuse);
-        cnt += __popc(__ballot_sync(0xffffffffu, w != 0));
-        if (w) npair += item_pairs(w, c.S);
+        const unsigned bal = __ballot_sync(0xffffffffu, w != 0);
+        if (w) {
+            seg[cnt + __popc(bal & lt)] = w;
+            npair += item_pairs(w, c.S);
+        }
+        cnt += __popc(bal);
     }
     for (int o = 16; o > 0; o >>= 1) {
         ntask += __shfl_xor_sync(0xffffffffu, ntask, o);
@@ -108,32 +118,6 @@ k_tile_count(CullArgs c, int32_t *__restrict__ counts, int32_t *__restrict__ tas
         tasks[t] = ntask;
         pairs[t] = active ? npair : 0;
         useful[t] = active ? nuse : 0;
-    }
-}
-
-__global__ void __launch_bounds__(kWarps * 32)
-k_tile_emit(CullArgs c, const int64_t *__restrict__ off, uint32_t *__restrict__ list, int64_t cap,
-            int32_t *__restrict__ err)
-{
-    if (c.stop && *c.stop) return;
-    const int64_t t = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (t >= c.nI * c.nb) return;
-    const int64_t I = t / c.nb, j = t % c.nb;
-    if (c.sym && j < (int64_t)c.R * I) return;
-    if (off[t + 1] > cap) {
-        if (lane == 0) atomicExch(err, 1);
-        return;
-    }
-    int64_t base = off[t];
-    const unsigned lt = (1u << lane) - 1u;
-    int dummy = 0, dummy2 = 0;
-    for (int64_t k0 = 0; k0 < c.nb; k0 += 32) {
-        if (!coarse_pass(c, I, k0, j)) continue;  // warp-uniform
-        const uint32_t w = tile_item(c, I, j, k0 + lane, dummy, dummy2);
-        const unsigned bal = __ballot_sync(0xffffffffu, w != 0);
-        if (w) list[base + __popc(bal & lt)] = w;
-        base += __popc(bal);
     }
 }
 
@@ -383,18 +367,7 @@ int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, i
         c.cW = int64_t(1) << (A->depth - 5);
     }
     const unsigned blocks = (unsigned)((T + kWarps - 1) / kWarps);
-    k_tile_count<<<blocks, kWarps * 32, 0, s>>>(c, ws->tcounts, ws->ttasks, ws->tpairs, ws->tuseful);
-    SPAMM_CK_LAUNCH();
-    // toff[0..T] offsets, toff[T+1] surviving triples, toff[T+2] issued slice-pair
-    // work, toff[T+3] slice pairs the surviving triples need
-    ws->tsym = sym;
-    ws->tactive = sym ? nI * nb - (int64_t)R * nI * (nI - 1) / 2 : T;
-    SPAMM_CK(cudaMemsetAsync(ws->torder, 0xFF, sizeof(int32_t) * ws->tactive, s));  // -1: no tile
-    k_tile_scan<<<1, kScanThreads, 0, s>>>(ws->stop, ws->tcounts, ws->ttasks, ws->tpairs, ws->tuseful, T,
-                                           ws->toff, ws->tnz, heaviest_first ? nullptr : ws->torder,
-                                           ws->toff + T + 1, ws->toff + T + 2, ws->toff + T + 3);
-    SPAMM_CK_LAUNCH();
-    const int64_t worst = T * nb;
+    const int64_t worst = T * nb;  // every tile owns a segment of nb items
     if (ws->tlist_cap < worst) {
         spamm_release(ws->tlist, s);
         ws->tlist = nullptr;
@@ -402,7 +375,17 @@ int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, i
         if ((rc = spamm_alloc((void **)&ws->tlist, sizeof(uint32_t) * worst, s))) return rc;
         ws->tlist_cap = worst;
     }
-    k_tile_emit<<<blocks, kWarps * 32, 0, s>>>(c, ws->toff, ws->tlist, ws->tlist_cap, ws->counter + 8);
+    k_tile_count<<<blocks, kWarps * 32, 0, s>>>(c, ws->tcounts, ws->ttasks, ws->tpairs, ws->tuseful, ws->tlist);
+    SPAMM_CK_LAUNCH();
+    // totals: toff[T] work items, toff[T+1] surviving triples, toff[T+2]
+    // issued slice-pair work, toff[T+3] slice pairs the surviving triples need
+    // (toff[0..T) the items' running count); the order of tiles with work
+    ws->tsym = sym;
+    ws->tactive = sym ? nI * nb - (int64_t)R * nI * (nI - 1) / 2 : T;
+    SPAMM_CK(cudaMemsetAsync(ws->torder, 0xFF, sizeof(int32_t) * ws->tactive, s));  // -1: no tile
+    k_tile_scan<<<1, kScanThreads, 0, s>>>(ws->stop, ws->tcounts, ws->ttasks, ws->tpairs, ws->tuseful, T,
+                                           ws->toff, ws->tnz, heaviest_first ? nullptr : ws->torder,
+                                           ws->toff + T + 1, ws->toff + T + 2, ws->toff + T + 3);
     SPAMM_CK_LAUNCH();
     if (heaviest_first) {
         SPAMM_CK(cudaMemsetAsync(ws->tbins, 0, sizeof(int32_t) * (nb + 1), s));
@@ -437,7 +420,7 @@ static void fill_prob(tc::TcProb &p, spamm_mat_t A, spamm_mat_t B, spamm_mat_t C
     p.slotB = B->slot;
     p.slotC = C->slot;
     p.leafC = C->leaf;
-    p.off = ws->toff;
+    p.cnt = ws->tcounts;
     p.list = ws->tlist;
     p.order = ws->torder;
     p.sigA = reinterpret_cast<const int32_t *>(A->scale + 1);

@@ -225,8 +225,8 @@ __device__ void sp2_finish(int mode, const double *idem_part, const double *diag
 // Elementwise pass over all leaves of X, one warp per leaf.
 //   mode 0: X <- (emax I - F) / (emax - emin)          (src = F)
 //   mode 1: X <- X2 if branch else 2 X - X2            (src = X2)
-// In mode 1 with x2off (the tensor path's tile offsets of X2's product, R
-// leaf rows per tile, symmetric or not), a leaf of X2 whose tile had no work
+// In mode 1 with x2cnt (the tensor path's work items per tile of X2's
+// product, R leaf rows per tile, symmetric or not), a leaf of X2 whose tile had no work
 // is zero and was not written: it is not read, and a leaf that is zero in
 // both X (squared norm 0) and X2 stays zero without being touched.
 // Writes the leaf's squared norm (exact, once rounded), its partial
@@ -238,7 +238,7 @@ k_sp2_elementwise(int mode, double *__restrict__ X, const double *__restrict__ s
                   int64_t P, int b,
                   double *__restrict__ n2, double *__restrict__ n2T, double *__restrict__ idem_part,
                   double *__restrict__ diag_part, Sp2State *st, Sp2Rule rule, double *__restrict__ hist,
-                  const int64_t *__restrict__ x2off, int R, int sym)
+                  const int32_t *__restrict__ x2cnt, int R, int sym)
 {
     __shared__ double sred[kWarps * 32];
     __shared__ bool s_last;
@@ -257,10 +257,9 @@ k_sp2_elementwise(int mode, double *__restrict__ X, const double *__restrict__ s
         const double *y = src + (int64_t)(ss < 0 ? 0 : ss) * bb;
         const bool diag = I == K;
         bool y0 = ss < 0;  // source leaf known to be zero
-        if (mode == 1 && x2off) {
+        if (mode == 1 && x2cnt) {
             const int64_t a = (sym && I > K) ? K : I, c = (sym && I > K) ? I : K;
-            const int64_t t = (a / R) * nb + c;
-            y0 = x2off[t + 1] == x2off[t];
+            y0 = x2cnt[(a / R) * nb + c] == 0;
         }
         // X_new = X2 or 2X - X2 = 0 with X = 0 = X2: nothing to read or write
         // (mode 0 writes every leaf of X: X0 = (emax I - F) / range)
@@ -515,13 +514,13 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
                 int r = spamm_multiply_into(X, X, tau, X2, &mo, sc.tr_part, st, false, nullptr, false, ev,
                                             sym ? 1 : 0, false, !tcpath);
                 if (r) return r;
-                const int64_t *x2off = tcpath ? X2->ws.toff : nullptr;
+                const int32_t *x2cnt = tcpath ? X2->ws.tcounts : nullptr;
                 k_sp2_decide<<<1, kRedThreads, 0, st>>>(sc.tr_part, nb, X2->ws.task_total, X2->ws.pair_units, Ne,
                                                         o.rule, sc.st);
                 SPAMM_CK_LAUNCH();
                 k_sp2_elementwise<<<ew_blocks, kWarps * 32, 0, st>>>(
                     1, X->leaf, X2->leaf, X->slot, X2->slot, F->n, nb, X->P, X->b, X->n2 + tier_offset(X->depth),
-                    X->n2T, sc.idem_part, sc.diag_part, sc.st, rule, sc.hist, x2off, 128 / X->b, sym ? 1 : 0);
+                    X->n2T, sc.idem_part, sc.diag_part, sc.st, rule, sc.hist, x2cnt, 128 / X->b, sym ? 1 : 0);
                 SPAMM_CK_LAUNCH();
                 if (coarse && (r = launch_pyramid(X, st))) return r;
                 if (timing) SPAMM_CK(spamm_event_record(ev[4], st));

@@ -216,8 +216,8 @@ struct TcProb {
     const int32_t *slotB;
     const int32_t *slotC;
     double *leafC;
-    const int64_t *off;    // tile work-list offsets
-    const uint32_t *list;  // work items
+    const int32_t *cnt;    // work items per tile
+    const uint32_t *list;  // work items: tile t's at [t nb, t nb + cnt[t])
     const int32_t *order;  // tile order (tile ids of this product; -1 after the tiles with work)
     const int32_t *sigA;   // sigma of A
     const int32_t *sigB;
@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
             const int64_t t = tt & 0xFFFFFF;
             const int64_t nb = P.nb;
             const int64_t I = t / nb, j = t % nb;
-            const int64_t e0 = P.off[t], e1 = P.off[t + 1];
+            const int64_t e0 = t * nb, e1 = e0 + P.cnt[t];
             for (int64_t base = e0; base < e1 && ok; base += 32) {
                 const int cnt = (int)(e1 - base < 32 ? e1 - base : 32);
                 uint32_t wl = 0;
@@ -480,8 +480,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t dacc = tmem + acc * kAccStride;
-                const int64_t e1 = P.off[t + 1];
-                for (int64_t e = P.off[t]; e < e1; e++) {
+                const int64_t e1 = t * P.nb + P.cnt[t];
+                for (int64_t e = t * P.nb; e < e1; e++) {
                     const uint32_t sl = consumed % kSlots;
                     if (!mbar_wait(smem_u32(&ready_bar[sl]), (consumed / kSlots) & 1, abort_v)) {
                         ok = false;
@@ -561,8 +561,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
             if (tt < 0) break;
             const TcProb &P = g.p[tt >> 24];
             const int64_t t = tt & 0xFFFFFF;
-            const int64_t e1 = P.off[t + 1];
-            for (int64_t e = P.off[t]; e < e1; e++) {
+            const int64_t e1 = t * P.nb + P.cnt[t];
+            for (int64_t e = t * P.nb; e < e1; e++) {
                 const uint32_t sl = consumed % kSlots;
                 int good = 1;
                 if (lane == 0) good = mbar_wait(smem_u32(&full_bar[sl]), (consumed / kSlots) & 1, abort_v);
@@ -644,7 +644,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
             const int64_t t = tt & 0xFFFFFF;
             const int64_t nb = P.nb;
             const int64_t I = t / nb, j = t % nb;
-            const bool has_work = P.off[t + 1] > P.off[t];
+            const bool has_work = P.cnt[t] > 0;
             if (!mbar_wait(smem_u32(&accf_bar[acc]), aph, abort_v)) {
                 if (lane == 0) atomicExch(g.err, 1);
                 abort_flag = 1;
