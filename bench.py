@@ -323,10 +323,17 @@ def cpu_baseline(h=None, iters=1):
     _, hist, _ = oracle.sp2(h, b, ne, tau, fixed_iters=iters)
     dt = time.perf_counter() - t0
     flops = 2.0 * b ** 3 * hist[:, oracle.H_TASKS].sum()
+    # the same oracle on one core: the first iteration only (bounded sample)
+    t1 = time.perf_counter()
+    _, hist1, _ = oracle.sp2(h, b, ne, tau, fixed_iters=1, nthreads=1)
+    dt1 = time.perf_counter() - t1
+    flops1 = 2.0 * b ** 3 * hist1[:, oracle.H_TASKS].sum()
     return {"value": flops / dt / 1e12, "unit": UNIT, "cores": oracle.num_threads(),
             "kind": "oracle", "seconds": dt,
             "sample": "%d SP2 iteration(s) of the N=4096 workload (Gershgorin start, "
-                      "X0^2 by recursive SpAMM)" % iters}
+                      "X0^2 by recursive SpAMM)" % iters,
+            "one_core": {"value": flops1 / dt1 / 1e12, "unit": UNIT, "cores": 1, "seconds": dt1,
+                         "sample": "1 SP2 iteration of the same workload"}}
 
 
 def run_precision_study(args):
