@@ -48,8 +48,9 @@ L2_BYTES = 129 * 1024 * 1024
 # DRAM bytes (read + write) per launch of the tensor-core leaf-product kernel
 # of this workload (mean over the 24 launches of one solve), from an ncu
 # capture of the kernel as it stands (k_gemm_tc<7, 2, 32>: swizzled operands,
-# prep warp, row-major tiles); set to None when the kernel changes.
-TC_TRAFFIC_BYTES_PER_LAUNCH = 487.7e6
+# prep warp, row-major hand-out of tiles with work, per-tile list segments);
+# set to None when the kernel changes.
+TC_TRAFFIC_BYTES_PER_LAUNCH = 488.4e6
 
 
 def _peaks():
