@@ -180,3 +180,17 @@ def test_autotuner_reports_every_candidate_and_picks_the_fastest(cuda_lib):
     # FP64: one schedule per leaf
     res64 = cuda_lib.autotune_batched(dense[:2], dense[:2], 1e-6, reps=1)
     assert [c[0] for c in res64["candidates"]] == [16, 32, 64]
+
+
+def test_batched_with_sparse_inputs(cuda_lib):
+    """Handles stored sparsely (drop threshold) in a batch equal single calls
+    and the dense handles of the zeroed matrices."""
+    sizes = [1100, 700, 1500]
+    hs = [synth.tb_hamiltonian(n, 20 + q, decay=0.8) for q, n in enumerate(sizes)]
+    A = [cuda_lib.tree_build(_dev(h), leaf=32, drop=1e-6) for h in hs]
+    assert all(a.stored < a.nb * a.nb for a in A)
+    for prec in (cuda_lib.FP64, cuda_lib.OZAKI_BF16):
+        C, st = cuda_lib.multiply_batched(A, A, 1e-8, prec=prec, stats=True)
+        for q in range(len(A)):
+            Cs, _ = cuda_lib.multiply(A[q], A[q], 1e-8, prec=prec)
+            assert np.array_equal(cuda_lib.to_dense(C[q]).cpu().numpy(), cuda_lib.to_dense(Cs).cpu().numpy())

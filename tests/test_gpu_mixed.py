@@ -374,3 +374,39 @@ def test_tiny_and_ragged_sizes(cuda_lib, n, prec_name, leaf):
         assert np.all(np.abs(got - ref) <= bound + 1e-300)
         if tau == 1e300:
             assert not np.any(got)
+
+
+def test_mixed_sp2_trace_above_rule_matches_fp64(cuda_lib):
+    """Branch rule 1 (X^2 iff tr X > Ne) on the tensor path: same task counts
+    and branches as the FP64 solve with the same rule, P within 1e-6."""
+    n = 1024
+    h = synth.tb_hamiltonian(n, 6)
+    F = cuda_lib.tree_build(_dev(h), leaf=32)
+    P64, r64 = cuda_lib.sp2_solve(F, n / 2, 1e-8, rule=cuda_lib.RULE_TRACE_ABOVE)
+    P, r = cuda_lib.sp2_solve(F, n / 2, 1e-8, rule=cuda_lib.RULE_TRACE_ABOVE, prec=cuda_lib.OZAKI_BF16,
+                              slices=7, fixed_iters=r64["iters"])
+    assert np.array_equal(r["history"][:, 3], r64["history"][:, 3])
+    assert np.array_equal(r["history"][:, 4], r64["history"][:, 4])
+    d = cuda_lib.to_dense(P).cpu().numpy() - cuda_lib.to_dense(P64).cpu().numpy()
+    assert np.linalg.norm(d) <= 1e-6
+
+
+def test_sp2_max_iter_returns_the_last_iterate(cuda_lib):
+    n = 512
+    h = synth.tb_hamiltonian(n, 7)
+    F = cuda_lib.tree_build(_dev(h), leaf=32)
+    for prec in (cuda_lib.FP64, cuda_lib.OZAKI_BF16):
+        P, r = cuda_lib.sp2_solve(F, n / 2, 1e-8, prec=prec, max_iter=3)
+        assert r["iters"] == 3 and r["stop_reason"] == cuda_lib.STOP_MAXITER and not r["converged"]
+        P3, r3 = cuda_lib.sp2_solve(F, n / 2, 1e-8, prec=prec, fixed_iters=3)
+        assert np.array_equal(cuda_lib.to_dense(P).cpu().numpy(), cuda_lib.to_dense(P3).cpu().numpy())
+
+
+def test_split_tf32_sp2_close_to_fp64(cuda_lib):
+    n = 1024
+    h = synth.tb_hamiltonian(n, 8)
+    F = cuda_lib.tree_build(_dev(h), leaf=32)
+    P64, r64 = cuda_lib.sp2_solve(F, n / 2, 1e-8)
+    P, r = cuda_lib.sp2_solve(F, n / 2, 1e-8, prec=cuda_lib.TF32X3, fixed_iters=r64["iters"])
+    d = np.linalg.norm(cuda_lib.to_dense(P).cpu().numpy() - cuda_lib.to_dense(P64).cpu().numpy())
+    assert d < 1e-3
