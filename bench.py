@@ -50,7 +50,7 @@ L2_BYTES = 129 * 1024 * 1024
 # capture of the kernel as it stands (k_gemm_tc<7, 2, 32>: swizzled operands,
 # prep warp, row-major hand-out of tiles with work, per-tile list segments);
 # set to None when the kernel changes.
-TC_TRAFFIC_BYTES_PER_LAUNCH = 488.4e6
+TC_TRAFFIC_BYTES_PER_LAUNCH = None
 
 
 def _peaks():

@@ -6,9 +6,10 @@
 // R I + R - 1 and one output leaf column j (M = 128 rows, N = b columns).
 // Its work list holds every k for which at least one of the R triples
 // (i, k, j) survives the culling test of Eq. 4, with an R-bit mask of the
-// survivors; leaves of culled triples are replaced by zeros, so each output
-// leaf receives exactly the products of its own task list (no extra
-// products, no missing ones).
+// survivors.  The MMAs of an item run over all R A leaves, with the TMEM
+// lanes (output rows) of culled triples disabled (the instruction's
+// disable-output-lane mask), so each output leaf receives exactly the
+// products of its own task list (no extra products, no missing ones).
 //
 // Slices.  With s slices per operand (see slice.cu), the MMAs for A slice p
 // multiply the 128 x b A slab by B slices q = zB..s-1-p (N = b (s - p - zB))
@@ -34,17 +35,14 @@
 // from one device counter over the concatenated orders, so one persistent
 // launch serves many independent SpAMMs.
 //
-// Kernel roles (224 threads, one CTA per SM, persistent):
+// Kernel roles (192 threads, one CTA per SM, persistent):
 //   warp 0     : producer; two bulk copies (cp.async.bulk) per work item:
 //                the needed slices of the R A leaves (one contiguous block of
 //                the tile-major array, stage layout [p][leaf][slice]) and of
 //                the B leaf, into a shared-memory byte ring, completion on
 //                the item's mbarrier;
-//   warp 6     : prep; once an item lands, zeroes the leaves of culled
-//                triples in it and marks it ready (so the MMA issuer never
-//                stalls on shared-memory stores);
 //   warp 1     : allocates 512 TMEM columns; lane 0 issues the tcgen05.mma
-//                of each ready item and commits to the item's "empty"
+//                of each landed item and commits to the item's "empty"
 //                barrier and, at the end of a tile, to the accumulator's
 //                "full" barrier;
 //   warps 2-5  : epilogue; tcgen05.ld of the s diagonal blocks of the row the
@@ -68,7 +66,7 @@ namespace tc {
 // zero slices) leave room for more items in flight.
 constexpr uint32_t kRingBytes = 216 * 1024;
 constexpr int kSlots = 16;  // work items in flight at most
-constexpr int kThreads = 224;
+constexpr int kThreads = 192;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kAccStride = 256;
 constexpr long long kTimeoutCycles = 8000000000ll;  // about 4 s at 2 GHz per wait
@@ -161,18 +159,34 @@ __device__ __forceinline__ uint32_t mma_idesc(int M, int N)
 }
 
 // D (TMEM) += A (smem) x B (smem); BF16 (E = 2, K = 16) or TF32 (E = 4,
-// K = 8): 32 bytes of K per instruction either way.
+// K = 8): 32 bytes of K per instruction either way.  Bit r of the 128-bit
+// mask dis (dis[0] bit 0 = lane 0) set: TMEM lane r of D keeps its value.
 template <int E>
-__device__ __forceinline__ void mma_issue(uint32_t dtmem, uint64_t da, uint64_t db, uint32_t idesc)
+__device__ __forceinline__ void mma_issue(uint32_t dtmem, uint64_t da, uint64_t db, uint32_t idesc,
+                                          const uint32_t (&dis)[4])
 {
     if (E == 4)
-        asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;" ::"r"(dtmem), "l"(da), "l"(db),
-                     "r"(idesc)
+        asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, {%4, %5, %6, %7}, 1;" ::"r"(dtmem),
+                     "l"(da), "l"(db), "r"(idesc), "r"(dis[0]), "r"(dis[1]), "r"(dis[2]), "r"(dis[3])
                      : "memory");
     else
-        asm volatile("tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, 1;" ::"r"(dtmem), "l"(da), "l"(db),
-                     "r"(idesc)
+        asm volatile("tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, {%4, %5, %6, %7}, 1;" ::"r"(dtmem),
+                     "l"(da), "l"(db), "r"(idesc), "r"(dis[0]), "r"(dis[1]), "r"(dis[2]), "r"(dis[3])
                      : "memory");
+}
+
+// Word q of the disable-output-lane mask of an item with kept-leaf mask
+// `mask`: the 32 TMEM lanes 32 q .. 32 q + 31 are rows of leaves
+// 32 q / B .. (32 q + 31) / B; a lane is disabled when its leaf is culled.
+template <int B>
+__device__ __forceinline__ uint32_t culled_lanes(uint32_t mask, int q)
+{
+    if (B >= 32) return ((mask >> (32 * q / B)) & 1u) ? 0u : 0xFFFFFFFFu;
+    uint32_t v = 0;
+#pragma unroll
+    for (int u = 0; u < 32 / B; u++)
+        if (!((mask >> (q * (32 / B) + u)) & 1u)) v |= ((1u << B) - 1u) << (u * B);
+    return v;
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar)
@@ -276,11 +290,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
     constexpr uint32_t kSBO = 8 * B * E;        // 8-row group stride
     constexpr uint32_t kAW = slice_atom_bytes<B, E>();  // swizzle atom width (bytes)
     constexpr int kMmaK = B * E / 32;           // instructions per slice pair
-    constexpr uint32_t kFull = (1u << R) - 1;
     static_assert(S * B <= (int)kAccStride, "accumulator exceeds its TMEM columns");
     static_assert((uint32_t)S * (R + 1) * kSlice <= kRingBytes, "work item exceeds the ring");
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ __align__(8) uint64_t full_bar[kSlots], ready_bar[kSlots], empty_bar[kSlots];
+    __shared__ __align__(8) uint64_t full_bar[kSlots], empty_bar[kSlots];
     __shared__ __align__(8) uint64_t accf_bar[2], acce_bar[2], done_bar;
     __shared__ uint32_t slot_off[kSlots];  // ring byte offset of each in-flight item
     __shared__ uint32_t slot_w[kSlots];    // its work-list entry
@@ -296,7 +309,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
     if (threadIdx.x == 0) {
         for (int q = 0; q < kSlots; q++) {
             mbar_init(smem_u32(&full_bar[q]), 1);
-            mbar_init(smem_u32(&ready_bar[q]), 1);
             mbar_init(smem_u32(&empty_bar[q]), 1);
         }
         for (int q = 0; q < 2; q++) {
@@ -306,7 +318,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
         mbar_init(smem_u32(&done_bar), 1);
         for (int q = 0; q < kTileRing; q++) {
             mbar_init(smem_u32(&tfull_bar[q]), 1);
-            mbar_init(smem_u32(&tempty_bar[q]), 6);  // MMA, prep and four epilogue warps
+            mbar_init(smem_u32(&tempty_bar[q]), 5);  // MMA and four epilogue warps
         }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -452,8 +464,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
         __syncwarp();
     } else if (warp == 1) {
         // ------------------------------ MMA issuer ------------------------------
-        // Lane 0 alone: waits until the prep warp has made an item ready, then
-        // issues its MMAs and commits them to the item's "empty" barrier and,
+        // Lane 0 alone: waits until an item has landed, then issues its MMAs and commits them to the item's "empty" barrier and,
         // at the end of a tile, to the accumulator's "full" barrier.
         if (lane == 0) {
             uint32_t consumed = 0, acc = 0, aph = 0;
@@ -483,7 +494,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                 const int64_t e1 = t * P.nb + P.cnt[t];
                 for (int64_t e = t * P.nb; e < e1; e++) {
                     const uint32_t sl = consumed % kSlots;
-                    if (!mbar_wait(smem_u32(&ready_bar[sl]), (consumed / kSlots) & 1, abort_v)) {
+                    if (!mbar_wait(smem_u32(&full_bar[sl]), (consumed / kSlots) & 1, abort_v)) {
                         ok = false;
                         break;
                     }
@@ -491,6 +502,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                     const uint32_t w = slot_w[sl], pos = slot_off[sl];
                     const int za = item_za(w), zb = item_zb(w);
                     const int m = S - za - zb;
+                    const uint32_t mask = item_mask(w);
+                    const uint32_t dis[4] = {culled_lanes<B>(mask, 0), culled_lanes<B>(mask, 1),
+                                             culled_lanes<B>(mask, 2), culled_lanes<B>(mask, 3)};
                     const uint32_t sa = sbase + pos;                        // A slice za
                     const uint32_t sb = sa + (uint32_t)m * R * kSlice;      // B slice zb
                     // descriptors advance by adding (bytes >> 4) to the address field
@@ -507,7 +521,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                             // address moves by 32 B, across atoms by 8 AW bytes
                             const uint32_t kb = (uint32_t)(32 * h);
                             const uint64_t adv = ((kb / kAW) * 8 * kAW + kb % kAW) >> 4;
-                            mma_issue<E>(dcol, da + adv, db0 + adv, idesc);
+                            mma_issue<E>(dcol, da + adv, db0 + adv, idesc, dis);
                         }
                         idesc -= (uint32_t)(B >> 3) << 17;  // N shrinks by b
                         dcol += B;
@@ -531,74 +545,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
             mbar_wait(smem_u32(&done_bar), 0, abort_v);
         }
         __syncwarp();
-    } else if (warp == 6) {
-        // ------------------------------ prep ------------------------------
-        // Once an item lands, the warp zeroes the leaves of culled triples in
-        // it (generic-proxy stores made visible to the tensor core's async
-        // proxy by fence.proxy.async) and marks the item ready.
-        uint32_t consumed = 0;
-        bool ok = true;
-        uint32_t tq = 0, tph = 0;
-        for (;;) {
-            int32_t tt = -1;
-            int tgood = 1;
-            if (lane == 0) {
-                tgood = mbar_wait(smem_u32(&tfull_bar[tq]), tph, abort_v);
-                if (tgood) {
-                    tt = tile_q[tq];
-                    mbar_arrive(smem_u32(&tempty_bar[tq]));
-                }
-            }
-            tt = __shfl_sync(0xffffffffu, tt, 0);
-            if (!__shfl_sync(0xffffffffu, tgood, 0)) {
-                ok = false;
-                break;
-            }
-            if (++tq == kTileRing) {
-                tq = 0;
-                tph ^= 1;
-            }
-            if (tt < 0) break;
-            const TcProb &P = g.p[tt >> 24];
-            const int64_t t = tt & 0xFFFFFF;
-            const int64_t e1 = t * P.nb + P.cnt[t];
-            for (int64_t e = t * P.nb; e < e1; e++) {
-                const uint32_t sl = consumed % kSlots;
-                int good = 1;
-                if (lane == 0) good = mbar_wait(smem_u32(&full_bar[sl]), (consumed / kSlots) & 1, abort_v);
-                if (!__shfl_sync(0xffffffffu, good, 0)) {
-                    ok = false;
-                    break;
-                }
-                // lane 0 observed the landed data and the item's metadata
-                // (written before the arrive that released them); the warp
-                // barrier orders the other lanes' reads after that observation
-                __syncwarp();
-                const uint32_t w = slot_w[sl], pos = slot_off[sl];
-                const uint32_t mask = item_mask(w);
-                const int m = S - item_za(w) - item_zb(w);
-                if (mask != kFull) {
-                    const uint4 zero4 = make_uint4(0, 0, 0, 0);
-                    for (int L = 0; L < R; L++) {
-                        if (mask & (1u << L)) continue;
-                        for (int pp = 0; pp < m; pp++) {
-                            uint4 *z = reinterpret_cast<uint4 *>(ring + pos + (pp * R + L) * kSlice);
-#pragma unroll
-                            for (int q = 0; q < (int)(kSlice / 512); q++) z[q * 32 + lane] = zero4;
-                        }
-                    }
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&ready_bar[sl]));
-                consumed++;
-            }
-            if (!ok) break;
-        }
-        if (!ok) {
-            if (lane == 0) atomicExch(g.err, 1);
-            abort_flag = 1;
-        }
     } else {
         // ------------------------------ epilogue (warps 2-5) ------------------------------
         const int quad = warp & 3;             // TMEM lane quadrant of this warp
