@@ -79,15 +79,22 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines = []
+        self.start = 0
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            # nvidia-smi's start-up (NVML initialisation) must not overlap the
+            # timed region: wait for its first sample, count only later ones
+            t0 = time.time()
+            while not self.lines and self.proc.poll() is None and time.time() - t0 < 10:
+                time.sleep(0.01)
+            self.start = len(self.lines)
         except OSError:
             self.proc = None
         return self
@@ -107,7 +114,8 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        # samples taken inside the region (the last one before it if none)
+        for ln in (self.lines[self.start:] or self.lines[-1:]):
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 7:
                 continue
@@ -667,7 +675,7 @@ def run_reference(args):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--prec", choices=["fp64", "ozaki"], default="ozaki")

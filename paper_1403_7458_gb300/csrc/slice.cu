@@ -113,6 +113,9 @@ k_slice(const int32_t *__restrict__ stop, const double *__restrict__ leaf, const
     using W = typename std::conditional<E == 4, uint32_t, uint16_t>::type;
     constexpr int R = 128 / B;               // leaf rows per tile
     constexpr int kU4 = B * B * E / 16;      // 16-byte chunks per slice
+    constexpr int kThreads = 256;            // the launch's block size
+    constexpr int kPerThread = B * B / kThreads;
+    static_assert(B * B % kThreads == 0, "leaf elements must be a multiple of the block size");
     __shared__ __align__(16) W sa[S * B * B];
     __shared__ unsigned long long s_xmax;
     if (stop && *stop) return;  // the SP2 loop has already stopped
@@ -129,9 +132,14 @@ k_slice(const int32_t *__restrict__ stop, const double *__restrict__ leaf, const
         __syncthreads();
         unsigned long long xmax = 0;
         const double *src = leaf + (int64_t)sl * (B * B);
-        for (int q = threadIdx.x; q < B * B; q += blockDim.x) {
+        double xs[kPerThread];  // all loads of the leaf issued before any is used
+#pragma unroll
+        for (int u = 0; u < kPerThread; u++) xs[u] = src[threadIdx.x + kThreads * u];
+#pragma unroll
+        for (int u = 0; u < kPerThread; u++) {
+            const int q = threadIdx.x + kThreads * u;
             const int r = q / B, l = q % B;
-            const double x = src[q];
+            const double x = xs[u];
             const uint64_t X = float_split ? 0 : slice_int(x, sigma, S);
             const bool neg = x < 0.0;
             xmax = X > xmax ? X : xmax;
@@ -161,13 +169,15 @@ k_slice(const int32_t *__restrict__ stop, const double *__restrict__ leaf, const
         const uint4 *ss = reinterpret_cast<const uint4 *>(sa);
         if (perleaf) {
             uint4 *d = reinterpret_cast<uint4 *>(perleaf + (int64_t)sl * (S * B * B * E));
-            for (int q = threadIdx.x; q < S * kU4; q += blockDim.x) d[q] = ss[q];
+#pragma unroll
+            for (int q = threadIdx.x; q < S * kU4; q += kThreads) d[q] = ss[q];
         }
         if (tileA && !perleaf_transposed) {
             // tile-major: block (I, k) holds [p][L][slice] for its R rows
             const int64_t I = i / R, L = i % R;
             uint4 *d = reinterpret_cast<uint4 *>(tileA + ((I * nb + k) * S * R + L) * (int64_t)(B * B * E));
-            for (int q = threadIdx.x; q < S * kU4; q += blockDim.x) d[(q / kU4) * (R * kU4) + (q % kU4)] = ss[q];
+#pragma unroll
+            for (int q = threadIdx.x; q < S * kU4; q += kThreads) d[(q / kU4) * (R * kU4) + (q % kU4)] = ss[q];
         }
         __syncthreads();
     }

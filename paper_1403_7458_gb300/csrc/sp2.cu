@@ -54,7 +54,8 @@ struct Sp2Rule {
     int32_t fixed_iters, max_iter;
 };
 
-constexpr int kWarps = 8;
+constexpr int kEwWarps = 8;        // elementwise pass: warps per block (one leaf per warp at a time)
+constexpr int kEwBlocksPerSm = 3;  // and resident blocks per SM (register cap 85)
 constexpr int kRedThreads = 1024;
 constexpr int kBatch = 4;  // SP2 iterations enqueued between reads of the state
 
@@ -172,8 +173,8 @@ __device__ double block_sum_fixed(const double *v, int64_t count, double *sbuf)
 // The last block to finish an elementwise pass reduces the per-leaf partials
 // in a fixed order, records the iteration's history row and applies the
 // stopping rule (mode 1).
-__device__ void sp2_finish(int mode, const double *idem_part, const double *diag_part, int64_t nb,
-                           Sp2State *st, const Sp2Rule &rule, double *hist, double *sred, bool *s_last)
+__device__ void sp2_finish(int mode, const double *idem_part, int64_t idem_count, const double *diag_part,
+                           int64_t nb, Sp2State *st, const Sp2Rule &rule, double *hist, double *sred, bool *s_last)
 {
     __threadfence();
     __syncthreads();
@@ -181,7 +182,7 @@ __device__ void sp2_finish(int mode, const double *idem_part, const double *diag
     __syncthreads();
     if (!*s_last) return;
     __threadfence();
-    double e2 = block_sum_fixed(idem_part, nb * nb, sred);
+    double e2 = block_sum_fixed(idem_part, idem_count, sred);
     double tn = block_sum_fixed(diag_part, nb, sred);
     if (threadIdx.x == 0) {
         st->tn = tn;
@@ -222,39 +223,49 @@ __device__ void sp2_finish(int mode, const double *idem_part, const double *diag
 }
 
 
-// Elementwise pass over all leaves of X, one warp per leaf.
+// Elementwise pass over all leaves of X, one warp per leaf (persistent
+// warps stride over the leaves).
 //   mode 0: X <- (emax I - F) / (emax - emin)          (src = F)
 //   mode 1: X <- X2 if branch else 2 X - X2            (src = X2)
 // In mode 1 with x2cnt (the tensor path's work items per tile of X2's
 // product, R leaf rows per tile, symmetric or not), a leaf of X2 whose tile had no work
 // is zero and was not written: it is not read, and a leaf that is zero in
 // both X (squared norm 0) and X2 stays zero without being touched.
-// Writes the leaf's squared norm (exact, once rounded), its partial
-// ||X2 - X||^2 (mode 1) and, for diagonal leaves, its trace.  The last block
-// reduces the partials and stores e and the new trace in the state.
-__global__ void __launch_bounds__(kWarps * 32)
+// Writes the leaf's squared norm (exact, once rounded) and, for diagonal
+// leaves, its trace.  Each warp adds the partial ||X2 - X||^2 of its leaves
+// in leaf order, and the block adds its warps' sums in warp order into
+// idem_part[block] (mode 1).  The last block reduces the partials and stores
+// e and the new trace in the state.
+// A lane handles elements lane + 32 u of the leaf, in chunks of kCh rows of
+// 32 whose loads are all issued before any is used; the squares are summed
+// in a second pass over the written leaf (from L2), once the leaf's largest
+// exponent is known.
+template <int B>
+__global__ void __launch_bounds__(kEwWarps * 32, kEwBlocksPerSm)
 k_sp2_elementwise(int mode, double *__restrict__ X, const double *__restrict__ src,
                   const int32_t *__restrict__ slot, const int32_t *__restrict__ src_slot, int64_t n, int64_t nb,
-                  int64_t P, int b,
-                  double *__restrict__ n2, double *__restrict__ n2T, double *__restrict__ idem_part,
+                  int64_t P, double *__restrict__ n2, double *__restrict__ n2T, double *__restrict__ idem_part,
                   double *__restrict__ diag_part, Sp2State *st, Sp2Rule rule, double *__restrict__ hist,
                   const int32_t *__restrict__ x2cnt, int R, int sym)
 {
-    __shared__ double sred[kWarps * 32];
+    constexpr int BB = B * B;
+    constexpr int kPer = BB / 32;              // elements per lane
+    constexpr int kCh = kPer < 8 ? kPer : 8;   // rows of 32 per chunk
+    __shared__ double sred[kEwWarps * 32];
+    __shared__ double s_idem[kEwWarps];
     __shared__ bool s_last;
     if (mode == 1 && *(volatile int32_t *)&st->stopped) return;
-    const int lane = threadIdx.x & 31;
-    const int64_t w = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
-    const int bb = b * b;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t nwarps = (int64_t)gridDim.x * kEwWarps;
     const bool take_sq = st->branch != 0;
     const double emax = st->emax, range = st->emax - st->emin;
-    if (w < nb * nb) {
+    double idem_w = 0.0;  // lane 0: this warp's leaves, in order
+    for (int64_t w = (int64_t)blockIdx.x * kEwWarps + warp; w < nb * nb; w += nwarps) {
         const int64_t I = w / nb, K = w % nb;
-        const int64_t base = (int64_t)slot[w] * bb;
-        double *x = X + base;
+        double *x = X + (int64_t)slot[w] * BB;
         // the source in mode 0 is F, which may leave zero leaves unstored
         const int32_t ss = src_slot[w];
-        const double *y = src + (int64_t)(ss < 0 ? 0 : ss) * bb;
+        const double *y = src + (int64_t)(ss < 0 ? 0 : ss) * BB;
         const bool diag = I == K;
         bool y0 = ss < 0;  // source leaf known to be zero
         if (mode == 1 && x2cnt) {
@@ -263,37 +274,54 @@ k_sp2_elementwise(int mode, double *__restrict__ X, const double *__restrict__ s
         }
         // X_new = X2 or 2X - X2 = 0 with X = 0 = X2: nothing to read or write
         // (mode 0 writes every leaf of X: X0 = (emax I - F) / range)
-        const bool untouched = mode == 1 && y0 && n2[I * P + K] == 0.0;
-        if (untouched && lane == 0) {
-            idem_part[w] = 0.0;
-            if (diag) diag_part[I] = 0.0;
+        if (mode == 1 && y0 && n2[I * P + K] == 0.0) {  // warp-uniform
+            if (lane == 0 && diag) diag_part[I] = 0.0;
+            continue;
         }
-        if (!untouched) {
         double idem = 0.0;
         int ek = 0;
-        for (int q = lane; q < bb; q += 32) {
-            double yv = y0 ? 0.0 : y[q], nv;
-            if (mode == 0) {
-                const int r = q / b;
-                nv = ((diag && r == q % b && I * b + r < n) ? emax : 0.0) - yv;
-                nv = nv / range;
-            } else {
-                double xv = x[q];
-                double d = yv - xv;
-                idem = fma(d, d, idem);
-                nv = take_sq ? yv : fma(2.0, xv, -yv);
+#pragma unroll 1
+        for (int c0 = 0; c0 < kPer; c0 += kCh) {
+            double yv[kCh], xv[kCh];
+#pragma unroll
+            for (int u = 0; u < kCh; u++) {
+                const int q = lane + 32 * (c0 + u);
+                yv[u] = y0 ? 0.0 : y[q];
+                xv[u] = mode == 1 ? x[q] : 0.0;
             }
-            x[q] = nv;
-            ek = max(ek, exp_key(nv));
+#pragma unroll
+            for (int u = 0; u < kCh; u++) {
+                const int q = lane + 32 * (c0 + u);
+                double nv;
+                if (mode == 0) {
+                    const int r = q / B;
+                    nv = ((diag && r == q % B && I * B + r < n) ? emax : 0.0) - yv[u];
+                    nv = nv / range;
+                } else {
+                    const double d = yv[u] - xv[u];
+                    idem = fma(d, d, idem);
+                    nv = take_sq ? yv[u] : fma(2.0, xv[u], -yv[u]);
+                }
+                x[q] = nv;
+                ek = max(ek, exp_key(nv));
+            }
         }
         ek = warp_max_int(ek);
         __syncwarp();
         u128 acc = 0;
         double dsum = 0.0;
-        if (ek > 0)
-            for (int q = lane; q < bb; q += 32) acc += sq_term(x[q], ek);
+        if (ek > 0) {
+#pragma unroll 1
+            for (int c0 = 0; c0 < kPer; c0 += kCh) {
+                double v[kCh];
+#pragma unroll
+                for (int u = 0; u < kCh; u++) v[u] = x[lane + 32 * (c0 + u)];
+#pragma unroll
+                for (int u = 0; u < kCh; u++) acc += sq_term(v[u], ek);
+            }
+        }
         if (diag)
-            for (int r = lane; r < b; r += 32) dsum += x[r * b + r];
+            for (int r = lane; r < B; r += 32) dsum += x[r * B + r];
         acc = warp_sum_u128(acc);
         for (int o = 16; o > 0; o >>= 1) {
             idem += __shfl_xor_sync(0xffffffffu, idem, o);
@@ -304,12 +332,70 @@ k_sp2_elementwise(int mode, double *__restrict__ X, const double *__restrict__ s
             n2[I * P + K] = r;
             n2T[K * P + I] = r;
             if (r > 0.0) atomicAdd(&st->nonzero, 1ull);  // fill statistics
-            idem_part[w] = idem;
+            idem_w += idem;
             if (diag) diag_part[I] = dsum;
         }
-        }  // !untouched
+        __syncwarp();
     }
-    sp2_finish(mode, idem_part, diag_part, nb, st, rule, hist, sred, &s_last);
+    if (lane == 0) s_idem[warp] = idem_w;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double e = 0.0;
+        for (int q = 0; q < kEwWarps; q++) e += s_idem[q];
+        idem_part[blockIdx.x] = e;
+    }
+    sp2_finish(mode, idem_part, gridDim.x, diag_part, nb, st, rule, hist, sred, &s_last);
+}
+
+// Blocks of the elementwise pass resident on the whole GPU at once (queried
+// once per device; the grid, and so the order of the partial sums, is fixed
+// for a device).
+template <int B>
+int64_t ew_grid_cap()
+{
+    static int per_sm[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+    int occ = __atomic_load_n(&per_sm[dev & 63], __ATOMIC_ACQUIRE);
+    if (occ == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sp2_elementwise<B>, kEwWarps * 32, 0) != cudaSuccess ||
+            occ < 1)
+            occ = 1;
+        __atomic_store_n(&per_sm[dev & 63], occ, __ATOMIC_RELEASE);
+    }
+    return (int64_t)spamm_num_sms() * occ;
+}
+
+// Launch of the elementwise pass for leaf size b (16, 32 or 64): persistent
+// blocks, as many as fit on the GPU at once (fewer when there are fewer
+// leaves); idem_part needs one entry per block.
+template <int B>
+void launch_elementwise_b(cudaStream_t s, int mode, double *X, const double *src, const int32_t *slot,
+                          const int32_t *src_slot, int64_t n, int64_t nb, int64_t P, double *n2, double *n2T,
+                          double *idem_part, double *diag_part, Sp2State *st, Sp2Rule rule, double *hist,
+                          const int32_t *x2cnt, int R, int sym)
+{
+    const int64_t cap = ew_grid_cap<B>();
+    const int64_t need = (nb * nb + kEwWarps - 1) / kEwWarps;
+    const unsigned grid = (unsigned)(need < cap ? need : cap);
+    k_sp2_elementwise<B><<<grid, kEwWarps * 32, 0, s>>>(mode, X, src, slot, src_slot, n, nb, P, n2, n2T, idem_part,
+                                                    diag_part, st, rule, hist, x2cnt, R, sym);
+}
+
+void launch_elementwise(int b, cudaStream_t s, int mode, double *X, const double *src, const int32_t *slot,
+                        const int32_t *src_slot, int64_t n, int64_t nb, int64_t P, double *n2, double *n2T,
+                        double *idem_part, double *diag_part, Sp2State *st, Sp2Rule rule, double *hist,
+                        const int32_t *x2cnt, int R, int sym)
+{
+    if (b == 16)
+        launch_elementwise_b<16>(s, mode, X, src, slot, src_slot, n, nb, P, n2, n2T, idem_part, diag_part, st,
+                                 rule, hist, x2cnt, R, sym);
+    else if (b == 32)
+        launch_elementwise_b<32>(s, mode, X, src, slot, src_slot, n, nb, P, n2, n2T, idem_part, diag_part, st,
+                                 rule, hist, x2cnt, R, sym);
+    else
+        launch_elementwise_b<64>(s, mode, X, src, slot, src_slot, n, nb, P, n2, n2T, idem_part, diag_part, st,
+                                 rule, hist, x2cnt, R, sym);
 }
 
 
@@ -422,7 +508,6 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
     cudaGraphExec_t gexec = nullptr;
     int64_t graph_launches = 0;
     int graphed = 0;  // iterations run by graph replays
-    unsigned ew_blocks = (unsigned)((G + kWarps - 1) / kWarps);
 
 #define SP2_TRY(x)                 \
     do {                           \
@@ -492,10 +577,8 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
     SP2_LAUNCHED();
     k_gershgorin_bounds<<<1, kRedThreads, 0, s>>>(sc.lo, sc.hi, F->n, sc.st);
     SP2_LAUNCHED();
-    k_sp2_elementwise<<<ew_blocks, kWarps * 32, 0, s>>>(0, X->leaf, F->leaf, X->slot, F->slot, F->n, nb, X->P, X->b,
-                                                        X->n2 + tier_offset(X->depth), X->n2T,
-                                                        sc.idem_part, sc.diag_part, sc.st,
-                                                        Sp2Rule{Ne, 0, 0, 0, 1}, sc.hist, nullptr, 1, 0);
+    launch_elementwise(X->b, s, 0, X->leaf, F->leaf, X->slot, F->slot, F->n, nb, X->P, X->n2 + tier_offset(X->depth),
+                       X->n2T, sc.idem_part, sc.diag_part, sc.st, Sp2Rule{Ne, 0, 0, 0, 1}, sc.hist, nullptr, 1, 0);
     SP2_LAUNCHED();
     // upper tiers of the iterate: the cull's early skip reads them (rebuilt
     // only where the skip pays; otherwise marked stale and not used)
@@ -518,9 +601,9 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
                 k_sp2_decide<<<1, kRedThreads, 0, st>>>(sc.tr_part, nb, X2->ws.task_total, X2->ws.pair_units, Ne,
                                                         o.rule, sc.st);
                 SPAMM_CK_LAUNCH();
-                k_sp2_elementwise<<<ew_blocks, kWarps * 32, 0, st>>>(
-                    1, X->leaf, X2->leaf, X->slot, X2->slot, F->n, nb, X->P, X->b, X->n2 + tier_offset(X->depth),
-                    X->n2T, sc.idem_part, sc.diag_part, sc.st, rule, sc.hist, x2cnt, 128 / X->b, sym ? 1 : 0);
+                launch_elementwise(X->b, st, 1, X->leaf, X2->leaf, X->slot, X2->slot, F->n, nb, X->P,
+                                   X->n2 + tier_offset(X->depth), X->n2T, sc.idem_part, sc.diag_part, sc.st, rule,
+                                   sc.hist, x2cnt, 128 / X->b, sym ? 1 : 0);
                 SPAMM_CK_LAUNCH();
                 if (coarse && (r = launch_pyramid(X, st))) return r;
                 if (timing) SPAMM_CK(spamm_event_record(ev[4], st));
