@@ -543,8 +543,7 @@ int spamm_multiply_into(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t C,
         if (ev) SPAMM_CK(spamm_event_record(ev[1], s));
         rc = launch_gemm_tc(A, B, C, ws, tr_part, sl, el, s, fsplit);
         if (rc) return rc;
-        const int64_t R = 128 / A->b;
-        const int64_t T = ((A->nb + R - 1) / R) * A->nb;
+        const int64_t T = ws->tT;
         ws->task_total = ws->toff + T + 1;
         ws->pair_units = ws->toff + T + 3;
         if (need_total) {
@@ -836,8 +835,7 @@ extern "C" int spamm_multiply_batched(int32_t count, const spamm_mat_t *A, const
             int64_t v[4] = {0, 0, 0, 0};
             cudaError_t e;
             if (tcp) {
-                const int64_t R = 128 / leaf, T = ((nb + R - 1) / R) * nb;
-                e = cudaMemcpyAsync(v, w[q]->toff + T, sizeof(int64_t) * 4, cudaMemcpyDeviceToHost, s);
+                e = cudaMemcpyAsync(v, w[q]->toff + w[q]->tT, sizeof(int64_t) * 4, cudaMemcpyDeviceToHost, s);
             } else {
                 e = cudaMemcpyAsync(v + 1, w[q]->off + nb * nb, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
             }

@@ -7,8 +7,9 @@
 namespace {
 
 // ---------------------------------------------------------------------------
-// tile cull: work lists of items (k, mask, zA, zB); tile t = I * nb + j owns
-// the list segment [t nb, t nb + count[t])
+// tile cull: work lists of items (k, masks, zA, zB); tile t = I * nbt + J
+// (columns j = W J .. W J + W - 1, nbt = ceil(nb / W)) owns the list
+// segment [t nb, t nb + count[t])
 // ---------------------------------------------------------------------------
 constexpr int kWarps = 8;
 
@@ -20,9 +21,10 @@ struct CullArgs {
     int64_t cW;
     const uint8_t *zA, *zB;        // leading zero slices per slot
     const int32_t *slotA, *slotB;  // slot maps (B: of the matrix whose slices serve as B)
-    int64_t nb, P, nI;
+    int64_t nb, P, nI, nbt;
     double tau2;
     int sym, S, R;  // R = 128 / b leaf rows per tile
+    int W;          // output leaf columns per tile (1, or 2 at leaf 32)
     const int32_t *stop;  // set once an SP2 loop has stopped: nothing to do
 };
 
@@ -78,6 +80,56 @@ __device__ __forceinline__ int item_pairs(uint32_t w, int S)
     return m * (m + 1) / 2;
 }
 
+// Work item of a two-column tile (I, J) at k (leaf 32, R = 4; tc::item_make2),
+// or 0.  Symmetric mode keeps only the triples of stored leaves (i <= j): a
+// leaf below the diagonal is the mirror of one above it.
+__device__ __forceinline__ uint32_t tile_item2(const CullArgs &c, int64_t I, int64_t J, int64_t k, int &ntask,
+                                               int &npair)
+{
+    if (k >= c.nb) return 0;
+    uint32_t mask[2] = {0u, 0u};
+    int zbv[2] = {7, 7};
+    int za = c.S;
+#pragma unroll
+    for (int cc = 0; cc < 2; cc++) {
+        const int64_t j = 2 * J + cc;
+        if (j >= c.nb) continue;
+        const double b = __ldg(c.n2BT + j * c.P + k);
+        if (b == 0.0) continue;
+        const int zb = c.sym ? c.zA[c.slotA[j * c.nb + k]] : c.zB[c.slotB[k * c.nb + j]];
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            const int64_t i = 4 * I + r;
+            if (i < c.nb && (!c.sym || i <= j) && keep_product(__ldg(c.n2A + i * c.P + k), b, c.tau2)) {
+                ntask += !c.sym ? 1 : (i < j ? 2 : 1);
+                const int zr = c.zA[c.slotA[i * c.nb + k]];
+                if (zr + zb < c.S) {
+                    const int mr = c.S - zr - zb;
+                    npair += mr * (mr + 1) / 2;
+                    mask[cc] |= 1u << r;
+                    za = zr < za ? zr : za;
+                }
+            }
+        }
+        if (mask[cc]) zbv[cc] = zb;
+    }
+    if (!(mask[0] | mask[1])) return 0;
+    return tc::item_make2((uint32_t)k, mask[0], mask[1], za, zbv[0], zbv[1]);
+}
+
+// Slice pairs a two-column item issues (its columns share zA).
+__device__ __forceinline__ int item_pairs2(uint32_t w, int S)
+{
+    int n = 0;
+#pragma unroll
+    for (int cc = 0; cc < 2; cc++) {
+        if (!tc::item_mask_col<4, 2>(w, cc)) continue;
+        const int m = S - tc::item_za(w) - tc::item_zb_col(w, cc);
+        n += m * (m + 1) / 2;
+    }
+    return n;
+}
+
 // One warp per tile: tests the candidates k (ballot), writes the tile's work
 // items into its own segment of the list, [t nb, t nb + count), and counts
 // them, the surviving triples and the slice pairs.
@@ -88,9 +140,11 @@ k_tile_count(CullArgs c, int32_t *__restrict__ counts, int32_t *__restrict__ tas
     if (c.stop && *c.stop) return;
     const int64_t t = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    if (t >= c.nI * c.nb) return;
-    const int64_t I = t / c.nb, j = t % c.nb;
-    const bool active = !c.sym || j >= (int64_t)c.R * I;
+    if (t >= c.nI * c.nbt) return;
+    const int64_t I = t / c.nbt, J = t % c.nbt;
+    // symmetric mode: a tile entirely below the block diagonal is formed as
+    // a mirror (its last column is left of its first row)
+    const bool active = !c.sym || (int64_t)c.W * J + c.W - 1 >= (int64_t)c.R * I;
     int cnt = 0, ntask = 0, npair = 0, nuse = 0;
     if (!active) {  // symmetric mode: a lower-triangle tile is formed as a mirror
         if (lane == 0) counts[t] = tasks[t] = pairs[t] = useful[t] = 0;
@@ -99,12 +153,14 @@ k_tile_count(CullArgs c, int32_t *__restrict__ counts, int32_t *__restrict__ tas
     uint32_t *seg = list + t * c.nb;
     const unsigned lt = (1u << lane) - 1u;
     for (int64_t k0 = 0; k0 < c.nb; k0 += 32) {
-        if (!coarse_pass(c, I, k0, j)) continue;  // warp-uniform
-        const uint32_t w = tile_item(c, I, j, k0 + lane, ntask, nuse);
+        // the W columns lie in one 32-leaf block column (W divides 32)
+        if (!coarse_pass(c, I, k0, (int64_t)c.W * J)) continue;  // warp-uniform
+        const uint32_t w = c.W == 2 ? tile_item2(c, I, J, k0 + lane, ntask, nuse)
+                                    : tile_item(c, I, J, k0 + lane, ntask, nuse);
         const unsigned bal = __ballot_sync(0xffffffffu, w != 0);
         if (w) {
             seg[cnt + __popc(bal & lt)] = w;
-            npair += item_pairs(w, c.S);
+            npair += c.W == 2 ? item_pairs2(w, c.S) : item_pairs(w, c.S);
         }
         cnt += __popc(bal);
     }
@@ -215,19 +271,20 @@ __global__ void k_tile_bins_scan(const int32_t *__restrict__ stop, int32_t *__re
 }
 
 // Zeroes the output leaves of tiles without work (they are never handed
-// out): one warp per (tile, leaf row); in symmetric mode leaf (i, j), i < j,
-// and its mirror (j, i).
+// out): one warp per (tile, leaf row, tile column); in symmetric mode leaf
+// (i, j), i <= j, and its mirror (j, i) (a leaf below the diagonal is the
+// mirror of one above it).
 __global__ void __launch_bounds__(kWarps * 32)
-k_tile_zero(const int32_t *__restrict__ stop, const int32_t *__restrict__ counts, int64_t nb, int64_t nI, int R,
-            int sym, int b, const int32_t *__restrict__ slotC, double *__restrict__ leafC)
+k_tile_zero(const int32_t *__restrict__ stop, const int32_t *__restrict__ counts, int64_t nb, int64_t nI,
+            int64_t nbt, int R, int W, int sym, int b, const int32_t *__restrict__ slotC, double *__restrict__ leafC)
 {
     if (stop && *stop) return;
     const int64_t w = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    if (w >= nI * nb * R) return;
-    const int64_t t = w / R, L = w % R;
-    const int64_t I = t / nb, j = t % nb, i = (int64_t)R * I + L;
-    if (counts[t] > 0 || i >= nb || (sym && (j < (int64_t)R * I || i > j))) return;
+    if (w >= nI * nbt * R * W) return;
+    const int64_t t = w / (R * W), L = (w / W) % R, cc = w % W;
+    const int64_t I = t / nbt, j = W * (t % nbt) + cc, i = (int64_t)R * I + L;
+    if (counts[t] > 0 || i >= nb || j >= nb || (sym && i > j)) return;
     const double2 z = make_double2(0.0, 0.0);
     double2 *d = reinterpret_cast<double2 *>(leafC + (int64_t)slotC[i * nb + j] * b * b);
     for (int q = lane; q < b * b / 2; q += 32) d[q] = z;
@@ -315,8 +372,8 @@ int tc_mode_ok(int prec, int slices, int leaf)
 int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, int sym, int slices,
                  cudaStream_t s, bool heaviest_first)
 {
-    const int R = 128 / A->b;
-    const int64_t nb = A->nb, P = A->P, nI = (nb + R - 1) / R, T = nI * nb;
+    const int R = 128 / A->b, W = tc::tile_width(A->b, slices);
+    const int64_t nb = A->nb, P = A->P, nI = (nb + R - 1) / R, nbt = (nb + W - 1) / W, T = nI * nbt;
     if (T >= (int64_t(1) << 24)) {
         spamm_set_error("tensor-core path: %lld tiles exceed 2^24", (long long)T);
         return SPAMM_E_NOTSUP;
@@ -354,6 +411,8 @@ int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, i
     c.nb = nb;
     c.P = P;
     c.nI = nI;
+    c.nbt = nbt;
+    c.W = W;
     c.tau2 = tau * tau;
     c.sym = sym;
     c.S = slices;
@@ -367,7 +426,7 @@ int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, i
         c.cW = int64_t(1) << (A->depth - 5);
     }
     const unsigned blocks = (unsigned)((T + kWarps - 1) / kWarps);
-    const int64_t worst = T * nb;  // every tile owns a segment of nb items
+    const int64_t worst = T * nb;  // every tile owns a segment of nb items (one per k)
     if (ws->tlist_cap < worst) {
         spamm_release(ws->tlist, s);
         ws->tlist = nullptr;
@@ -381,7 +440,18 @@ int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, i
     // issued slice-pair work, toff[T+3] slice pairs the surviving triples need
     // (toff[0..T) the items' running count); the order of tiles with work
     ws->tsym = sym;
-    ws->tactive = sym ? nI * nb - (int64_t)R * nI * (nI - 1) / 2 : T;
+    ws->tw = W;
+    ws->tT = T;
+    // hand-out positions: the active tiles (symmetric: tile row I starts at
+    // tile column floor(R I / W), the first whose last column reaches row R I)
+    ws->tactive = T;
+    if (sym) {
+        ws->tactive = 0;
+        for (int64_t I = 0; I < nI; I++) {
+            const int64_t j0 = (int64_t)R * I / W;
+            ws->tactive += nbt > j0 ? nbt - j0 : 0;
+        }
+    }
     SPAMM_CK(cudaMemsetAsync(ws->torder, 0xFF, sizeof(int32_t) * ws->tactive, s));  // -1: no tile
     k_tile_scan<<<1, kScanThreads, 0, s>>>(ws->stop, ws->tcounts, ws->ttasks, ws->tpairs, ws->tuseful, T,
                                            ws->toff, ws->tnz, heaviest_first ? nullptr : ws->torder,
@@ -402,11 +472,11 @@ int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, i
 
 int tc_zero_empty_tiles(spamm_mat_t C, SpammWorkspace *ws, cudaStream_t s)
 {
-    const int R = 128 / C->b;
-    const int64_t nb = C->nb, nI = (nb + R - 1) / R;
-    const int64_t warps = nI * nb * R;
-    k_tile_zero<<<(unsigned)((warps + kWarps - 1) / kWarps), kWarps * 32, 0, s>>>(ws->stop, ws->tcounts, nb, nI, R,
-                                                                                ws->tsym, C->b, C->slot, C->leaf);
+    const int R = 128 / C->b, W = ws->tw;
+    const int64_t nb = C->nb, nI = (nb + R - 1) / R, nbt = (nb + W - 1) / W;
+    const int64_t warps = nI * nbt * R * W;
+    k_tile_zero<<<(unsigned)((warps + kWarps - 1) / kWarps), kWarps * 32, 0, s>>>(
+        ws->stop, ws->tcounts, nb, nI, nbt, R, W, ws->tsym, C->b, C->slot, C->leaf);
     SPAMM_CK_LAUNCH();
     return SPAMM_OK;
 }
@@ -427,9 +497,10 @@ static void fill_prob(tc::TcProb &p, spamm_mat_t A, spamm_mat_t B, spamm_mat_t C
     p.sigB = reinterpret_cast<const int32_t *>(B->scale + 1);
     p.tr_part = tr_part;
     p.nb = A->nb;
+    p.nbt = (A->nb + ws->tw - 1) / ws->tw;
     p.pos0 = pos0;
     p.sym = ws->tsym;
-    p.pad_ = 0;
+    p.tw = ws->tw;
 }
 
 static int launch_args(tc::TcArgs &a, int leaf, int slices, int e, cudaStream_t s)

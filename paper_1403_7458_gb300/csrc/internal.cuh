@@ -31,7 +31,8 @@ struct SpammWorkspace {
     int32_t *counter = nullptr;  // work counters and error flags (16 ints)
     double *tr_part = nullptr;   // per leaf row partial traces (nb)
     int64_t tr_cap = 0;
-    // tensor-core path: tile work lists (tile t = I * nb + j, I = i / R)
+    // tensor-core path: tile work lists (tile t = I * nbt + J: leaf rows
+    // R I .. R I + R - 1, leaf columns tw J .. tw J + tw - 1, nbt = ceil(nb / tw))
     int32_t *tcounts = nullptr;  // work items per tile
     int32_t *ttasks = nullptr;   // surviving triples per tile
     int32_t *tpairs = nullptr;   // slice-pair work per tile (sum of m(m+1)/2)
@@ -40,7 +41,7 @@ struct SpammWorkspace {
     int32_t *torder = nullptr;   // tile hand-out order (row-major or heaviest first), tiles with work only, then -1
     int32_t *tnz = nullptr;      // rank of each tile among the tiles with work
     int32_t *tbins = nullptr;    // nb + 1 histogram bins
-    uint32_t *tlist = nullptr;   // k | mask << 15 | zA << 23 | zB << 26
+    uint32_t *tlist = nullptr;   // k | mask << 15 | zA << 23 | zB << 26 (two columns: tc::item_make2)
     int64_t tile_cap = 0, tlist_cap = 0;
     const int64_t *task_total = nullptr;  // device: surviving triples of the last cull
     const int64_t *pair_units = nullptr;  // device: slice pairs needed (tensor path), else null
@@ -49,6 +50,8 @@ struct SpammWorkspace {
     int64_t tactive = 0;                  // tiles in the order list of the last tile cull
     const int32_t *stop = nullptr;        // device flag: when set, the product's kernels return at once
     int tsym = 0;                         // last tile cull was symmetric
+    int tw = 1;                           // output leaf columns per tile of the last tile cull
+    int64_t tT = 0;                       // tiles of the last tile cull (totals at toff + tT)
 };
 
 struct spamm_mat {

@@ -228,7 +228,8 @@ __device__ void sp2_finish(int mode, const double *idem_part, int64_t idem_count
 //   mode 0: X <- (emax I - F) / (emax - emin)          (src = F)
 //   mode 1: X <- X2 if branch else 2 X - X2            (src = X2)
 // In mode 1 with x2cnt (the tensor path's work items per tile of X2's
-// product, R leaf rows per tile, symmetric or not), a leaf of X2 whose tile had no work
+// product, R leaf rows by tw leaf columns per tile, symmetric or not), a
+// leaf of X2 whose tile had no work
 // is zero and was not written: it is not read, and a leaf that is zero in
 // both X (squared norm 0) and X2 stays zero without being touched.
 // Writes the leaf's squared norm (exact, once rounded) and, for diagonal
@@ -246,7 +247,7 @@ k_sp2_elementwise(int mode, double *__restrict__ X, const double *__restrict__ s
                   const int32_t *__restrict__ slot, const int32_t *__restrict__ src_slot, int64_t n, int64_t nb,
                   int64_t P, double *__restrict__ n2, double *__restrict__ n2T, double *__restrict__ idem_part,
                   double *__restrict__ diag_part, Sp2State *st, Sp2Rule rule, double *__restrict__ hist,
-                  const int32_t *__restrict__ x2cnt, int R, int sym)
+                  const int32_t *__restrict__ x2cnt, int R, int tw, int sym)
 {
     constexpr int BB = B * B;
     constexpr int kPer = BB / 32;              // elements per lane
@@ -270,7 +271,7 @@ k_sp2_elementwise(int mode, double *__restrict__ X, const double *__restrict__ s
         bool y0 = ss < 0;  // source leaf known to be zero
         if (mode == 1 && x2cnt) {
             const int64_t a = (sym && I > K) ? K : I, c = (sym && I > K) ? I : K;
-            y0 = x2cnt[(a / R) * nb + c] == 0;
+            y0 = x2cnt[(a / R) * ((nb + tw - 1) / tw) + c / tw] == 0;
         }
         // X_new = X2 or 2X - X2 = 0 with X = 0 = X2: nothing to read or write
         // (mode 0 writes every leaf of X: X0 = (emax I - F) / range)
@@ -373,29 +374,29 @@ template <int B>
 void launch_elementwise_b(cudaStream_t s, int mode, double *X, const double *src, const int32_t *slot,
                           const int32_t *src_slot, int64_t n, int64_t nb, int64_t P, double *n2, double *n2T,
                           double *idem_part, double *diag_part, Sp2State *st, Sp2Rule rule, double *hist,
-                          const int32_t *x2cnt, int R, int sym)
+                          const int32_t *x2cnt, int R, int tw, int sym)
 {
     const int64_t cap = ew_grid_cap<B>();
     const int64_t need = (nb * nb + kEwWarps - 1) / kEwWarps;
     const unsigned grid = (unsigned)(need < cap ? need : cap);
     k_sp2_elementwise<B><<<grid, kEwWarps * 32, 0, s>>>(mode, X, src, slot, src_slot, n, nb, P, n2, n2T, idem_part,
-                                                    diag_part, st, rule, hist, x2cnt, R, sym);
+                                                    diag_part, st, rule, hist, x2cnt, R, tw, sym);
 }
 
 void launch_elementwise(int b, cudaStream_t s, int mode, double *X, const double *src, const int32_t *slot,
                         const int32_t *src_slot, int64_t n, int64_t nb, int64_t P, double *n2, double *n2T,
                         double *idem_part, double *diag_part, Sp2State *st, Sp2Rule rule, double *hist,
-                        const int32_t *x2cnt, int R, int sym)
+                        const int32_t *x2cnt, int R, int tw, int sym)
 {
     if (b == 16)
         launch_elementwise_b<16>(s, mode, X, src, slot, src_slot, n, nb, P, n2, n2T, idem_part, diag_part, st,
-                                 rule, hist, x2cnt, R, sym);
+                                 rule, hist, x2cnt, R, tw, sym);
     else if (b == 32)
         launch_elementwise_b<32>(s, mode, X, src, slot, src_slot, n, nb, P, n2, n2T, idem_part, diag_part, st,
-                                 rule, hist, x2cnt, R, sym);
+                                 rule, hist, x2cnt, R, tw, sym);
     else
         launch_elementwise_b<64>(s, mode, X, src, slot, src_slot, n, nb, P, n2, n2T, idem_part, diag_part, st,
-                                 rule, hist, x2cnt, R, sym);
+                                 rule, hist, x2cnt, R, tw, sym);
 }
 
 
@@ -578,7 +579,7 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
     k_gershgorin_bounds<<<1, kRedThreads, 0, s>>>(sc.lo, sc.hi, F->n, sc.st);
     SP2_LAUNCHED();
     launch_elementwise(X->b, s, 0, X->leaf, F->leaf, X->slot, F->slot, F->n, nb, X->P, X->n2 + tier_offset(X->depth),
-                       X->n2T, sc.idem_part, sc.diag_part, sc.st, Sp2Rule{Ne, 0, 0, 0, 1}, sc.hist, nullptr, 1, 0);
+                       X->n2T, sc.idem_part, sc.diag_part, sc.st, Sp2Rule{Ne, 0, 0, 0, 1}, sc.hist, nullptr, 1, 1, 0);
     SP2_LAUNCHED();
     // upper tiers of the iterate: the cull's early skip reads them (rebuilt
     // only where the skip pays; otherwise marked stale and not used)
@@ -603,7 +604,7 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
                 SPAMM_CK_LAUNCH();
                 launch_elementwise(X->b, st, 1, X->leaf, X2->leaf, X->slot, X2->slot, F->n, nb, X->P,
                                    X->n2 + tier_offset(X->depth), X->n2T, sc.idem_part, sc.diag_part, sc.st, rule,
-                                   sc.hist, x2cnt, 128 / X->b, sym ? 1 : 0);
+                                   sc.hist, x2cnt, 128 / X->b, X2->ws.tw, sym ? 1 : 0);
                 SPAMM_CK_LAUNCH();
                 if (coarse && (r = launch_pyramid(X, st))) return r;
                 if (timing) SPAMM_CK(spamm_event_record(ev[4], st));

@@ -3,17 +3,20 @@
 // translation units that instantiate it per leaf size.
 //
 // Tiles.  A tile is R = 128 / b consecutive output leaf rows i = R I ..
-// R I + R - 1 and one output leaf column j (M = 128 rows, N = b columns).
-// Its work list holds every k for which at least one of the R triples
-// (i, k, j) survives the culling test of Eq. 4, with an R-bit mask of the
-// survivors.  The MMAs of an item run over all R A leaves, with the TMEM
-// lanes (output rows) of culled triples disabled (the instruction's
+// R I + R - 1 and W consecutive output leaf columns j = W J .. W J + W - 1
+// (W = 2 at leaf 32, else 1; M = 128 rows).  Its work list holds every k
+// for which at least one of its R W triples (i, k, j) survives the culling
+// test of Eq. 4, with an R-bit mask of the survivors per column: the item's
+// A slab (the R leaves (i, k)) is copied once for all W columns.  The MMAs
+// of a column run over all R A leaves, with the TMEM lanes (output rows) of
+// that column's culled triples disabled (the instruction's
 // disable-output-lane mask), so each output leaf receives exactly the
 // products of its own task list (no extra products, no missing ones).
 //
 // Slices.  With s slices per operand (see slice.cu), the MMAs for A slice p
 // multiply the 128 x b A slab by B slices q = zB..s-1-p (N = b (s - p - zB))
-// and accumulate into TMEM columns [b (p + zB), b s): column block d then
+// of a column's B leaf and accumulate into that column's TMEM columns
+// [b (p + zB), b s) (column c's block starts at c s b): column block d then
 // holds S_d = sum_{p+q=d} sum_k sum_l dA_p dB_q.  Pairs with p + q >= s are
 // never formed, nor pairs with p < zA or q < zB, where zA (the least over
 // the item's kept A leaves) and zB count leading slices that are zero in
@@ -48,8 +51,10 @@
 //   warps 2-5  : epilogue; tcgen05.ld of the s diagonal blocks of the row the
 //                thread owns, combine, FP64 store, diagonal traces.
 // Two accumulators (TMEM columns 0 and 256) let the epilogue of one tile run
-// under the MMAs of the next.  Every wait is bounded (SM cycle counter); on
-// timeout the kernel records the error, drains and frees TMEM, and returns.
+// under the MMAs of the next when a tile's W s b columns fit in 256 (else
+// one accumulator: at leaf 32 with 7 slices a tile takes 448 columns).
+// Every wait is bounded (SM cycle counter); on timeout the kernel records
+// the error, drains and frees TMEM, and returns.
 //
 // Roofline: tensor pipe.  Useful work 2 b^3 per surviving triple; issued
 // tensor work 2 * 128 * b * b per slice pair of a work item.
@@ -81,6 +86,20 @@ __host__ __device__ constexpr uint32_t item_make(uint32_t k, uint32_t mask, int 
 {
     return k | (mask << 15) | ((uint32_t)za << 23) | ((uint32_t)zb << 26);
 }
+// Tiles of two output leaf columns (leaf 32, R = 4): mask bits 0-3 are
+// column 0's kept rows, bits 4-7 column 1's; zB of column c at bits 26 + 3 c
+// (7 for a column without kept rows).
+__host__ __device__ constexpr uint32_t item_make2(uint32_t k, uint32_t mask0, uint32_t mask1, int za, int zb0,
+                                                  int zb1)
+{
+    return k | (mask0 << 15) | (mask1 << 19) | ((uint32_t)za << 23) | ((uint32_t)zb0 << 26) | ((uint32_t)zb1 << 29);
+}
+template <int R, int W>
+__host__ __device__ constexpr uint32_t item_mask_col(uint32_t w, int c)
+{
+    return (item_mask(w) >> (c * R)) & ((1u << R) - 1u);
+}
+__host__ __device__ constexpr int item_zb_col(uint32_t w, int c) { return (int)((w >> (26 + 3 * c)) & 7); }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -237,9 +256,10 @@ struct TcProb {
     const int32_t *sigB;
     double *tr_part;       // diagonal-leaf traces (may be null; b = 32 only)
     int64_t nb;
+    int64_t nbt;           // tiles per tile row: ceil(nb / W), W output leaf columns per tile
     int64_t pos0;          // first hand-out position of this product
     int32_t sym;           // symmetric product: upper block triangle + mirror
-    int32_t pad_;
+    int32_t tw;            // output leaf columns per tile of its work lists
 };
 
 struct TcArgs {
@@ -282,7 +302,7 @@ __device__ __forceinline__ int find_prob(const TcArgs &g, int64_t pos)
     return lo;
 }
 
-template <int S, int E, int B>
+template <int S, int E, int B, int W>
 __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__ TcArgs g)
 {
     constexpr int R = 128 / B;                  // leaf rows per tile
@@ -290,8 +310,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
     constexpr uint32_t kSBO = 8 * B * E;        // 8-row group stride
     constexpr uint32_t kAW = slice_atom_bytes<B, E>();  // swizzle atom width (bytes)
     constexpr int kMmaK = B * E / 32;           // instructions per slice pair
-    static_assert(S * B <= (int)kAccStride, "accumulator exceeds its TMEM columns");
-    static_assert((uint32_t)S * (R + 1) * kSlice <= kRingBytes, "work item exceeds the ring");
+    constexpr uint32_t kColAcc = S * B;         // TMEM columns per output leaf column
+    // two accumulators (columns 0 and kAccStride) when a tile's fit in half
+    // of TMEM, else one
+    constexpr int kNAcc = W * S * B <= (int)kAccStride ? 2 : 1;
+    static_assert(W * S * B <= (int)kTmemCols, "accumulators exceed TMEM");
+    static_assert(R * W <= 8, "the item's masks exceed 8 bits");
+    static_assert((uint32_t)S * (R + W) * kSlice <= kRingBytes, "work item exceeds the ring");
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t full_bar[kSlots], empty_bar[kSlots];
     __shared__ __align__(8) uint64_t accf_bar[2], acce_bar[2], done_bar;
@@ -338,7 +363,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
     // must sit at addresses aligned to their repeat
     const uint32_t sraw = smem_u32(smem);
     const uint32_t sbase = (sraw + 1023u) & ~1023u;
-    uint8_t *const ring = smem + (sbase - sraw);
     volatile int *abort_v = &abort_flag;
 
     if (warp == 0) {
@@ -389,26 +413,43 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
             const TcProb &P = g.p[tt >> 24];
             const int64_t t = tt & 0xFFFFFF;
             const int64_t nb = P.nb;
-            const int64_t I = t / nb, j = t % nb;
+            const int64_t I = t / P.nbt, J = t % P.nbt;
             const int64_t e0 = t * nb, e1 = e0 + P.cnt[t];
             for (int64_t base = e0; base < e1 && ok; base += 32) {
                 const int cnt = (int)(e1 - base < 32 ? e1 - base : 32);
                 uint32_t wl = 0;
-                int64_t bl = 0;
+                int64_t bl[W];
+#pragma unroll
+                for (int c = 0; c < W; c++) bl[c] = 0;
                 if (lane < cnt) {
                     wl = P.list[base + lane];
                     const int64_t kk = item_k(wl);
-                    bl = P.sym ? P.slotA[j * nb + kk] : P.slotB[kk * nb + j];
+#pragma unroll
+                    for (int c = 0; c < W; c++) {
+                        const int64_t j = W * J + c;
+                        if (j < nb && item_mask_col<R, W>(wl, c))
+                            bl[c] = P.sym ? P.slotA[j * nb + kk] : P.slotB[kk * nb + j];
+                    }
                 }
                 for (int q = 0; q < cnt; q++) {
                     const uint32_t w = __shfl_sync(0xffffffffu, wl, q);
-                    const int64_t bslot = __shfl_sync(0xffffffffu, bl, q);
+                    int64_t bslot[W];
+#pragma unroll
+                    for (int c = 0; c < W; c++) bslot[c] = __shfl_sync(0xffffffffu, bl[c], q);
                     int good = 1;
                     if (lane == 0) {
                         const int64_t k = item_k(w);
-                        const int za = item_za(w), zb = item_zb(w);
-                        const int m = S - za - zb;  // slices needed from each operand
-                        const uint32_t need = (uint32_t)m * (R + 1) * kSlice;
+                        const int za = item_za(w);
+                        int mc[W], mA = 0;
+                        uint32_t need = 0;
+#pragma unroll
+                        for (int c = 0; c < W; c++) {
+                            // slices needed from column c's B leaf (none: column absent)
+                            mc[c] = item_mask_col<R, W>(w, c) ? S - za - item_zb_col(w, c) : 0;
+                            mA = mc[c] > mA ? mc[c] : mA;
+                            need += (uint32_t)mc[c] * kSlice;
+                        }
+                        need += (uint32_t)mA * R * kSlice;
                         uint32_t pos = (uint32_t)(alloc_ptr % kRingBytes);
                         if (pos + need > kRingBytes) {
                             alloc_ptr += kRingBytes - pos;
@@ -432,14 +473,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                             end_ptr[sl] = new_end;
                             alloc_ptr = new_end;
                             const uint32_t fb = smem_u32(&full_bar[sl]);
-                            const uint32_t dst = sbase + pos;
+                            uint32_t dst = sbase + pos;
                             mbar_expect_tx(fb, need);
-                            // A: slices za..za+m-1 of the R rows' leaves, one contiguous block
+                            // A: slices za..za+mA-1 of the R rows' leaves, one contiguous block
                             bulk_g2s(dst, P.slA + ((I * nb + k) * S + za) * (int64_t)(R * kSlice),
-                                     (uint32_t)m * R * kSlice, fb);
-                            // B: slices zb..zb+m-1 of leaf (k, j) (symmetric: leaf (j, k))
-                            bulk_g2s(dst + (uint32_t)m * R * kSlice,
-                                     P.slB + bslot * (int64_t)(S * kSlice) + zb * kSlice, (uint32_t)m * kSlice, fb);
+                                     (uint32_t)mA * R * kSlice, fb);
+                            dst += (uint32_t)mA * R * kSlice;
+                            // B: slices zb..S-1-za of leaf (k, j) per present column
+                            // (symmetric: leaf (j, k))
+#pragma unroll
+                            for (int c = 0; c < W; c++) {
+                                if (mc[c] <= 0) continue;
+                                bulk_g2s(dst, P.slB + bslot[c] * (int64_t)(S * kSlice) + item_zb_col(w, c) * kSlice,
+                                         (uint32_t)mc[c] * kSlice, fb);
+                                dst += (uint32_t)mc[c] * kSlice;
+                            }
                             issued++;
                         }
                     }
@@ -464,8 +512,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
         __syncwarp();
     } else if (warp == 1) {
         // ------------------------------ MMA issuer ------------------------------
-        // Lane 0 alone: waits until an item has landed, then issues its MMAs and commits them to the item's "empty" barrier and,
-        // at the end of a tile, to the accumulator's "full" barrier.
+        // Lane 0 alone: waits until an item has landed, then issues its MMAs
+        // (per present column, with the TMEM lanes of that column's culled
+        // leaf rows disabled) and commits them to the item's "empty" barrier
+        // and, at the end of a tile, to the accumulator's "full" barrier.
         if (lane == 0) {
             uint32_t consumed = 0, acc = 0, aph = 0;
             bool ok = true;
@@ -500,38 +550,48 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t w = slot_w[sl], pos = slot_off[sl];
-                    const int za = item_za(w), zb = item_zb(w);
-                    const int m = S - za - zb;
-                    const uint32_t mask = item_mask(w);
-                    const uint32_t dis[4] = {culled_lanes<B>(mask, 0), culled_lanes<B>(mask, 1),
-                                             culled_lanes<B>(mask, 2), culled_lanes<B>(mask, 3)};
-                    const uint32_t sa = sbase + pos;                        // A slice za
-                    const uint32_t sb = sa + (uint32_t)m * R * kSlice;      // B slice zb
+                    const int za = item_za(w);
+                    int mc[W], mA = 0;
+#pragma unroll
+                    for (int c = 0; c < W; c++) {
+                        mc[c] = item_mask_col<R, W>(w, c) ? S - za - item_zb_col(w, c) : 0;
+                        mA = mc[c] > mA ? mc[c] : mA;
+                    }
+                    const uint32_t sa = sbase + pos;                  // A slice za
+                    uint32_t sb = sa + (uint32_t)mA * R * kSlice;     // B slices of the first present column
                     // descriptors advance by adding (bytes >> 4) to the address field
                     // (shared addresses stay below 256 KB, so the field never carries)
                     const uint64_t da0 = smem_desc<kAW>(sa, kSBO);
-                    const uint64_t db0 = smem_desc<kAW>(sb, kSBO);
-                    uint32_t idesc = mma_idesc<E>(128, B * m);
-                    uint32_t dcol = dacc + B * (za + zb);
-                    for (int pp = 0; pp < m; pp++) {
-                        const uint64_t da = da0 + (uint64_t)(pp * (R * kSlice / 16));
 #pragma unroll
-                        for (int h = 0; h < kMmaK; h++) {
-                            // 32 bytes of K each: inside a swizzle atom the start
-                            // address moves by 32 B, across atoms by 8 AW bytes
-                            const uint32_t kb = (uint32_t)(32 * h);
-                            const uint64_t adv = ((kb / kAW) * 8 * kAW + kb % kAW) >> 4;
-                            mma_issue<E>(dcol, da + adv, db0 + adv, idesc, dis);
+                    for (int c = 0; c < W; c++) {
+                        if (mc[c] <= 0) continue;
+                        const uint32_t mask = item_mask_col<R, W>(w, c);
+                        const uint32_t dis[4] = {culled_lanes<B>(mask, 0), culled_lanes<B>(mask, 1),
+                                                 culled_lanes<B>(mask, 2), culled_lanes<B>(mask, 3)};
+                        const uint64_t db0 = smem_desc<kAW>(sb, kSBO);
+                        uint32_t idesc = mma_idesc<E>(128, B * mc[c]);
+                        uint32_t dcol = dacc + c * kColAcc + B * (za + item_zb_col(w, c));
+                        for (int pp = 0; pp < mc[c]; pp++) {
+                            const uint64_t da = da0 + (uint64_t)(pp * (R * kSlice / 16));
+#pragma unroll
+                            for (int h = 0; h < kMmaK; h++) {
+                                // 32 bytes of K each: inside a swizzle atom the start
+                                // address moves by 32 B, across atoms by 8 AW bytes
+                                const uint32_t kb = (uint32_t)(32 * h);
+                                const uint64_t adv = ((kb / kAW) * 8 * kAW + kb % kAW) >> 4;
+                                mma_issue<E>(dcol, da + adv, db0 + adv, idesc, dis);
+                            }
+                            idesc -= (uint32_t)(B >> 3) << 17;  // N shrinks by b
+                            dcol += B;
                         }
-                        idesc -= (uint32_t)(B >> 3) << 17;  // N shrinks by b
-                        dcol += B;
+                        sb += (uint32_t)mc[c] * kSlice;
                     }
                     mma_commit(smem_u32(&empty_bar[sl]));
                     consumed++;
                 }
                 if (!ok) break;
                 mma_commit(smem_u32(&accf_bar[acc]));
-                if (++acc == 2) {
+                if (++acc == (uint32_t)kNAcc) {
                     acc = 0;
                     aph ^= 1;
                 }
@@ -551,18 +611,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
         const int row = quad * 32 + lane;      // tile row 0..127
         const int L = row / B, r = row % B;    // leaf within tile, row within leaf
         const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
-        // both accumulators start at zero (first phase of their "empty" barriers)
-        for (int b = 0; b < 2; b++) {
-            for (int d = 0; d < S; d++)
+        // the accumulators start at zero (first phase of their "empty" barriers)
+        for (int b = 0; b < kNAcc; b++) {
+            for (int d = 0; d < W * S; d++)
                 for (int h = 0; h < B / 16; h++) tmem_zero16(tmem + b * kAccStride + lane_off + B * d + 16 * h);
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
-        if (lane == 0) {
-            mbar_arrive(smem_u32(&acce_bar[0]));
-            mbar_arrive(smem_u32(&acce_bar[1]));
-        }
+        if (lane == 0)
+            for (int b = 0; b < kNAcc; b++) mbar_arrive(smem_u32(&acce_bar[b]));
         uint32_t acc = 0, aph = 0;
         uint32_t tq = 0, tph = 0;
         for (;;) {
@@ -589,7 +647,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
             const TcProb &P = g.p[tt >> 24];
             const int64_t t = tt & 0xFFFFFF;
             const int64_t nb = P.nb;
-            const int64_t I = t / nb, j = t % nb;
+            const int64_t I = t / P.nbt, J = t % P.nbt;
             const bool has_work = P.cnt[t] > 0;
             if (!mbar_wait(smem_u32(&accf_bar[acc]), aph, abort_v)) {
                 if (lane == 0) atomicExch(g.err, 1);
@@ -598,52 +656,71 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int64_t i = (int64_t)R * I + L;
-            // symmetric mode: leaf (i, j) is written only for i <= j, and for
-            // i < j its transpose goes to leaf (j, i)
-            const bool store = i < nb && (!P.sym || i <= j);
             const int kexp = g.float_split ? 0 : *P.sigA + *P.sigB - 7 * S - 7;
-            double *dst = store ? P.leafC + (int64_t)P.slotC[i * nb + j] * (B * B) + r * B : nullptr;
-            double *mir = (store && P.sym && i < j) ? P.leafC + (int64_t)P.slotC[j * nb + i] * (B * B) + r : nullptr;
             double diag = 0.0;
-            const uint32_t tbase = tmem + acc * kAccStride + lane_off;
+            bool on_diag = false;
+#pragma unroll 1
+            for (int c = 0; c < W; c++) {
+                const int64_t j = W * J + c;
+                if (j >= nb) break;  // no such column (nothing was accumulated there)
+                // symmetric mode: leaf (i, j) is written only for i <= j, and for
+                // i < j its transpose goes to leaf (j, i)
+                const bool store = i < nb && (!P.sym || i <= j);
+                double *dst = store ? P.leafC + (int64_t)P.slotC[i * nb + j] * (B * B) + r * B : nullptr;
+                double *mir =
+                    (store && P.sym && i < j) ? P.leafC + (int64_t)P.slotC[j * nb + i] * (B * B) + r : nullptr;
+                const uint32_t tbase = tmem + acc * kAccStride + c * kColAcc + lane_off;
+                if (i == j) on_diag = true;
 #pragma unroll
-            for (int h = 0; h < B / 16; h++) {
-                long long cint[16];   // exact slices: integer combination
-                double cflt[16];      // float split: FP64 sum of the FP32 diagonals
+                for (int h = 0; h < B / 16; h++) {
+                    // the S diagonals of these 16 columns: all loads issued,
+                    // one wait, the accumulator zeroed for the next tile
+                    uint32_t v[S][16];
+                    if (has_work) {
 #pragma unroll
-                for (int c = 0; c < 16; c++) {
-                    cint[c] = 0;
-                    cflt[c] = 0.0;
-                }
-                if (has_work) {
-#pragma unroll
-                    for (int d = 0; d < S; d++) {
-                        uint32_t v[16];
-                        tmem_ld16(tbase + B * d + 16 * h, v);
+                        for (int d = 0; d < S; d++) tmem_ld16(tbase + B * d + 16 * h, v[d]);
                         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                        if (g.float_split) {
 #pragma unroll
-                            for (int c = 0; c < 16; c++) cflt[c] += (double)__uint_as_float(v[c]);
-                        } else {
+                        for (int d = 0; d < S; d++) tmem_zero16(tbase + B * d + 16 * h);
+                    } else {
 #pragma unroll
-                            for (int c = 0; c < 16; c++)
-                                cint[c] += (long long)__float2ll_rn(__uint_as_float(v[c])) * (1ll << (7 * (S - 1 - d)));
-                        }
-                        tmem_zero16(tbase + B * d + 16 * h);
+                        for (int d = 0; d < S; d++)
+#pragma unroll
+                            for (int q = 0; q < 16; q++) v[d][q] = 0u;
                     }
-                }
-                if (store) {
+                    // exact slices: integer combination; float split: FP64 sum
+                    double res[16];
+                    if (g.float_split) {
 #pragma unroll
-                    for (int c = 0; c < 16; c += 2) {
-                        const int col = 16 * h + c;
-                        double2 v;
-                        v.x = g.float_split ? cflt[c] : i64_scaled(cint[c], kexp);
-                        v.y = g.float_split ? cflt[c + 1] : i64_scaled(cint[c + 1], kexp);
-                        if (col == (r & ~1)) diag = (r & 1) ? v.y : v.x;
-                        reinterpret_cast<double2 *>(dst)[col >> 1] = v;
-                        if (mir) {
-                            mir[col * B] = v.x;
-                            mir[(col + 1) * B] = v.y;
+                        for (int q = 0; q < 16; q++) {
+                            double a = 0.0;
+#pragma unroll
+                            for (int d = 0; d < S; d++) a += (double)__uint_as_float(v[d][q]);
+                            res[q] = a;
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 16; q++) {
+                            long long a = 0;
+#pragma unroll
+                            for (int d = 0; d < S; d++)
+                                a += (long long)__float2ll_rn(__uint_as_float(v[d][q])) * (1ll << (7 * (S - 1 - d)));
+                            res[q] = i64_scaled(a, kexp);
+                        }
+                    }
+                    if (store) {
+#pragma unroll
+                        for (int q = 0; q < 16; q += 2) {
+                            const int col = 16 * h + q;
+                            double2 v;
+                            v.x = res[q];
+                            v.y = res[q + 1];
+                            if (i == j && col == (r & ~1)) diag = (r & 1) ? v.y : v.x;
+                            reinterpret_cast<double2 *>(dst)[col >> 1] = v;
+                            if (mir) {
+                                mir[col * B] = v.x;
+                                mir[(col + 1) * B] = v.y;
+                            }
                         }
                     }
                 }
@@ -652,15 +729,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&acce_bar[acc]));
-            if (++acc == 2) {
+            if (++acc == (uint32_t)kNAcc) {
                 acc = 0;
                 aph ^= 1;
             }
             if (B <= 32 && P.tr_part) {
                 // fixed butterfly over the B rows of a diagonal leaf (a warp
-                // holds 32 / B whole leaves; the condition is warp-uniform)
+                // holds 32 / B whole leaves, each within one tile column; the
+                // condition is uniform over each leaf's rows)
                 for (int o = B / 2; o > 0; o >>= 1) diag += __shfl_xor_sync(0xffffffffu, diag, o);
-                if (r == 0 && store && i == j) P.tr_part[i] = diag;
+                if (r == 0 && on_diag && i < nb) P.tr_part[i] = diag;
             }
         }
     }
@@ -672,16 +750,29 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                      : "memory");
 }
 
+// Output leaf columns per tile: two at leaf 32 when the tile's accumulators
+// still fit twice in TMEM (s <= 4 slices: the A slab of an item serves both
+// columns, and the epilogue of one tile runs under the MMAs of the next),
+// one otherwise (measured: with a single accumulator the tile epilogue is
+// exposed and costs more than the shared A slab saves).
+constexpr int tile_width(int B, int S) { return (B == 32 && 2 * S * B <= (int)kAccStride) ? 2 : 1; }
+
 template <int S, int E, int B>
 int launch_k(const TcArgs &a, cudaStream_t s)
 {
+    constexpr int W = tile_width(B, S);
+    for (int m = 0; m < a.nprob; m++)
+        if (a.p[m].tw != W) {
+            spamm_set_error("tensor-core kernel: work lists of %d-column tiles, kernel built for %d", a.p[m].tw, W);
+            return SPAMM_E_INVAL;
+        }
     const size_t smem = kRingBytes + 1024;  // + alignment slack of the ring
     static unsigned long long configured = 0;
-    if (int rc = spamm_smem_attr(k_gemm_tc<S, E, B>, smem, configured)) return rc;
+    if (int rc = spamm_smem_attr(k_gemm_tc<S, E, B, W>, smem, configured)) return rc;
     int64_t grid = spamm_num_sms();
     if (grid > a.T) grid = a.T;
     if (grid < 1) grid = 1;
-    k_gemm_tc<S, E, B><<<(unsigned)grid, kThreads, smem, s>>>(a);
+    k_gemm_tc<S, E, B, W><<<(unsigned)grid, kThreads, smem, s>>>(a);
     SPAMM_CK_LAUNCH();
     return SPAMM_OK;
 }
