@@ -47,10 +47,10 @@ UNIT = "TFLOP/s"
 L2_BYTES = 129 * 1024 * 1024
 # DRAM bytes (read + write) per launch of the tensor-core leaf-product kernel
 # of this workload (mean over the 24 launches of one solve), from an ncu
-# capture of the kernel as it stands (k_gemm_tc<7, 2, 32>: swizzled operands,
-# prep warp, row-major hand-out of tiles with work, per-tile list segments);
-# set to None when the kernel changes.
-TC_TRAFFIC_BYTES_PER_LAUNCH = None
+# capture of the kernel as it stands (k_gemm_tc<7, 2, 32, 1>: one-column
+# tiles, culled leaf rows masked out of the MMAs, row-major hand-out of tiles
+# with work); set to None when the kernel changes.
+TC_TRAFFIC_BYTES_PER_LAUNCH = 490.8e6
 
 
 def _peaks():
@@ -278,7 +278,7 @@ def run_ours(args):
     else:
         peak = peaks.get("bf16_tflops_sustained", 1700.0)
         bound = "tensor"
-        kern = "k_gemm_tc<%d, 2, 32>" % slices
+        kern = "k_gemm_tc<%d, 2, 32, %d>" % (slices, 2 if slices <= 4 else 1)  # tile width: leaf columns
         peak_note = "bf16 tensor, sustained, %s (MEASURED_PEAKS.json)" % peak_src
         # tensor work of the surviving products: each slice pair that is not
         # identically zero, on the tiles actually formed (symmetric half)
@@ -579,7 +579,7 @@ def run_large_study(args):
         "roofline": {"fp64": {"bound": "alu", "kernel": "k_gemm_fp64<32>", "unit": "TFLOP/s",
                               "achieved": r64["flops_useful"] / (r64["ms_gemm"] * 1e-3) / 1e12,
                               "peak": fp64_peak_tflops()},
-                     "mixed": {"bound": "tensor", "kernel": "k_gemm_tc<7,2,32>", "unit": "TFLOP/s",
+                     "mixed": {"bound": "tensor", "kernel": "k_gemm_tc<7,2,32,1>", "unit": "TFLOP/s",
                                "achieved": r["flops_tensor"] / (r["ms_gemm"] * 1e-3) / 1e12,
                                "peak": bf16, "peak_source": "bf16 sustained, %s" % peak_src}},
         "memory": mem, "generation_s": gen_s,

@@ -207,6 +207,7 @@ extern "C" void spamm_free(spamm_mat_t m)
     spamm_release(m->n2T, s);
     spamm_release(m->slA, s);
     spamm_release(m->slB, s);
+    spamm_release(m->tmapA, s);
     spamm_release(m->zlead, s);
     spamm_release(m->scale, s);
     ws_free(&m->ws, s);
@@ -219,8 +220,10 @@ extern "C" void spamm_release_scratch(spamm_mat_t m, void *stream)
     cudaStream_t s = (cudaStream_t)stream;
     spamm_release(m->slA, s);
     spamm_release(m->slB, s);
+    spamm_release(m->tmapA, s);
     spamm_release(m->zlead, s);
     m->slA = m->slB = nullptr;
+    m->tmapA = nullptr;
     m->zlead = nullptr;
     m->sl_s = m->sl_e = 0;
     m->slB_transposed = -1;
@@ -477,12 +480,17 @@ int ws_reserve_groups(SpammWorkspace *ws, int64_t groups, int64_t nb, cudaStream
 }
 
 // Slices of the operands of A x B (tensor-core path): A's tile-major array
-// and B's per-leaf array (B-role layout; for a symmetric product A == B, the
-// A-role layout of the transpose).
+// and B's per-leaf array (B-role layout).  A symmetric product A == B reads
+// its B leaves (the A-role layout of the transpose leaves) from the
+// tile-major array itself, through tensor maps: no per-leaf array.
 static int slice_operands(spamm_mat_t A, spamm_mat_t B, int sl, int el, int symm, cudaStream_t s,
                           const int32_t *stop, bool unit, bool fsplit)
 {
-    if (A == B) return launch_slices(A, sl, el, true, true, !symm, s, stop, unit, fsplit);
+    if (A == B && symm) {
+        if (int rc = launch_slices(A, sl, el, true, false, false, s, stop, unit, fsplit)) return rc;
+        return slices_tmaps(A, s);
+    }
+    if (A == B) return launch_slices(A, sl, el, true, true, true, s, stop, unit, fsplit);
     int rc = launch_slices(A, sl, el, true, false, false, s, stop, unit, fsplit);
     if (rc) return rc;
     return launch_slices(B, sl, el, false, true, true, s, stop, unit, fsplit);

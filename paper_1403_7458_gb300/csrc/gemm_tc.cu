@@ -24,7 +24,6 @@ struct CullArgs {
     int64_t nb, P, nI, nbt;
     double tau2;
     int sym, S, R;  // R = 128 / b leaf rows per tile
-    int W;          // output leaf columns per tile (1, or 2 at leaf 32)
     const int32_t *stop;  // set once an SP2 loop has stopped: nothing to do
 };
 
@@ -133,6 +132,7 @@ __device__ __forceinline__ int item_pairs2(uint32_t w, int S)
 // One warp per tile: tests the candidates k (ballot), writes the tile's work
 // items into its own segment of the list, [t nb, t nb + count), and counts
 // them, the surviving triples and the slice pairs.
+template <int W>
 __global__ void __launch_bounds__(kWarps * 32)
 k_tile_count(CullArgs c, int32_t *__restrict__ counts, int32_t *__restrict__ tasks,
              int32_t *__restrict__ pairs, int32_t *__restrict__ useful, uint32_t *__restrict__ list)
@@ -144,7 +144,7 @@ k_tile_count(CullArgs c, int32_t *__restrict__ counts, int32_t *__restrict__ tas
     const int64_t I = t / c.nbt, J = t % c.nbt;
     // symmetric mode: a tile entirely below the block diagonal is formed as
     // a mirror (its last column is left of its first row)
-    const bool active = !c.sym || (int64_t)c.W * J + c.W - 1 >= (int64_t)c.R * I;
+    const bool active = !c.sym || (int64_t)W * J + W - 1 >= (int64_t)c.R * I;
     int cnt = 0, ntask = 0, npair = 0, nuse = 0;
     if (!active) {  // symmetric mode: a lower-triangle tile is formed as a mirror
         if (lane == 0) counts[t] = tasks[t] = pairs[t] = useful[t] = 0;
@@ -154,13 +154,15 @@ k_tile_count(CullArgs c, int32_t *__restrict__ counts, int32_t *__restrict__ tas
     const unsigned lt = (1u << lane) - 1u;
     for (int64_t k0 = 0; k0 < c.nb; k0 += 32) {
         // the W columns lie in one 32-leaf block column (W divides 32)
-        if (!coarse_pass(c, I, k0, (int64_t)c.W * J)) continue;  // warp-uniform
-        const uint32_t w = c.W == 2 ? tile_item2(c, I, J, k0 + lane, ntask, nuse)
-                                    : tile_item(c, I, J, k0 + lane, ntask, nuse);
+        if (!coarse_pass(c, I, k0, (int64_t)W * J)) continue;  // warp-uniform
+        uint32_t w;
+        if constexpr (W == 2) w = tile_item2(c, I, J, k0 + lane, ntask, nuse);
+        else w = tile_item(c, I, J, k0 + lane, ntask, nuse);
         const unsigned bal = __ballot_sync(0xffffffffu, w != 0);
         if (w) {
             seg[cnt + __popc(bal & lt)] = w;
-            npair += c.W == 2 ? item_pairs2(w, c.S) : item_pairs(w, c.S);
+            if constexpr (W == 2) npair += item_pairs2(w, c.S);
+            else npair += item_pairs(w, c.S);
         }
         cnt += __popc(bal);
     }
@@ -412,7 +414,6 @@ int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, i
     c.P = P;
     c.nI = nI;
     c.nbt = nbt;
-    c.W = W;
     c.tau2 = tau * tau;
     c.sym = sym;
     c.S = slices;
@@ -434,7 +435,10 @@ int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, i
         if ((rc = spamm_alloc((void **)&ws->tlist, sizeof(uint32_t) * worst, s))) return rc;
         ws->tlist_cap = worst;
     }
-    k_tile_count<<<blocks, kWarps * 32, 0, s>>>(c, ws->tcounts, ws->ttasks, ws->tpairs, ws->tuseful, ws->tlist);
+    if (W == 2)
+        k_tile_count<2><<<blocks, kWarps * 32, 0, s>>>(c, ws->tcounts, ws->ttasks, ws->tpairs, ws->tuseful, ws->tlist);
+    else
+        k_tile_count<1><<<blocks, kWarps * 32, 0, s>>>(c, ws->tcounts, ws->ttasks, ws->tpairs, ws->tuseful, ws->tlist);
     SPAMM_CK_LAUNCH();
     // totals: toff[T] work items, toff[T+1] surviving triples, toff[T+2]
     // issued slice-pair work, toff[T+3] slice pairs the surviving triples need
@@ -485,7 +489,9 @@ static void fill_prob(tc::TcProb &p, spamm_mat_t A, spamm_mat_t B, spamm_mat_t C
                       double *tr_part, int64_t pos0)
 {
     p.slA = A->slA;
-    p.slB = B->slB;  // per-leaf slices: B-role layout, or (symmetric) A-role of the transpose
+    p.slB = B->slB;  // per-leaf slices: B-role layout
+    // symmetric product: the B leaves come from the tile-major array (A == B)
+    p.tmB = ws->tsym ? B->tmapA : nullptr;
     p.slotA = A->slot;
     p.slotB = B->slot;
     p.slotC = C->slot;

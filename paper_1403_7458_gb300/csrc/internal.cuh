@@ -72,6 +72,10 @@ struct spamm_mat {
     uint8_t *slA = nullptr;           // A operand, tile-major [I][k][p][L] (R leaf rows per block)
     uint8_t *slB = nullptr;           // per-leaf [p][..] array (B operand)
     int slB_transposed = -1;          // layout of slB: 1 = B-role (transposed), 0 = A-role
+    // tensor maps (CUtensorMap, 128 B each) of slA seen from the B role of a
+    // symmetric product: map m - 1 copies m consecutive slices of one leaf
+    // (slice.cu); null when not built
+    void *tmapA = nullptr;
     uint8_t *zlead = nullptr;         // leading all-zero slices per slot
     int sl_s = 0;
     int sl_e = 0;                     // bytes per slice element
@@ -193,6 +197,9 @@ static inline int prec_elem(int prec) { return (prec == SPAMM_TF32 || prec == SP
 // (the caller guarantees |x| < 2, as SP2 does for its iterates).
 constexpr int32_t kFlagUnitScale = 1 << 30;
 int slices_alloc(spamm_mat_t m, int s, int e, bool tile_a, bool per_leaf, cudaStream_t st);
+// Tensor maps of m's tile-major array for B-role copies (built once per
+// allocation of the array; a kernel writes them, so the call can be captured).
+int slices_tmaps(spamm_mat_t m, cudaStream_t st);
 int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, int sym, int slices,
                  cudaStream_t s, bool heaviest_first = false);
 // Zero the output leaves of tiles without work (never handed out).

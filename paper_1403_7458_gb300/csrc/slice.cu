@@ -28,7 +28,10 @@
 // is 0) is recorded: slice pairs touching them contribute exactly nothing.
 //
 // Roofline: HBM-bound; per element 8 B read, 2 e s B written (both roles).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <string.h>
 
 #include <type_traits>
 
@@ -201,6 +204,8 @@ int slices_alloc(spamm_mat_t m, int s, int e, bool tile_a, bool per_leaf, cudaSt
         spamm_release(m->slA, st);
         spamm_release(m->slB, st);
         spamm_release(m->zlead, st);
+        spamm_release(m->tmapA, st);
+        m->tmapA = nullptr;
         m->slA = m->slB = nullptr;
         m->zlead = nullptr;
         m->sl_s = s;
@@ -218,6 +223,76 @@ int slices_alloc(spamm_mat_t m, int s, int e, bool tile_a, bool per_leaf, cudaSt
     if (per_leaf && !m->slB) {
         if ((rc = spamm_alloc((void **)&m->slB, per * m->nslots, st))) return rc;
     }
+    return SPAMM_OK;
+}
+
+namespace {
+
+constexpr int kMaxTmaps = 7;  // box heights 1..s, s <= 7
+struct TmapSet {
+    CUtensorMap t[kMaxTmaps];
+};
+
+__global__ void k_store_tmaps(const __grid_constant__ TmapSet src, int count, uint4 *dst)
+{
+    const uint4 *w = reinterpret_cast<const uint4 *>(&src.t[0]);
+    for (int i = threadIdx.x; i < count * (int)(sizeof(CUtensorMap) / 16); i += blockDim.x) dst[i] = w[i];
+}
+
+}  // namespace
+
+// The tile-major array as a 5-D tensor of 8-byte words: (word of a chunk of
+// at most 2 KB, chunk of a slice, leaf L of the tile, slice q, block I nb + k),
+// strides 8 B, chunk, slice, R slices, s R slices.  Map h - 1 has the box
+// {chunk, chunks, 1, h, 1}: the slices q0 .. q0 + h - 1 of one leaf, which
+// land in shared memory one after another, as the B operand wants them.
+int slices_tmaps(spamm_mat_t m, cudaStream_t st)
+{
+    if (m->tmapA) return SPAMM_OK;
+    const int S = m->sl_s, b = m->b, R = 128 / b;
+    if (!m->slA || S < 1 || S > kMaxTmaps) {
+        spamm_set_error("slices_tmaps: no tile-major slices (or %d slices) to map", S);
+        return SPAMM_E_INVAL;
+    }
+    const uint64_t slice = (uint64_t)b * b * m->sl_e, words = slice / 8;
+    const uint64_t c0 = words < 256 ? words : 256, nch = words / c0;
+    const int64_t nI = (m->nb + R - 1) / R;
+    cuuint64_t dim[5] = {(cuuint64_t)c0, (cuuint64_t)nch, (cuuint64_t)R, (cuuint64_t)S, (cuuint64_t)(nI * m->nb)};
+    cuuint64_t stride[4] = {(cuuint64_t)(c0 * 8), (cuuint64_t)slice, (cuuint64_t)(slice * R),
+                            (cuuint64_t)(slice * R * S)};
+    cuuint32_t elem[5] = {1, 1, 1, 1, 1};
+    // the driver's encoder, looked up through the runtime (the library does
+    // not link the driver library directly)
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn) {
+            spamm_set_error("cuTensorMapEncodeTiled is not available from the driver");
+            return SPAMM_E_CUDA;
+        }
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    TmapSet set;
+    memset(&set, 0, sizeof(set));
+    for (int h = 1; h <= S; h++) {
+        cuuint32_t box[5] = {(cuuint32_t)c0, (cuuint32_t)nch, 1, (cuuint32_t)h, 1};
+        const CUresult r = encode(&set.t[h - 1], CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, m->slA, dim,
+                                                  stride, box, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            spamm_set_error("cuTensorMapEncodeTiled failed (%d) for the B-role view of the slices", (int)r);
+            return SPAMM_E_CUDA;
+        }
+    }
+    void *d = nullptr;
+    if (int rc = spamm_alloc(&d, sizeof(CUtensorMap) * S, st)) return rc;
+    k_store_tmaps<<<1, 64, 0, st>>>(set, S, reinterpret_cast<uint4 *>(d));
+    SPAMM_CK_LAUNCH();
+    m->tmapA = d;
     return SPAMM_OK;
 }
 

@@ -154,6 +154,25 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
         : "memory");
 }
 
+// Tensor copy of a 5-D box (tile mode) from the tensor described by the map
+// at `map` (global memory) into shared memory, completion on the mbarrier.
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const void *map, int c0, int c1, int c2, int c3, int c4,
+                                            uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5, %6}], [%7];" ::"r"(dst),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+        : "memory");
+}
+
+// The tensor maps were written to global memory by an earlier kernel:
+// order those writes before the tensor copies that read the map.
+__device__ __forceinline__ void tmap_acquire(const void *map)
+{
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
+}
+
 // tcgen05 shared-memory descriptor of a K-major swizzled operand: start
 // address, leading offset (unused by swizzled K-major layouts: 16 B), stride
 // offset (8-row groups), version 1, swizzle mode for an atom of AW bytes
@@ -252,6 +271,8 @@ struct TcProb {
     const int32_t *cnt;    // work items per tile
     const uint32_t *list;  // work items: tile t's at [t nb, t nb + cnt[t])
     const int32_t *order;  // tile order (tile ids of this product; -1 after the tiles with work)
+    const void *tmB;       // symmetric product: tensor maps of slA for the B leaves (map h - 1:
+                           // h slices of one leaf), used instead of slB; else null
     const int32_t *sigA;   // sigma of A
     const int32_t *sigB;
     double *tr_part;       // diagonal-leaf traces (may be null; b = 32 only)
@@ -375,6 +396,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
         uint32_t issued = 0, released = 0;
         bool ok = true;
         uint32_t tq = 0, tph = 0;
+        if (lane == 0)
+            for (int mp = 0; mp < g.nprob; mp++)
+                if (g.p[mp].tmB)
+                    for (int h = 0; h < S; h++) tmap_acquire(static_cast<const uint8_t *>(g.p[mp].tmB) + 128 * h);
         for (;;) {
             // take the next tile and hand it to the MMA and epilogue warps
             int32_t tt = -1;
@@ -427,7 +452,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
 #pragma unroll
                     for (int c = 0; c < W; c++) {
                         const int64_t j = W * J + c;
-                        if (j < nb && item_mask_col<R, W>(wl, c))
+                        if (j < nb && item_mask_col<R, W>(wl, c) && !P.tmB)
                             bl[c] = P.sym ? P.slotA[j * nb + kk] : P.slotB[kk * nb + j];
                     }
                 }
@@ -480,12 +505,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                                      (uint32_t)mA * R * kSlice, fb);
                             dst += (uint32_t)mA * R * kSlice;
                             // B: slices zb..S-1-za of leaf (k, j) per present column
-                            // (symmetric: leaf (j, k))
+                            // (symmetric: leaf (j, k), from the tile-major array
+                            // when tensor maps are given)
 #pragma unroll
                             for (int c = 0; c < W; c++) {
                                 if (mc[c] <= 0) continue;
-                                bulk_g2s(dst, P.slB + bslot[c] * (int64_t)(S * kSlice) + item_zb_col(w, c) * kSlice,
-                                         (uint32_t)mc[c] * kSlice, fb);
+                                if (P.tmB) {
+                                    const int64_t j = W * J + c;
+                                    tma_load_5d(dst, static_cast<const uint8_t *>(P.tmB) + 128 * (mc[c] - 1), 0, 0,
+                                                (int)(j % R), item_zb_col(w, c), (int)((j / R) * nb + k), fb);
+                                } else {
+                                    bulk_g2s(dst,
+                                             P.slB + bslot[c] * (int64_t)(S * kSlice) + item_zb_col(w, c) * kSlice,
+                                             (uint32_t)mc[c] * kSlice, fb);
+                                }
                                 dst += (uint32_t)mc[c] * kSlice;
                             }
                             issued++;
