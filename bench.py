@@ -46,11 +46,12 @@ METRIC = "SpAMM leaf TFLOP/s over the SP2 solve (useful FLOPs of surviving produ
 UNIT = "TFLOP/s"
 L2_BYTES = 129 * 1024 * 1024
 # DRAM bytes (read + write) per launch of the tensor-core leaf-product kernel
-# of this workload (mean over the 24 launches of one solve), from an ncu
-# capture of the kernel as it stands (k_gemm_tc<7, 2, 32, 1>: one-column
-# tiles, culled leaf rows masked out of the MMAs, row-major hand-out of tiles
-# with work); set to None when the kernel changes.
-TC_TRAFFIC_BYTES_PER_LAUNCH = 490.8e6
+# of this workload (mean over launches of one solve), from an ncu capture of
+# the kernel as it stands (k_gemm_tc<7, 2, 32, 1>: one-column tiles, culled
+# leaf rows masked out of the MMAs, B leaves by tensor copies from the
+# tile-major slices, row-major hand-out of tiles with work); set to None when
+# the kernel changes.
+TC_TRAFFIC_BYTES_PER_LAUNCH = 402.0e6
 
 
 def _peaks():
