@@ -39,6 +39,11 @@
 
 namespace {
 
+// Threads of a slicing block (one leaf at a time): small blocks keep more
+// leaves in flight per SM, the kernel being bound by each leaf's chain of
+// dependent loads rather than by bandwidth.
+constexpr int kSliceThreads = 128;
+
 // max |x| over the stored leaves, as the IEEE bit pattern (monotone for
 // non-negative doubles), by integer atomicMax: exact and order-free.
 __global__ void k_absmax(const int32_t *__restrict__ stop, const double *__restrict__ leaf, int64_t count,
@@ -106,7 +111,7 @@ __device__ __forceinline__ uint32_t slice_elem(uint64_t X, bool neg, int p, int 
 // leaf rows (R = 128 / B): slices of the leaf staged in shared memory in the
 // core-matrix layout, then copied to the per-leaf and/or tile-major arrays.
 template <int S, int E, int B>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kSliceThreads)
 k_slice(const int32_t *__restrict__ stop, const double *__restrict__ leaf, const int32_t *__restrict__ slot,
         const double *__restrict__ n2, int64_t P, int64_t nb, int64_t rows,
         const unsigned long long *__restrict__ maxbits, int32_t *__restrict__ sigma_out,
@@ -116,7 +121,7 @@ k_slice(const int32_t *__restrict__ stop, const double *__restrict__ leaf, const
     using W = typename std::conditional<E == 4, uint32_t, uint16_t>::type;
     constexpr int R = 128 / B;               // leaf rows per tile
     constexpr int kU4 = B * B * E / 16;      // 16-byte chunks per slice
-    constexpr int kThreads = 256;            // the launch's block size
+    constexpr int kThreads = kSliceThreads;  // the launch's block size
     constexpr int kPerThread = B * B / kThreads;
     static_assert(B * B % kThreads == 0, "leaf elements must be a multiple of the block size");
     __shared__ __align__(16) W sa[S * B * B];
@@ -126,11 +131,13 @@ k_slice(const int32_t *__restrict__ stop, const double *__restrict__ leaf, const
     if (blockIdx.x == 0 && threadIdx.x == 0 && sigma_out) *sigma_out = sigma;
     for (int64_t pos = blockIdx.x; pos < rows * nb; pos += gridDim.x) {
         const int64_t i = pos / nb, k = pos % nb;
+        // slot and norm loads issued together (the norm does not wait for the slot)
         const int32_t sl = i < nb ? slot[i * nb + k] : -1;
+        const double nrm = i < nb ? n2[i * P + k] : 0.0;
         // a leaf of squared norm 0 (and a padding position) takes part in no
         // product: it is never in a work item's mask (A) and never a listed
         // B leaf, so its slices are never read unmasked; skip it
-        if (sl < 0 || n2[i * P + k] == 0.0) continue;  // block-uniform
+        if (sl < 0 || nrm == 0.0) continue;  // block-uniform
         if (threadIdx.x == 0) s_xmax = 0;
         __syncthreads();
         unsigned long long xmax = 0;
@@ -303,7 +310,7 @@ void slice_launch(unsigned grid, cudaStream_t st, const int32_t *stop, spamm_mat
                   unsigned long long *mx, int32_t *sig, uint8_t *ta, uint8_t *pl, int tr, uint8_t *zl,
                   int float_split)
 {
-    k_slice<S, E, B><<<grid, 256, 0, st>>>(stop, m->leaf, m->slot, m->n2 + tier_offset(m->depth), m->P, m->nb,
+    k_slice<S, E, B><<<grid, kSliceThreads, 0, st>>>(stop, m->leaf, m->slot, m->n2 + tier_offset(m->depth), m->P, m->nb,
                                            rows, mx, sig, ta, pl, tr, zl, sig + 1, float_split);
 }
 

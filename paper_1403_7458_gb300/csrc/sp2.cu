@@ -24,6 +24,7 @@
 #include <stddef.h>
 #include <string.h>
 
+#include <type_traits>
 #include <vector>
 
 #include "internal.cuh"
@@ -281,32 +282,42 @@ k_sp2_elementwise(int mode, double *__restrict__ X, const double *__restrict__ s
         }
         double idem = 0.0;
         int ek = 0;
+        // the update's kind is uniform over the launch: one loop per kind, so
+        // that no FP64 operation of another kind is issued (the FP64 pipe is
+        // this kernel's bottleneck)
+        auto pass1 = [&](auto kind) {
+            constexpr int K = decltype(kind)::value;  // 0: X0, 1: X <- X2, 2: X <- 2X - X2
 #pragma unroll 1
-        for (int c0 = 0; c0 < kPer; c0 += kCh) {
-            double yv[kCh], xv[kCh];
+            for (int c0 = 0; c0 < kPer; c0 += kCh) {
+                double yv[kCh], xv[kCh];
 #pragma unroll
-            for (int u = 0; u < kCh; u++) {
-                const int q = lane + 32 * (c0 + u);
-                yv[u] = y0 ? 0.0 : y[q];
-                xv[u] = mode == 1 ? x[q] : 0.0;
-            }
-#pragma unroll
-            for (int u = 0; u < kCh; u++) {
-                const int q = lane + 32 * (c0 + u);
-                double nv;
-                if (mode == 0) {
-                    const int r = q / B;
-                    nv = ((diag && r == q % B && I * B + r < n) ? emax : 0.0) - yv[u];
-                    nv = nv / range;
-                } else {
-                    const double d = yv[u] - xv[u];
-                    idem = fma(d, d, idem);
-                    nv = take_sq ? yv[u] : fma(2.0, xv[u], -yv[u]);
+                for (int u = 0; u < kCh; u++) {
+                    const int q = lane + 32 * (c0 + u);
+                    yv[u] = y0 ? 0.0 : y[q];
+                    xv[u] = K != 0 ? x[q] : 0.0;
                 }
-                x[q] = nv;
-                ek = max(ek, exp_key(nv));
+#pragma unroll
+                for (int u = 0; u < kCh; u++) {
+                    const int q = lane + 32 * (c0 + u);
+                    double nv;
+                    if constexpr (K == 0) {
+                        const int r = q / B;
+                        nv = ((diag && r == q % B && I * B + r < n) ? emax : 0.0) - yv[u];
+                        nv = nv / range;
+                    } else {
+                        const double d = yv[u] - xv[u];
+                        idem = fma(d, d, idem);
+                        if constexpr (K == 1) nv = yv[u];
+                        else nv = fma(2.0, xv[u], -yv[u]);
+                    }
+                    x[q] = nv;
+                    ek = max(ek, exp_key(nv));
+                }
             }
-        }
+        };
+        if (mode == 0) pass1(std::integral_constant<int, 0>());
+        else if (take_sq) pass1(std::integral_constant<int, 1>());
+        else pass1(std::integral_constant<int, 2>());
         ek = warp_max_int(ek);
         __syncwarp();
         u128 acc = 0;
