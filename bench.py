@@ -502,7 +502,7 @@ def run_batch_study(args):
                      "peak": tf32_peak, "unit": "TFLOP/s",
                      "frac": st["flops_issued"] / (stt["ms_gemm"] * 1e-3) / 1e12 / tf32_peak,
                      "peak_source": "TF32 = 1.1/2.25 x the %s sustained BF16 peak (nominal ratio)" % peak_src,
-                     "note": "issued tensor work (tiles of 128 rows, culled leaves zero-filled)"},
+                     "note": "issued tensor work (tiles of 128 rows; culled leaf rows masked out of the MMA)"},
         "max_rel_err_vs_fp64": rel,
         "generation_s": gen_s,
         "l2": "flushed between steps",
