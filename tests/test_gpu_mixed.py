@@ -158,15 +158,18 @@ def test_mixed_sp2_matches_fp64_sp2(cuda_lib, n, s):
     assert np.linalg.norm(pm @ pm - pm) < 1e-5
 
 
-def test_mixed_sp2_symmetric_mode_is_bit_identical(cuda_lib):
+@pytest.mark.parametrize("n,s,leaf", [(1000, 7, 32), (1050, 4, 32), (1050, 3, 32), (500, 7, 16)])
+def test_mixed_sp2_symmetric_mode_is_bit_identical(cuda_lib, n, s, leaf):
     """Forming only the upper block triangle of X^2 and mirroring it gives
     the same bits as forming every leaf (exact slice arithmetic on an exactly
-    symmetric iterate)."""
-    n = 1000
+    symmetric iterate).  The symmetric product reads its B leaves from the
+    tile-major slices by tensor copies, the full product from the per-leaf
+    transposed array; s <= 4 at leaf 32 runs two-column tiles (odd leaf
+    counts: the last tile has one column)."""
     h = synth.tb_hamiltonian(n, 4)
-    F = cuda_lib.tree_build(_dev(h), leaf=32)
-    Ps, rs = cuda_lib.sp2_solve(F, n / 2, 1e-8, prec=cuda_lib.OZAKI_BF16, fixed_iters=12)
-    Pf, rf = cuda_lib.sp2_solve(F, n / 2, 1e-8, prec=cuda_lib.OZAKI_BF16, fixed_iters=12,
+    F = cuda_lib.tree_build(_dev(h), leaf=leaf)
+    Ps, rs = cuda_lib.sp2_solve(F, n / 2, 1e-8, prec=cuda_lib.OZAKI_BF16, slices=s, fixed_iters=12)
+    Pf, rf = cuda_lib.sp2_solve(F, n / 2, 1e-8, prec=cuda_lib.OZAKI_BF16, slices=s, fixed_iters=12,
                                 symmetric=False)
     assert rs["symmetric"] == 1 and rf["symmetric"] == 0
     ps = cuda_lib.to_dense(Ps).cpu().numpy()
@@ -279,12 +282,14 @@ def test_tile_cull_counts_match_oracle_with_early_skip(cuda_lib, prec_name, leaf
     assert st["tasks"] == want_aa
 
 
-@pytest.mark.parametrize("prec_name,leaf", [("OZAKI_BF16", 32), ("TF32", 64), ("BF16X3", 16)])
-def test_tiles_without_work_are_zero_in_a_reused_output(cuda_lib, prec_name, leaf):
+@pytest.mark.parametrize("prec_name,leaf,n", [("OZAKI_BF16", 32, 1000), ("TF32", 64, 1000), ("BF16X3", 16, 1000),
+                                              ("TF32", 32, 1050), ("BF16X3", 32, 1000)])
+def test_tiles_without_work_are_zero_in_a_reused_output(cuda_lib, prec_name, leaf, n):
     """Tiles without work are never handed out; their output leaves are
     zeroed by a separate pass.  Reuse an output that held a dense product
-    and check that a sparse product overwrites every leaf."""
-    n = 1000
+    and check that a sparse product overwrites every leaf (two-column tiles
+    at leaf 32 for the float splits; n = 1050: an odd number of leaf
+    columns)."""
     h = synth.tb_hamiltonian(n, 8, decay=1.0)
     A = cuda_lib.tree_build(_dev(h), leaf=leaf)
     prec = getattr(cuda_lib, prec_name)
