@@ -260,6 +260,19 @@ __device__ __forceinline__ double i64_scaled(long long v, int k)
     return sign ? -r : r;
 }
 
+// The same value, RN(v * 2^k), from the hardware conversion: RN(v) (ties to
+// even) scaled by 2^k through the exponent field, exact while the result is
+// normal; the integer routine handles subnormal and overflowing results.
+__device__ __forceinline__ double i64_scaled_fast(long long v, int k)
+{
+    if (v == 0) return 0.0;
+    const double f = __ll2double_rn(v);
+    const uint64_t u = (uint64_t)__double_as_longlong(f);
+    const int e = (int)((u >> 52) & 0x7FF) + k;
+    if (e >= 1 && e <= 2046) return __longlong_as_double((long long)(u + ((uint64_t)(int64_t)k << 52)));
+    return i64_scaled(v, k);
+}
+
 // One product of a launch.
 struct TcProb {
     const uint8_t *slA;    // A operand: tile-major [I][k][p][L][slice]
@@ -738,7 +751,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
 #pragma unroll
                             for (int d = 0; d < S; d++)
                                 a += (long long)__float2ll_rn(__uint_as_float(v[d][q])) * (1ll << (7 * (S - 1 - d)));
-                            res[q] = i64_scaled(a, kexp);
+                            res[q] = i64_scaled_fast(a, kexp);
                         }
                     }
                     if (store) {
