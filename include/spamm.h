@@ -269,9 +269,10 @@ void spamm_free(spamm_mat_t M);
 
 /*
  * Free the scratch a handle keeps for later products: its tensor-core slices
- * (the largest buffers of the mixed path: 2 e s bytes per stored element
- * for s slices of e-byte elements, in two layouts) and the task lists of the
- * product it was the output of.  The matrix, its norms and its shape are
+ * (the largest buffers of the mixed path: e s bytes per stored element and
+ * layout for s slices of e-byte elements; one layout when the handle was only
+ * used in symmetric products, such as the SP2 iterate, two otherwise) and the
+ * task lists of the product it was the output of.  The matrix, its norms and its shape are
  * untouched; the next product that needs the scratch allocates it again.
  * Stream-ordered on `stream`.  No-op for NULL.
  */
