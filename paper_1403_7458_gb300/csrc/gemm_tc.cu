@@ -376,6 +376,10 @@ int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, i
 {
     const int R = 128 / A->b, W = tc::tile_width(A->b, slices);
     const int64_t nb = A->nb, P = A->P, nI = (nb + R - 1) / R, nbt = (nb + W - 1) / W, T = nI * nbt;
+    if (W == 2 && R != 4) {  // tile_item2 builds the masks of 4-row tiles
+        spamm_set_error("tensor-core path: two-column tiles need leaf 32 (got %d)", A->b);
+        return SPAMM_E_NOTSUP;
+    }
     if (T >= (int64_t(1) << 24)) {
         spamm_set_error("tensor-core path: %lld tiles exceed 2^24", (long long)T);
         return SPAMM_E_NOTSUP;
