@@ -72,3 +72,39 @@ def test_binding_structs_match_the_header(tmp_path):
         assert int(got["%s size" % cname]) == ctypes.sizeof(cls), cname
         for f, _ in cls._fields_:
             assert int(got["%s.%s" % (cname, f)]) == getattr(cls, f).offset, (cname, f)
+
+
+def test_binding_constants_match_the_header(tmp_path):
+    """Status codes, precision modes, flags, SP2 rules, stop reasons and
+    history columns of the binding equal the values include/spamm.h defines
+    (printed by a program compiled here with the host C compiler)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no host C compiler")
+    from paper_1403_7458_gb300 import spamm
+    pairs = {
+        "SPAMM_OK": spamm.OK, "SPAMM_E_INVAL": spamm.E_INVAL, "SPAMM_E_NOMEM": spamm.E_NOMEM,
+        "SPAMM_E_CUDA": spamm.E_CUDA, "SPAMM_E_CAPACITY": spamm.E_CAPACITY, "SPAMM_E_TIMEOUT": spamm.E_TIMEOUT,
+        "SPAMM_E_NOCONV": spamm.E_NOCONV, "SPAMM_E_NOTSUP": spamm.E_NOTSUP,
+        "SPAMM_FP64": spamm.FP64, "SPAMM_OZAKI_BF16": spamm.OZAKI_BF16, "SPAMM_BF16": spamm.BF16,
+        "SPAMM_BF16X3": spamm.BF16X3, "SPAMM_TF32": spamm.TF32, "SPAMM_TF32X3": spamm.TF32X3,
+        "SPAMM_F_TIMING": spamm.F_TIMING, "SPAMM_F_NOSYM": spamm.F_NOSYM, "SPAMM_F_HEAVIEST": spamm.F_HEAVIEST,
+        "SPAMM_F_NOGRAPH": spamm.F_NOGRAPH, "SPAMM_TUNE_MAX": spamm.TUNE_MAX,
+        "SP2_RULE_TRACE_DISTANCE": spamm.RULE_TRACE_DISTANCE, "SP2_RULE_TRACE_ABOVE": spamm.RULE_TRACE_ABOVE,
+        "SP2_STOP_CONVERGED": spamm.STOP_CONVERGED, "SP2_STOP_STAGNATED": spamm.STOP_STAGNATED,
+        "SP2_STOP_FIXED": spamm.STOP_FIXED, "SP2_STOP_MAXITER": spamm.STOP_MAXITER,
+        "SP2_H_FILL": spamm.H_FILL, "SP2_H_COLS": spamm.H_COLS,
+    }
+    lines = ["#include <stdio.h>", '#include "spamm.h"', "int main(void) {"]
+    for cname in pairs:
+        lines.append('printf("%s %%d\\n", (int)(%s));' % (cname, cname))
+    lines += ["return 0; }"]
+    src = tmp_path / "consts.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "consts"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {k: int(v) for k, v in (line.split() for line in out if line)}
+    for cname, value in pairs.items():
+        assert got[cname] == value, (cname, got[cname], value)
