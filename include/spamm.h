@@ -18,6 +18,8 @@
  *     wait for it.
  *   - Handles (spamm_mat_t) own their device memory, are created by the
  *     library and released with spamm_free().  Inputs are never modified.
+ *     Device memory is drawn from the library's own stream-ordered pool,
+ *     which keeps freed memory cached until spamm_trim().
  *   - Matrices are cut into b x b leaves (b = 16, 32 or 64).  The leaf grid
  *     is nb x nb, nb = ceil(n / b); the norm quadtree has depth d with
  *     2^d >= nb, tier 0 the root, tier d the leaves.  Padding up to 2^d is
@@ -277,6 +279,18 @@ void spamm_free(spamm_mat_t M);
  * Stream-ordered on `stream`.  No-op for NULL.
  */
 void spamm_release_scratch(spamm_mat_t M, void *stream);
+
+/*
+ * Return the device memory the library keeps cached to the driver.  Device
+ * memory comes from a pool owned by the library (one per device, created on
+ * first use) that keeps freed memory for the library's later allocations:
+ * repeated products and SP2 solves then reuse it instead of mapping it anew.
+ * This call waits for the current device (cudaDeviceSynchronize), then
+ * releases every byte of that pool that no live handle uses; the next
+ * allocation maps memory again.  Blocking.  Errors: E_CUDA.  The paper has
+ * no counterpart.
+ */
+int spamm_trim(void);
 
 /*
  * Self-test of the device watchdog that bounds every wait inside the

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "scan.cuh"
 
 // ---------------------------------------------------------------------------
 // Errors
@@ -55,17 +56,63 @@ int64_t spamm_launch_count() { return g_launches; }
 // ---------------------------------------------------------------------------
 // Memory (stream-ordered allocator)
 // ---------------------------------------------------------------------------
+// The library's own stream-ordered pool on each device, created on first
+// use.  It keeps freed memory for the library's next allocations instead of
+// returning it to the driver at every synchronisation (mapping tens of GB
+// anew for every SP2 solve costs tens of milliseconds); spamm_trim() hands
+// the unused part back.
+static cudaMemPool_t g_pools[64] = {};
+static std::mutex g_pool_mu;
+
+static cudaError_t pool_of_current(cudaMemPool_t *pool)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> l(g_pool_mu);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        if ((e = cudaMemPoolCreate(&p, &props)) != cudaSuccess) return e;
+        uint64_t keep = ~uint64_t(0);
+        if ((e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) {
+            cudaMemPoolDestroy(p);
+            return e;
+        }
+        g_pools[dev] = p;
+    }
+    *pool = g_pools[dev];
+    return cudaSuccess;
+}
+
 int spamm_alloc(void **p, size_t bytes, cudaStream_t s)
 {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMallocAsync(p, bytes, s);
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = pool_of_current(&pool);
+    if (e == cudaSuccess) e = cudaMallocFromPoolAsync(p, bytes, pool, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
-        spamm_set_error("cudaMallocAsync(%zu bytes): %s", bytes, cudaGetErrorString(e));
+        spamm_set_error("cudaMallocFromPoolAsync(%zu bytes): %s", bytes, cudaGetErrorString(e));
         return SPAMM_E_NOMEM;
     }
+    return SPAMM_OK;
+}
+
+extern "C" int spamm_trim(void)
+{
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = pool_of_current(&pool);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemPoolTrimTo(pool, 0);
+    if (e != cudaSuccess) return spamm_cuda_fail(e, "spamm_trim", __FILE__, __LINE__);
     return SPAMM_OK;
 }
 
@@ -194,6 +241,7 @@ static void ws_free(SpammWorkspace *ws, cudaStream_t s)
     spamm_release(ws->klist, s);
     spamm_release(ws->counter, s);
     spamm_release(ws->tr_part, s);
+    spamm_release(ws->scan_part, s);
     *ws = SpammWorkspace();
 }
 
@@ -476,6 +524,18 @@ int ws_reserve_groups(SpammWorkspace *ws, int64_t groups, int64_t nb, cudaStream
         if ((rc = spamm_alloc((void **)&ws->tr_part, sizeof(double) * nb, s))) return rc;
         ws->tr_cap = nb;
     }
+    return SPAMM_OK;
+}
+
+int ws_reserve_scan(SpammWorkspace *ws, int64_t G, cudaStream_t s)
+{
+    const int64_t words = scan::part_words(G);
+    if (ws->scan_cap >= words) return SPAMM_OK;
+    spamm_release(ws->scan_part, s);
+    ws->scan_part = nullptr;
+    ws->scan_cap = 0;
+    if (int rc = spamm_alloc((void **)&ws->scan_part, sizeof(int64_t) * words, s)) return rc;
+    ws->scan_cap = words;
     return SPAMM_OK;
 }
 

@@ -15,11 +15,13 @@
 //           column of j (Algorithm 1's early occlusion: a parent's squared
 //           norm is never below a child's, so no leaf triple under a failing
 //           parent pair can pass);
-//   scan  : exclusive prefix sum of the counts (one block);
+//   scan  : exclusive prefix sum of the counts (three launches over many
+//           blocks, scan.cuh);
 //   emit  : the warps re-test and write each passing k at its ballot rank.
 // Roofline: ALU/latency bound on the candidate tests; HBM/L2 traffic is the
 // two leaf-norm rows per group (16 nb bytes) plus 4 bytes per task written.
 #include "internal.cuh"
+#include "scan.cuh"
 
 namespace {
 
@@ -59,36 +61,6 @@ k_cull_count(const int32_t *__restrict__ stop, const double *__restrict__ n2A,
         cnt += __popc(__ballot_sync(0xffffffffu, p));
     }
     if (lane == 0) counts[g] = cnt;
-}
-
-constexpr int kScanThreads = 1024;
-
-__global__ void __launch_bounds__(kScanThreads)
-k_scan(const int32_t *__restrict__ stop, const int32_t *__restrict__ counts, int64_t G,
-       int64_t *__restrict__ off)
-{
-    if (stop && *stop) return;  // the SP2 loop has already stopped
-    __shared__ int64_t part[kScanThreads];
-    int t = threadIdx.x;
-    int64_t chunk = (G + kScanThreads - 1) / kScanThreads;
-    int64_t lo = t * chunk, hi = lo + chunk < G ? lo + chunk : G;
-    int64_t s = 0;
-    for (int64_t q = lo; q < hi; q++) s += counts[q];
-    part[t] = s;
-    __syncthreads();
-    // Hillis-Steele inclusive scan over the 1024 partial sums
-    for (int o = 1; o < kScanThreads; o <<= 1) {
-        int64_t v = t >= o ? part[t - o] : 0;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
-    }
-    int64_t run = part[t] - s;
-    for (int64_t q = lo; q < hi; q++) {
-        off[q] = run;
-        run += counts[q];
-    }
-    if (t == kScanThreads - 1) off[G] = part[t];
 }
 
 __global__ void __launch_bounds__(kWarps * 32)
@@ -149,8 +121,19 @@ int spamm_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, int
     k_cull_count<<<blocks, kWarps * 32, 0, s>>>(ws->stop, A->n2 + tier_offset(A->depth), B->n2T, nb, P, tau2, co,
                                                 ws->counts);
     SPAMM_CK_LAUNCH();
-    k_scan<<<1, kScanThreads, 0, s>>>(ws->stop, ws->counts, G, ws->off);
-    SPAMM_CK_LAUNCH();
+    if (int rc = ws_reserve_scan(ws, G, s)) return rc;
+    {
+        const int64_t nch = (G + scan::kChunk - 1) / scan::kChunk > 0 ? (G + scan::kChunk - 1) / scan::kChunk : 1;
+        scan::k_sums<false><<<(unsigned)nch, scan::kThreads, 0, s>>>(ws->stop, ws->counts, nullptr, nullptr, nullptr,
+                                                                      G, ws->scan_part);
+        SPAMM_CK_LAUNCH();
+        scan::k_top<false><<<1, scan::kTopThreads, 0, s>>>(ws->stop, ws->scan_part, nch, ws->off + G, nullptr,
+                                                           nullptr, nullptr);
+        SPAMM_CK_LAUNCH();
+        scan::k_apply<false><<<(unsigned)nch, scan::kThreads, 0, s>>>(ws->stop, ws->counts, G, ws->scan_part,
+                                                                       ws->off, nullptr, nullptr);
+        SPAMM_CK_LAUNCH();
+    }
     int64_t worst = G * nb;
     int64_t total = -1;
     if (need_total || (!worst_case && ws->klist_cap < worst && worst * 4 > kEagerListBytes)) {

@@ -3,6 +3,7 @@
 // kernel in tc_kernel.cuh (single products and batches); instantiates the
 // kernel for leaf 32.
 #include "tc_kernel.cuh"
+#include "scan.cuh"
 
 namespace {
 
@@ -176,74 +177,6 @@ k_tile_count(CullArgs c, int32_t *__restrict__ counts, int32_t *__restrict__ tas
         tasks[t] = ntask;
         pairs[t] = active ? npair : 0;
         useful[t] = active ? nuse : 0;
-    }
-}
-
-constexpr int kScanThreads = 1024;
-
-// exclusive scan of counts -> off (one block), the rank of every tile among
-// the tiles with work -> nz (and, when order is given, the row-major order
-// of those tiles), plus the totals of tasks / pairs / useful pairs
-__global__ void __launch_bounds__(kScanThreads)
-k_tile_scan(const int32_t *__restrict__ stop, const int32_t *__restrict__ counts, const int32_t *__restrict__ tasks,
-            const int32_t *__restrict__ pairs, const int32_t *__restrict__ useful, int64_t G,
-            int64_t *__restrict__ off, int32_t *__restrict__ nz, int32_t *__restrict__ order,
-            int64_t *__restrict__ task_total, int64_t *__restrict__ pair_total, int64_t *__restrict__ useful_total)
-{
-    __shared__ int64_t part[kScanThreads];
-    __shared__ int32_t zpart[kScanThreads];
-    __shared__ int64_t tpart[kScanThreads];
-    __shared__ int64_t ppart[kScanThreads];
-    __shared__ int64_t upart[kScanThreads];
-    if (stop && *stop) return;  // the SP2 loop has already stopped
-    const int t = threadIdx.x;
-    const int64_t chunk = (G + kScanThreads - 1) / kScanThreads;
-    const int64_t lo = t * chunk, hi = lo + chunk < G ? lo + chunk : G;
-    int64_t s = 0, ts = 0, ps = 0, us = 0;
-    int32_t zs = 0;
-    for (int64_t q = lo; q < hi; q++) {
-        s += counts[q];
-        zs += counts[q] > 0;
-        ts += tasks[q];
-        ps += pairs[q];
-        us += useful[q];
-    }
-    part[t] = s;
-    zpart[t] = zs;
-    tpart[t] = ts;
-    ppart[t] = ps;
-    upart[t] = us;
-    __syncthreads();
-    for (int o = 1; o < kScanThreads; o <<= 1) {
-        const int64_t v = t >= o ? part[t - o] : 0;
-        const int32_t z = t >= o ? zpart[t - o] : 0;
-        __syncthreads();
-        part[t] += v;
-        zpart[t] += z;
-        __syncthreads();
-    }
-    for (int o = kScanThreads / 2; o > 0; o >>= 1) {
-        if (t < o) {
-            tpart[t] += tpart[t + o];
-            ppart[t] += ppart[t + o];
-            upart[t] += upart[t + o];
-        }
-        __syncthreads();
-    }
-    int64_t run = part[t] - s;
-    int32_t zrun = zpart[t] - zs;
-    for (int64_t q = lo; q < hi; q++) {
-        off[q] = run;
-        nz[q] = zrun;
-        if (order && counts[q] > 0) order[zrun] = (int32_t)q;  // row-major hand-out order
-        run += counts[q];
-        zrun += counts[q] > 0;
-    }
-    if (t == kScanThreads - 1) off[G] = part[t];
-    if (t == 0) {
-        *task_total = tpart[0];
-        *pair_total = ppart[0];
-        *useful_total = upart[0];
     }
 }
 
@@ -461,10 +394,21 @@ int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, i
         }
     }
     SPAMM_CK(cudaMemsetAsync(ws->torder, 0xFF, sizeof(int32_t) * ws->tactive, s));  // -1: no tile
-    k_tile_scan<<<1, kScanThreads, 0, s>>>(ws->stop, ws->tcounts, ws->ttasks, ws->tpairs, ws->tuseful, T,
-                                           ws->toff, ws->tnz, heaviest_first ? nullptr : ws->torder,
-                                           ws->toff + T + 1, ws->toff + T + 2, ws->toff + T + 3);
-    SPAMM_CK_LAUNCH();
+    // offsets, ranks among the tiles with work and the row-major order of
+    // those; totals at toff[T .. T+3]
+    if ((rc = ws_reserve_scan(ws, T, s))) return rc;
+    {
+        const int64_t nch = (T + scan::kChunk - 1) / scan::kChunk;
+        scan::k_sums<true><<<(unsigned)nch, scan::kThreads, 0, s>>>(ws->stop, ws->tcounts, ws->ttasks, ws->tpairs,
+                                                                     ws->tuseful, T, ws->scan_part);
+        SPAMM_CK_LAUNCH();
+        scan::k_top<true><<<1, scan::kTopThreads, 0, s>>>(ws->stop, ws->scan_part, nch, ws->toff + T,
+                                                          ws->toff + T + 1, ws->toff + T + 2, ws->toff + T + 3);
+        SPAMM_CK_LAUNCH();
+        scan::k_apply<true><<<(unsigned)nch, scan::kThreads, 0, s>>>(ws->stop, ws->tcounts, T, ws->scan_part, ws->toff,
+                                                                      ws->tnz, heaviest_first ? nullptr : ws->torder);
+        SPAMM_CK_LAUNCH();
+    }
     if (heaviest_first) {
         SPAMM_CK(cudaMemsetAsync(ws->tbins, 0, sizeof(int32_t) * (nb + 1), s));
         k_tile_hist<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(ws->stop, ws->tcounts, nb, T, sym, R, ws->tbins);

@@ -52,6 +52,8 @@ struct SpammWorkspace {
     int tsym = 0;                         // last tile cull was symmetric
     int tw = 1;                           // output leaf columns per tile of the last tile cull
     int64_t tT = 0;                       // tiles of the last tile cull (totals at toff + tT)
+    int64_t *scan_part = nullptr;         // chunk partials of the multi-block scans (scan.cuh)
+    int64_t scan_cap = 0;                 // int64 words
 };
 
 struct spamm_mat {
@@ -149,6 +151,8 @@ int spamm_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws,
                int64_t nb, int64_t P, cudaStream_t s, bool need_total, int64_t *total_host,
                bool worst_case = false);
 int ws_reserve_groups(SpammWorkspace *ws, int64_t groups, int64_t nb, cudaStream_t s);
+// Room for the chunk partials of a scan over G entries in ws->scan_part.
+int ws_reserve_scan(SpammWorkspace *ws, int64_t G, cudaStream_t s);
 // The FP64 cull of an nb x nb leaf grid reserves its worst-case list (and so
 // never waits for the stream once reserved).
 bool spamm_cull_never_waits(int64_t nb);

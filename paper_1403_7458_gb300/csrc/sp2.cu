@@ -3,7 +3,9 @@
 //
 // Per solve:
 //   gershgorin : one thread per matrix row sums |f_ij| (j != i) in column
-//                order; a one-block kernel takes min / max of f_ii -/+ sum;
+//                order (chunked vector loads, the next chunk in flight while
+//                the current one is summed); a one-block kernel takes
+//                min / max of f_ii -/+ sum;
 //   x0         : X0 = (emax I - F) / (emax - emin), fused with X0's leaf norms
 //                and its trace.
 // Per iteration (all on the device; the host enqueues iterations in batches
@@ -60,25 +62,62 @@ constexpr int kEwBlocksPerSm = 3;  // and resident blocks per SM (register cap 8
 constexpr int kRedThreads = 1024;
 constexpr int kBatch = 4;  // SP2 iterations enqueued between reads of the state
 
-__global__ void k_gershgorin_rows(const double *__restrict__ leaf, const int32_t *__restrict__ slot,
-                                  int64_t n, int b, int64_t nb, double *__restrict__ lo,
-                                  double *__restrict__ hi)
+// Row sums of |f_ij| (j != i) in column order, one thread per matrix row
+// (the same order as the plain sequential sum, so the bounds are bit-equal
+// to it).  The row's segment of each stored leaf is read in chunks of up to
+// 32 values with vector loads, and the next chunk's loads are issued before
+// the current chunk is summed, so that many loads are in flight per thread
+// (the kernel streams every stored leaf of F once: HBM-bound).  Absent
+// leaves are zero and skipped (adding +0 leaves the sum unchanged).
+template <int B>
+__global__ void __launch_bounds__(128)
+k_gershgorin_rows(const double *__restrict__ leaf, const int32_t *__restrict__ slot, int64_t n, int64_t nb,
+                  double *__restrict__ lo, double *__restrict__ hi)
 {
-    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr int CH = B < 32 ? B : 32;  // values per chunk
+    constexpr int NCH = B / CH;          // chunks per leaf row segment
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
-    int64_t I = r / b, rr = r % b;
+    const int64_t I = r / B;
+    const int rr = (int)(r % B);
+    const int32_t *srow = slot + I * nb;
+    auto next_stored = [&](int64_t K) {
+        while (K < nb && __ldg(srow + K) < 0) K++;
+        return K;
+    };
+    auto load = [&](int64_t K, int h, double2 (&v)[CH / 2]) {
+        const double2 *p =
+            reinterpret_cast<const double2 *>(leaf + (int64_t)__ldg(srow + K) * (B * B) + rr * B + h * CH);
+#pragma unroll
+        for (int u = 0; u < CH / 2; u++) v[u] = __ldg(p + u);
+    };
     double s = 0.0, d = 0.0;
-    for (int64_t K = 0; K < nb; K++) {
-        int32_t sl = slot[I * nb + K];
-        if (sl < 0) continue;
-        const double *row = leaf + (int64_t)sl * b * b + rr * b;
-        for (int c = 0; c < b; c++) {
-            int64_t col = K * b + c;
-            if (col >= n) break;
-            double v = row[c];
-            if (col == r) d = v;
-            else s += fabs(v);
+    int64_t K = next_stored(0);
+    int h = 0;
+    double2 cur[CH / 2], nxt[CH / 2];
+    if (K < nb) load(K, 0, cur);
+    while (K < nb) {
+        int64_t K2 = K;
+        int h2 = h + 1;
+        if (h2 == NCH) {
+            h2 = 0;
+            K2 = next_stored(K + 1);
         }
+        if (K2 < nb) load(K2, h2, nxt);
+        const int64_t c0 = K * B + h * CH;
+#pragma unroll
+        for (int u = 0; u < CH; u++) {
+            const int64_t col = c0 + u;
+            const double v = (u & 1) ? cur[u >> 1].y : cur[u >> 1].x;
+            if (col < n) {
+                if (col == r) d = v;
+                else s += fabs(v);
+            }
+        }
+        K = K2;
+        h = h2;
+#pragma unroll
+        for (int u = 0; u < CH / 2; u++) cur[u] = nxt[u];
     }
     lo[r] = d - s;
     hi[r] = d + s;
@@ -280,6 +319,18 @@ k_sp2_elementwise(int mode, double *__restrict__ X, const double *__restrict__ s
             if (lane == 0 && diag) diag_part[I] = 0.0;
             continue;
         }
+        // X0 of an off-diagonal leaf that F does not store: (0 - 0) / range
+        // = +0 in every element; written without the divisions
+        if (mode == 0 && y0 && !diag) {  // warp-uniform
+            const double2 z = make_double2(0.0, 0.0);
+#pragma unroll 4
+            for (int q = lane; q < BB / 2; q += 32) reinterpret_cast<double2 *>(x)[q] = z;
+            if (lane == 0) {
+                n2[I * P + K] = 0.0;
+                n2T[K * P + I] = 0.0;
+            }
+            continue;
+        }
         double idem = 0.0;
         int ek = 0;
         // the update's kind is uniform over the launch: one loop per kind, so
@@ -301,9 +352,12 @@ k_sp2_elementwise(int mode, double *__restrict__ X, const double *__restrict__ s
                     const int q = lane + 32 * (c0 + u);
                     double nv;
                     if constexpr (K == 0) {
+                        // (emax [i == j] - f_ij) / range; an off-diagonal zero
+                        // gives +0 (no division), a nonzero -f_ij / range
+                        // (0 - f equals -f exactly for f != 0)
                         const int r = q / B;
-                        nv = ((diag && r == q % B && I * B + r < n) ? emax : 0.0) - yv[u];
-                        nv = nv / range;
+                        if (diag && r == q % B && I * B + r < n) nv = (emax - yv[u]) / range;
+                        else nv = yv[u] == 0.0 ? 0.0 : -yv[u] / range;
                     } else {
                         const double d = yv[u] - xv[u];
                         idem = fma(d, d, idem);
@@ -584,8 +638,12 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
         SP2_CUDA(cudaStreamSynchronize(s));
         sym = asym == 0;
     }
-    k_gershgorin_rows<<<(unsigned)((F->n + 255) / 256), 256, 0, s>>>(F->leaf, F->slot, F->n, F->b,
-                                                                      nb, sc.lo, sc.hi);
+    {
+        const unsigned gb = (unsigned)((F->n + 127) / 128);
+        if (F->b == 16) k_gershgorin_rows<16><<<gb, 128, 0, s>>>(F->leaf, F->slot, F->n, nb, sc.lo, sc.hi);
+        else if (F->b == 32) k_gershgorin_rows<32><<<gb, 128, 0, s>>>(F->leaf, F->slot, F->n, nb, sc.lo, sc.hi);
+        else k_gershgorin_rows<64><<<gb, 128, 0, s>>>(F->leaf, F->slot, F->n, nb, sc.lo, sc.hi);
+    }
     SP2_LAUNCHED();
     k_gershgorin_bounds<<<1, kRedThreads, 0, s>>>(sc.lo, sc.hi, F->n, sc.st);
     SP2_LAUNCHED();

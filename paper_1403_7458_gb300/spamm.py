@@ -106,6 +106,7 @@ def load():
     lib.spamm_task_list.argtypes = [P, P, dbl, P, P, i64, ctypes.POINTER(i64), P]
     lib.spamm_cull_noalloc.argtypes = [P, i64, P, i64, i64, dbl, P, P, i64, P]
     lib.spamm_watchdog_selftest.argtypes = [i32, P]
+    lib.spamm_trim.argtypes = []
     lib.spamm_free.argtypes = [P]
     lib.spamm_free.restype = None
     lib.spamm_release_scratch.argtypes = [P, P]
@@ -118,7 +119,8 @@ def load():
                               ctypes.POINTER(_Sp2Report), P]
     for name in ("spamm_tree_build", "spamm_multiply", "spamm_multiply_batched", "spamm_autotune_batched",
                  "spamm_to_dense", "spamm_norms",
-                 "spamm_info", "spamm_task_list", "sp2_solve", "spamm_cull_noalloc", "spamm_watchdog_selftest"):
+                 "spamm_info", "spamm_task_list", "sp2_solve", "spamm_cull_noalloc", "spamm_watchdog_selftest",
+                 "spamm_trim"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -291,6 +293,12 @@ def watchdog_selftest(ms: int = 100, stream=None) -> int:
 def release_scratch(M: Matrix, stream=None):
     """Free the slices and task lists a handle keeps for later products."""
     load().spamm_release_scratch(M.handle, _stream(stream))
+
+
+def trim():
+    """Hand the device memory the library keeps cached back to the driver
+    (waits for the device)."""
+    _check(load().spamm_trim(), "spamm_trim")
 
 
 def to_dense(M: Matrix, out=None, stream=None):
