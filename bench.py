@@ -1,33 +1,39 @@
 #!/usr/bin/env python3
 """Benchmark: SP2 spectral projection driven by SpAMM on one GB300.
 
-Workload: the N = 4096 tight-binding Hamiltonian on Morton-ordered 3-D
-three-site clusters (h_ij = -exp(-r_ij / 1.2 A), cut at 1e-12, on-site -/+2
-by site parity), Ne = N/2, Gershgorin start, tau = 1e-8, leaf 32.  One step
-is one complete SP2 solve: norm quadtree, culling, leaf products and the
-fused SP2 update for every iteration until the stopping rule fires.
+Workload (the large single SP2): the N = 65536 tight-binding Hamiltonian on
+Morton-ordered 3-D three-site clusters, h_ij = -exp(-r_ij / 1.0 A) cut at
+1e-12, on-site -/+2 by site parity, Ne = N/2, Gershgorin start, tau = 1e-8,
+leaf 32.  F is stored sparsely (leaves with ||leaf||_F <= 1e-12 are not
+stored); the iterates use the dense leaf grid.  One step is one complete
+SP2 solve: norm quadtree, culling, leaf products and the fused SP2 update
+for every iteration until the stopping rule fires.
 
-Printed metric: useful SpAMM leaf throughput over the whole solve, i.e.
+Printed metric: SP2 solve time and SpAMM leaf throughput, mixed precision vs
+plain FP64.  `value` is the useful SpAMM leaf throughput of the mixed solve,
 2 b^3 x (surviving leaf triples summed over iterations) / solve time, in
-TFLOP/s; `ms_per_step` is the SP2 solve time.  The timed steps use the
+TFLOP/s; `ms_per_step` is the mixed SP2 solve time.  The timed steps use the
 mixed-precision leaf products (exact BF16 slices on the tensor cores, FP64
 norms, traces and updates); the same workload is then solved with FP64 leaf
 products, and the line reports that solve time, the speedup and
 ||P_mixed - P_FP64||_F.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec ozaki|fp64] [--slices S]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec ozaki|fp64] [--slices S] [--bench-n N]
   python bench.py --impl reference ...   (the FP64 CPU oracle, bounded sample)
   python bench.py --study precision [--n 16384] [--taus ...]   (modes vs FP64 SP2)
   python bench.py --study batch [--batch 64] [--batch-prec tf32] (many SpAMMs, one launch)
   python bench.py --study large [--n-large 65536]   (one large SP2, mixed vs FP64)
   python bench.py --study spamm [--spamm-n 1024]     (single products, time per product)
 
-N > 1 runs independent replicas (one solve per GPU, launched with torchrun);
-value = all ranks' useful FLOPs / the slowest rank's time.
+N > 1 runs independent replicas (one solve per GPU); without torchrun in
+the environment, `--gpus N` starts the N ranks itself through
+torch.distributed.run.  value = all ranks' useful FLOPs / the slowest
+rank's time.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -39,19 +45,34 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = {"workload": "sp2_tb_hamiltonian", "n": 4096, "leaf": 32, "tau": 1e-8,
-            "ne": 2048, "decay_A": 1.2, "onsite": 2.0, "start": "gershgorin",
-            "stop": "trace+idempotency or stagnation"}
-METRIC = "SpAMM leaf TFLOP/s over the SP2 solve (useful FLOPs of surviving products)"
+WORKLOAD = {"workload": "sp2_tb_hamiltonian_large", "n": 65536, "leaf": 32, "tau": 1e-8,
+            "ne": 32768, "decay_A": 1.0, "onsite": 2.0, "cut": 1e-12, "drop": 1e-12,
+            "storage": "F: sparse leaves (||leaf||_F > 1e-12 stored); X, X^2: dense leaf grid",
+            "start": "gershgorin", "stop": "trace+idempotency or stagnation"}
+METRIC = "SP2 solve time & SpAMM leaf TFLOP/s, mixed vs FP64 plain, at ||ΔP||_F≤1e-6"
 UNIT = "TFLOP/s"
 L2_BYTES = 129 * 1024 * 1024
+# Principal block of the Hamiltonian that the CPU oracle solves as its
+# bounded sample (one SP2 iteration): all cores / one core / reference arm.
+CPU_SAMPLE_N = 16384
+CPU_SAMPLE_N_ONE_CORE = 4096
+REF_SAMPLE_N = 8192
 # DRAM bytes (read + write) per launch of the tensor-core leaf-product kernel
-# of this workload (mean over launches of one solve), from an ncu capture of
-# the kernel as it stands (k_gemm_tc<7, 2, 32, 1>: one-column tiles, culled
-# leaf rows masked out of the MMAs, B leaves by tensor copies from the
-# tile-major slices, row-major hand-out of tiles with work); set to None when
-# the kernel changes.
-TC_TRAFFIC_BYTES_PER_LAUNCH = 394.1e6
+# on this workload (mean over the launches of one solve) from an ncu capture,
+# with the SHA-256 prefix of the kernel source it was taken on: the figure is
+# reported only while tc_kernel.cuh is unchanged.
+TC_TRAFFIC = {"source_sha256_16": None, "bytes_per_launch": None}
+
+
+def _tc_traffic():
+    src = os.path.join(ROOT, "paper_1403_7458_gb300", "csrc", "tc_kernel.cuh")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    if TC_TRAFFIC["source_sha256_16"] == sha:
+        return TC_TRAFFIC["bytes_per_launch"]
+    return None
 
 
 def _peaks():
@@ -170,7 +191,6 @@ def _barrier(world):
 
 
 def run_ours(args):
-    import numpy as np
     import torch
     from paper_1403_7458_gb300 import spamm, synth
 
@@ -183,11 +203,21 @@ def run_ours(args):
     spamm.load()
     prec = spamm.OZAKI_BF16 if args.prec == "ozaki" else spamm.FP64
     slices = args.slices if prec == spamm.OZAKI_BF16 else 0
-    n, b, tau, ne = WORKLOAD["n"], WORKLOAD["leaf"], WORKLOAD["tau"], WORKLOAD["ne"]
-    h = synth.tb_hamiltonian(n, seed=rank)
-    hd = torch.from_numpy(h).to(dev)
+    n, b, tau = args.bench_n, WORKLOAD["leaf"], WORKLOAD["tau"]
+    ne = n // 2
+    decay, drop = WORKLOAD["decay_A"], WORKLOAD["drop"]
+    gib = lambda x: x / 2.0 ** 30
+    t_gen = time.perf_counter()
+    h = synth.tb_hamiltonian_torch(n, seed=rank, decay=decay)   # built on the device
+    F = spamm.tree_build(h, leaf=b, drop=drop)                  # sparse leaf storage
+    torch.cuda.synchronize()
+    # host copy of F for the end-to-end leg (pinned: its H2D is timed there)
+    h_pin = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+    h_pin.copy_(h)
+    del h
+    torch.cuda.empty_cache()
+    gen_s = time.perf_counter() - t_gen
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
-    F = spamm.tree_build(hd, leaf=b)
     P = None
 
     def solve(timing=False, p=prec, sl=slices, out=None):
@@ -200,7 +230,7 @@ def run_ours(args):
     # ---- device-timed region: inputs resident in HBM ----
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    flops = tflops = gemm_ms = 0.0
+    flops = tflops = gemm_ms = cull_ms = upd_ms = 0.0
     iters = launches = 0
     step_ms = []
     with ClockSampler(local) as clk:
@@ -219,6 +249,8 @@ def run_ours(args):
             flops += rep["flops_useful"]
             tflops += rep["flops_tensor"]
             gemm_ms += rep["ms_gemm"]
+            cull_ms += rep["ms_cull"]
+            upd_ms += rep["ms_update"]
             iters += rep["iters"]
             launches += rep["launches"]
         torch.cuda.synchronize()
@@ -227,40 +259,56 @@ def run_ours(args):
     t_max = reduce_max_over_ranks(total_ms, world, dev)
     flops_all = reduce_sum_over_ranks(flops, world, dev)
     value = flops_all / (t_max * 1e-3) / 1e12
-    p_main = spamm.to_dense(P)
-    idem = torch.linalg.norm(p_main @ p_main - p_main).item()
-    trace_err = abs(torch.trace(p_main).item() - ne)
-    stop_reason = rep["stop_reason"]
+    mem_free_mixed = gib(torch.cuda.mem_get_info()[0])
+    main_rep = rep
+    spamm.release_scratch(P)
 
-    # ---- the same workload with FP64 leaf products ----
+    # ---- the same workload with FP64 leaf products (one solve) ----
     fp64 = None
     if prec != spamm.FP64 and not args.no_fp64_leg:
-        P64, _ = solve(p=spamm.FP64, sl=0)
-        f_ms = []
-        for _ in range(2):
-            flush.zero_()
-            ev0.record(stream)
-            P64, r64 = solve(p=spamm.FP64, sl=0, out=P64)
-            ev1.record(stream)
-            ev1.synchronize()
-            f_ms.append(ev0.elapsed_time(ev1))
+        flush.zero_()
+        ev0.record(stream)
+        P64, r64 = solve(p=spamm.FP64, sl=0, timing=True)
+        ev1.record(stream)
+        ev1.synchronize()
+        f_ms = ev0.elapsed_time(ev1)
+        spamm.release_scratch(P64)
+        spamm.trim()
+        d = spamm.to_dense(P)
+        trace_err = abs(torch.trace(d).item() - ne)
         p64 = spamm.to_dense(P64)
-        fp64 = {"solve_ms": sum(f_ms) / len(f_ms), "iters": r64["iters"],
-                "speedup_mixed_vs_fp64": (sum(f_ms) / len(f_ms)) / (t_max / args.steps),
-                "dP_fro_mixed_vs_fp64": torch.linalg.norm(p_main - p64).item(),
-                "value_fp64": r64["flops_useful"] / (r64["ms_total"] * 1e-3) / 1e12}
+        P64.free()
+        d.sub_(p64)                             # P_mixed - P_FP64, in place
+        del p64
+        dP = torch.linalg.norm(d).item()
+        del d
+        torch.cuda.empty_cache()
+        fp64 = {"solve_ms": f_ms, "iters": r64["iters"], "stop_reason": r64["stop_reason"],
+                "symmetric": r64["symmetric"], "speedup_mixed_vs_fp64": f_ms / (t_max / args.steps),
+                "dP_fro_mixed_vs_fp64": dP, "value_fp64": r64["flops_useful"] / (f_ms * 1e-3) / 1e12,
+                "ms_cull": r64["ms_cull"], "ms_gemm": r64["ms_gemm"], "ms_update": r64["ms_update"],
+                "gemm_tflops": r64["flops_useful"] / (r64["ms_gemm"] * 1e-3) / 1e12,
+                "gemm_frac_of_fp64_peak": r64["flops_useful"] / (r64["ms_gemm"] * 1e-3) / 1e12 / fp64_peak_tflops()}
+    else:
+        spamm.trim()
+        d = spamm.to_dense(P)
+        trace_err = abs(torch.trace(d).item() - ne)
+        del d
+        torch.cuda.empty_cache()
+    P.free()
+    spamm.trim()
 
     # ---- end to end through the C ABI with host buffers ----
-    h_pin = torch.from_numpy(h).pin_memory()
-    p_pin = torch.empty((n, n), dtype=torch.float64).pin_memory()
+    e2e_steps = min(args.steps, args.e2e_steps)
+    p_pin = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
     e2e_flops = 0.0
     _barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        F2 = spamm.tree_build(h_pin.numpy(), leaf=b)        # host pointer: H2D inside
+    for _ in range(e2e_steps):
+        F2 = spamm.tree_build(h_pin.numpy(), leaf=b, drop=drop)   # host pointer: H2D inside
         P2, rep2 = spamm.sp2_solve(F2, ne, tau, prec=prec, slices=slices)
-        spamm.to_dense(P2, out=p_pin.numpy())               # host pointer: D2H inside
+        spamm.to_dense(P2, out=p_pin.numpy())                     # host pointer: D2H inside
         e2e_flops += rep2["flops_useful"]
         F2.free()
         P2.free()
@@ -276,19 +324,25 @@ def run_ours(args):
         kern = "k_gemm_fp64<32>"
         peak_note = "FP64 FMA: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz (nominal 1.25 TFLOP/s)"
         alg_flops = flops
+        traffic = None
+        burst = None
     else:
         peak = peaks.get("bf16_tflops_sustained", 1700.0)
+        burst = peaks.get("bf16_tflops", 1900.0)
         bound = "tensor"
-        kern = "k_gemm_tc<%d, 2, 32, %d>" % (slices, 2 if slices <= 4 else 1)  # tile width: leaf columns
-        peak_note = "bf16 tensor, sustained, %s (MEASURED_PEAKS.json)" % peak_src
+        kern = "k_gemm_tc (%d exact BF16 slices, leaf 32)" % slices
+        peak_note = ("bf16 tensor, sustained (the kernel runs inside a ~1 s solve), %s (MEASURED_PEAKS.json)"
+                     % peak_src)
         # tensor work of the surviving products: each slice pair that is not
         # identically zero, on the tiles actually formed (symmetric half)
         alg_flops = tflops
+        traffic = _tc_traffic() if slices == 7 and n == WORKLOAD["n"] else None
     achieved = alg_flops / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else None
-    traffic = TC_TRAFFIC_BYTES_PER_LAUNCH if (prec == spamm.OZAKI_BF16 and slices == 7) else None
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                 "kernel": kern, "peak_source": peak_note,
+                "frac_of_burst_peak": (achieved / burst) if (achieved and burst) else None,
+                "launches_per_solve": main_rep["iters"],
                 "useful_leaf_tflops_in_kernel": flops / (gemm_ms * 1e-3) / 1e12 if gemm_ms else None,
                 "kernel_share_of_step": gemm_ms / total_ms if total_ms else None}
 
@@ -298,22 +352,31 @@ def run_ours(args):
         "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if prec == spamm.FP64 else "bf16-slices/f32-acc/f64",
-        "data": "synthetic (seeded tight-binding Hamiltonian, Morton-ordered 3-D clusters)",
-        "config": dict(WORKLOAD, prec=args.prec, slices=slices,
+        "data": "synthetic (seeded tight-binding Hamiltonian, Morton-ordered 3-D clusters, built on the device)",
+        "config": dict(WORKLOAD, n=n, ne=ne, prec=args.prec, slices=slices,
                        parallelism="replicas" if world > 1 else "1gpu",
                        l2="flushed between steps; working set > L2"),
         "sp2": {"iters_per_solve": iters / args.steps, "solve_ms": t_max / args.steps,
-                "step_ms": step_ms, "idempotency": idem, "trace_err": trace_err,
-                "stop_reason": stop_reason},
+                "step_ms": step_ms, "idempotency": main_rep["idem_err"], "trace_err": trace_err,
+                "stop_reason": main_rep["stop_reason"], "symmetric": main_rep["symmetric"],
+                "ms_cull_per_solve": cull_ms / args.steps, "ms_gemm_per_solve": gemm_ms / args.steps,
+                "ms_update_per_solve": upd_ms / args.steps,
+                "tensor_over_useful_flops": tflops / flops if flops else None,
+                "stored_leaves_F": F.stored, "hbm_free_gib_during_mixed": mem_free_mixed,
+                "setup_s": gen_s},
         "fp64_plain": fp64,
         "roofline": roofline,
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * n * n,
-                "d2h_bytes_per_step": 8 * n * n, "seconds": e2e_s},
+                "d2h_bytes_per_step": 8 * n * n, "seconds": e2e_s, "steps": e2e_steps,
+                "path": "spamm_tree_build(host F, sparse) + sp2_solve + spamm_to_dense(host P), pinned buffers"},
         "gpu_launches": launches,
     }
+    del p_pin
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(h, iters=args.cpu_iters)
+        h_np = h_pin.numpy()
+        line["cpu_baseline"] = cpu_baseline(h_np, n)
+    F.free()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -321,29 +384,41 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(h=None, iters=1):
-    """The FP64 CPU oracle on the host cores: `iters` SP2 iterations of the
-    same workload (fixed-iteration mode), useful leaf FLOPs / wall time."""
+def _oracle_sp2_sample(f, tau, leaf, nthreads=0):
+    """One SP2 iteration by the CPU oracle (Gershgorin bounds, X0, X0^2 by
+    the recursive SpAMM of Algorithm 1) on the matrix f; (useful FLOPs,
+    seconds)."""
+    import oracle
+    m = f.shape[0]
+    t0 = time.perf_counter()
+    _, hist, _ = oracle.sp2(f, leaf, m // 2, tau, fixed_iters=1, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    return 2.0 * leaf ** 3 * hist[:, oracle.H_TASKS].sum(), dt
+
+
+def cpu_baseline(h=None, n=None):
+    """The FP64 CPU oracle on the host cores, on a bounded sample of the same
+    workload: one SP2 iteration of the leading principal block (the first
+    sites along the Morton curve) of the Hamiltonian; useful leaf FLOPs /
+    wall time.  Also on one core, on a smaller block."""
+    import numpy as np
     import oracle
     from paper_1403_7458_gb300 import synth
-    n, b, tau, ne = WORKLOAD["n"], WORKLOAD["leaf"], WORKLOAD["tau"], WORKLOAD["ne"]
-    if h is None:
-        h = synth.tb_hamiltonian(n, seed=0)
-    t0 = time.perf_counter()
-    _, hist, _ = oracle.sp2(h, b, ne, tau, fixed_iters=iters)
-    dt = time.perf_counter() - t0
-    flops = 2.0 * b ** 3 * hist[:, oracle.H_TASKS].sum()
-    # the same oracle on one core: the first iteration only (bounded sample)
-    t1 = time.perf_counter()
-    _, hist1, _ = oracle.sp2(h, b, ne, tau, fixed_iters=1, nthreads=1)
-    dt1 = time.perf_counter() - t1
-    flops1 = 2.0 * b ** 3 * hist1[:, oracle.H_TASKS].sum()
+    n = n or WORKLOAD["n"]
+    b, tau, decay = WORKLOAD["leaf"], WORKLOAD["tau"], WORKLOAD["decay_A"]
+    m = min(CPU_SAMPLE_N, n)
+    m1 = min(CPU_SAMPLE_N_ONE_CORE, n)
+    blk = (np.ascontiguousarray(h[:m, :m]) if h is not None
+           else synth.tb_hamiltonian_block(n, m, seed=0, decay=decay))
+    flops, dt = _oracle_sp2_sample(blk, tau, b)
+    flops1, dt1 = _oracle_sp2_sample(np.ascontiguousarray(blk[:m1, :m1]), tau, b, nthreads=1)
     return {"value": flops / dt / 1e12, "unit": UNIT, "cores": oracle.num_threads(),
             "kind": "oracle", "seconds": dt,
-            "sample": "%d SP2 iteration(s) of the N=4096 workload (Gershgorin start, "
-                      "X0^2 by recursive SpAMM)" % iters,
+            "sample": ("one SP2 iteration (Gershgorin bounds, X0, X0^2 by the recursive SpAMM) of the "
+                       "leading %d x %d principal block of the N=%d Hamiltonian (first %d sites along "
+                       "the Morton curve), leaf %d, tau %g" % (m, m, n, m, b, tau)),
             "one_core": {"value": flops1 / dt1 / 1e12, "unit": UNIT, "cores": 1, "seconds": dt1,
-                         "sample": "1 SP2 iteration of the same workload"}}
+                         "sample": "the same on the leading %d x %d block" % (m1, m1)}}
 
 
 def run_precision_study(args):
@@ -649,28 +724,42 @@ def run_reference(args):
         return
     import oracle
     from paper_1403_7458_gb300 import synth
-    n, b, tau, ne = WORKLOAD["n"], WORKLOAD["leaf"], WORKLOAD["tau"], WORKLOAD["ne"]
-    h = synth.tb_hamiltonian(n, seed=0)
+    n, b, tau, decay = args.bench_n, WORKLOAD["leaf"], WORKLOAD["tau"], WORKLOAD["decay_A"]
+    m = min(REF_SAMPLE_N, n)
+    blk = synth.tb_hamiltonian_block(n, m, seed=0, decay=decay)
     for _ in range(args.warmup):
-        oracle.sp2(h, b, ne, tau, fixed_iters=1)
-    t0 = time.perf_counter()
-    flops = 0.0
+        _oracle_sp2_sample(blk, tau, b)
+    flops = secs = 0.0
     for _ in range(args.steps):
-        _, hist, _ = oracle.sp2(h, b, ne, tau, fixed_iters=1)
-        flops += 2.0 * b ** 3 * hist[:, oracle.H_TASKS].sum()
-    dt = time.perf_counter() - t0
-    value = flops / dt / 1e12
+        f, dt = _oracle_sp2_sample(blk, tau, b)
+        flops += f
+        secs += dt
+    value = flops / secs / 1e12
+    sample = ("one SP2 iteration (Gershgorin bounds, X0, X0^2 by the recursive SpAMM) of the leading "
+              "%d x %d principal block of the N=%d Hamiltonian per step" % (m, m, n))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(WORKLOAD, prec="fp64", parallelism="cpu"),
+            "config": dict(WORKLOAD, n=n, ne=n // 2, prec="fp64", parallelism="cpu", sample_n=m),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
-                             "kind": "oracle",
-                             "sample": "one SP2 iteration (X0^2) of the N=4096 workload per step"},
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _spawn_ranks(args, argv):
+    """Start args.gpus ranks of this script through torch.distributed.run (one
+    process per GPU) when it was not launched that way."""
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+           "--nproc-per-node", str(args.gpus), "--master-addr", "127.0.0.1",
+           "--master-port", str(port), os.path.abspath(__file__)] + list(argv)
+    return subprocess.call(cmd)
 
 
 def main(argv=None):
@@ -681,7 +770,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--prec", choices=["fp64", "ozaki"], default="ozaki")
     ap.add_argument("--slices", type=int, default=7)
-    ap.add_argument("--cpu-iters", type=int, default=12)
+    ap.add_argument("--bench-n", type=int, default=WORKLOAD["n"])
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-leg", action="store_true")
     ap.add_argument("--study", choices=["none", "precision", "batch", "large", "spamm"], default="none")
@@ -695,6 +785,11 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ and args.study == "none":
+        sys.exit(_spawn_ranks(args, sys.argv[1:] if argv is None else argv))
+    if args.study == "none" and args.gpus != world:
+        sys.exit("bench.py: --gpus %d but WORLD_SIZE=%d" % (args.gpus, world))
     if args.study == "precision":
         run_precision_study(args)
     elif args.study == "batch":

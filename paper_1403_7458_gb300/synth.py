@@ -27,7 +27,7 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = ["water_sites", "morton3", "distances", "decaying_matrix",
-           "tb_hamiltonian", "tb_hamiltonian_torch", "batch_sizes"]
+           "tb_hamiltonian", "tb_hamiltonian_block", "tb_hamiltonian_torch", "batch_sizes"]
 
 _MORTON_BITS = 21
 
@@ -110,6 +110,26 @@ def tb_hamiltonian(n: int, seed: int, decay: float = 1.2, onsite: float = 2.0,
     h = np.empty((n, n))
     step = 1024
     for r0 in range(0, n, step):
+        blk = -np.exp(-distances(pos, slice(r0, r0 + step)) / decay)
+        blk[np.abs(blk) < cut] = 0.0
+        h[r0:r0 + step] = blk
+    np.fill_diagonal(h, np.where(gen % 2 == 0, -onsite, onsite))
+    return h
+
+
+def tb_hamiltonian_block(n: int, m: int, seed: int, decay: float = 1.2, onsite: float = 2.0,
+                         cut: float = 1e-12) -> np.ndarray:
+    """The leading m x m principal block of `tb_hamiltonian(n, seed, ...)`
+    (the first m sites along the Morton curve), built without forming the
+    n x n matrix."""
+    if not 0 < m <= n:
+        raise ValueError("need 0 < m <= n")
+    rng = np.random.default_rng(seed)
+    pos, gen = water_sites(n, rng)
+    pos, gen = pos[:m], gen[:m]
+    h = np.empty((m, m))
+    step = 1024
+    for r0 in range(0, m, step):
         blk = -np.exp(-distances(pos, slice(r0, r0 + step)) / decay)
         blk[np.abs(blk) < cut] = 0.0
         h[r0:r0 + step] = blk

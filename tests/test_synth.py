@@ -65,3 +65,10 @@ def test_hamiltonian_torch_matches_numpy_generator():
         assert np.array_equal(h == 0, ht == 0)
         assert np.array_equal(np.diag(h), np.diag(ht))
         assert np.allclose(h, ht, rtol=1e-14, atol=0)
+
+
+def test_hamiltonian_block_is_the_leading_principal_block():
+    from paper_1403_7458_gb300 import synth
+    full = synth.tb_hamiltonian(1500, seed=3, decay=1.0)
+    blk = synth.tb_hamiltonian_block(1500, 700, seed=3, decay=1.0)
+    assert np.array_equal(blk, full[:700, :700])
