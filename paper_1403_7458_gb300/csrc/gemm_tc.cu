@@ -476,8 +476,8 @@ int launch_gemm_tc(spamm_mat_t A, spamm_mat_t B, spamm_mat_t C, SpammWorkspace *
         return SPAMM_E_NOTSUP;
     }
     // diagonal leaves of tiles without work are never handed out: their
-    // traces are 0
-    if (tr_part) SPAMM_CK(cudaMemsetAsync(tr_part, 0, sizeof(double) * A->nb, s));
+    // traces are 0 (two partial traces per leaf row, see the epilogue)
+    if (tr_part) SPAMM_CK(cudaMemsetAsync(tr_part, 0, sizeof(double) * 2 * A->nb, s));
     thread_local tc::TcArgs a;  // large (one table entry used); host-side staging only
     fill_prob(a.p[0], A, B, C, ws, tr_part, 0);
     a.nprob = 1;

@@ -466,12 +466,12 @@ void launch_elementwise(int b, cudaStream_t s, int mode, double *X, const double
 
 
 __global__ void __launch_bounds__(kRedThreads)
-k_sp2_decide(const double *__restrict__ tr_part, int64_t nb, const int64_t *__restrict__ off_end,
+k_sp2_decide(const double *__restrict__ tr_part, int64_t ntr, const int64_t *__restrict__ off_end,
              const int64_t *__restrict__ units, double Ne, int rule, Sp2State *st)
 {
     __shared__ double sred[kRedThreads];
     if (*(volatile int32_t *)&st->stopped) return;
-    double t2 = block_sum_fixed(tr_part, nb, sred);
+    double t2 = block_sum_fixed(tr_part, ntr, sred);  // diagonal-leaf (partial) traces
     if (threadIdx.x == 0) {
         double t1 = st->tn;
         int take;
@@ -599,7 +599,7 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
     SP2_TRY(spamm_alloc((void **)&sc.hi, sizeof(double) * F->n, s));
     SP2_TRY(spamm_alloc((void **)&sc.idem_part, sizeof(double) * G, s));
     SP2_TRY(spamm_alloc((void **)&sc.diag_part, sizeof(double) * nb, s));
-    SP2_TRY(spamm_alloc((void **)&sc.tr_part, sizeof(double) * nb, s));
+    SP2_TRY(spamm_alloc((void **)&sc.tr_part, sizeof(double) * 2 * nb, s));  // tensor path: two per leaf row
     SP2_TRY(spamm_alloc((void **)&sc.flag, sizeof(int32_t) * 4, s));
     SP2_TRY(spamm_alloc((void **)&sc.hist, sizeof(double) * SP2_H_COLS * limit, s));
     SP2_CUDA(cudaMallocHost((void **)&sc.host, sizeof(Sp2State)));
@@ -668,7 +668,8 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
                                             sym ? 1 : 0, false, !tcpath);
                 if (r) return r;
                 const int32_t *x2cnt = tcpath ? X2->ws.tcounts : nullptr;
-                k_sp2_decide<<<1, kRedThreads, 0, st>>>(sc.tr_part, nb, X2->ws.task_total, X2->ws.pair_units, Ne,
+                k_sp2_decide<<<1, kRedThreads, 0, st>>>(sc.tr_part, tcpath ? 2 * nb : nb, X2->ws.task_total,
+                                                        X2->ws.pair_units, Ne,
                                                         o.rule, sc.st);
                 SPAMM_CK_LAUNCH();
                 launch_elementwise(X->b, st, 1, X->leaf, X2->leaf, X->slot, X2->slot, F->n, nb, X->P,

@@ -38,7 +38,7 @@
 // from one device counter over the concatenated orders, so one persistent
 // launch serves many independent SpAMMs.
 //
-// Kernel roles (192 threads, one CTA per SM, persistent):
+// Kernel roles (320 threads, one CTA per SM, persistent):
 //   warp 0     : producer; two bulk copies (cp.async.bulk) per work item:
 //                the needed slices of the R A leaves (one contiguous block of
 //                the tile-major array, stage layout [p][leaf][slice]) and of
@@ -48,8 +48,10 @@
 //                of each landed item and commits to the item's "empty"
 //                barrier and, at the end of a tile, to the accumulator's
 //                "full" barrier;
-//   warps 2-5  : epilogue; tcgen05.ld of the s diagonal blocks of the row the
-//                thread owns, combine, FP64 store, diagonal traces.
+//   warps 2-9  : epilogue, two warps per TMEM lane quadrant (each takes half
+//                of a tile column's 16-column groups); tcgen05.ld of the s
+//                diagonal blocks of the row the thread owns, combine, FP64
+//                store, partial diagonal traces (two per leaf row).
 // Two accumulators (TMEM columns 0 and 256) let the epilogue of one tile run
 // under the MMAs of the next when a tile's W s b columns fit in 256 (else
 // one accumulator: at leaf 32 with 7 slices a tile takes 448 columns).
@@ -71,7 +73,8 @@ namespace tc {
 // zero slices) leave room for more items in flight.
 constexpr uint32_t kRingBytes = 216 * 1024;
 constexpr int kSlots = 16;  // work items in flight at most
-constexpr int kThreads = 192;
+constexpr int kEpiWarps = 8;  // two epilogue warps per TMEM lane quadrant
+constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kAccStride = 256;
 constexpr long long kTimeoutCycles = 8000000000ll;  // about 4 s at 2 GHz per wait
@@ -273,6 +276,84 @@ __device__ __forceinline__ double i64_scaled_fast(long long v, int k)
     return i64_scaled(v, k);
 }
 
+// Exact combination of the diagonal sums of one output element (exact
+// slices): RN(2^k sum_{d >= d0} S_d 128^(S-1-d)), every S_d an integer held
+// in FP32 (integer-valued whatever its size).
+// Fast path, when every |S_d| is below 2^22 and the int64 total cannot
+// overflow (|S_d| 128^(S-1-d) < 2^59): each S_d becomes an int32 by the
+// magic-number addition (f + 1.5 2^23 puts the integer in the low mantissa
+// bits: one FP32 add, one integer subtract, both full-rate, where a
+// float-to-int64 conversion runs on a slow unit), the int64 total is formed
+// with shifts and adds and rounded once.  Otherwise a 128-bit total
+// (float-to-int64 conversions, exact for integer-valued floats).
+template <int S>
+__device__ __noinline__ double combine_exact_slow(const uint32_t *f, int d0, int k)
+{
+    // every |S_d| < 2^31 (the usual case off the fast path): int32
+    // conversions, the terms with shifts >= 28 in hi (scaled down by 2^28,
+    // |hi| < 2^46) and the rest in lo (|lo| < 2^53); both convert exactly and
+    // one fused multiply-add rounds hi 2^28 + lo once
+    bool medium = true;
+    for (int d = d0; d < S; d++) medium = medium && fabsf(__uint_as_float(f[d])) < 2147483648.0f;
+    if (medium) {
+        long long hi = 0, lo = 0;
+        for (int d = d0; d < S; d++) {
+            const int sh = 7 * (S - 1 - d);
+            const long long iv = __float2int_rn(__uint_as_float(f[d]));
+            if (sh >= 28) hi += iv << (sh - 28);
+            else lo += iv << sh;
+        }
+        const double x = fma((double)hi, 268435456.0, (double)lo);  // RN(hi 2^28 + lo)
+        if (x == 0.0) return 0.0;
+        const uint64_t u = (uint64_t)__double_as_longlong(x);
+        const int e = (int)((u >> 52) & 0x7FF) + k;
+        if (e >= 1 && e <= 2046) return __longlong_as_double((long long)(u + ((uint64_t)(int64_t)k << 52)));
+    }
+    __int128 a = 0;
+    for (int d = d0; d < S; d++)
+        a += (__int128)__float2ll_rn(__uint_as_float(f[d])) << (7 * (S - 1 - d));
+    if (a == 0) return 0.0;
+    const bool neg = a < 0;
+    const double r = u128_round_scaled((u128)(neg ? -a : a), k);
+    return neg ? -r : r;
+}
+
+// The 16 values of one TMEM load group at once (straight-line code, so that
+// the 16 chains interleave): fast path for all of them when every one
+// qualifies, else the 128-bit path for each.
+template <int S>
+__device__ __forceinline__ void combine_exact16(const uint32_t (&v)[S][16], int d0, int k, double (&res)[16])
+{
+    bool fast = true;
+    long long a[16];
+#pragma unroll
+    for (int q = 0; q < 16; q++) a[q] = 0;
+#pragma unroll
+    for (int d = 0; d < S; d++) {
+        if (d < d0) continue;  // warp-uniform: diagonals below d0 are zero
+        const int sh = 7 * (S - 1 - d);
+        const float lim = sh + 22 <= 59 ? 4194304.0f : __int_as_float((127 + 59 - sh) << 23);  // 2^min(22, 59 - sh)
+#pragma unroll
+        for (int q = 0; q < 16; q++) {
+            const float f = __uint_as_float(v[d][q]);
+            fast = fast && fabsf(f) < lim;
+            const int iv = __float_as_int(f + 12582912.0f) - 0x4B400000;
+            a[q] += (long long)iv << sh;
+        }
+    }
+    if (fast) {
+#pragma unroll
+        for (int q = 0; q < 16; q++) res[q] = i64_scaled_fast(a[q], k);
+    } else {
+        for (int q = 0; q < 16; q++) {
+            uint32_t f[S];
+#pragma unroll
+            for (int d = 0; d < S; d++) f[d] = v[d][q];
+            res[q] = combine_exact_slow<S>(f, d0, k);
+        }
+    }
+}
+
 // One product of a launch.
 struct TcProb {
     const uint8_t *slA;    // A operand: tile-major [I][k][p][L][slice]
@@ -288,7 +369,7 @@ struct TcProb {
                            // h slices of one leaf), used instead of slB; else null
     const int32_t *sigA;   // sigma of A
     const int32_t *sigB;
-    double *tr_part;       // diagonal-leaf traces (may be null; b = 32 only)
+    double *tr_part;       // diagonal-leaf partial traces, two per leaf row (may be null; b <= 32)
     int64_t nb;
     int64_t nbt;           // tiles per tile row: ceil(nb / W), W output leaf columns per tile
     int64_t pos0;          // first hand-out position of this product
@@ -372,12 +453,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
         }
         for (int q = 0; q < 2; q++) {
             mbar_init(smem_u32(&accf_bar[q]), 1);
-            mbar_init(smem_u32(&acce_bar[q]), 4);
+            mbar_init(smem_u32(&acce_bar[q]), kEpiWarps);
         }
         mbar_init(smem_u32(&done_bar), 1);
         for (int q = 0; q < kTileRing; q++) {
             mbar_init(smem_u32(&tfull_bar[q]), 1);
-            mbar_init(smem_u32(&tempty_bar[q]), 5);  // MMA and four epilogue warps
+            mbar_init(smem_u32(&tempty_bar[q]), 1 + kEpiWarps);  // MMA and the epilogue warps
         }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -652,7 +733,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
         }
         __syncwarp();
     } else {
-        // ------------------------------ epilogue (warps 2-5) ------------------------------
+        // ------------------------------ epilogue (warps 2-9) ------------------------------
+        // Two warps per TMEM lane quadrant (a warp may only access the lanes
+        // 32 (warp % 4) .. + 31): member m of the quadrant handles the
+        // 16-column groups h in [m HPM, (m + 1) HPM) of every tile column.
+        constexpr int NH = B / 16, HPM = (NH + 1) / 2;
+        const int m = (warp - 2) >> 2;
+        const int h_lo = m * HPM, h_hi = min(NH, h_lo + HPM);
         const int quad = warp & 3;             // TMEM lane quadrant of this warp
         const int row = quad * 32 + lane;      // tile row 0..127
         const int L = row / B, r = row % B;    // leaf within tile, row within leaf
@@ -660,7 +747,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
         // the accumulators start at zero (first phase of their "empty" barriers)
         for (int b = 0; b < kNAcc; b++) {
             for (int d = 0; d < W * S; d++)
-                for (int h = 0; h < B / 16; h++) tmem_zero16(tmem + b * kAccStride + lane_off + B * d + 16 * h);
+                for (int h = h_lo; h < h_hi; h++) tmem_zero16(tmem + b * kAccStride + lane_off + B * d + 16 * h);
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -695,6 +782,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
             const int64_t nb = P.nb;
             const int64_t I = t / P.nbt, J = t % P.nbt;
             const bool has_work = P.cnt[t] > 0;
+            // the least diagonal any item of the tile touches per column (za +
+            // zb over its items): the diagonals below it were never written and
+            // are still zero, so they are neither read, cleared nor combined
+            int d0[W];
+#pragma unroll
+            for (int c = 0; c < W; c++) d0[c] = S;
+            {
+                const int64_t e0 = t * nb, e1 = e0 + P.cnt[t];
+                for (int64_t e = e0 + lane; e < e1; e += 32) {
+                    const uint32_t w = P.list[e];
+#pragma unroll
+                    for (int c = 0; c < W; c++)
+                        if (item_mask_col<R, W>(w, c)) d0[c] = min(d0[c], item_za(w) + item_zb_col(w, c));
+                }
+#pragma unroll
+                for (int c = 0; c < W; c++) {
+                    d0[c] = g.float_split ? 0 : warp_min_int(d0[c]);
+                    if (d0[c] > S) d0[c] = S;
+                }
+            }
             if (!mbar_wait(smem_u32(&accf_bar[acc]), aph, abort_v)) {
                 if (lane == 0) atomicExch(g.err, 1);
                 abort_flag = 1;
@@ -717,17 +824,29 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                     (store && P.sym && i < j) ? P.leafC + (int64_t)P.slotC[j * nb + i] * (B * B) + r : nullptr;
                 const uint32_t tbase = tmem + acc * kAccStride + c * kColAcc + lane_off;
                 if (i == j) on_diag = true;
+                int dc = S;  // d0 of column c (static indexing of d0[])
 #pragma unroll
-                for (int h = 0; h < B / 16; h++) {
+                for (int cc = 0; cc < W; cc++)
+                    if (cc == c) dc = d0[cc];
+#pragma unroll
+                for (int hh = 0; hh < HPM; hh++) {
+                    const int h = h_lo + hh;
+                    if (h >= h_hi) break;  // warp-uniform
                     // the S diagonals of these 16 columns: all loads issued,
                     // one wait, the accumulator zeroed for the next tile
                     uint32_t v[S][16];
                     if (has_work) {
 #pragma unroll
-                        for (int d = 0; d < S; d++) tmem_ld16(tbase + B * d + 16 * h, v[d]);
+                        for (int d = 0; d < S; d++) {
+                            if (d >= dc) tmem_ld16(tbase + B * d + 16 * h, v[d]);
+                            else
+#pragma unroll
+                                for (int q = 0; q < 16; q++) v[d][q] = 0u;
+                        }
                         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                        for (int d = 0; d < S; d++) tmem_zero16(tbase + B * d + 16 * h);
+                        for (int d = 0; d < S; d++)
+                            if (d >= dc) tmem_zero16(tbase + B * d + 16 * h);
                     } else {
 #pragma unroll
                         for (int d = 0; d < S; d++)
@@ -745,14 +864,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                             res[q] = a;
                         }
                     } else {
-#pragma unroll
-                        for (int q = 0; q < 16; q++) {
-                            long long a = 0;
-#pragma unroll
-                            for (int d = 0; d < S; d++)
-                                a += (long long)__float2ll_rn(__uint_as_float(v[d][q])) * (1ll << (7 * (S - 1 - d)));
-                            res[q] = i64_scaled_fast(a, kexp);
-                        }
+                        combine_exact16<S>(v, dc, kexp, res);
                     }
                     if (store) {
 #pragma unroll
@@ -782,9 +894,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
             if (B <= 32 && P.tr_part) {
                 // fixed butterfly over the B rows of a diagonal leaf (a warp
                 // holds 32 / B whole leaves, each within one tile column; the
-                // condition is uniform over each leaf's rows)
+                // condition is uniform over each leaf's rows); member m holds
+                // the diagonal elements in its column groups and writes its
+                // partial trace to tr_part[2 i + m]
                 for (int o = B / 2; o > 0; o >>= 1) diag += __shfl_xor_sync(0xffffffffu, diag, o);
-                if (r == 0 && on_diag && i < nb) P.tr_part[i] = diag;
+                if (r == 0 && on_diag && i < nb) P.tr_part[2 * i + m] = diag;
             }
         }
     }
