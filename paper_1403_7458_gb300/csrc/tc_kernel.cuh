@@ -576,7 +576,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                         }
                         const unsigned long long new_end = alloc_ptr + need;
                         // wait (in order) for released items until the region and a slot are free
-                        while (new_end - free_ptr > kRingBytes || issued - released >= (uint32_t)kSlots) {
+                        for (;;) {
+                            // nothing in flight: the wrap padding before the region holds
+                            // nothing either (an item larger than the space left after the
+                            // last wrap would otherwise wait for space that never frees)
+                            if (released == issued) free_ptr = alloc_ptr;
+                            if (new_end - free_ptr <= kRingBytes && issued - released < (uint32_t)kSlots) break;
                             const uint32_t rs = released % kSlots;
                             if (!mbar_wait(smem_u32(&empty_bar[rs]), (released / kSlots) & 1, abort_v)) {
                                 good = 0;
