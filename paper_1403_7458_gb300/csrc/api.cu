@@ -592,7 +592,7 @@ int spamm_multiply_into(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t C,
         ws->task_total = ws->off + A->nb * A->nb;
         ws->pair_units = nullptr;
         if (ev) SPAMM_CK(spamm_event_record(ev[1], s));
-        rc = launch_gemm_fp64(A, B, C, ws, tr_part, s);
+        rc = launch_gemm_fp64(A, B, C, ws, tr_part, s, (sym && A == B) ? 1 : 0);
     } else if (prec_is_tc(prec)) {
         const int sl = prec_slices(prec, opts ? opts->slices : 0);
         const int el = prec_elem(prec);

@@ -1,6 +1,9 @@
 // gemm_fp64.cu -- grouped FP64 leaf products C_ij = sum_{k in S_ij} A_ik B_kj
 // (the dense leaf product of Algorithm 1, applied to every surviving triple).
 //
+// Symmetric products (A == B exactly symmetric, as in SP2) form only the
+// output leaves i <= j and store each C_ij (i < j) also as C_ji = C_ij^T.
+//
 // Output-stationary: one CTA owns one output leaf (i, j) at a time, so no two
 // CTAs write the same C leaf and no lock or atomic on C is needed (the paper's
 // OpenMP lock on C has no counterpart here).  CTAs are persistent and pull
@@ -45,6 +48,7 @@ struct FpProb {
     double *n2CT;
     double *tr_part;
     int64_t g0;  // first output-leaf number of this product
+    int32_t sym; // A == B exactly symmetric: only leaves i <= j are formed, C_ji = C_ij^T
 };
 
 struct GemmArgs {
@@ -81,6 +85,21 @@ __device__ __forceinline__ void stage_leaf(double *dst, const double *src, int t
     for (int q = tid; q < chunks; q += kThreads) cp_async16(dst + 2 * q, src + 2 * q);
 }
 
+// (i, j) of entry x of the upper block triangle (i <= j) in row-major order:
+// row i starts at i nb - i (i - 1) / 2.
+__device__ __forceinline__ void upper_pair(int64_t x, int64_t nb, int64_t &i, int64_t &j)
+{
+    const double b = 2.0 * (double)nb + 1.0;
+    int64_t r = (int64_t)floor((b - sqrt(b * b - 8.0 * (double)x)) * 0.5);
+    auto start = [nb](int64_t q) { return q * nb - q * (q - 1) / 2; };
+    if (r < 0) r = 0;
+    if (r > nb - 1) r = nb - 1;
+    while (r > 0 && start(r) > x) r--;
+    while (r + 1 < nb && start(r + 1) <= x) r++;
+    i = r;
+    j = x - start(r) + r;
+}
+
 template <int B>
 __global__ void __launch_bounds__(kThreads) k_gemm_fp64(const __grid_constant__ GemmArgs g)
 {
@@ -104,8 +123,13 @@ __global__ void __launch_bounds__(kThreads) k_gemm_fp64(const __grid_constant__ 
         const int64_t gg = s_group;
         if (gg >= G) break;
         const FpProb &P = g.p[find_prob(g, gg)];
-        const int64_t grp = gg - P.g0;
-        const int64_t i = grp / P.nb, j = grp % P.nb;
+        int64_t i, j;
+        if (P.sym) upper_pair(gg - P.g0, P.nb, i, j);
+        else {
+            i = (gg - P.g0) / P.nb;
+            j = (gg - P.g0) % P.nb;
+        }
+        const int64_t grp = i * P.nb + j;
         const int64_t t0 = P.off[grp], t1 = P.off[grp + 1];
 
         double acc[T::TR][T::TC];
@@ -165,6 +189,15 @@ __global__ void __launch_bounds__(kThreads) k_gemm_fp64(const __grid_constant__ 
             reinterpret_cast<double2 *>(dst)[q] = v;
             emax = max(emax, max(exp_key(v.x), exp_key(v.y)));
         }
+        if (P.sym && i < j) {
+            // the mirror leaf C_ji = C_ij^T (bit-identical to forming it: the
+            // same products in the same order, the factors swapped)
+            double *mir = P.leafC + (int64_t)P.slotC[j * P.nb + i] * B * B;
+            for (int q = tid; q < B * B / 2; q += kThreads) {
+                const int rr = (2 * q) / B, cc = (2 * q) % B;
+                reinterpret_cast<double2 *>(mir)[q] = make_double2(Cs[cc * B + rr], Cs[(cc + 1) * B + rr]);
+            }
+        }
         emax = warp_max_int(emax);
         if ((tid & 31) == 0) s_red_i[tid >> 5] = emax;
         __syncthreads();
@@ -183,6 +216,10 @@ __global__ void __launch_bounds__(kThreads) k_gemm_fp64(const __grid_constant__ 
             double r = emax > 0 ? sq_sum_round(tot, emax) : 0.0;
             P.n2C[i * P.P + j] = r;
             P.n2CT[j * P.P + i] = r;
+            if (P.sym && i < j) {  // a transposed leaf has the same exact squared norm
+                P.n2C[j * P.P + i] = r;
+                P.n2CT[i * P.P + j] = r;
+            }
             if (i == j && P.tr_part) {
                 double tr = 0.0;
                 for (int q = 0; q < B; q++) tr += Cs[q * B + q];
@@ -229,6 +266,7 @@ static void fill_prob(FpProb &p, spamm_mat_t A, spamm_mat_t B, spamm_mat_t C, Sp
     p.n2CT = C->n2T;
     p.tr_part = tr_part;
     p.g0 = g0;
+    p.sym = 0;
 }
 
 static int launch_args(GemmArgs &g, int leaf, cudaStream_t s)
@@ -245,12 +283,13 @@ static int launch_args(GemmArgs &g, int leaf, cudaStream_t s)
 }
 
 int launch_gemm_fp64(spamm_mat_t A, spamm_mat_t B, spamm_mat_t C, SpammWorkspace *ws,
-                     double *tr_part, cudaStream_t s)
+                     double *tr_part, cudaStream_t s, int sym)
 {
     thread_local GemmArgs g;  // large (one table entry used); host-side staging only
     fill_prob(g.p[0], A, B, C, ws, tr_part, 0);
+    g.p[0].sym = sym ? 1 : 0;
     g.nprob = 1;
-    g.G = A->nb * A->nb;
+    g.G = sym ? A->nb * (A->nb + 1) / 2 : A->nb * A->nb;
     g.counter = ws->counter;
     g.stop = ws->stop;
     return launch_args(g, A->b, s);

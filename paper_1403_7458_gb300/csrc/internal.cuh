@@ -160,8 +160,8 @@ bool spamm_cull_never_waits(int64_t nb);
 // C = SpAMM(A, B, tau) into an existing handle (api.cu).  ev (optional, 4
 // events) is recorded before the cull, before the products, before and after
 // C's upper norm tiers.
-// sym: A == B is exactly symmetric; the tensor-core path then forms only the
-// upper block triangle of C and mirrors it (bit-identical, half the work).
+// sym: A == B is exactly symmetric; both paths then form only the upper
+// block triangle of C and mirror it (bit-identical, half the work).
 // zero_empty = false (tensor path): leaves of tiles without work are left
 // unwritten; the caller treats them as zero through ws->toff (SP2 does).
 int spamm_multiply_into(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t C,
@@ -226,7 +226,7 @@ int launch_gemm_fp64_batched(int count, const spamm_mat_t *A, const spamm_mat_t 
 
 // Leaf products (gemm_fp64.cu)
 int launch_gemm_fp64(spamm_mat_t A, spamm_mat_t B, spamm_mat_t C, SpammWorkspace *ws,
-                     double *tr_part, cudaStream_t s);
+                     double *tr_part, cudaStream_t s, int sym = 0);
 
 // ---------------------------------------------------------------------------
 // Device helpers

@@ -629,7 +629,7 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
             goto done;
         }
     }
-    if (prec_is_tc(o.prec) && !(o.flags & SPAMM_F_NOSYM)) {
+    if (!(o.flags & SPAMM_F_NOSYM)) {
         SP2_CUDA(cudaMemsetAsync(sc.flag, 0, sizeof(int32_t), s));
         k_symmetry<<<(unsigned)((G + 7) / 8), 256, 0, s>>>(F->leaf, F->slot, nb, F->b, sc.flag);
         SP2_LAUNCHED();

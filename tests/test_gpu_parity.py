@@ -167,6 +167,23 @@ def test_sp2_fp64_matches_oracle(cuda_lib, n, b, tau):
     assert np.linalg.norm(p - p_ref) <= 1e-10 + 10 * hist[-1, oracle.H_IDEM]
 
 
+@pytest.mark.parametrize("n,b", [(1000, 32), (777, 16), (900, 64)])
+def test_sp2_fp64_symmetric_mode_is_bit_identical(cuda_lib, n, b):
+    """FP64 leaf products of an exactly symmetric iterate: forming only the
+    upper block triangle of X^2 and storing each C_ij also as C_ji^T gives
+    the same bits as forming every leaf (the mirror sums the same products
+    in the same order, factors swapped)."""
+    h = synth.tb_hamiltonian(n, 7)
+    F = cuda_lib.tree_build(_dev(h), leaf=b)
+    Ps, rs = cuda_lib.sp2_solve(F, n / 2, 1e-8, fixed_iters=10)
+    Pf, rf = cuda_lib.sp2_solve(F, n / 2, 1e-8, fixed_iters=10, symmetric=False)
+    assert rs["symmetric"] == 1 and rf["symmetric"] == 0
+    ps = cuda_lib.to_dense(Ps).cpu().numpy()
+    assert np.array_equal(ps, cuda_lib.to_dense(Pf).cpu().numpy())
+    assert np.array_equal(ps, ps.T)
+    assert np.array_equal(rs["history"], rf["history"])
+
+
 def test_sp2_first_iterations_config1_size(cuda_lib):
     """N = 4096 tight-binding Hamiltonian, tau = 1e-8: the oracle runs three
     SP2 iterations (fixed-iteration mode) and the GPU must agree on every
