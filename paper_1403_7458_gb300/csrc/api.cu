@@ -242,6 +242,7 @@ static void ws_free(SpammWorkspace *ws, cudaStream_t s)
     spamm_release(ws->counter, s);
     spamm_release(ws->tr_part, s);
     spamm_release(ws->scan_part, s);
+    spamm_release(ws->cmask, s);
     *ws = SpammWorkspace();
 }
 

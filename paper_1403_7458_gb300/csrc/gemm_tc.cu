@@ -20,6 +20,12 @@ struct CullArgs {
     // step of k at once (null when the quadtree is shallower)
     const double *cA, *cB;
     int64_t cW;
+    // per coarse pair (block row of A, block column of B), the bit set of
+    // the coarse k-blocks that pass (cwords words of 32 bits per pair; null
+    // when the coarse tier is not used)
+    const uint32_t *cmask;
+    int64_t nc, cwords;
+    int denseA, denseB;  // identity slot maps: leaf (i, k) is slot i nb + k
     const uint8_t *zA, *zB;        // leading zero slices per slot
     const int32_t *slotA, *slotB;  // slot maps (B: of the matrix whose slices serve as B)
     int64_t nb, P, nI, nbt;
@@ -36,26 +42,38 @@ __device__ __forceinline__ uint32_t tile_item(const CullArgs &c, int64_t I, int6
                                               int &npair)
 {
     if (k >= c.nb) return 0;
+    // every load of the candidate issued before any is used (one round trip)
     const double b = __ldg(c.n2BT + j * c.P + k);
+    const int64_t sbi = c.sym ? (c.denseA ? j * c.nb + k : -1) : (c.denseB ? k * c.nb + j : -1);
+    double a[8];
+    int zr[8];
+#pragma unroll
+    for (int r = 0; r < 8; r++) {
+        const int64_t i = (int64_t)c.R * I + r;
+        const bool in = r < c.R && i < c.nb;
+        a[r] = in ? __ldg(c.n2A + i * c.P + k) : 0.0;
+        zr[r] = (in && c.denseA) ? c.zA[i * c.nb + k] : 0;
+    }
+    int zb = sbi >= 0 ? (c.sym ? c.zA[sbi] : c.zB[sbi]) : 0;
     if (b == 0.0) return 0;  // B leaf zero (or not stored): no triple of the step survives
     // B operand leaf (k, j); in symmetric mode its image is leaf (j, k)'s A role
-    const int zb = c.sym ? c.zA[c.slotA[j * c.nb + k]] : c.zB[c.slotB[k * c.nb + j]];
+    if (sbi < 0) zb = c.sym ? c.zA[c.slotA[j * c.nb + k]] : c.zB[c.slotB[k * c.nb + j]];
     uint32_t mask = 0;
     int za = c.S;
 #pragma unroll
     for (int r = 0; r < 8; r++) {
         const int64_t i = (int64_t)c.R * I + r;
-        if (r < c.R && i < c.nb && keep_product(__ldg(c.n2A + i * c.P + k), b, c.tau2)) {
+        if (r < c.R && i < c.nb && keep_product(a[r], b, c.tau2)) {
             // symmetric mode counts the whole product's triples from the
             // active tiles alone: (i, k, j) survives iff (j, k, i) does, so
             // a leaf above the diagonal stands for itself and its mirror
             ntask += !c.sym ? 1 : (i < j ? 2 : (i == j ? 1 : 0));
-            const int zr = c.zA[c.slotA[i * c.nb + k]];
-            if (zr + zb < c.S) {
-                const int mr = c.S - zr - zb;
+            const int z = c.denseA ? zr[r] : c.zA[c.slotA[i * c.nb + k]];
+            if (z + zb < c.S) {
+                const int mr = c.S - z - zb;
                 npair += mr * (mr + 1) / 2;
                 mask |= 1u << r;
-                za = zr < za ? zr : za;
+                za = z < za ? z : za;
             }
         }
     }
@@ -64,16 +82,11 @@ __device__ __forceinline__ uint32_t tile_item(const CullArgs &c, int64_t I, int6
 }
 
 // Early occlusion (Algorithm 1): the R rows of tile I lie in one block row
-// of the 32 x 32-leaf tier (R divides 32), so when that block row of A and
-// the block of B holding (k0 .. k0+31, j) fail the test, every triple of the
-// step fails (a parent's squared norm is never below a child's).
-__device__ __forceinline__ bool coarse_pass(const CullArgs &c, int64_t I, int64_t k0, int64_t j)
-{
-    const int64_t i = (int64_t)c.R * I;
-    return !c.cA || keep_product(__ldg(c.cA + (i >> 5) * c.cW + (k0 >> 5)),
-                                 __ldg(c.cB + (k0 >> 5) * c.cW + (j >> 5)), c.tau2);
-}
-
+// of the 32 x 32-leaf tier (R divides 32) and its W columns in one block
+// column, so when that block row of A and the block of B holding
+// (k0 .. k0+31, j) fail the test, every triple of the step fails (a parent's
+// squared norm is never below a child's).  The passing blocks of each coarse
+// pair are found once (k_coarse_mask) and every tile of the pair reads them.
 __device__ __forceinline__ int item_pairs(uint32_t w, int S)
 {
     const int m = S - tc::item_za(w) - tc::item_zb(w);
@@ -130,6 +143,28 @@ __device__ __forceinline__ int item_pairs2(uint32_t w, int S)
     return n;
 }
 
+// Bit sets of the passing coarse k-blocks: one warp per coarse pair (block
+// row ci of A, block column cj of B in the tier whose blocks are 32 x 32
+// leaves); bit kc of the pair's set is the culling test of Eq. 4 on the
+// blocks (ci, kc) and (kc, cj).  A leaf triple can pass only inside a
+// passing block pair (a parent's squared norm is never below a child's).
+__global__ void k_coarse_mask(const int32_t *__restrict__ stop, const double *__restrict__ cA,
+                              const double *__restrict__ cB, int64_t cW, int64_t nc, int64_t cwords, double tau2,
+                              uint32_t *__restrict__ mask)
+{
+    if (stop && *stop) return;
+    const int64_t pr = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (pr >= nc * nc) return;
+    const int64_t ci = pr / nc, cj = pr % nc;
+    for (int64_t wd = 0; wd < cwords; wd++) {
+        const int64_t kc = wd * 32 + lane;
+        const bool p = kc < nc && keep_product(__ldg(cA + ci * cW + kc), __ldg(cB + kc * cW + cj), tau2);
+        const unsigned bal = __ballot_sync(0xffffffffu, p);
+        if (lane == 0) mask[pr * cwords + wd] = bal;
+    }
+}
+
 // One warp per tile: tests the candidates k (ballot), writes the tile's work
 // items into its own segment of the list, [t nb, t nb + count), and counts
 // them, the surviving triples and the slice pairs.
@@ -153,19 +188,30 @@ k_tile_count(CullArgs c, int32_t *__restrict__ counts, int32_t *__restrict__ tas
     }
     uint32_t *seg = list + t * c.nb;
     const unsigned lt = (1u << lane) - 1u;
-    for (int64_t k0 = 0; k0 < c.nb; k0 += 32) {
-        // the W columns lie in one 32-leaf block column (W divides 32)
-        if (!coarse_pass(c, I, k0, (int64_t)W * J)) continue;  // warp-uniform
-        uint32_t w;
-        if constexpr (W == 2) w = tile_item2(c, I, J, k0 + lane, ntask, nuse);
-        else w = tile_item(c, I, J, k0 + lane, ntask, nuse);
-        const unsigned bal = __ballot_sync(0xffffffffu, w != 0);
-        if (w) {
-            seg[cnt + __popc(bal & lt)] = w;
-            if constexpr (W == 2) npair += item_pairs2(w, c.S);
-            else npair += item_pairs(w, c.S);
+    // the steps of 32 candidates k0 .. k0 + 31 to test: the coarse blocks
+    // whose pair with the tile's block row and column passes (precomputed
+    // bit sets), else every step
+    const int64_t nsteps = (c.nb + 31) / 32;
+    const uint32_t *cm = c.cmask ? c.cmask + (((int64_t)c.R * I >> 5) * c.nc + (((int64_t)W * J) >> 5)) * c.cwords
+                                 : nullptr;
+    for (int64_t wd = 0; wd < (nsteps + 31) / 32; wd++) {
+        uint32_t bits = cm ? __ldg(cm + wd) : 0xFFFFFFFFu;  // warp-uniform
+        while (bits) {
+            const int64_t kc = wd * 32 + (__ffs(bits) - 1);
+            bits &= bits - 1;
+            if (kc >= nsteps) break;
+            const int64_t k0 = kc * 32;
+            uint32_t w;
+            if constexpr (W == 2) w = tile_item2(c, I, J, k0 + lane, ntask, nuse);
+            else w = tile_item(c, I, J, k0 + lane, ntask, nuse);
+            const unsigned bal = __ballot_sync(0xffffffffu, w != 0);
+            if (w) {
+                seg[cnt + __popc(bal & lt)] = w;
+                if constexpr (W == 2) npair += item_pairs2(w, c.S);
+                else npair += item_pairs(w, c.S);
+            }
+            cnt += __popc(bal);
         }
-        cnt += __popc(bal);
     }
     for (int o = 16; o > 0; o >>= 1) {
         ntask += __shfl_xor_sync(0xffffffffu, ntask, o);
@@ -358,10 +404,27 @@ int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, i
     c.stop = ws->stop;
     c.cA = c.cB = nullptr;
     c.cW = 0;
+    c.cmask = nullptr;
+    c.nc = (nb + 31) / 32;
+    c.cwords = (c.nc + 31) / 32;
+    c.denseA = spamm_mat_dense(A);
+    c.denseB = spamm_mat_dense(B);
     if (A->depth >= 5 && A->tiers_ok && B->tiers_ok) {
         c.cA = A->n2 + tier_offset(A->depth - 5);
         c.cB = B->n2 + tier_offset(B->depth - 5);
         c.cW = int64_t(1) << (A->depth - 5);
+        const int64_t words = c.nc * c.nc * c.cwords;
+        if (ws->cmask_cap < words) {
+            spamm_release(ws->cmask, s);
+            ws->cmask = nullptr;
+            ws->cmask_cap = 0;
+            if ((rc = spamm_alloc((void **)&ws->cmask, sizeof(uint32_t) * words, s))) return rc;
+            ws->cmask_cap = words;
+        }
+        k_coarse_mask<<<(unsigned)((c.nc * c.nc + 7) / 8), 256, 0, s>>>(ws->stop, c.cA, c.cB, c.cW, c.nc, c.cwords,
+                                                                         c.tau2, ws->cmask);
+        SPAMM_CK_LAUNCH();
+        c.cmask = ws->cmask;
     }
     const unsigned blocks = (unsigned)((T + kWarps - 1) / kWarps);
     const int64_t worst = T * nb;  // every tile owns a segment of nb items (one per k)

@@ -52,6 +52,8 @@ struct SpammWorkspace {
     int tsym = 0;                         // last tile cull was symmetric
     int tw = 1;                           // output leaf columns per tile of the last tile cull
     int64_t tT = 0;                       // tiles of the last tile cull (totals at toff + tT)
+    uint32_t *cmask = nullptr;            // tile cull: passing coarse k-blocks per coarse (row, column) pair
+    int64_t cmask_cap = 0;                // uint32 words
     int64_t *scan_part = nullptr;         // chunk partials of the multi-block scans (scan.cuh)
     int64_t scan_cap = 0;                 // int64 words
 };
