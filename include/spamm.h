@@ -49,13 +49,23 @@ extern "C" {
 typedef enum {
     /* FP64 operands, FP64 fused multiply-add accumulation. */
     SPAMM_FP64 = 0,
-    /* Exact-slice mixed precision on the tcgen05 tensor cores: every matrix
-     * row (of A) and column (of B) gets a power-of-two scale; the scaled
-     * values are cut into `slices` signed 7-bit integer slices held in BF16;
-     * slice pairs (p, q) with p + q < slices are multiplied with FP32
-     * accumulation in tensor memory (exact for integers below 2^24) and
-     * combined in FP64.  Error-free splitting after Ozaki, Ogita, Oishi and
-     * Rump (2012). */
+    /* Exact-slice mixed precision on the tcgen05 tensor cores: each matrix
+     * gets one power-of-two scale 2^sigma with max|x| < 2^sigma (SP2 fixes
+     * sigma = 1 for its iterates, |x| < 2); every element is rounded to
+     * 7 s bits below 2^sigma and cut into s = `slices` base-128 digits with
+     * the element's sign, held exactly in BF16.  Elements below about
+     * 2^(sigma - 7 s) keep no digits, so accuracy is absolute, relative to
+     * the largest element.  Slice pairs (p, q) with p + q < s are multiplied
+     * (exact products) and summed per diagonal d = p + q in FP32 in tensor
+     * memory; the diagonals are combined exactly (integer arithmetic,
+     * 128-bit when needed) and rounded once to FP64.  A diagonal's sum is
+     * exact while the absolute values of its terms add up to less than 2^24
+     * per output element (then the result is the exact product of the
+     * sliced operands, rounded once); beyond that FP32 rounds it, by at most
+     * about 2^-23 of the running sum per accumulation step (leading
+     * diagonal: FP32-level relative accuracy).  The library does not check
+     * that condition on the device.  Splitting after Ozaki, Ogita, Oishi
+     * and Rump (2012). */
     SPAMM_OZAKI_BF16 = 1,
     /* One BF16 term per operand (x rounded to BF16), FP32 accumulation on the
      * tensor cores: the plain low-precision product of the precision study. */
@@ -258,9 +268,11 @@ int spamm_task_list(spamm_mat_t A, spamm_mat_t B, double tau, int64_t *off_host,
  * klist  : device, room for cap uint32 (may be NULL when cap = 0).  When the
  *          total exceeds cap, groups that do not fit are not written: compare
  *          off[nb*nb] with cap after the stream reaches this work.
- * Asynchronous on `stream`.  The first call on a device looks up the scratch
- * array's device address (once per device).  All calls share the scratch:
- * calls whose GPU work overlaps (unordered streams) race on it.
+ * Asynchronous on `stream`.  Every call looks up the scratch array's device
+ * address in the current context; the first call on a device may load the
+ * library's device code, so make it before any stream capture.  All calls
+ * share the scratch: calls whose GPU work overlaps (unordered streams) race
+ * on it.
  */
 int spamm_cull_noalloc(const double *n2A, int64_t lda, const double *n2B, int64_t ldb,
                        int64_t nb, double tau, int64_t *off, uint32_t *klist, int64_t cap,

@@ -16,9 +16,9 @@
 //     (e.g. on two streams without ordering between them) race on it;
 //   - the array keeps the previous call's counts; every count a call reads is
 //     written earlier in the same call, so nothing has to start at zero.
-//   - the first call on a device looks up the array's device address with
-//     cudaGetSymbolAddress (once per device, with that device current).
-#include <mutex>
+//   - every call looks up the array's device address in the current context
+//     with cudaGetSymbolAddress; the first call on a device may load the
+//     module, so make it before any stream capture.
 
 #include "internal.cuh"
 
@@ -30,31 +30,20 @@ namespace {
 
 constexpr int kWarps = 8;
 constexpr int kScanThreads = 1024;
-constexpr int kMaxDevices = 64;
 
-std::mutex g_setup_mutex;
-int32_t *g_counts_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device (looked up on
-// the first call per device).
+// Device address of the scratch array in the current context, looked up on
+// every call: an address cached per device ordinal would go stale when the
+// context is destroyed and recreated (cudaDeviceReset), and the lookup is
+// cheap once the module is loaded.  The first call on a device may load the
+// module, so it belongs before any stream capture.
 int scratch_address(int32_t **out)
 {
-    int dev = 0;
-    SPAMM_CK(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) {
-        spamm_set_error("spamm_cull_noalloc: device ordinal %d out of range", dev);
-        return SPAMM_E_INVAL;
-    }
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_counts_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_counts);
-        if (e != cudaSuccess || !p)
-            return spamm_cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidSymbol,
-                                   "cudaGetSymbolAddress(g_noalloc_counts)", __FILE__, __LINE__);
-        g_counts_addr[dev] = static_cast<int32_t *>(p);
-    }
-    *out = g_counts_addr[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_counts);
+    if (e != cudaSuccess || !p)
+        return spamm_cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidSymbol, "cudaGetSymbolAddress(g_noalloc_counts)",
+                               __FILE__, __LINE__);
+    *out = static_cast<int32_t *>(p);
     return SPAMM_OK;
 }
 

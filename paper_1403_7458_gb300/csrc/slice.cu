@@ -5,8 +5,9 @@
 // X = round(|x| 2^(7s - sigma)) <= 2^(7s), and cut into s base-128 digits,
 //     X = sum_p d_p 128^(s-1-p),  d_0 in [0, 128], d_p in [0, 127] (p > 0),
 // each carrying the sign of x.  Digits are integers of at most 8 bits, so
-// BF16 holds them exactly, their pairwise products are exact in FP32, and
-// sums of such products stay exact while they are below 2^24.
+// BF16 holds them exactly and their pairwise products are exact in FP32;
+// a sum of such products is exact while the absolute values of its terms
+// add up to less than 2^24 (beyond that FP32 rounds it).
 // (Error-free splitting after Ozaki, Ogita, Oishi and Rump, 2012.)
 //
 // Float splits instead store s_0 = round(x), s_1 = round(x - s_0), ... in

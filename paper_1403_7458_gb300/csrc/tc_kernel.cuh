@@ -22,11 +22,13 @@
 // the item's kept A leaves) and zB count leading slices that are zero in
 // every element: those products are exactly zero.  An item whose kept leaves
 // all have zA + zB >= s contributes exactly nothing and is not listed.  For
-// exact (Ozaki) slices the S_d are integers and the epilogue forms
+// exact (Ozaki) slices the S_d are integer-valued FP32 sums (exact while the
+// absolute values of a diagonal's terms add up to less than 2^24, rounded by
+// FP32 beyond that) and the epilogue forms
 //     C = 2^(sigmaA + sigmaB - 7s - 7) * sum_d S_d 128^(s-1-d)
-// with integer arithmetic and one rounding to FP64; for float splits (BF16
-// or TF32 terms) it forms C = sum_d S_d in FP64.  It then zeroes the
-// accumulator for the next tile.
+// exactly (int64, or 128-bit when the total could overflow) with one
+// rounding to FP64; for float splits (BF16 or TF32 terms) it forms
+// C = sum_d S_d in FP64.  It then zeroes the accumulator for the next tile.
 //
 // Element types.  BF16 slices use tcgen05.mma kind::f16 (K = 16 per
 // instruction), TF32 slices kind::tf32 (K = 8); either way one instruction

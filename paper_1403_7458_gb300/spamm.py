@@ -339,8 +339,23 @@ def task_list(A: Matrix, B: Matrix, tau: float, stream=None):
 
 def cull_noalloc(n2a, n2b, nb: int, tau: float, off, klist, stream=None):
     """spamm_cull_noalloc on caller-owned CUDA tensors: n2a, n2b (float64,
-    >= nb x nb, row-major), off (int64, nb*nb + 1), klist (int32/uint32-sized,
-    any length).  Asynchronous; off[-1] holds the total."""
+    >= nb x nb, rows contiguous), off (int64, >= nb*nb + 1 entries), klist
+    (4-byte elements, contiguous, any length, or None).  Asynchronous;
+    off[nb*nb] holds the total.  The tensors are checked here (device, type,
+    layout, size), since the C call can only trust the pointers it gets."""
+    import torch
+    nb = int(nb)
+    for name, t in (("n2a", n2a), ("n2b", n2b)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.dim() == 2):
+            raise ValueError("%s: 2-D float64 CUDA tensor expected" % name)
+        if t.stride(1) != 1 or t.shape[0] < nb or t.shape[1] < nb or t.stride(0) < nb:
+            raise ValueError("%s: needs >= nb x nb with contiguous rows" % name)
+    if not (isinstance(off, torch.Tensor) and off.is_cuda and off.dtype == torch.int64 and off.is_contiguous()
+            and off.numel() >= nb * nb + 1):
+        raise ValueError("off: contiguous int64 CUDA tensor of >= nb*nb + 1 entries expected")
+    if klist is not None and not (isinstance(klist, torch.Tensor) and klist.is_cuda and klist.element_size() == 4
+                                  and klist.is_contiguous()):
+        raise ValueError("klist: contiguous CUDA tensor of 4-byte elements expected")
     cap = klist.numel() if klist is not None else 0
     _check(load().spamm_cull_noalloc(
         ctypes.c_void_p(n2a.data_ptr()), n2a.stride(0), ctypes.c_void_p(n2b.data_ptr()),

@@ -5,7 +5,10 @@
    rounded half-up to X = round(|x| 2^(7s - sigma)), cut into base-128 digits;
    slice pairs p + q < s summed exactly per diagonal d = p + q;
    C = RN(2^(sigmaA + sigmaB - 7s - 7) sum_d S_d 128^(s-1-d)).  The model
-   also confirms every |S_d| stays below 2^24, where FP32 sums are exact.
+   also confirms that the sum of the absolute values of every diagonal's
+   terms stays below 2^24, so that every partial FP32 sum is exact whatever
+   the order of accumulation.  Beyond that the diagonals round in FP32
+   (tested separately on a dense matrix near 0.99).
 2. Against the FP64 oracle (the definition of SpAMM) within the rigorous
    elementwise bound of the slicing:
      |dC_ij| <= sum_l over kept leaves of (|a_il| eb + ea |b_lj| + ea eb
@@ -62,12 +65,19 @@ def _model(a, b, leaf, tau, s):
     da = [pad(x) for x in da]
     db = [pad(x) for x in db]
     S = np.zeros((s, npad, npad), dtype=np.int64)
+    T = np.zeros((s, npad, npad), dtype=np.int64)   # sums of |terms| per diagonal
+    aa = [np.abs(x) for x in da]
+    ab = [np.abs(x) for x in db]
     for i, k, j in tasks:
         ri, rk, rj = slice(i * leaf, (i + 1) * leaf), slice(k * leaf, (k + 1) * leaf), slice(j * leaf, (j + 1) * leaf)
         for p in range(s):
             for q in range(s - p):
                 S[p + q, ri, rj] += da[p][ri, rk] @ db[q][rk, rj]
-    assert np.abs(S).max() < 2 ** 24, "model: FP32 sums would not be exact"
+                T[p + q, ri, rj] += aa[p][ri, rk] @ ab[q][rk, rj]
+    # every partial FP32 sum of a diagonal is exact when the sum of the
+    # absolute values of its terms stays below 2^24 (in whatever order the
+    # tensor core adds them): the condition under which the bits must match
+    assert T.max() < 2 ** 24, "model: FP32 sums would not be provably exact"
     cint = np.zeros((npad, npad), dtype=object)
     for d in range(s):
         cint = cint + S[d].astype(object) * (128 ** (s - 1 - d))
@@ -90,6 +100,67 @@ def test_mixed_spamm_bit_exact_vs_integer_model(cuda_lib, n, tau, s, seed, leaf)
     want, tasks, _, _ = _model(a, b, leaf, tau, s)
     assert st["tasks"] == len(tasks)
     assert np.array_equal(got, want), np.abs(got - want).max()
+
+
+def test_exact_slices_dense_near_constant_within_fp32_accumulation_bound(cuda_lib):
+    """A dense matrix of entries near 0.99 at N = 4096 (leaf 32, 7 slices,
+    tau = 0: 128 products per output leaf, all slices nonzero): the diagonal
+    sums reach about 2^26, beyond the 2^24 below which FP32 sums of integers
+    are exact.  The result is then the sliced product with each diagonal
+    rounded in FP32: on sampled output leaves it lies within that rounding
+    bound of the exact integer model (each accumulation step rounds to at
+    most 2 units of 2^-23 of the running magnitude, which the sum of |terms|
+    bounds), and within FP32-level relative accuracy of the FP64 product.
+    The combination of the diagonals must not overflow (it did in int64
+    before: S_0 2^42 > 2^63)."""
+    n, leaf, s = 4096, 32, 7
+    rng = np.random.default_rng(21)
+    a = 0.99 + 0.005 * rng.uniform(-1.0, 1.0, size=(n, n))
+    A = cuda_lib.tree_build(_dev(a), leaf=leaf)
+    C, st = cuda_lib.multiply(A, A, 0.0, prec=cuda_lib.OZAKI_BF16, slices=s, stats=True)
+    assert st["tasks"] == (n // leaf) ** 3
+    got = cuda_lib.to_dense(C).cpu().numpy()
+    da, sg = _digits(a, s)
+    e = 2 * sg - 7 * s - 7
+    worst = 0.0
+    for i, j in [(0, 0), (5, 77), (127, 3), (64, 64), (31, 100), (90, 127)]:
+        ri, rj = slice(i * leaf, (i + 1) * leaf), slice(j * leaf, (j + 1) * leaf)
+        Sd = [np.zeros((leaf, leaf), dtype=np.int64) for _ in range(s)]
+        Td = [np.zeros((leaf, leaf), dtype=np.int64) for _ in range(s)]
+        for p in range(s):
+            for q in range(s - p):
+                Sd[p + q] += da[p][ri, :] @ da[q][:, rj]
+                Td[p + q] += np.abs(da[p][ri, :]) @ np.abs(da[q][:, rj])
+        assert max(t.max() for t in Td) > 2 ** 24          # the case the test is about
+        exact = sum(Sd[d].astype(object) * (128 ** (s - 1 - d)) for d in range(s))
+        model = np.vectorize(lambda v: math.ldexp(float(v), e))(exact).astype(np.float64)
+        # accumulation steps into diagonal d of one element: (d + 1) slice
+        # pairs x 2 instructions (K = 16 each) for every one of the 128 k
+        bound = sum(math.ldexp(1.0, e + 7 * (s - 1 - d)) * (2 * (d + 1) * (n // leaf)) * 2.0 ** -22
+                    * Td[d].astype(np.float64) for d in range(s))
+        g = got[ri, rj]
+        assert np.all(np.abs(g - model) <= bound + 2.0 ** -52 * np.abs(model))
+        ref = a[ri, :] @ a[:, rj]
+        worst = max(worst, float(np.max(np.abs(g - ref) / np.abs(ref))))
+    assert worst < 1e-4, worst                         # FP32-level over 256 accumulation steps
+
+
+def test_sp2_slicing_overflow_is_reported(cuda_lib):
+    """SP2 slices its iterates with the fixed scale |x| < 2.  Culling every
+    product (tau huge) turns the iteration into X <- 2X while tr X < Ne, so
+    the iterate diag(0, ..., 0, 1) of F = diag(2, ..., 2, -2) reaches 4 in
+    its third iteration; the solve must fail with E_INVAL and say so, not
+    compute with saturated digits."""
+    n = 64
+    f = np.diag(np.r_[np.full(n - 1, 2.0), -2.0])
+    F = cuda_lib.tree_build(_dev(f), leaf=32)
+    with pytest.raises(cuda_lib.SpammError) as ei:
+        cuda_lib.sp2_solve(F, n / 2, 1e10, prec=cuda_lib.OZAKI_BF16, slices=7, fixed_iters=4)
+    assert ei.value.status == cuda_lib.E_INVAL
+    assert "slicing range" in str(ei.value)
+    # the same solve with FP64 leaf products runs (no slicing)
+    P, r = cuda_lib.sp2_solve(F, n / 2, 1e10, fixed_iters=4)
+    assert r["iters"] == 4
 
 
 @pytest.mark.parametrize("n,tau,s", [(512, 1e-6, 5), (384, 1e-8, 6), (256, 1e-3, 4)])

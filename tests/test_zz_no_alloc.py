@@ -69,3 +69,25 @@ def test_noalloc_rejects_oversize_and_reports_total(cuda_lib):
     cuda_lib.cull_noalloc(_norm_grid(cuda_lib, A), _norm_grid(cuda_lib, A), A.nb, 1e-6, off, None)
     torch.cuda.synchronize()
     assert np.array_equal(off.cpu().numpy(), ref_off)
+
+
+def test_noalloc_binding_checks_the_tensors(cuda_lib):
+    """The binding checks what the C call cannot: device, element type,
+    contiguous rows and sizes (a short off or a 2-byte klist would let the
+    kernels write past the caller's buffers)."""
+    import torch
+    nb = 8
+    n2 = torch.ones((nb, nb), dtype=torch.float64, device="cuda")
+    off = torch.zeros((nb * nb + 1,), dtype=torch.int64, device="cuda")
+    k = torch.zeros((16,), dtype=torch.int32, device="cuda")
+    bad = [
+        (n2.float(), n2, off, k),                                         # float32 norms
+        (n2.cpu(), n2, off, k),                                           # host tensor
+        (n2[:, :4], n2, off, k),                                          # fewer than nb columns
+        (n2.t().contiguous().t()[:, :], n2, off[:-1], k),                 # off too short
+        (n2, n2, off, torch.zeros((16,), dtype=torch.int16, device="cuda")),  # 2-byte klist
+        (n2, n2, off.int(), k),                                           # int32 offsets
+    ]
+    for a, b, o, kk in bad:
+        with pytest.raises(ValueError):
+            cuda_lib.cull_noalloc(a, b, nb, 1e-6, o, kk)
