@@ -579,7 +579,7 @@ int ws_check_errors(SpammWorkspace *ws, cudaStream_t s)
 int spamm_multiply_into(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t C,
                         const spamm_opts_t *opts, double *tr_part, cudaStream_t s,
                         bool need_total, int64_t *tasks_out, bool build_pyramid,
-                        cudaEvent_t *ev, int sym, bool slices_ready, bool zero_empty)
+                        cudaEvent_t *ev, int sym, bool slices_ready, bool zero_empty, bool mirror)
 {
     int prec = opts ? opts->prec : SPAMM_FP64;
     if (ev) SPAMM_CK(spamm_event_record(ev[0], s));
@@ -609,6 +609,7 @@ int spamm_multiply_into(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t C,
         const bool heavy = opts && (opts->flags & SPAMM_F_HEAVIEST);
         if ((rc = tc_tile_cull(A, B, tau, ws, symm, sl, s, heavy))) return rc;
         if (zero_empty && (rc = tc_zero_empty_tiles(C, ws, s))) return rc;
+        ws->tmirror = mirror ? 1 : 0;
         if (ev) SPAMM_CK(spamm_event_record(ev[1], s));
         rc = launch_gemm_tc(A, B, C, ws, tr_part, sl, el, s, fsplit);
         if (rc) return rc;

@@ -518,6 +518,7 @@ static void fill_prob(tc::TcProb &p, spamm_mat_t A, spamm_mat_t B, spamm_mat_t C
     p.pos0 = pos0;
     p.sym = ws->tsym;
     p.tw = ws->tw;
+    p.mirror = ws->tmirror;
 }
 
 static int launch_args(tc::TcArgs &a, int leaf, int slices, int e, cudaStream_t s)

@@ -51,6 +51,7 @@ struct SpammWorkspace {
     const int32_t *stop = nullptr;        // device flag: when set, the product's kernels return at once
     int tsym = 0;                         // last tile cull was symmetric
     int tw = 1;                           // output leaf columns per tile of the last tile cull
+    int tmirror = 1;                      // symmetric tensor-core product: also store C_ji = C_ij^T
     int64_t tT = 0;                       // tiles of the last tile cull (totals at toff + tT)
     uint32_t *cmask = nullptr;            // tile cull: passing coarse k-blocks per coarse (row, column) pair
     int64_t cmask_cap = 0;                // uint32 words
@@ -164,12 +165,15 @@ bool spamm_cull_never_waits(int64_t nb);
 // C's upper norm tiers.
 // sym: A == B is exactly symmetric; both paths then form only the upper
 // block triangle of C and mirror it (bit-identical, half the work).
+// mirror = false (symmetric tensor path): only the leaves i <= j are
+// stored; the caller reads C_ji as the transpose of C_ij (SP2 does).
 // zero_empty = false (tensor path): leaves of tiles without work are left
 // unwritten; the caller treats them as zero through ws->toff (SP2 does).
 int spamm_multiply_into(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t C,
                         const spamm_opts_t *opts, double *tr_part, cudaStream_t s,
                         bool need_total, int64_t *tasks_out, bool build_pyramid,
-                        cudaEvent_t *ev, int sym = 0, bool slices_ready = false, bool zero_empty = true);
+                        cudaEvent_t *ev, int sym = 0, bool slices_ready = false, bool zero_empty = true,
+                        bool mirror = true);
 
 // Read and clear the device-side error words of a product (blocking).
 int ws_check_errors(SpammWorkspace *ws, cudaStream_t s);

@@ -287,7 +287,7 @@ k_sp2_elementwise(int mode, double *__restrict__ X, const double *__restrict__ s
                   const int32_t *__restrict__ slot, const int32_t *__restrict__ src_slot, int64_t n, int64_t nb,
                   int64_t P, double *__restrict__ n2, double *__restrict__ n2T, double *__restrict__ idem_part,
                   double *__restrict__ diag_part, Sp2State *st, Sp2Rule rule, double *__restrict__ hist,
-                  const int32_t *__restrict__ x2cnt, int R, int tw, int sym)
+                  const int32_t *__restrict__ x2cnt, int R, int tw, int sym, int tlow)
 {
     constexpr int BB = B * B;
     constexpr int kPer = BB / 32;              // elements per lane
@@ -305,7 +305,10 @@ k_sp2_elementwise(int mode, double *__restrict__ X, const double *__restrict__ s
         const int64_t I = w / nb, K = w % nb;
         double *x = X + (int64_t)slot[w] * BB;
         // the source in mode 0 is F, which may leave zero leaves unstored
-        const int32_t ss = src_slot[w];
+        // mode 1 with tlow: X2 stores only its leaves I <= K, a lower leaf
+        // is read as the transpose of leaf (K, I)
+        const bool tr = mode == 1 && tlow && I > K;
+        const int32_t ss = src_slot[tr ? K * nb + I : w];
         const double *y = src + (int64_t)(ss < 0 ? 0 : ss) * BB;
         const bool diag = I == K;
         bool y0 = ss < 0;  // source leaf known to be zero
@@ -344,7 +347,7 @@ k_sp2_elementwise(int mode, double *__restrict__ X, const double *__restrict__ s
 #pragma unroll
                 for (int u = 0; u < kCh; u++) {
                     const int q = lane + 32 * (c0 + u);
-                    yv[u] = y0 ? 0.0 : y[q];
+                    yv[u] = y0 ? 0.0 : y[tr ? (q % B) * B + q / B : q];
                     xv[u] = K != 0 ? x[q] : 0.0;
                 }
 #pragma unroll
@@ -439,29 +442,29 @@ template <int B>
 void launch_elementwise_b(cudaStream_t s, int mode, double *X, const double *src, const int32_t *slot,
                           const int32_t *src_slot, int64_t n, int64_t nb, int64_t P, double *n2, double *n2T,
                           double *idem_part, double *diag_part, Sp2State *st, Sp2Rule rule, double *hist,
-                          const int32_t *x2cnt, int R, int tw, int sym)
+                          const int32_t *x2cnt, int R, int tw, int sym, int tlow)
 {
     const int64_t cap = ew_grid_cap<B>();
     const int64_t need = (nb * nb + kEwWarps - 1) / kEwWarps;
     const unsigned grid = (unsigned)(need < cap ? need : cap);
     k_sp2_elementwise<B><<<grid, kEwWarps * 32, 0, s>>>(mode, X, src, slot, src_slot, n, nb, P, n2, n2T, idem_part,
-                                                    diag_part, st, rule, hist, x2cnt, R, tw, sym);
+                                                    diag_part, st, rule, hist, x2cnt, R, tw, sym, tlow);
 }
 
 void launch_elementwise(int b, cudaStream_t s, int mode, double *X, const double *src, const int32_t *slot,
                         const int32_t *src_slot, int64_t n, int64_t nb, int64_t P, double *n2, double *n2T,
                         double *idem_part, double *diag_part, Sp2State *st, Sp2Rule rule, double *hist,
-                        const int32_t *x2cnt, int R, int tw, int sym)
+                        const int32_t *x2cnt, int R, int tw, int sym, int tlow = 0)
 {
     if (b == 16)
         launch_elementwise_b<16>(s, mode, X, src, slot, src_slot, n, nb, P, n2, n2T, idem_part, diag_part, st,
-                                 rule, hist, x2cnt, R, tw, sym);
+                                 rule, hist, x2cnt, R, tw, sym, tlow);
     else if (b == 32)
         launch_elementwise_b<32>(s, mode, X, src, slot, src_slot, n, nb, P, n2, n2T, idem_part, diag_part, st,
-                                 rule, hist, x2cnt, R, tw, sym);
+                                 rule, hist, x2cnt, R, tw, sym, tlow);
     else
         launch_elementwise_b<64>(s, mode, X, src, slot, src_slot, n, nb, P, n2, n2T, idem_part, diag_part, st,
-                                 rule, hist, x2cnt, R, tw, sym);
+                                 rule, hist, x2cnt, R, tw, sym, tlow);
 }
 
 
@@ -664,8 +667,10 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
         auto enqueue = [&](cudaStream_t st, int batch) -> int {
             for (int q = 0; q < batch; q++) {
                 cudaEvent_t *ev = timing ? evs + 5 * q : nullptr;
+                // tensor path, symmetric: X2 keeps only its leaves i <= j (the
+                // update reads a lower leaf as the transpose of its mirror)
                 int r = spamm_multiply_into(X, X, tau, X2, &mo, sc.tr_part, st, false, nullptr, false, ev,
-                                            sym ? 1 : 0, false, !tcpath);
+                                            sym ? 1 : 0, false, !tcpath, !(tcpath && sym));
                 if (r) return r;
                 const int32_t *x2cnt = tcpath ? X2->ws.tcounts : nullptr;
                 k_sp2_decide<<<1, kRedThreads, 0, st>>>(sc.tr_part, tcpath ? 2 * nb : nb, X2->ws.task_total,
@@ -674,7 +679,7 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
                 SPAMM_CK_LAUNCH();
                 launch_elementwise(X->b, st, 1, X->leaf, X2->leaf, X->slot, X2->slot, F->n, nb, X->P,
                                    X->n2 + tier_offset(X->depth), X->n2T, sc.idem_part, sc.diag_part, sc.st, rule,
-                                   sc.hist, x2cnt, 128 / X->b, X2->ws.tw, sym ? 1 : 0);
+                                   sc.hist, x2cnt, 128 / X->b, X2->ws.tw, sym ? 1 : 0, (tcpath && sym) ? 1 : 0);
                 SPAMM_CK_LAUNCH();
                 if (coarse && (r = launch_pyramid(X, st))) return r;
                 if (timing) SPAMM_CK(spamm_event_record(ev[4], st));

@@ -377,6 +377,7 @@ struct TcProb {
     int64_t pos0;          // first hand-out position of this product
     int32_t sym;           // symmetric product: upper block triangle + mirror
     int32_t tw;            // output leaf columns per tile of its work lists
+    int32_t mirror;        // symmetric product: also store C_ji = C_ij^T (else leaves i <= j only)
 };
 
 struct TcArgs {
@@ -828,7 +829,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                 const bool store = i < nb && (!P.sym || i <= j);
                 double *dst = store ? P.leafC + (int64_t)P.slotC[i * nb + j] * (B * B) + r * B : nullptr;
                 double *mir =
-                    (store && P.sym && i < j) ? P.leafC + (int64_t)P.slotC[j * nb + i] * (B * B) + r : nullptr;
+                    (store && P.sym && P.mirror && i < j) ? P.leafC + (int64_t)P.slotC[j * nb + i] * (B * B) + r
+                                                          : nullptr;
                 const uint32_t tbase = tmem + acc * kAccStride + c * kColAcc + lane_off;
                 if (i == j) on_diag = true;
                 int dc = S;  // d0 of column c (static indexing of d0[])
