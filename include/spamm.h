@@ -361,10 +361,12 @@ typedef struct {
     double emin, emax;    /* Gershgorin bounds of F                        */
     int64_t tasks_total;  /* surviving leaf triples over all iterations    */
     double flops_useful;  /* 2 b^3 tasks_total                             */
-    double flops_tensor;  /* tensor-core work of the surviving products:
-                             2 b^3 per slice pair that is not identically
-                             zero (leading zero slices skipped), products
-                             of the mirrored half excluded; FP64: = above */
+    double flops_tensor;  /* arithmetic of the leaf products formed:
+                             tensor path: 2 b^3 per slice pair of a
+                             surviving product that is not identically
+                             zero (leading zero slices skipped); FP64:
+                             2 b^3 per leaf product formed; both exclude
+                             the mirrored half of a symmetric product */
     double ms_total;      /* device time of the whole solve                */
     double ms_cull;       /* SPAMM_F_TIMING: summed time of cull (+ slicing) */
     double ms_gemm;       /*   ... of the leaf products                     */

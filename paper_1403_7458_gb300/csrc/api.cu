@@ -241,6 +241,7 @@ static void ws_free(SpammWorkspace *ws, cudaStream_t s)
     spamm_release(ws->klist, s);
     spamm_release(ws->counter, s);
     spamm_release(ws->tr_part, s);
+    spamm_release(ws->exec, s);
     spamm_release(ws->scan_part, s);
     spamm_release(ws->cmask, s);
     *ws = SpammWorkspace();
@@ -518,6 +519,7 @@ int ws_reserve_groups(SpammWorkspace *ws, int64_t groups, int64_t nb, cudaStream
         if ((rc = spamm_alloc((void **)&ws->counter, sizeof(int32_t) * 16, s))) return rc;
         SPAMM_CK(cudaMemsetAsync(ws->counter, 0, sizeof(int32_t) * 16, s));
     }
+    if (!ws->exec && (rc = spamm_alloc((void **)&ws->exec, sizeof(int64_t), s))) return rc;
     if (ws->tr_cap < nb) {
         spamm_release(ws->tr_part, s);
         ws->tr_part = nullptr;
@@ -591,7 +593,7 @@ int spamm_multiply_into(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t C,
         rc = spamm_cull(A, B, tau, ws, A->nb, A->P, s, need_total, &total);
         if (rc) return rc;
         ws->task_total = ws->off + A->nb * A->nb;
-        ws->pair_units = nullptr;
+        ws->pair_units = ws->exec;  // leaf products formed (half of them when symmetric)
         if (ev) SPAMM_CK(spamm_event_record(ev[1], s));
         rc = launch_gemm_fp64(A, B, C, ws, tr_part, s, (sym && A == B) ? 1 : 0);
     } else if (prec_is_tc(prec)) {

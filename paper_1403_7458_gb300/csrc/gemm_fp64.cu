@@ -49,6 +49,7 @@ struct FpProb {
     double *tr_part;
     int64_t g0;  // first output-leaf number of this product
     int32_t sym; // A == B exactly symmetric: only leaves i <= j are formed, C_ji = C_ij^T
+    int64_t *exec;  // leaf products formed (may be null)
 };
 
 struct GemmArgs {
@@ -113,6 +114,8 @@ __global__ void __launch_bounds__(kThreads) k_gemm_fp64(const __grid_constant__ 
 
     if (g.stop && *g.stop) return;
     const int tid = threadIdx.x;
+    int64_t formed = 0;      // leaf products this CTA formed (thread 0)
+    int64_t *exec_out = nullptr;
     const int r0 = (tid / T::COLT) * T::TR;
     const int c0 = (tid % T::COLT) * T::TC;
     const int64_t G = g.G;
@@ -131,6 +134,8 @@ __global__ void __launch_bounds__(kThreads) k_gemm_fp64(const __grid_constant__ 
         }
         const int64_t grp = i * P.nb + j;
         const int64_t t0 = P.off[grp], t1 = P.off[grp + 1];
+        formed += t1 - t0;
+        exec_out = P.exec;
 
         double acc[T::TR][T::TC];
 #pragma unroll
@@ -228,6 +233,8 @@ __global__ void __launch_bounds__(kThreads) k_gemm_fp64(const __grid_constant__ 
         }
         __syncthreads();
     }
+    if (tid == 0 && exec_out && formed) atomicAdd(reinterpret_cast<unsigned long long *>(exec_out),
+                                                  (unsigned long long)formed);
 }
 
 template <int B>
@@ -267,6 +274,7 @@ static void fill_prob(FpProb &p, spamm_mat_t A, spamm_mat_t B, spamm_mat_t C, Sp
     p.tr_part = tr_part;
     p.g0 = g0;
     p.sym = 0;
+    p.exec = nullptr;
 }
 
 static int launch_args(GemmArgs &g, int leaf, cudaStream_t s)
@@ -288,6 +296,8 @@ int launch_gemm_fp64(spamm_mat_t A, spamm_mat_t B, spamm_mat_t C, SpammWorkspace
     thread_local GemmArgs g;  // large (one table entry used); host-side staging only
     fill_prob(g.p[0], A, B, C, ws, tr_part, 0);
     g.p[0].sym = sym ? 1 : 0;
+    g.p[0].exec = ws->exec;
+    if (ws->exec) SPAMM_CK(cudaMemsetAsync(ws->exec, 0, sizeof(int64_t), s));
     g.nprob = 1;
     g.G = sym ? A->nb * (A->nb + 1) / 2 : A->nb * A->nb;
     g.counter = ws->counter;

@@ -29,6 +29,7 @@ struct SpammWorkspace {
     int64_t klist_cap = 0;
     int64_t groups_cap = 0;
     int32_t *counter = nullptr;  // work counters and error flags (16 ints)
+    int64_t *exec = nullptr;     // FP64 path: leaf products formed by the last product
     double *tr_part = nullptr;   // per leaf row partial traces (nb)
     int64_t tr_cap = 0;
     // tensor-core path: tile work lists (tile t = I * nbt + J: leaf rows

@@ -1,8 +1,9 @@
 // norms.cu -- the norm quadtree (Sec. 2, Eqs. 1-3).
 //
-// Leaf tier: one warp per leaf reads the b x b FP64 block once (coalesced,
-// 16-byte loads), finds the largest exponent, and accumulates the squares in
-// 128-bit fixed point (order-independent, see internal.cuh).  The squared norm
+// Leaf tier: one warp per leaf reads the b x b FP64 block (coalesced, 16-byte
+// loads; once, kept in registers, for b <= 32), finds the largest exponent,
+// and accumulates the squares in 128-bit fixed point (order-independent, see
+// internal.cuh).  The squared norm
 // is rounded once and written to the leaf grid and to its transpose.
 // Upper tiers: each parent is the once-rounded exact sum of its four children
 // (Eq. 3, squared); one kernel per group of up to five tiers.
@@ -41,6 +42,45 @@ k_leaf_norms(const double *__restrict__ leaf, const int32_t *__restrict__ slot, 
                 double2 v = __ldg(src + q);
                 acc += sq_term(v.x, emax) + sq_term(v.y, emax);
             }
+            acc = warp_sum_u128(acc);
+            r = sq_sum_round(acc, emax);
+        }
+    }
+    if (lane == 0) {
+        n2[I * P + K] = r;
+        n2T[K * P + I] = r;
+    }
+}
+
+// The same for leaves of up to 32 x 32: each lane keeps its b^2 / 32 values
+// in registers between the exponent pass and the accumulation, so every
+// leaf is read from memory once.
+template <int B>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
+k_leaf_norms_reg(const double *__restrict__ leaf, const int32_t *__restrict__ slot, int64_t nb, int64_t P,
+                 double *__restrict__ n2, double *__restrict__ n2T)
+{
+    constexpr int NV = B * B / 64;  // 16-byte loads per lane
+    static_assert(NV >= 1 && B * B % 64 == 0, "leaf too small");
+    const int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (w >= P * P) return;
+    const int64_t I = w / P, K = w % P;
+    double r = 0.0;
+    const int32_t s = (I < nb && K < nb) ? slot[I * nb + K] : -1;
+    if (s >= 0) {  // warp-uniform
+        const double2 *src = reinterpret_cast<const double2 *>(leaf + (int64_t)s * (B * B));
+        double2 v[NV];
+#pragma unroll
+        for (int u = 0; u < NV; u++) v[u] = __ldg(src + lane + 32 * u);
+        int emax = 0;
+#pragma unroll
+        for (int u = 0; u < NV; u++) emax = max(emax, max(exp_key(v[u].x), exp_key(v[u].y)));
+        emax = warp_max_int(emax);
+        if (emax > 0) {
+            u128 acc = 0;
+#pragma unroll
+            for (int u = 0; u < NV; u++) acc += sq_term(v[u].x, emax) + sq_term(v[u].y, emax);
             acc = warp_sum_u128(acc);
             r = sq_sum_round(acc, emax);
         }
@@ -101,8 +141,16 @@ int launch_leaf_norms(spamm_mat_t m, cudaStream_t s)
 {
     int64_t leaves = m->P * m->P;
     int64_t blocks = (leaves + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    k_leaf_norms<<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(
-        m->leaf, m->slot, m->nb, m->P, m->b * m->b, m->n2 + tier_offset(m->depth), m->n2T);
+    double *n2 = m->n2 + tier_offset(m->depth);
+    if (m->b == 16)
+        k_leaf_norms_reg<16><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(m->leaf, m->slot, m->nb, m->P, n2,
+                                                                               m->n2T);
+    else if (m->b == 32)
+        k_leaf_norms_reg<32><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(m->leaf, m->slot, m->nb, m->P, n2,
+                                                                               m->n2T);
+    else  // 64 x 64 leaves: 128 values per lane would not stay in registers; two reads
+        k_leaf_norms<<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(m->leaf, m->slot, m->nb, m->P, m->b * m->b,
+                                                                      n2, m->n2T);
     SPAMM_CK_LAUNCH();
     return launch_pyramid(m, s);
 }

@@ -781,8 +781,7 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
         report->emax = h.emax;
         report->tasks_total = tasks_total;
         report->flops_useful = 2.0 * double(F->b) * F->b * F->b * double(tasks_total);
-        report->flops_tensor = prec_is_tc(o.prec) ? 2.0 * double(F->b) * F->b * F->b * double(h.units)
-                                                  : report->flops_useful;
+        report->flops_tensor = 2.0 * double(F->b) * F->b * F->b * double(h.units);
         report->ms_total = ms;
         report->ms_cull = ms_cull;
         report->ms_gemm = ms_gemm;

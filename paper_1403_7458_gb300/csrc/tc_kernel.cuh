@@ -440,6 +440,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
     __shared__ __align__(8) uint64_t accf_bar[2], acce_bar[2], done_bar;
     __shared__ uint32_t slot_off[kSlots];  // ring byte offset of each in-flight item
     __shared__ uint32_t slot_w[kSlots];    // its work-list entry
+    __shared__ unsigned long long slot_end[kSlots];  // its end in the producer's cumulative ring pointer
     __shared__ int32_t tile_q[kTileRing];  // tiles handed out (product << 24 | tile), -1 = no more
     __shared__ __align__(8) uint64_t tfull_bar[kTileRing], tempty_bar[kTileRing];
     __shared__ uint32_t tmem_holder;
@@ -489,7 +490,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
         // then allocates ring space and issues the copies item by item.
         // cumulative byte pointers (allocation incl. wrap padding, release)
         unsigned long long alloc_ptr = 0, free_ptr = 0;
-        unsigned long long end_ptr[kSlots];
+        uint32_t ring_pos = 0;  // alloc_ptr modulo the ring size
         uint32_t issued = 0, released = 0;
         bool ok = true;
         uint32_t tq = 0, tph = 0;
@@ -553,85 +554,86 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                             bl[c] = P.sym ? P.slotA[j * nb + kk] : P.slotB[kk * nb + j];
                     }
                 }
+                // The whole warp runs the per-item bookkeeping (the values are
+                // uniform across its lanes, so it never diverges); lane 0 alone
+                // issues the copies.
                 for (int q = 0; q < cnt; q++) {
                     const uint32_t w = __shfl_sync(0xffffffffu, wl, q);
                     int64_t bslot[W];
 #pragma unroll
                     for (int c = 0; c < W; c++) bslot[c] = __shfl_sync(0xffffffffu, bl[c], q);
-                    int good = 1;
+                    const int64_t k = item_k(w);
+                    const int za = item_za(w);
+                    int mc[W], mA = 0;
+                    uint32_t need = 0;
+#pragma unroll
+                    for (int c = 0; c < W; c++) {
+                        // slices needed from column c's B leaf (none: column absent)
+                        mc[c] = item_mask_col<R, W>(w, c) ? S - za - item_zb_col(w, c) : 0;
+                        mA = mc[c] > mA ? mc[c] : mA;
+                        need += (uint32_t)mc[c] * kSlice;
+                    }
+                    need += (uint32_t)mA * R * kSlice;
+                    if (ring_pos + need > kRingBytes) {  // the item does not fit before the end: wrap
+                        alloc_ptr += kRingBytes - ring_pos;
+                        ring_pos = 0;
+                    }
+                    const uint32_t pos = ring_pos;
+                    const unsigned long long new_end = alloc_ptr + need;
+                    // wait (in order) for released items until the region and a slot are free
+                    for (;;) {
+                        // nothing in flight: the wrap padding before the region holds
+                        // nothing either (an item larger than the space left after the
+                        // last wrap would otherwise wait for space that never frees)
+                        if (released == issued) free_ptr = alloc_ptr;
+                        if (new_end - free_ptr <= kRingBytes && issued - released < (uint32_t)kSlots) break;
+                        const uint32_t rs = released % kSlots;
+                        if (!mbar_wait(smem_u32(&empty_bar[rs]), (released / kSlots) & 1, abort_v)) {
+                            ok = false;
+                            break;
+                        }
+                        free_ptr = slot_end[rs];
+                        released++;
+                    }
+                    ok = __all_sync(0xffffffffu, ok);
+                    if (!ok) break;
+                    const uint32_t sl = issued % kSlots;
                     if (lane == 0) {
-                        const int64_t k = item_k(w);
-                        const int za = item_za(w);
-                        int mc[W], mA = 0;
-                        uint32_t need = 0;
+                        slot_off[sl] = pos;
+                        slot_w[sl] = w;
+                        slot_end[sl] = new_end;
+                        const uint32_t fb = smem_u32(&full_bar[sl]);
+                        uint32_t dst = sbase + pos;
+                        mbar_expect_tx(fb, need);
+                        // A: slices za..za+mA-1 of the R rows' leaves, one contiguous block
+                        bulk_g2s(dst, P.slA + ((I * nb + k) * S + za) * (int64_t)(R * kSlice),
+                                 (uint32_t)mA * R * kSlice, fb);
+                        dst += (uint32_t)mA * R * kSlice;
+                        // B: slices zb..S-1-za of leaf (k, j) per present column
+                        // (symmetric: leaf (j, k), from the tile-major array
+                        // when tensor maps are given)
 #pragma unroll
                         for (int c = 0; c < W; c++) {
-                            // slices needed from column c's B leaf (none: column absent)
-                            mc[c] = item_mask_col<R, W>(w, c) ? S - za - item_zb_col(w, c) : 0;
-                            mA = mc[c] > mA ? mc[c] : mA;
-                            need += (uint32_t)mc[c] * kSlice;
-                        }
-                        need += (uint32_t)mA * R * kSlice;
-                        uint32_t pos = (uint32_t)(alloc_ptr % kRingBytes);
-                        if (pos + need > kRingBytes) {
-                            alloc_ptr += kRingBytes - pos;
-                            pos = 0;
-                        }
-                        const unsigned long long new_end = alloc_ptr + need;
-                        // wait (in order) for released items until the region and a slot are free
-                        for (;;) {
-                            // nothing in flight: the wrap padding before the region holds
-                            // nothing either (an item larger than the space left after the
-                            // last wrap would otherwise wait for space that never frees)
-                            if (released == issued) free_ptr = alloc_ptr;
-                            if (new_end - free_ptr <= kRingBytes && issued - released < (uint32_t)kSlots) break;
-                            const uint32_t rs = released % kSlots;
-                            if (!mbar_wait(smem_u32(&empty_bar[rs]), (released / kSlots) & 1, abort_v)) {
-                                good = 0;
-                                break;
+                            if (mc[c] <= 0) continue;
+                            if (P.tmB) {
+                                const int64_t j = W * J + c;
+                                tma_load_5d(dst, static_cast<const uint8_t *>(P.tmB) + 128 * (mc[c] - 1), 0, 0,
+                                            (int)(j % R), item_zb_col(w, c), (int)((j / R) * nb + k), fb);
+                            } else {
+                                bulk_g2s(dst,
+                                         P.slB + bslot[c] * (int64_t)(S * kSlice) + item_zb_col(w, c) * kSlice,
+                                         (uint32_t)mc[c] * kSlice, fb);
                             }
-                            free_ptr = end_ptr[rs];
-                            released++;
-                        }
-                        if (good) {
-                            const uint32_t sl = issued % kSlots;
-                            slot_off[sl] = pos;
-                            slot_w[sl] = w;
-                            end_ptr[sl] = new_end;
-                            alloc_ptr = new_end;
-                            const uint32_t fb = smem_u32(&full_bar[sl]);
-                            uint32_t dst = sbase + pos;
-                            mbar_expect_tx(fb, need);
-                            // A: slices za..za+mA-1 of the R rows' leaves, one contiguous block
-                            bulk_g2s(dst, P.slA + ((I * nb + k) * S + za) * (int64_t)(R * kSlice),
-                                     (uint32_t)mA * R * kSlice, fb);
-                            dst += (uint32_t)mA * R * kSlice;
-                            // B: slices zb..S-1-za of leaf (k, j) per present column
-                            // (symmetric: leaf (j, k), from the tile-major array
-                            // when tensor maps are given)
-#pragma unroll
-                            for (int c = 0; c < W; c++) {
-                                if (mc[c] <= 0) continue;
-                                if (P.tmB) {
-                                    const int64_t j = W * J + c;
-                                    tma_load_5d(dst, static_cast<const uint8_t *>(P.tmB) + 128 * (mc[c] - 1), 0, 0,
-                                                (int)(j % R), item_zb_col(w, c), (int)((j / R) * nb + k), fb);
-                                } else {
-                                    bulk_g2s(dst,
-                                             P.slB + bslot[c] * (int64_t)(S * kSlice) + item_zb_col(w, c) * kSlice,
-                                             (uint32_t)mc[c] * kSlice, fb);
-                                }
-                                dst += (uint32_t)mc[c] * kSlice;
-                            }
-                            issued++;
+                            dst += (uint32_t)mc[c] * kSlice;
                         }
                     }
-                    if (!__shfl_sync(0xffffffffu, good, 0)) {
-                        ok = false;
-                        break;
-                    }
+                    __syncwarp();
+                    alloc_ptr = new_end;
+                    ring_pos += need;
+                    issued++;
                 }
             }
+            if (!ok) break;  // a wait gave up: no further tiles
         }
         if (lane == 0) {
             if (!ok) {

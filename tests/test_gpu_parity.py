@@ -182,6 +182,10 @@ def test_sp2_fp64_symmetric_mode_is_bit_identical(cuda_lib, n, b):
     assert np.array_equal(ps, cuda_lib.to_dense(Pf).cpu().numpy())
     assert np.array_equal(ps, ps.T)
     assert np.array_equal(rs["history"], rf["history"])
+    # leaf products formed: all of them in the full product, the upper block
+    # triangle (diagonal leaves once, the others for both) when symmetric
+    assert rf["flops_tensor"] == rf["flops_useful"]
+    assert rs["flops_useful"] / 2 <= rs["flops_tensor"] < rs["flops_useful"]
 
 
 def test_sp2_first_iterations_config1_size(cuda_lib):
