@@ -812,16 +812,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                     if (d0[c] > S) d0[c] = S;
                 }
             }
+            // the output leaves' slots and the scale, loaded while the tile's
+            // products are still running
+            const int64_t i = (int64_t)R * I + L;
+            const int kexp = g.float_split ? 0 : *P.sigA + *P.sigB - 7 * S - 7;
+            int32_t oslot[W];
+#pragma unroll
+            for (int c = 0; c < W; c++) {
+                const int64_t j = W * J + c;
+                oslot[c] = (i < nb && j < nb && (!P.sym || i <= j)) ? __ldg(P.slotC + i * nb + j) : 0;
+            }
             if (!mbar_wait(smem_u32(&accf_bar[acc]), aph, abort_v)) {
                 if (lane == 0) atomicExch(g.err, 1);
                 abort_flag = 1;
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int64_t i = (int64_t)R * I + L;
-            const int kexp = g.float_split ? 0 : *P.sigA + *P.sigB - 7 * S - 7;
             double diag = 0.0;
             bool on_diag = false;
+            bool released = false;  // this warp has released the accumulator
 #pragma unroll 1
             for (int c = 0; c < W; c++) {
                 const int64_t j = W * J + c;
@@ -829,7 +838,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                 // symmetric mode: leaf (i, j) is written only for i <= j, and for
                 // i < j its transpose goes to leaf (j, i)
                 const bool store = i < nb && (!P.sym || i <= j);
-                double *dst = store ? P.leafC + (int64_t)P.slotC[i * nb + j] * (B * B) + r * B : nullptr;
+                int32_t osl = 0;  // oslot[c] (static indexing)
+#pragma unroll
+                for (int cc = 0; cc < W; cc++)
+                    if (cc == c) osl = oslot[cc];
+                double *dst = store ? P.leafC + (int64_t)osl * (B * B) + r * B : nullptr;
                 double *mir =
                     (store && P.sym && P.mirror && i < j) ? P.leafC + (int64_t)P.slotC[j * nb + i] * (B * B) + r
                                                           : nullptr;
@@ -843,6 +856,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                 for (int hh = 0; hh < HPM; hh++) {
                     const int h = h_lo + hh;
                     if (h >= h_hi) break;  // warp-uniform
+                    // the last group of the tile this warp handles: once its
+                    // values are in registers and its columns cleared, the
+                    // accumulator is released (the combination and the stores
+                    // below need no tensor memory)
+                    const bool last = (h + 1 >= h_hi) && (c + 1 >= W || W * J + c + 1 >= nb);
                     // the S diagonals of these 16 columns: all loads issued,
                     // one wait, the accumulator zeroed for the next tile
                     uint32_t v[S][16];
@@ -863,6 +881,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                         for (int d = 0; d < S; d++)
 #pragma unroll
                             for (int q = 0; q < 16; q++) v[d][q] = 0u;
+                    }
+                    if (last && !released) {
+                        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(smem_u32(&acce_bar[acc]));
+                        released = true;
                     }
                     // exact slices: integer combination; float split: FP64 sum
                     double res[16];
@@ -894,10 +919,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                     }
                 }
             }
-            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&acce_bar[acc]));
+            if (!released) {  // no group of this warp (e.g. every column past the matrix)
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&acce_bar[acc]));
+            }
             if (++acc == (uint32_t)kNAcc) {
                 acc = 0;
                 aph ^= 1;
