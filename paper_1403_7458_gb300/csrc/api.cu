@@ -231,6 +231,7 @@ static void ws_free(SpammWorkspace *ws, cudaStream_t s)
     spamm_release(ws->ttasks, s);
     spamm_release(ws->tpairs, s);
     spamm_release(ws->tuseful, s);
+    spamm_release(ws->td0, s);
     spamm_release(ws->toff, s);
     spamm_release(ws->torder, s);
     spamm_release(ws->tnz, s);

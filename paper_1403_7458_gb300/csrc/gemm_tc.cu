@@ -34,41 +34,79 @@ struct CullArgs {
     const int32_t *stop;  // set once an SP2 loop has stopped: nothing to do
 };
 
+// The A side of the candidates k of one step (one per lane): the squared
+// norms and leading-zero counts of the R leaves (i, k), i = R I .. R I + R-1,
+// loaded once and tested against every tile column of the warp.
+template <int R>
+struct StepA {
+    double a[R];
+    int z[R];
+    __device__ __forceinline__ bool any() const
+    {
+        bool v = false;
+#pragma unroll
+        for (int r = 0; r < R; r++) v = v || a[r] != 0.0;
+        return v;
+    }
+};
+
+template <int R>
+__device__ __forceinline__ void load_step_a(const CullArgs &c, int64_t I, int64_t k, StepA<R> &s)
+{
+    // every load of the candidate issued before any is used (one round trip)
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        const int64_t i = (int64_t)R * I + r;
+        const bool in = k < c.nb && i < c.nb;
+        s.a[r] = in ? __ldg(c.n2A + i * c.P + k) : 0.0;
+        s.z[r] = (in && c.denseA) ? c.zA[i * c.nb + k] : 0;
+    }
+    if (!c.denseA)
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int64_t i = (int64_t)R * I + r;
+            // a leaf of nonzero norm is stored (its slot is valid)
+            if (s.a[r] != 0.0) s.z[r] = c.zA[c.slotA[i * c.nb + k]];
+        }
+}
+
+// Leading-zero slices of the B operand leaf (k, j) (symmetric: its image is
+// leaf (j, k)'s A role): from an identity slot map, else -1 (to be looked up
+// through the slot map once the leaf is known to be stored).
+__device__ __forceinline__ int zb_dense(const CullArgs &c, int64_t j, int64_t k)
+{
+    if (c.sym) return c.denseA ? c.zA[j * c.nb + k] : -1;
+    return c.denseB ? c.zB[k * c.nb + j] : -1;
+}
+__device__ __forceinline__ int zb_slot(const CullArgs &c, int64_t j, int64_t k)
+{
+    return c.sym ? c.zA[c.slotA[j * c.nb + k]] : c.zB[c.slotB[k * c.nb + j]];
+}
+
 // Work item of tile (I, j) at k (tc::item_make), or 0 when no kept leaf has a
-// nonzero product.  *ntask += surviving triples (symmetric mode: of the whole
-// product, see below);
-// *npair += slice pairs those triples need (p >= zA_i, q >= zB, p + q < S).
-__device__ __forceinline__ uint32_t tile_item(const CullArgs &c, int64_t I, int64_t j, int64_t k, int &ntask,
-                                              int &npair)
+// nonzero product.  ntask += surviving triples (symmetric mode: of the whole
+// product, see below); npair += slice pairs those triples need (p >= zA_i,
+// q >= zB, p + q < S).
+template <int R>
+__device__ __forceinline__ uint32_t tile_item(const CullArgs &c, const StepA<R> &s, int64_t I, int64_t j, int64_t k,
+                                              int &ntask, int &npair)
 {
     if (k >= c.nb) return 0;
-    // every load of the candidate issued before any is used (one round trip)
     const double b = __ldg(c.n2BT + j * c.P + k);
-    const int64_t sbi = c.sym ? (c.denseA ? j * c.nb + k : -1) : (c.denseB ? k * c.nb + j : -1);
-    double a[8];
-    int zr[8];
-#pragma unroll
-    for (int r = 0; r < 8; r++) {
-        const int64_t i = (int64_t)c.R * I + r;
-        const bool in = r < c.R && i < c.nb;
-        a[r] = in ? __ldg(c.n2A + i * c.P + k) : 0.0;
-        zr[r] = (in && c.denseA) ? c.zA[i * c.nb + k] : 0;
-    }
-    int zb = sbi >= 0 ? (c.sym ? c.zA[sbi] : c.zB[sbi]) : 0;
+    int zb = zb_dense(c, j, k);  // issued with the norm
     if (b == 0.0) return 0;  // B leaf zero (or not stored): no triple of the step survives
-    // B operand leaf (k, j); in symmetric mode its image is leaf (j, k)'s A role
-    if (sbi < 0) zb = c.sym ? c.zA[c.slotA[j * c.nb + k]] : c.zB[c.slotB[k * c.nb + j]];
+    if (zb < 0) zb = zb_slot(c, j, k);
     uint32_t mask = 0;
     int za = c.S;
 #pragma unroll
-    for (int r = 0; r < 8; r++) {
-        const int64_t i = (int64_t)c.R * I + r;
-        if (r < c.R && i < c.nb && keep_product(a[r], b, c.tau2)) {
+    for (int r = 0; r < R; r++) {
+        const int64_t i = (int64_t)R * I + r;
+        if (i < c.nb && keep_product(s.a[r], b, c.tau2)) {
             // symmetric mode counts the whole product's triples from the
             // active tiles alone: (i, k, j) survives iff (j, k, i) does, so
             // a leaf above the diagonal stands for itself and its mirror
             ntask += !c.sym ? 1 : (i < j ? 2 : (i == j ? 1 : 0));
-            const int z = c.denseA ? zr[r] : c.zA[c.slotA[i * c.nb + k]];
+            const int z = s.z[r];
             if (z + zb < c.S) {
                 const int mr = c.S - z - zb;
                 npair += mr * (mr + 1) / 2;
@@ -81,12 +119,7 @@ __device__ __forceinline__ uint32_t tile_item(const CullArgs &c, int64_t I, int6
     return tc::item_make((uint32_t)k, mask, za, zb);
 }
 
-// Early occlusion (Algorithm 1): the R rows of tile I lie in one block row
-// of the 32 x 32-leaf tier (R divides 32) and its W columns in one block
-// column, so when that block row of A and the block of B holding
-// (k0 .. k0+31, j) fail the test, every triple of the step fails (a parent's
-// squared norm is never below a child's).  The passing blocks of each coarse
-// pair are found once (k_coarse_mask) and every tile of the pair reads them.
+// Slice pairs a one-column item issues.
 __device__ __forceinline__ int item_pairs(uint32_t w, int S)
 {
     const int m = S - tc::item_za(w) - tc::item_zb(w);
@@ -96,26 +129,33 @@ __device__ __forceinline__ int item_pairs(uint32_t w, int S)
 // Work item of a two-column tile (I, J) at k (leaf 32, R = 4; tc::item_make2),
 // or 0.  Symmetric mode keeps only the triples of stored leaves (i <= j): a
 // leaf below the diagonal is the mirror of one above it.
-__device__ __forceinline__ uint32_t tile_item2(const CullArgs &c, int64_t I, int64_t J, int64_t k, int &ntask,
-                                               int &npair)
+__device__ __forceinline__ uint32_t tile_item2(const CullArgs &c, const StepA<4> &s, int64_t I, int64_t J,
+                                               int64_t k, int &ntask, int &npair)
 {
     if (k >= c.nb) return 0;
     uint32_t mask[2] = {0u, 0u};
     int zbv[2] = {7, 7};
     int za = c.S;
+    double bn[2];
+    int zbl[2];
+#pragma unroll
+    for (int cc = 0; cc < 2; cc++) {  // both columns' loads issued together
+        const int64_t j = 2 * J + cc;
+        bn[cc] = j < c.nb ? __ldg(c.n2BT + j * c.P + k) : 0.0;
+        zbl[cc] = j < c.nb ? zb_dense(c, j, k) : 0;
+    }
 #pragma unroll
     for (int cc = 0; cc < 2; cc++) {
         const int64_t j = 2 * J + cc;
-        if (j >= c.nb) continue;
-        const double b = __ldg(c.n2BT + j * c.P + k);
-        if (b == 0.0) continue;
-        const int zb = c.sym ? c.zA[c.slotA[j * c.nb + k]] : c.zB[c.slotB[k * c.nb + j]];
+        const double b = bn[cc];
+        if (j >= c.nb || b == 0.0) continue;
+        const int zb = zbl[cc] >= 0 ? zbl[cc] : zb_slot(c, j, k);
 #pragma unroll
         for (int r = 0; r < 4; r++) {
             const int64_t i = 4 * I + r;
-            if (i < c.nb && (!c.sym || i <= j) && keep_product(__ldg(c.n2A + i * c.P + k), b, c.tau2)) {
+            if (i < c.nb && (!c.sym || i <= j) && keep_product(s.a[r], b, c.tau2)) {
                 ntask += !c.sym ? 1 : (i < j ? 2 : 1);
-                const int zr = c.zA[c.slotA[i * c.nb + k]];
+                const int zr = s.z[r];
                 if (zr + zb < c.S) {
                     const int mr = c.S - zr - zb;
                     npair += mr * (mr + 1) / 2;
@@ -143,11 +183,17 @@ __device__ __forceinline__ int item_pairs2(uint32_t w, int S)
     return n;
 }
 
+// Early occlusion (Algorithm 1): the R rows of tile I lie in one block row
+// of the 32 x 32-leaf tier (R divides 32) and its W columns in one block
+// column, so when that block row of A and the block of B holding
+// (k0 .. k0+31, j) fail the test, every triple of the step fails (a parent's
+// squared norm is never below a child's).  The passing blocks of each coarse
+// pair are found once (k_coarse_mask) and every tile of the pair reads them.
+//
 // Bit sets of the passing coarse k-blocks: one warp per coarse pair (block
 // row ci of A, block column cj of B in the tier whose blocks are 32 x 32
 // leaves); bit kc of the pair's set is the culling test of Eq. 4 on the
-// blocks (ci, kc) and (kc, cj).  A leaf triple can pass only inside a
-// passing block pair (a parent's squared norm is never below a child's).
+// blocks (ci, kc) and (kc, cj).
 __global__ void k_coarse_mask(const int32_t *__restrict__ stop, const double *__restrict__ cA,
                               const double *__restrict__ cB, int64_t cW, int64_t nc, int64_t cwords, double tau2,
                               uint32_t *__restrict__ mask)
@@ -165,64 +211,119 @@ __global__ void k_coarse_mask(const int32_t *__restrict__ stop, const double *__
     }
 }
 
-// One warp per tile: tests the candidates k (ballot), writes the tile's work
-// items into its own segment of the list, [t nb, t nb + count), and counts
-// them, the surviving triples and the slice pairs.
-template <int W>
-__global__ void __launch_bounds__(kWarps * 32)
+// Leaf columns of a tile row that one warp of k_tile_count culls (a divisor
+// of the coarse tier's 32, so that they share one coarse block column).
+constexpr int kCullCols = 16;
+
+// One warp per tile row I and kCullCols leaf columns (kCullCols / W tiles):
+// for each step of 32 candidates k (lane = k) it loads the A side once and
+// tests it against every tile of the warp (ballot), writing each tile's work
+// items into the tile's own segment of the list, [t nb, t nb + count), in
+// increasing k.  Per tile it counts the items, the surviving triples and the
+// slice pairs; d0[t] receives, per tile column c (4 bits at 4 c), the least
+// zA + zB over the column's items (the lowest diagonal its products touch; S
+// when it has none).  Lane jt holds the counts of the warp's tile jt.
+template <int W, int R>
+__global__ void __launch_bounds__(kWarps * 32, R <= 4 ? 4 : 3)
 k_tile_count(CullArgs c, int32_t *__restrict__ counts, int32_t *__restrict__ tasks,
-             int32_t *__restrict__ pairs, int32_t *__restrict__ useful, uint32_t *__restrict__ list)
+             int32_t *__restrict__ pairs, int32_t *__restrict__ useful, int32_t *__restrict__ d0out,
+             uint32_t *__restrict__ list)
 {
+    constexpr int NT = kCullCols / W;  // tiles per warp
+    static_assert(NT <= 32, "a lane holds the counts of one tile");
+    static_assert(W == 1 || R == 4, "two-column tiles have four leaf rows");
     if (c.stop && *c.stop) return;
-    const int64_t t = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const int64_t gw = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    if (t >= c.nI * c.nbt) return;
-    const int64_t I = t / c.nbt, J = t % c.nbt;
-    // symmetric mode: a tile entirely below the block diagonal is formed as
-    // a mirror (its last column is left of its first row)
-    const bool active = !c.sym || (int64_t)W * J + W - 1 >= (int64_t)c.R * I;
-    int cnt = 0, ntask = 0, npair = 0, nuse = 0;
-    if (!active) {  // symmetric mode: a lower-triangle tile is formed as a mirror
-        if (lane == 0) counts[t] = tasks[t] = pairs[t] = useful[t] = 0;
-        return;
+    const int64_t ncg = (c.nbt + NT - 1) / NT;  // tile groups per tile row
+    if (gw >= c.nI * ncg) return;
+    const int64_t I = gw / ncg, J0 = (gw % ncg) * NT;
+    const int nt = (int)(c.nbt - J0 < NT ? c.nbt - J0 : NT);  // tiles of this warp
+    // symmetric mode: a tile entirely below the block diagonal (its last
+    // column left of its first row) is formed as a mirror; the active tiles
+    // are jt >= jt0
+    int jt0 = 0;
+    if (c.sym) {
+        const int64_t jmin = ((int64_t)R * I + 1 + W - 1) / W - 1;  // least J with W J + W - 1 >= R I
+        jt0 = jmin <= J0 ? 0 : (int)(jmin - J0 < nt ? jmin - J0 : nt);
     }
-    uint32_t *seg = list + t * c.nb;
+    int cnt = 0, ntask = 0, npair = 0, nuse = 0;  // of tile J0 + lane
+    int dmin[W];
+#pragma unroll
+    for (int cc = 0; cc < W; cc++) dmin[cc] = c.S;
     const unsigned lt = (1u << lane) - 1u;
-    // the steps of 32 candidates k0 .. k0 + 31 to test: the coarse blocks
-    // whose pair with the tile's block row and column passes (precomputed
-    // bit sets), else every step
-    const int64_t nsteps = (c.nb + 31) / 32;
-    const uint32_t *cm = c.cmask ? c.cmask + (((int64_t)c.R * I >> 5) * c.nc + (((int64_t)W * J) >> 5)) * c.cwords
-                                 : nullptr;
-    for (int64_t wd = 0; wd < (nsteps + 31) / 32; wd++) {
-        uint32_t bits = cm ? __ldg(cm + wd) : 0xFFFFFFFFu;  // warp-uniform
-        while (bits) {
-            const int64_t kc = wd * 32 + (__ffs(bits) - 1);
-            bits &= bits - 1;
-            if (kc >= nsteps) break;
-            const int64_t k0 = kc * 32;
-            uint32_t w;
-            if constexpr (W == 2) w = tile_item2(c, I, J, k0 + lane, ntask, nuse);
-            else w = tile_item(c, I, J, k0 + lane, ntask, nuse);
-            const unsigned bal = __ballot_sync(0xffffffffu, w != 0);
-            if (w) {
-                seg[cnt + __popc(bal & lt)] = w;
-                if constexpr (W == 2) npair += item_pairs2(w, c.S);
-                else npair += item_pairs(w, c.S);
+    if (jt0 < nt) {
+        // the steps of 32 candidates k0 .. k0 + 31 to test: the coarse
+        // blocks whose pair with the warp's block row and column passes
+        // (precomputed bit sets), else every step
+        const int64_t nsteps = (c.nb + 31) / 32;
+        const uint32_t *cm =
+            c.cmask ? c.cmask + (((int64_t)R * I >> 5) * c.nc + (((int64_t)W * J0) >> 5)) * c.cwords : nullptr;
+        for (int64_t wd = 0; wd < (nsteps + 31) / 32; wd++) {
+            uint32_t bits = cm ? __ldg(cm + wd) : 0xFFFFFFFFu;  // warp-uniform
+            while (bits) {
+                const int64_t kc = wd * 32 + (__ffs(bits) - 1);
+                bits &= bits - 1;
+                if (kc >= nsteps) break;
+                const int64_t k = kc * 32 + lane;
+                StepA<R> sa;
+                load_step_a<R>(c, I, k, sa);
+                if (!__any_sync(0xffffffffu, sa.any())) continue;  // no A leaf of the step is nonzero
+                for (int jt = jt0; jt < nt; jt++) {
+                    const int64_t J = J0 + jt;
+                    int tk = 0, tp = 0;
+                    uint32_t w;
+                    if constexpr (W == 2) w = tile_item2(c, sa, I, J, k, tk, tp);
+                    else w = tile_item<R>(c, sa, I, J, k, tk, tp);
+                    const unsigned bal = __ballot_sync(0xffffffffu, w != 0);
+                    // nothing survives and nothing is listed (a kept triple below
+                    // the diagonal of a symmetric product counts 0 but may be listed)
+                    if (!__any_sync(0xffffffffu, tk != 0 || w != 0)) continue;
+                    const int base = __shfl_sync(0xffffffffu, cnt, jt);
+                    int pr = 0, d[W];
+#pragma unroll
+                    for (int cc = 0; cc < W; cc++) d[cc] = c.S;
+                    if (w) {
+                        list[(I * c.nbt + J) * c.nb + base + __popc(bal & lt)] = w;
+                        if constexpr (W == 2) {
+                            pr = item_pairs2(w, c.S);
+#pragma unroll
+                            for (int cc = 0; cc < 2; cc++)
+                                if (tc::item_mask_col<4, 2>(w, cc)) d[cc] = tc::item_za(w) + tc::item_zb_col(w, cc);
+                        } else {
+                            pr = item_pairs(w, c.S);
+                            d[0] = tc::item_za(w) + tc::item_zb(w);
+                        }
+                    }
+                    const int sk = __reduce_add_sync(0xffffffffu, tk);
+                    const int su = __reduce_add_sync(0xffffffffu, tp);
+                    const int sp = __reduce_add_sync(0xffffffffu, pr);
+                    int dm[W];
+#pragma unroll
+                    for (int cc = 0; cc < W; cc++) dm[cc] = (int)__reduce_min_sync(0xffffffffu, (unsigned)d[cc]);
+                    if (lane == jt) {
+                        cnt += __popc(bal);
+                        ntask += sk;
+                        nuse += su;
+                        npair += sp;
+#pragma unroll
+                        for (int cc = 0; cc < W; cc++) dmin[cc] = min(dmin[cc], dm[cc]);
+                    }
+                }
             }
-            cnt += __popc(bal);
         }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        ntask += __shfl_xor_sync(0xffffffffu, ntask, o);
-        npair += __shfl_xor_sync(0xffffffffu, npair, o);
-        nuse += __shfl_xor_sync(0xffffffffu, nuse, o);
-    }
-    if (lane == 0) {
+    if (lane < nt) {
+        const int64_t t = I * c.nbt + J0 + lane;
+        const bool active = lane >= jt0;
+        int packed = 0;
+#pragma unroll
+        for (int cc = 0; cc < W; cc++) packed |= min(dmin[cc], c.S) << (4 * cc);
         counts[t] = active ? cnt : 0;
-        tasks[t] = ntask;
+        tasks[t] = active ? ntask : 0;
         pairs[t] = active ? npair : 0;
         useful[t] = active ? nuse : 0;
+        d0out[t] = active ? packed : (W == 2 ? (c.S | c.S << 4) : c.S);
     }
 }
 
@@ -373,7 +474,8 @@ int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, i
         spamm_release(ws->tbins, s);
         spamm_release(ws->tuseful, s);
         spamm_release(ws->tnz, s);
-        ws->tcounts = ws->ttasks = ws->tpairs = ws->tuseful = ws->torder = ws->tbins = ws->tnz = nullptr;
+        spamm_release(ws->td0, s);
+        ws->tcounts = ws->ttasks = ws->tpairs = ws->tuseful = ws->torder = ws->tbins = ws->tnz = ws->td0 = nullptr;
         ws->toff = nullptr;
         ws->tile_cap = 0;
         if ((rc = spamm_alloc((void **)&ws->tcounts, sizeof(int32_t) * T, s))) return rc;
@@ -383,6 +485,7 @@ int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, i
         if ((rc = spamm_alloc((void **)&ws->toff, sizeof(int64_t) * (T + 4), s))) return rc;
         if ((rc = spamm_alloc((void **)&ws->torder, sizeof(int32_t) * T, s))) return rc;
         if ((rc = spamm_alloc((void **)&ws->tnz, sizeof(int32_t) * T, s))) return rc;
+        if ((rc = spamm_alloc((void **)&ws->td0, sizeof(int32_t) * T, s))) return rc;
         if ((rc = spamm_alloc((void **)&ws->tbins, sizeof(int32_t) * (nb + 1), s))) return rc;
         ws->tile_cap = T;
     }
@@ -426,7 +529,9 @@ int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, i
         SPAMM_CK_LAUNCH();
         c.cmask = ws->cmask;
     }
-    const unsigned blocks = (unsigned)((T + kWarps - 1) / kWarps);
+    // one warp per tile row and kCullCols leaf columns
+    const int64_t cull_warps = nI * ((nbt + kCullCols / W - 1) / (kCullCols / W));
+    const unsigned blocks = (unsigned)((cull_warps + kWarps - 1) / kWarps);
     const int64_t worst = T * nb;  // every tile owns a segment of nb items (one per k)
     if (ws->tlist_cap < worst) {
         spamm_release(ws->tlist, s);
@@ -435,10 +540,9 @@ int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, i
         if ((rc = spamm_alloc((void **)&ws->tlist, sizeof(uint32_t) * worst, s))) return rc;
         ws->tlist_cap = worst;
     }
-    if (W == 2)
-        k_tile_count<2><<<blocks, kWarps * 32, 0, s>>>(c, ws->tcounts, ws->ttasks, ws->tpairs, ws->tuseful, ws->tlist);
-    else
-        k_tile_count<1><<<blocks, kWarps * 32, 0, s>>>(c, ws->tcounts, ws->ttasks, ws->tpairs, ws->tuseful, ws->tlist);
+    auto kern = W == 2 ? k_tile_count<2, 4> : R == 8 ? k_tile_count<1, 8> : R == 4 ? k_tile_count<1, 4>
+                                                                                 : k_tile_count<1, 2>;
+    kern<<<blocks, kWarps * 32, 0, s>>>(c, ws->tcounts, ws->ttasks, ws->tpairs, ws->tuseful, ws->td0, ws->tlist);
     SPAMM_CK_LAUNCH();
     // totals: toff[T] work items, toff[T+1] surviving triples, toff[T+2]
     // issued slice-pair work, toff[T+3] slice pairs the surviving triples need
@@ -508,6 +612,7 @@ static void fill_prob(tc::TcProb &p, spamm_mat_t A, spamm_mat_t B, spamm_mat_t C
     p.slotC = C->slot;
     p.leafC = C->leaf;
     p.cnt = ws->tcounts;
+    p.d0 = ws->td0;
     p.list = ws->tlist;
     p.order = ws->torder;
     p.sigA = reinterpret_cast<const int32_t *>(A->scale + 1);

@@ -38,6 +38,7 @@ struct SpammWorkspace {
     int32_t *ttasks = nullptr;   // surviving triples per tile
     int32_t *tpairs = nullptr;   // slice-pair work per tile (sum of m(m+1)/2)
     int32_t *tuseful = nullptr;  // slice pairs the tile's surviving triples need
+    int32_t *td0 = nullptr;      // per tile, 4 bits per column: least zA + zB over its items (S: none)
     int64_t *toff = nullptr;     // T + 2: offsets, then the triple total
     int32_t *torder = nullptr;   // tile hand-out order (row-major or heaviest first), tiles with work only, then -1
     int32_t *tnz = nullptr;      // rank of each tile among the tiles with work

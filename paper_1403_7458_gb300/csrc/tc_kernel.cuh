@@ -80,7 +80,7 @@ constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kAccStride = 256;
 constexpr long long kTimeoutCycles = 8000000000ll;  // about 4 s at 2 GHz per wait
-constexpr int kTileRing = 4;  // tiles handed from the producer to the other roles
+constexpr int kTileRing = 8;  // tiles handed from the producer to the other roles
 
 // Work item of tile (I, j) at k: k | mask << 15 | zA << 23 | zB << 26.
 __host__ __device__ constexpr uint32_t item_k(uint32_t w) { return w & 0x7FFF; }
@@ -365,6 +365,7 @@ struct TcProb {
     const int32_t *slotC;
     double *leafC;
     const int32_t *cnt;    // work items per tile
+    const int32_t *d0;     // per tile, 4 bits per column: least zA + zB of its items (S: none)
     const uint32_t *list;  // work items: tile t's at [t nb, t nb + cnt[t])
     const int32_t *order;  // tile order (tile ids of this product; -1 after the tiles with work)
     const void *tmB;       // symmetric product: tensor maps of slA for the B leaves (map h - 1:
@@ -442,6 +443,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
     __shared__ uint32_t slot_w[kSlots];    // its work-list entry
     __shared__ unsigned long long slot_end[kSlots];  // its end in the producer's cumulative ring pointer
     __shared__ int32_t tile_q[kTileRing];  // tiles handed out (product << 24 | tile), -1 = no more
+    __shared__ int32_t tile_n[kTileRing];  // their work-item counts
+    __shared__ int32_t tile_d[kTileRing];  // and least diagonals (4 bits per column)
     __shared__ __align__(8) uint64_t tfull_bar[kTileRing], tempty_bar[kTileRing];
     __shared__ uint32_t tmem_holder;
     __shared__ int abort_flag;
@@ -500,7 +503,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                     for (int h = 0; h < S; h++) tmap_acquire(static_cast<const uint8_t *>(g.p[mp].tmB) + 128 * h);
         for (;;) {
             // take the next tile and hand it to the MMA and epilogue warps
-            int32_t tt = -1;
+            int32_t tt = -1, tn = 0;
             int tgood = 1;
             if (lane == 0) {
                 if (!mbar_wait(smem_u32(&tempty_bar[tq]), tph ^ 1, abort_v)) {
@@ -513,6 +516,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                         const int32_t o = g.p[mp].order[pos - g.p[mp].pos0];
                         if (o >= 0) {
                             tt = (mp << 24) | o;
+                            tn = g.p[mp].cnt[o];
+                            tile_n[tq] = tn;
+                            tile_d[tq] = g.p[mp].d0[o];
                             break;
                         }
                         // the rest of this product's order holds no tile with
@@ -524,6 +530,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                 }
             }
             tt = __shfl_sync(0xffffffffu, tt, 0);
+            tn = __shfl_sync(0xffffffffu, tn, 0);
             if (!__shfl_sync(0xffffffffu, tgood, 0)) {
                 ok = false;
                 break;
@@ -537,7 +544,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
             const int64_t t = tt & 0xFFFFFF;
             const int64_t nb = P.nb;
             const int64_t I = t / P.nbt, J = t % P.nbt;
-            const int64_t e0 = t * nb, e1 = e0 + P.cnt[t];
+            const int64_t e0 = t * nb, e1 = e0 + tn;
             for (int64_t base = e0; base < e1 && ok; base += 32) {
                 const int cnt = (int)(e1 - base < 32 ? e1 - base : 32);
                 uint32_t wl = 0;
@@ -662,7 +669,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                     ok = false;
                     break;
                 }
-                const int32_t tt = tile_q[tq];
+                const int32_t tt = tile_q[tq], tn = tile_n[tq];
                 mbar_arrive(smem_u32(&tempty_bar[tq]));
                 if (++tq == kTileRing) {
                     tq = 0;
@@ -678,7 +685,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t dacc = tmem + acc * kAccStride;
-                const int64_t e1 = t * P.nb + P.cnt[t];
+                const int64_t e1 = t * P.nb + tn;
                 for (int64_t e = t * P.nb; e < e1; e++) {
                     const uint32_t sl = consumed % kSlots;
                     if (!mbar_wait(smem_u32(&full_bar[sl]), (consumed / kSlots) & 1, abort_v)) {
@@ -767,16 +774,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
         uint32_t acc = 0, aph = 0;
         uint32_t tq = 0, tph = 0;
         for (;;) {
-            int32_t tt = -1;
+            int32_t tt = -1, tn = 0, td = 0;
             int tgood = 1;
             if (lane == 0) {
                 tgood = mbar_wait(smem_u32(&tfull_bar[tq]), tph, abort_v);
                 if (tgood) {
                     tt = tile_q[tq];
+                    tn = tile_n[tq];
+                    td = tile_d[tq];
                     mbar_arrive(smem_u32(&tempty_bar[tq]));
                 }
             }
             tt = __shfl_sync(0xffffffffu, tt, 0);
+            tn = __shfl_sync(0xffffffffu, tn, 0);
+            td = __shfl_sync(0xffffffffu, td, 0);
             if (!__shfl_sync(0xffffffffu, tgood, 0)) {
                 if (lane == 0) atomicExch(g.err, 1);
                 abort_flag = 1;
@@ -791,26 +802,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
             const int64_t t = tt & 0xFFFFFF;
             const int64_t nb = P.nb;
             const int64_t I = t / P.nbt, J = t % P.nbt;
-            const bool has_work = P.cnt[t] > 0;
-            // the least diagonal any item of the tile touches per column (za +
-            // zb over its items): the diagonals below it were never written and
+            const bool has_work = tn > 0;
+            // the least diagonal any item of the tile touches per column (from
+            // the tile cull): the diagonals below it were never written and
             // are still zero, so they are neither read, cleared nor combined
             int d0[W];
 #pragma unroll
-            for (int c = 0; c < W; c++) d0[c] = S;
-            {
-                const int64_t e0 = t * nb, e1 = e0 + P.cnt[t];
-                for (int64_t e = e0 + lane; e < e1; e += 32) {
-                    const uint32_t w = P.list[e];
-#pragma unroll
-                    for (int c = 0; c < W; c++)
-                        if (item_mask_col<R, W>(w, c)) d0[c] = min(d0[c], item_za(w) + item_zb_col(w, c));
-                }
-#pragma unroll
-                for (int c = 0; c < W; c++) {
-                    d0[c] = g.float_split ? 0 : warp_min_int(d0[c]);
-                    if (d0[c] > S) d0[c] = S;
-                }
+            for (int c = 0; c < W; c++) {
+                d0[c] = g.float_split ? 0 : (td >> (4 * c)) & 15;
+                if (d0[c] > S) d0[c] = S;
             }
             // the output leaves' slots and the scale, loaded while the tile's
             // products are still running
