@@ -382,8 +382,10 @@ __device__ __forceinline__ uint16_t slice_digit_bf16(uint64_t X, bool neg, int p
 {
     uint32_t d = (uint32_t)(X >> (7 * (S - 1 - p)));
     if (p > 0) d &= 127u;
-    const float f = neg ? -(float)d : (float)d;  // integer d <= 128: exact in BF16
-    return (uint16_t)(__float_as_uint(f) >> 16);
+    // the FP32 value d (exact: d <= 128 < 2^23) from the bits of 2^23 + d,
+    // minus 2^23; d <= 128 is exact in BF16 too, so the top half is its BF16
+    const uint32_t f = __float_as_uint(__int_as_float(0x4B000000 | (int)d) - 8388608.0f);
+    return (uint16_t)((f >> 16) | (neg ? 0x8000u : 0u));
 }
 
 // Layout of one slice of a B x B leaf with E-byte elements, as the tcgen05

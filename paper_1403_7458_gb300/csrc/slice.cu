@@ -143,25 +143,59 @@ k_slice(const int32_t *__restrict__ stop, const double *__restrict__ leaf, const
         __syncthreads();
         unsigned long long xmax = 0;
         const double *src = leaf + (int64_t)sl * (B * B);
-        double xs[kPerThread];  // all loads of the leaf issued before any is used
+        if (perleaf && perleaf_transposed) {
+            double xs[kPerThread];  // all loads of the leaf issued before any is used
 #pragma unroll
-        for (int u = 0; u < kPerThread; u++) xs[u] = src[threadIdx.x + kThreads * u];
+            for (int u = 0; u < kPerThread; u++) xs[u] = src[threadIdx.x + kThreads * u];
 #pragma unroll
-        for (int u = 0; u < kPerThread; u++) {
-            const int q = threadIdx.x + kThreads * u;
-            const int r = q / B, l = q % B;
-            const double x = xs[u];
-            const uint64_t X = float_split ? 0 : slice_int(x, sigma, S);
-            const bool neg = x < 0.0;
-            xmax = X > xmax ? X : xmax;
-            // outside |x| < 2^sigma (possible only with a caller-fixed scale)
-            if (!float_split && (X > (1ull << (7 * S)) || !(fabs(x) <= 1e300))) atomicExch(overflow, 1);
-            double rest = x;  // float split: s_p = round(x - s_0 - ... - s_{p-1})
-            // [p][g][cc][8 x ce]; transposed: element (r, l) stored as (l, r)
-            const int o = ((perleaf_transposed && perleaf) ? slice_byte_offset<B, E>(l, r)
-                                                           : slice_byte_offset<B, E>(r, l)) / E;
+            for (int u = 0; u < kPerThread; u++) {
+                const int q = threadIdx.x + kThreads * u;
+                const int r = q / B, l = q % B;
+                const double x = xs[u];
+                const uint64_t X = float_split ? 0 : slice_int(x, sigma, S);
+                const bool neg = x < 0.0;
+                xmax = X > xmax ? X : xmax;
+                // outside |x| < 2^sigma (possible only with a caller-fixed scale)
+                if (!float_split && (X > (1ull << (7 * S)) || !(fabs(x) <= 1e300))) atomicExch(overflow, 1);
+                double rest = x;  // float split: s_p = round(x - s_0 - ... - s_{p-1})
+                // [p][g][cc][8 x ce], element (r, l) stored as (l, r)
+                const int o = slice_byte_offset<B, E>(l, r) / E;
 #pragma unroll
-            for (int p = 0; p < S; p++) sa[p * B * B + o] = (W)slice_elem<E>(X, neg, p, S, float_split, rest);
+                for (int p = 0; p < S; p++) sa[p * B * B + o] = (W)slice_elem<E>(X, neg, p, S, float_split, rest);
+            }
+        } else {
+            // untransposed: elements (r, l) and (r, l + 1), l even, are
+            // neighbours in every slice, so a thread takes such pairs and
+            // stores both with one shared-memory store per slice
+            using W2 = typename std::conditional<E == 4, uint2, uint32_t>::type;
+            constexpr int kPairs = kPerThread / 2;
+            double2 xs[kPairs];  // all loads of the leaf issued before any is used
+#pragma unroll
+            for (int u = 0; u < kPairs; u++) xs[u] = reinterpret_cast<const double2 *>(src)[threadIdx.x + kThreads * u];
+#pragma unroll
+            for (int u = 0; u < kPairs; u++) {
+                const int q = 2 * (threadIdx.x + kThreads * u);
+                const int r = q / B, l = q % B;
+                const double x0 = xs[u].x, x1 = xs[u].y;
+                const uint64_t X0 = float_split ? 0 : slice_int(x0, sigma, S);
+                const uint64_t X1 = float_split ? 0 : slice_int(x1, sigma, S);
+                xmax = X0 > xmax ? X0 : xmax;
+                xmax = X1 > xmax ? X1 : xmax;
+                if (!float_split && (X0 > (1ull << (7 * S)) || X1 > (1ull << (7 * S)) || !(fabs(x0) <= 1e300) ||
+                                     !(fabs(x1) <= 1e300)))
+                    atomicExch(overflow, 1);
+                double rest0 = x0, rest1 = x1;
+                W2 *sp = reinterpret_cast<W2 *>(reinterpret_cast<uint8_t *>(sa) + slice_byte_offset<B, E>(r, l));
+#pragma unroll
+                for (int p = 0; p < S; p++) {
+                    const uint32_t v0 = slice_elem<E>(X0, x0 < 0.0, p, S, float_split, rest0);
+                    const uint32_t v1 = slice_elem<E>(X1, x1 < 0.0, p, S, float_split, rest1);
+                    W2 pr;
+                    if constexpr (E == 4) pr = make_uint2(v0, v1);
+                    else pr = (v0 & 0xFFFFu) | (v1 << 16);
+                    sp[p * (B * B * E / sizeof(W2))] = pr;
+                }
+            }
         }
         for (int o = 16; o > 0; o >>= 1) {
             const unsigned long long v = __shfl_xor_sync(0xffffffffu, xmax, o);

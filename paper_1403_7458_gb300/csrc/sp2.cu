@@ -263,6 +263,20 @@ __device__ void sp2_finish(int mode, const double *idem_part, int64_t idem_count
 }
 
 
+// An FP64 value cut to FP32 (the fraction truncated to 23 bits; values
+// below the FP32 normal range become 0) by integer operations alone: for the
+// squares of the idempotency error, where a relative error below 2^-22 per
+// term is immaterial and an FP64 multiply-add per element is not.  Values of
+// magnitude 2^128 and beyond, infinities and NaNs become infinities.
+__device__ __forceinline__ float f64_to_f32_trunc(double x)
+{
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    const int e = (int)((hi >> 20) & 0x7FF) - 896;                 // FP32 biased exponent
+    const uint32_t m = __funnelshift_l(lo, hi, 3) & 0x7FFFFFu;    // top 23 fraction bits
+    if (e >= 255) return __int_as_float(0x7F800000);
+    return e > 0 ? __uint_as_float((hi & 0x80000000u) | ((uint32_t)e << 23) | m) : 0.0f;
+}
+
 // Elementwise pass over all leaves of X, one warp per leaf (persistent
 // warps stride over the leaves).
 //   mode 0: X <- (emax I - F) / (emax - emin)          (src = F)
@@ -334,7 +348,7 @@ k_sp2_elementwise(int mode, double *__restrict__ X, const double *__restrict__ s
             }
             continue;
         }
-        double idem = 0.0;
+        float idem = 0.0f;  // this lane's sum of d^2 over the leaf (see below)
         int ek = 0;
         // the update's kind is uniform over the launch: one loop per kind, so
         // that no FP64 operation of another kind is issued (the FP64 pipe is
@@ -362,8 +376,11 @@ k_sp2_elementwise(int mode, double *__restrict__ X, const double *__restrict__ s
                         if (diag && r == q % B && I * B + r < n) nv = (emax - yv[u]) / range;
                         else nv = yv[u] == 0.0 ? 0.0 : -yv[u] / range;
                     } else {
-                        const double d = yv[u] - xv[u];
-                        idem = fma(d, d, idem);
+                        // d = x2 - x in FP64; d^2 summed in FP32 from d cut to
+                        // FP32 by integer operations (no FP64 multiply-add:
+                        // the FP64 pipe bounds this kernel)
+                        const float df = f64_to_f32_trunc(yv[u] - xv[u]);
+                        idem = fmaf(df, df, idem);
                         if constexpr (K == 1) nv = yv[u];
                         else nv = fma(2.0, xv[u], -yv[u]);
                     }
@@ -392,8 +409,9 @@ k_sp2_elementwise(int mode, double *__restrict__ X, const double *__restrict__ s
         if (diag)
             for (int r = lane; r < B; r += 32) dsum += x[r * B + r];
         acc = warp_sum_u128(acc);
+        double idem_d = (double)idem;
         for (int o = 16; o > 0; o >>= 1) {
-            idem += __shfl_xor_sync(0xffffffffu, idem, o);
+            idem_d += __shfl_xor_sync(0xffffffffu, idem_d, o);
             dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
         }
         if (lane == 0) {
@@ -401,7 +419,7 @@ k_sp2_elementwise(int mode, double *__restrict__ X, const double *__restrict__ s
             n2[I * P + K] = r;
             n2T[K * P + I] = r;
             if (r > 0.0) atomicAdd(&st->nonzero, 1ull);  // fill statistics
-            idem_w += idem;
+            idem_w += idem_d;
             if (diag) diag_part[I] = dsum;
         }
         __syncwarp();
