@@ -613,6 +613,7 @@ int spamm_multiply_into(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t C,
         if ((rc = tc_tile_cull(A, B, tau, ws, symm, sl, s, heavy))) return rc;
         if (zero_empty && (rc = tc_zero_empty_tiles(C, ws, s))) return rc;
         ws->tmirror = mirror ? 1 : 0;
+        ws->tskip_idle = zero_empty ? 0 : 1;
         if (ev) SPAMM_CK(spamm_event_record(ev[1], s));
         rc = launch_gemm_tc(A, B, C, ws, tr_part, sl, el, s, fsplit);
         if (rc) return rc;
@@ -869,6 +870,7 @@ extern "C" int spamm_multiply_batched(int32_t count, const spamm_mat_t *A, const
                 rc = tc_tile_cull(a[q], b[q], tau[ord[q]], w[q], 0, sl, sq,
                                   opts && (opts->flags & SPAMM_F_HEAVIEST));
             if (rc == SPAMM_OK) rc = tc_zero_empty_tiles(c[q], w[q], sq);
+            w[q]->tskip_idle = 0;  // every output leaf is written
         }
     }
     if (aux) {

@@ -220,9 +220,11 @@ constexpr int kCullCols = 16;
 // tests it against every tile of the warp (ballot), writing each tile's work
 // items into the tile's own segment of the list, [t nb, t nb + count), in
 // increasing k.  Per tile it counts the items, the surviving triples and the
-// slice pairs; d0[t] receives, per tile column c (4 bits at 4 c), the least
-// zA + zB over the column's items (the lowest diagonal its products touch; S
-// when it has none).  Lane jt holds the counts of the warp's tile jt.
+// slice pairs; d0[t] receives, per tile column c, the least zA + zB over the
+// column's items (4 bits at 4 c: the lowest diagonal its products touch; S
+// when it has none) and the leaf rows any of them keeps (R bits at 8 + 8 c:
+// the output leaves with work).  Lane jt holds the counts of the warp's
+// tile jt.
 template <int W, int R>
 __global__ void __launch_bounds__(kWarps * 32, R <= 4 ? 4 : 3)
 k_tile_count(CullArgs c, int32_t *__restrict__ counts, int32_t *__restrict__ tasks,
@@ -249,8 +251,12 @@ k_tile_count(CullArgs c, int32_t *__restrict__ counts, int32_t *__restrict__ tas
     }
     int cnt = 0, ntask = 0, npair = 0, nuse = 0;  // of tile J0 + lane
     int dmin[W];
+    uint32_t rows[W];
 #pragma unroll
-    for (int cc = 0; cc < W; cc++) dmin[cc] = c.S;
+    for (int cc = 0; cc < W; cc++) {
+        dmin[cc] = c.S;
+        rows[cc] = 0;
+    }
     const unsigned lt = (1u << lane) - 1u;
     if (jt0 < nt) {
         // the steps of 32 candidates k0 .. k0 + 31 to test: the coarse
@@ -280,34 +286,40 @@ k_tile_count(CullArgs c, int32_t *__restrict__ counts, int32_t *__restrict__ tas
                     // the diagonal of a symmetric product counts 0 but may be listed)
                     if (!__any_sync(0xffffffffu, tk != 0 || w != 0)) continue;
                     const int base = __shfl_sync(0xffffffffu, cnt, jt);
-                    int pr = 0, d[W];
-#pragma unroll
-                    for (int cc = 0; cc < W; cc++) d[cc] = c.S;
+                    // the item's kept rows per column (8 / W bits each, from bit 0)
+                    // and its lowest diagonal per column (one-hot, 8 bits from
+                    // bit 8 + 8 c): one OR over the warp gives both
+                    int pr = 0;
+                    uint32_t bits = 0;
                     if (w) {
                         list[(I * c.nbt + J) * c.nb + base + __popc(bal & lt)] = w;
                         if constexpr (W == 2) {
                             pr = item_pairs2(w, c.S);
 #pragma unroll
-                            for (int cc = 0; cc < 2; cc++)
-                                if (tc::item_mask_col<4, 2>(w, cc)) d[cc] = tc::item_za(w) + tc::item_zb_col(w, cc);
+                            for (int cc = 0; cc < 2; cc++) {
+                                const uint32_t m = tc::item_mask_col<4, 2>(w, cc);
+                                if (m) bits |= m << (4 * cc) | 1u << (8 + 8 * cc + tc::item_za(w) + tc::item_zb_col(w, cc));
+                            }
                         } else {
                             pr = item_pairs(w, c.S);
-                            d[0] = tc::item_za(w) + tc::item_zb(w);
+                            bits = tc::item_mask(w) | 1u << (8 + tc::item_za(w) + tc::item_zb(w));
                         }
                     }
                     const int sk = __reduce_add_sync(0xffffffffu, tk);
                     const int su = __reduce_add_sync(0xffffffffu, tp);
                     const int sp = __reduce_add_sync(0xffffffffu, pr);
-                    int dm[W];
-#pragma unroll
-                    for (int cc = 0; cc < W; cc++) dm[cc] = (int)__reduce_min_sync(0xffffffffu, (unsigned)d[cc]);
+                    const uint32_t so = __reduce_or_sync(0xffffffffu, bits);
                     if (lane == jt) {
                         cnt += __popc(bal);
                         ntask += sk;
                         nuse += su;
                         npair += sp;
 #pragma unroll
-                        for (int cc = 0; cc < W; cc++) dmin[cc] = min(dmin[cc], dm[cc]);
+                        for (int cc = 0; cc < W; cc++) {
+                            const uint32_t dz = (so >> (8 + 8 * cc)) & 0xFFu;
+                            if (dz) dmin[cc] = min(dmin[cc], __ffs(dz) - 1);
+                            rows[cc] |= (so >> (8 / W * cc)) & ((1u << (8 / W)) - 1u);
+                        }
                     }
                 }
             }
@@ -318,7 +330,7 @@ k_tile_count(CullArgs c, int32_t *__restrict__ counts, int32_t *__restrict__ tas
         const bool active = lane >= jt0;
         int packed = 0;
 #pragma unroll
-        for (int cc = 0; cc < W; cc++) packed |= min(dmin[cc], c.S) << (4 * cc);
+        for (int cc = 0; cc < W; cc++) packed |= min(dmin[cc], c.S) << (4 * cc) | (int)(rows[cc] << (8 + 8 * cc));
         counts[t] = active ? cnt : 0;
         tasks[t] = active ? ntask : 0;
         pairs[t] = active ? npair : 0;
@@ -624,6 +636,7 @@ static void fill_prob(tc::TcProb &p, spamm_mat_t A, spamm_mat_t B, spamm_mat_t C
     p.sym = ws->tsym;
     p.tw = ws->tw;
     p.mirror = ws->tmirror;
+    p.skip_idle = ws->tskip_idle;
 }
 
 static int launch_args(tc::TcArgs &a, int leaf, int slices, int e, cudaStream_t s)

@@ -38,7 +38,8 @@ struct SpammWorkspace {
     int32_t *ttasks = nullptr;   // surviving triples per tile
     int32_t *tpairs = nullptr;   // slice-pair work per tile (sum of m(m+1)/2)
     int32_t *tuseful = nullptr;  // slice pairs the tile's surviving triples need
-    int32_t *td0 = nullptr;      // per tile, 4 bits per column: least zA + zB over its items (S: none)
+    int32_t *td0 = nullptr;      // per tile and column c: least zA + zB over its items (4 bits at 4 c; S:
+                                 // none), leaf rows with work (R bits at 8 + 8 c)
     int64_t *toff = nullptr;     // T + 2: offsets, then the triple total
     int32_t *torder = nullptr;   // tile hand-out order (row-major or heaviest first), tiles with work only, then -1
     int32_t *tnz = nullptr;      // rank of each tile among the tiles with work
@@ -54,6 +55,8 @@ struct SpammWorkspace {
     int tsym = 0;                         // last tile cull was symmetric
     int tw = 1;                           // output leaf columns per tile of the last tile cull
     int tmirror = 1;                      // symmetric tensor-core product: also store C_ji = C_ij^T
+    int tskip_idle = 0;                   // tensor-core product: leaves without work in tiles with work are
+                                          // not written (the caller reads the tile masks), else zeroed
     int64_t tT = 0;                       // tiles of the last tile cull (totals at toff + tT)
     uint32_t *cmask = nullptr;            // tile cull: passing coarse k-blocks per coarse (row, column) pair
     int64_t cmask_cap = 0;                // uint32 words

@@ -281,9 +281,9 @@ __device__ __forceinline__ float f64_to_f32_trunc(double x)
 // warps stride over the leaves).
 //   mode 0: X <- (emax I - F) / (emax - emin)          (src = F)
 //   mode 1: X <- X2 if branch else 2 X - X2            (src = X2)
-// In mode 1 with x2cnt (the tensor path's work items per tile of X2's
-// product, R leaf rows by tw leaf columns per tile, symmetric or not), a
-// leaf of X2 whose tile had no work
+// In mode 1 with x2rows (the tensor path's per-tile words of X2's product,
+// R leaf rows by tw leaf columns per tile, symmetric or not: bit 8 + 8 c + L
+// set when leaf row L of tile column c had work), a leaf of X2 without work
 // is zero and was not written: it is not read, and a leaf that is zero in
 // both X (squared norm 0) and X2 stays zero without being touched.
 // Writes the leaf's squared norm (exact, once rounded) and, for diagonal
@@ -301,7 +301,7 @@ k_sp2_elementwise(int mode, double *__restrict__ X, const double *__restrict__ s
                   const int32_t *__restrict__ slot, const int32_t *__restrict__ src_slot, int64_t n, int64_t nb,
                   int64_t P, double *__restrict__ n2, double *__restrict__ n2T, double *__restrict__ idem_part,
                   double *__restrict__ diag_part, Sp2State *st, Sp2Rule rule, double *__restrict__ hist,
-                  const int32_t *__restrict__ x2cnt, int R, int tw, int sym, int tlow)
+                  const int32_t *__restrict__ x2rows, int R, int tw, int sym, int tlow)
 {
     constexpr int BB = B * B;
     constexpr int kPer = BB / 32;              // elements per lane
@@ -326,9 +326,10 @@ k_sp2_elementwise(int mode, double *__restrict__ X, const double *__restrict__ s
         const double *y = src + (int64_t)(ss < 0 ? 0 : ss) * BB;
         const bool diag = I == K;
         bool y0 = ss < 0;  // source leaf known to be zero
-        if (mode == 1 && x2cnt) {
+        if (mode == 1 && x2rows) {
             const int64_t a = (sym && I > K) ? K : I, c = (sym && I > K) ? I : K;
-            y0 = x2cnt[(a / R) * ((nb + tw - 1) / tw) + c / tw] == 0;
+            const int32_t word = x2rows[(a / R) * ((nb + tw - 1) / tw) + c / tw];
+            y0 = !((word >> (8 + 8 * (c % tw) + a % R)) & 1);
         }
         // X_new = X2 or 2X - X2 = 0 with X = 0 = X2: nothing to read or write
         // (mode 0 writes every leaf of X: X0 = (emax I - F) / range)
@@ -460,29 +461,29 @@ template <int B>
 void launch_elementwise_b(cudaStream_t s, int mode, double *X, const double *src, const int32_t *slot,
                           const int32_t *src_slot, int64_t n, int64_t nb, int64_t P, double *n2, double *n2T,
                           double *idem_part, double *diag_part, Sp2State *st, Sp2Rule rule, double *hist,
-                          const int32_t *x2cnt, int R, int tw, int sym, int tlow)
+                          const int32_t *x2rows, int R, int tw, int sym, int tlow)
 {
     const int64_t cap = ew_grid_cap<B>();
     const int64_t need = (nb * nb + kEwWarps - 1) / kEwWarps;
     const unsigned grid = (unsigned)(need < cap ? need : cap);
     k_sp2_elementwise<B><<<grid, kEwWarps * 32, 0, s>>>(mode, X, src, slot, src_slot, n, nb, P, n2, n2T, idem_part,
-                                                    diag_part, st, rule, hist, x2cnt, R, tw, sym, tlow);
+                                                    diag_part, st, rule, hist, x2rows, R, tw, sym, tlow);
 }
 
 void launch_elementwise(int b, cudaStream_t s, int mode, double *X, const double *src, const int32_t *slot,
                         const int32_t *src_slot, int64_t n, int64_t nb, int64_t P, double *n2, double *n2T,
                         double *idem_part, double *diag_part, Sp2State *st, Sp2Rule rule, double *hist,
-                        const int32_t *x2cnt, int R, int tw, int sym, int tlow = 0)
+                        const int32_t *x2rows, int R, int tw, int sym, int tlow = 0)
 {
     if (b == 16)
         launch_elementwise_b<16>(s, mode, X, src, slot, src_slot, n, nb, P, n2, n2T, idem_part, diag_part, st,
-                                 rule, hist, x2cnt, R, tw, sym, tlow);
+                                 rule, hist, x2rows, R, tw, sym, tlow);
     else if (b == 32)
         launch_elementwise_b<32>(s, mode, X, src, slot, src_slot, n, nb, P, n2, n2T, idem_part, diag_part, st,
-                                 rule, hist, x2cnt, R, tw, sym, tlow);
+                                 rule, hist, x2rows, R, tw, sym, tlow);
     else
         launch_elementwise_b<64>(s, mode, X, src, slot, src_slot, n, nb, P, n2, n2T, idem_part, diag_part, st,
-                                 rule, hist, x2cnt, R, tw, sym, tlow);
+                                 rule, hist, x2rows, R, tw, sym, tlow);
 }
 
 
@@ -690,14 +691,14 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
                 int r = spamm_multiply_into(X, X, tau, X2, &mo, sc.tr_part, st, false, nullptr, false, ev,
                                             sym ? 1 : 0, false, !tcpath, !(tcpath && sym));
                 if (r) return r;
-                const int32_t *x2cnt = tcpath ? X2->ws.tcounts : nullptr;
+                const int32_t *x2rows = tcpath ? X2->ws.td0 : nullptr;
                 k_sp2_decide<<<1, kRedThreads, 0, st>>>(sc.tr_part, tcpath ? 2 * nb : nb, X2->ws.task_total,
                                                         X2->ws.pair_units, Ne,
                                                         o.rule, sc.st);
                 SPAMM_CK_LAUNCH();
                 launch_elementwise(X->b, st, 1, X->leaf, X2->leaf, X->slot, X2->slot, F->n, nb, X->P,
                                    X->n2 + tier_offset(X->depth), X->n2T, sc.idem_part, sc.diag_part, sc.st, rule,
-                                   sc.hist, x2cnt, 128 / X->b, X2->ws.tw, sym ? 1 : 0, (tcpath && sym) ? 1 : 0);
+                                   sc.hist, x2rows, 128 / X->b, X2->ws.tw, sym ? 1 : 0, (tcpath && sym) ? 1 : 0);
                 SPAMM_CK_LAUNCH();
                 if (coarse && (r = launch_pyramid(X, st))) return r;
                 if (timing) SPAMM_CK(spamm_event_record(ev[4], st));

@@ -365,7 +365,8 @@ struct TcProb {
     const int32_t *slotC;
     double *leafC;
     const int32_t *cnt;    // work items per tile
-    const int32_t *d0;     // per tile, 4 bits per column: least zA + zB of its items (S: none)
+    const int32_t *d0;     // per tile and column c: least zA + zB of its items (4 bits at 4 c; S: none),
+                           // leaf rows with work (R bits at 8 + 8 c)
     const uint32_t *list;  // work items: tile t's at [t nb, t nb + cnt[t])
     const int32_t *order;  // tile order (tile ids of this product; -1 after the tiles with work)
     const void *tmB;       // symmetric product: tensor maps of slA for the B leaves (map h - 1:
@@ -379,6 +380,7 @@ struct TcProb {
     int32_t sym;           // symmetric product: upper block triangle + mirror
     int32_t tw;            // output leaf columns per tile of its work lists
     int32_t mirror;        // symmetric product: also store C_ji = C_ij^T (else leaves i <= j only)
+    int32_t skip_idle;     // output leaves without work in a tile with work are not written (else zeroed)
 };
 
 struct TcArgs {
@@ -837,11 +839,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                 if (j >= nb) break;  // no such column (nothing was accumulated there)
                 // symmetric mode: leaf (i, j) is written only for i <= j, and for
                 // i < j its transpose goes to leaf (j, i)
-                const bool store = i < nb && (!P.sym || i <= j);
+                const bool store_leaf = i < nb && (!P.sym || i <= j);
                 int32_t osl = 0;  // oslot[c] (static indexing)
 #pragma unroll
                 for (int cc = 0; cc < W; cc++)
                     if (cc == c) osl = oslot[cc];
+                // a leaf row that none of the column's items keeps has an
+                // all-zero accumulator: it is not read (when its whole warp is
+                // idle), and it is written as zeros or, when the caller knows
+                // it from the tile masks, not at all
+                const bool idle = !((td >> (8 + 8 * c + L)) & 1);
+                const bool widle = __all_sync(0xffffffffu, idle);
+                const bool store = store_leaf && !(idle && P.skip_idle);
                 double *dst = store ? P.leafC + (int64_t)osl * (B * B) + r * B : nullptr;
                 double *mir =
                     (store && P.sym && P.mirror && i < j) ? P.leafC + (int64_t)P.slotC[j * nb + i] * (B * B) + r
@@ -863,6 +872,29 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                     const bool last = (h + 1 >= h_hi) && (c + 1 >= W || W * J + c + 1 >= nb);
                     // the S diagonals of these 16 columns: all loads issued,
                     // one wait, the accumulator zeroed for the next tile
+                    if (widle) {  // warp-uniform: every row of this warp is idle
+                        if (last && !released) {
+                            // (clears of an earlier column of the tile complete first)
+                            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(smem_u32(&acce_bar[acc]));
+                            released = true;
+                        }
+                        if (store) {
+                            const double2 z = make_double2(0.0, 0.0);
+#pragma unroll
+                            for (int q = 0; q < 16; q += 2) {
+                                const int col = 16 * h + q;
+                                reinterpret_cast<double2 *>(dst)[col >> 1] = z;
+                                if (mir) {
+                                    mir[col * B] = 0.0;
+                                    mir[(col + 1) * B] = 0.0;
+                                }
+                            }
+                        }
+                        continue;
+                    }
                     uint32_t v[S][16];
                     if (has_work) {
 #pragma unroll
