@@ -250,13 +250,7 @@ k_tile_count(CullArgs c, int32_t *__restrict__ counts, int32_t *__restrict__ tas
         jt0 = jmin <= J0 ? 0 : (int)(jmin - J0 < nt ? jmin - J0 : nt);
     }
     int cnt = 0, ntask = 0, npair = 0, nuse = 0;  // of tile J0 + lane
-    int dmin[W];
-    uint32_t rows[W];
-#pragma unroll
-    for (int cc = 0; cc < W; cc++) {
-        dmin[cc] = c.S;
-        rows[cc] = 0;
-    }
+    uint32_t tbits = 0;  // OR of the items' row and diagonal bits (see below)
     const unsigned lt = (1u << lane) - 1u;
     if (jt0 < nt) {
         // the steps of 32 candidates k0 .. k0 + 31 to test: the coarse
@@ -314,12 +308,7 @@ k_tile_count(CullArgs c, int32_t *__restrict__ counts, int32_t *__restrict__ tas
                         ntask += sk;
                         nuse += su;
                         npair += sp;
-#pragma unroll
-                        for (int cc = 0; cc < W; cc++) {
-                            const uint32_t dz = (so >> (8 + 8 * cc)) & 0xFFu;
-                            if (dz) dmin[cc] = min(dmin[cc], __ffs(dz) - 1);
-                            rows[cc] |= (so >> (8 / W * cc)) & ((1u << (8 / W)) - 1u);
-                        }
+                        tbits |= so;
                     }
                 }
             }
@@ -330,7 +319,11 @@ k_tile_count(CullArgs c, int32_t *__restrict__ counts, int32_t *__restrict__ tas
         const bool active = lane >= jt0;
         int packed = 0;
 #pragma unroll
-        for (int cc = 0; cc < W; cc++) packed |= min(dmin[cc], c.S) << (4 * cc) | (int)(rows[cc] << (8 + 8 * cc));
+        for (int cc = 0; cc < W; cc++) {
+            const uint32_t dz = (tbits >> (8 + 8 * cc)) & 0xFFu;  // diagonals that are some item's lowest
+            const uint32_t rows = (tbits >> (8 / W * cc)) & ((1u << (8 / W)) - 1u);
+            packed |= (dz ? min(__ffs(dz) - 1, c.S) : c.S) << (4 * cc) | (int)(rows << (8 + 8 * cc));
+        }
         counts[t] = active ? cnt : 0;
         tasks[t] = active ? ntask : 0;
         pairs[t] = active ? npair : 0;
