@@ -58,7 +58,7 @@ struct Sp2Rule {
 };
 
 constexpr int kEwWarps = 8;        // elementwise pass: warps per block (one leaf per warp at a time)
-constexpr int kEwBlocksPerSm = 3;  // and resident blocks per SM (register cap 85)
+constexpr int kEwBlocksPerSm = 4;  // and resident blocks per SM (register cap 64: more leaves in flight)
 constexpr int kRedThreads = 1024;
 constexpr int kBatch = 4;  // SP2 iterations enqueued between reads of the state
 
