@@ -127,103 +127,134 @@ k_slice(const int32_t *__restrict__ stop, const double *__restrict__ leaf, const
     static_assert(B * B % kThreads == 0, "leaf elements must be a multiple of the block size");
     __shared__ __align__(16) W sa[S * B * B];
     __shared__ unsigned long long s_xmax;
+    __shared__ int64_t s_pos[kThreads];  // positions of the chunk that have a leaf to slice
+    __shared__ int32_t s_slot[kThreads];
+    __shared__ int s_wcount[kThreads / 32];
     if (stop && *stop) return;  // the SP2 loop has already stopped
     const int sigma = sigma_of(*maxbits);
     if (blockIdx.x == 0 && threadIdx.x == 0 && sigma_out) *sigma_out = sigma;
-    for (int64_t pos = blockIdx.x; pos < rows * nb; pos += gridDim.x) {
-        const int64_t i = pos / nb, k = pos % nb;
-        // slot and norm loads issued together (the norm does not wait for the slot)
-        const int32_t sl = i < nb ? slot[i * nb + k] : -1;
-        const double nrm = i < nb ? n2[i * P + k] : 0.0;
-        // a leaf of squared norm 0 (and a padding position) takes part in no
-        // product: it is never in a work item's mask (A) and never a listed
-        // B leaf, so its slices are never read unmasked; skip it
-        if (sl < 0 || nrm == 0.0) continue;  // block-uniform
-        if (threadIdx.x == 0) s_xmax = 0;
-        __syncthreads();
-        unsigned long long xmax = 0;
-        const double *src = leaf + (int64_t)sl * (B * B);
-        if (perleaf && perleaf_transposed) {
-            double xs[kPerThread];  // all loads of the leaf issued before any is used
-#pragma unroll
-            for (int u = 0; u < kPerThread; u++) xs[u] = src[threadIdx.x + kThreads * u];
-#pragma unroll
-            for (int u = 0; u < kPerThread; u++) {
-                const int q = threadIdx.x + kThreads * u;
-                const int r = q / B, l = q % B;
-                const double x = xs[u];
-                const uint64_t X = float_split ? 0 : slice_int(x, sigma, S);
-                const bool neg = x < 0.0;
-                xmax = X > xmax ? X : xmax;
-                // outside |x| < 2^sigma (possible only with a caller-fixed scale)
-                if (!float_split && (X > (1ull << (7 * S)) || !(fabs(x) <= 1e300))) atomicExch(overflow, 1);
-                double rest = x;  // float split: s_p = round(x - s_0 - ... - s_{p-1})
-                // [p][g][cc][8 x ce], element (r, l) stored as (l, r)
-                const int o = slice_byte_offset<B, E>(l, r) / E;
-#pragma unroll
-                for (int p = 0; p < S; p++) sa[p * B * B + o] = (W)slice_elem<E>(X, neg, p, S, float_split, rest);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    // chunks of kThreads leaf positions: every thread tests one position
+    // (one round trip for the whole chunk), the block then slices the
+    // chunk's listed leaves one after the other
+    for (int64_t base = (int64_t)blockIdx.x * kThreads; base < rows * nb; base += (int64_t)gridDim.x * kThreads) {
+        {
+            const int64_t pos = base + threadIdx.x;
+            const int64_t i = pos / nb, k = pos % nb;
+            // slot and norm loads issued together (the norm does not wait for the slot)
+            const bool in = pos < rows * nb && i < nb;
+            const int32_t sl = in ? slot[i * nb + k] : -1;
+            const double nrm = in ? n2[i * P + k] : 0.0;
+            // a leaf of squared norm 0 (and a padding position) takes part in
+            // no product: it is never in a work item's mask (A) and never a
+            // listed B leaf, so its slices are never read unmasked; skip it
+            const bool need = sl >= 0 && nrm != 0.0;
+            const unsigned bal = __ballot_sync(0xffffffffu, need);
+            if (lane == 0) s_wcount[wid] = __popc(bal);
+            __syncthreads();
+            int at = __popc(bal & ((1u << lane) - 1u));
+            for (int q = 0; q < wid; q++) at += s_wcount[q];
+            if (need) {
+                s_pos[at] = pos;
+                s_slot[at] = sl;
             }
-        } else {
-            // untransposed: elements (r, l) and (r, l + 1), l even, are
-            // neighbours in every slice, so a thread takes such pairs and
-            // stores both with one shared-memory store per slice
-            using W2 = typename std::conditional<E == 4, uint2, uint32_t>::type;
-            constexpr int kPairs = kPerThread / 2;
-            double2 xs[kPairs];  // all loads of the leaf issued before any is used
+        }
+        __syncthreads();
+        int listed = 0;
+        for (int q = 0; q < kThreads / 32; q++) listed += s_wcount[q];
+        for (int li = 0; li < listed; li++) {
+            const int64_t pos = s_pos[li];
+            const int64_t i = pos / nb, k = pos % nb;
+            const int32_t sl = s_slot[li];
+            if (threadIdx.x == 0) s_xmax = 0;
+            __syncthreads();
+            unsigned long long xmax = 0;
+            const double *src = leaf + (int64_t)sl * (B * B);
+            if (perleaf && perleaf_transposed) {
+                double xs[kPerThread];  // all loads of the leaf issued before any is used
 #pragma unroll
-            for (int u = 0; u < kPairs; u++) xs[u] = reinterpret_cast<const double2 *>(src)[threadIdx.x + kThreads * u];
+                for (int u = 0; u < kPerThread; u++) xs[u] = src[threadIdx.x + kThreads * u];
 #pragma unroll
-            for (int u = 0; u < kPairs; u++) {
-                const int q = 2 * (threadIdx.x + kThreads * u);
-                const int r = q / B, l = q % B;
-                const double x0 = xs[u].x, x1 = xs[u].y;
-                const uint64_t X0 = float_split ? 0 : slice_int(x0, sigma, S);
-                const uint64_t X1 = float_split ? 0 : slice_int(x1, sigma, S);
-                xmax = X0 > xmax ? X0 : xmax;
-                xmax = X1 > xmax ? X1 : xmax;
-                if (!float_split && (X0 > (1ull << (7 * S)) || X1 > (1ull << (7 * S)) || !(fabs(x0) <= 1e300) ||
-                                     !(fabs(x1) <= 1e300)))
-                    atomicExch(overflow, 1);
-                double rest0 = x0, rest1 = x1;
-                W2 *sp = reinterpret_cast<W2 *>(reinterpret_cast<uint8_t *>(sa) + slice_byte_offset<B, E>(r, l));
+                for (int u = 0; u < kPerThread; u++) {
+                    const int q = threadIdx.x + kThreads * u;
+                    const int r = q / B, l = q % B;
+                    const double x = xs[u];
+                    const uint64_t X = float_split ? 0 : slice_int(x, sigma, S);
+                    const bool neg = x < 0.0;
+                    xmax = X > xmax ? X : xmax;
+                    // outside |x| < 2^sigma (possible only with a caller-fixed scale)
+                    if (!float_split && (X > (1ull << (7 * S)) || !(fabs(x) <= 1e300))) atomicExch(overflow, 1);
+                    double rest = x;  // float split: s_p = round(x - s_0 - ... - s_{p-1})
+                    // [p][g][cc][8 x ce], element (r, l) stored as (l, r)
+                    const int o = slice_byte_offset<B, E>(l, r) / E;
 #pragma unroll
-                for (int p = 0; p < S; p++) {
-                    const uint32_t v0 = slice_elem<E>(X0, x0 < 0.0, p, S, float_split, rest0);
-                    const uint32_t v1 = slice_elem<E>(X1, x1 < 0.0, p, S, float_split, rest1);
-                    W2 pr;
-                    if constexpr (E == 4) pr = make_uint2(v0, v1);
-                    else pr = (v0 & 0xFFFFu) | (v1 << 16);
-                    sp[p * (B * B * E / sizeof(W2))] = pr;
+                    for (int p = 0; p < S; p++) sa[p * B * B + o] = (W)slice_elem<E>(X, neg, p, S, float_split, rest);
+                }
+            } else {
+                // untransposed: elements (r, l) and (r, l + 1), l even, are
+                // neighbours in every slice, so a thread takes such pairs and
+                // stores both with one shared-memory store per slice
+                using W2 = typename std::conditional<E == 4, uint2, uint32_t>::type;
+                constexpr int kPairs = kPerThread / 2;
+                double2 xs[kPairs];  // all loads of the leaf issued before any is used
+#pragma unroll
+                for (int u = 0; u < kPairs; u++) xs[u] = reinterpret_cast<const double2 *>(src)[threadIdx.x + kThreads * u];
+#pragma unroll
+                for (int u = 0; u < kPairs; u++) {
+                    const int q = 2 * (threadIdx.x + kThreads * u);
+                    const int r = q / B, l = q % B;
+                    const double x0 = xs[u].x, x1 = xs[u].y;
+                    const uint64_t X0 = float_split ? 0 : slice_int(x0, sigma, S);
+                    const uint64_t X1 = float_split ? 0 : slice_int(x1, sigma, S);
+                    xmax = X0 > xmax ? X0 : xmax;
+                    xmax = X1 > xmax ? X1 : xmax;
+                    if (!float_split && (X0 > (1ull << (7 * S)) || X1 > (1ull << (7 * S)) || !(fabs(x0) <= 1e300) ||
+                                         !(fabs(x1) <= 1e300)))
+                        atomicExch(overflow, 1);
+                    double rest0 = x0, rest1 = x1;
+                    W2 *sp = reinterpret_cast<W2 *>(reinterpret_cast<uint8_t *>(sa) + slice_byte_offset<B, E>(r, l));
+#pragma unroll
+                    for (int p = 0; p < S; p++) {
+                        const uint32_t v0 = slice_elem<E>(X0, x0 < 0.0, p, S, float_split, rest0);
+                        const uint32_t v1 = slice_elem<E>(X1, x1 < 0.0, p, S, float_split, rest1);
+                        W2 pr;
+                        if constexpr (E == 4) pr = make_uint2(v0, v1);
+                        else pr = (v0 & 0xFFFFu) | (v1 << 16);
+                        sp[p * (B * B * E / sizeof(W2))] = pr;
+                    }
                 }
             }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long v = __shfl_xor_sync(0xffffffffu, xmax, o);
-            xmax = v > xmax ? v : xmax;
-        }
-        if ((threadIdx.x & 31) == 0 && xmax) atomicMax(&s_xmax, xmax);
-        __syncthreads();
-        if (threadIdx.x == 0 && zlead) {
-            // leading zero slices: X < 2^(7 (S - z)) for every element (float
-            // splits have none)
-            const unsigned long long xm = s_xmax;
-            const int bits = xm ? 64 - __clzll((long long)xm) : 0;
-            const int z = float_split ? 0 : S - (bits + 6) / 7;
-            zlead[sl] = (uint8_t)(z < 0 ? 0 : z);
-        }
-        const uint4 *ss = reinterpret_cast<const uint4 *>(sa);
-        if (perleaf) {
-            uint4 *d = reinterpret_cast<uint4 *>(perleaf + (int64_t)sl * (S * B * B * E));
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long v = __shfl_xor_sync(0xffffffffu, xmax, o);
+                xmax = v > xmax ? v : xmax;
+            }
+            if ((threadIdx.x & 31) == 0 && xmax) atomicMax(&s_xmax, xmax);
+            __syncthreads();
+            if (threadIdx.x == 0 && zlead) {
+                // leading zero slices: X < 2^(7 (S - z)) for every element (float
+                // splits have none)
+                const unsigned long long xm = s_xmax;
+                const int bits = xm ? 64 - __clzll((long long)xm) : 0;
+                const int z = float_split ? 0 : S - (bits + 6) / 7;
+                zlead[sl] = (uint8_t)(z < 0 ? 0 : z);
+            }
+            const uint4 *ss = reinterpret_cast<const uint4 *>(sa);
+            if (perleaf) {
+                uint4 *d = reinterpret_cast<uint4 *>(perleaf + (int64_t)sl * (S * B * B * E));
 #pragma unroll
-            for (int q = threadIdx.x; q < S * kU4; q += kThreads) d[q] = ss[q];
-        }
-        if (tileA && !perleaf_transposed) {
-            // tile-major: block (I, k) holds [p][L][slice] for its R rows
-            const int64_t I = i / R, L = i % R;
-            uint4 *d = reinterpret_cast<uint4 *>(tileA + ((I * nb + k) * S * R + L) * (int64_t)(B * B * E));
+                for (int q = threadIdx.x; q < S * kU4; q += kThreads) d[q] = ss[q];
+            }
+            if (tileA && !perleaf_transposed) {
+                // tile-major: block (I, k) holds [p][L][slice] for its R rows
+                const int64_t I = i / R, L = i % R;
+                uint4 *d = reinterpret_cast<uint4 *>(tileA + ((I * nb + k) * S * R + L) * (int64_t)(B * B * E));
 #pragma unroll
-            for (int q = threadIdx.x; q < S * kU4; q += kThreads) d[(q / kU4) * (R * kU4) + (q % kU4)] = ss[q];
+                for (int q = threadIdx.x; q < S * kU4; q += kThreads) d[(q / kU4) * (R * kU4) + (q % kU4)] = ss[q];
+            }
+            __syncthreads();
         }
+        // (the chunk's list and counts are rewritten only after the barrier
+        // that ends its last leaf, or this one when it listed none)
         __syncthreads();
     }
 }
@@ -409,7 +440,8 @@ int launch_slices(spamm_mat_t m, int s, int e, bool tile_a, bool per_leaf, bool 
     unsigned long long *mx = reinterpret_cast<unsigned long long *>(m->scale);
     int32_t *sig = reinterpret_cast<int32_t *>(m->scale + 1);
     const int64_t npos = rows * m->nb;
-    const unsigned grid = (unsigned)(npos < 65535 * 4 ? npos : 65535 * 4);
+    const int64_t chunks = (npos + kSliceThreads - 1) / kSliceThreads;  // a block takes kSliceThreads positions at a time
+    const unsigned grid = (unsigned)(chunks < 65535 * 4 ? chunks : 65535 * 4);
     // the tile-major array and a transposed per-leaf array need two passes
     const int passes = (tile_a && per_leaf && transposed) ? 2 : 1;
     for (int pass = 0; pass < passes; pass++) {
