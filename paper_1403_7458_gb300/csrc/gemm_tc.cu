@@ -41,13 +41,7 @@ template <int R>
 struct StepA {
     double a[R];
     int z[R];
-    __device__ __forceinline__ bool any() const
-    {
-        bool v = false;
-#pragma unroll
-        for (int r = 0; r < R; r++) v = v || a[r] != 0.0;
-        return v;
-    }
+    double amax;  // the largest of the a[r]: some row passes Eq. 4 iff this one does
 };
 
 template <int R>
@@ -68,6 +62,9 @@ __device__ __forceinline__ void load_step_a(const CullArgs &c, int64_t I, int64_
             // a leaf of nonzero norm is stored (its slot is valid)
             if (s.a[r] != 0.0) s.z[r] = c.zA[c.slotA[i * c.nb + k]];
         }
+    s.amax = s.a[0];
+#pragma unroll
+    for (int r = 1; r < R; r++) s.amax = fmax(s.amax, s.a[r]);
 }
 
 // Leading-zero slices of the B operand leaf (k, j) (symmetric: its image is
@@ -87,13 +84,12 @@ __device__ __forceinline__ int zb_slot(const CullArgs &c, int64_t j, int64_t k)
 // nonzero product.  ntask += surviving triples (symmetric mode: of the whole
 // product, see below); npair += slice pairs those triples need (p >= zA_i,
 // q >= zB, p + q < S).
+// b and zb: the squared norm of the B leaf and its zb_dense value.
 template <int R>
 __device__ __forceinline__ uint32_t tile_item(const CullArgs &c, const StepA<R> &s, int64_t I, int64_t j, int64_t k,
-                                              int &ntask, int &npair)
+                                              double b, int zb, int &ntask, int &npair)
 {
     if (k >= c.nb) return 0;
-    const double b = __ldg(c.n2BT + j * c.P + k);
-    int zb = zb_dense(c, j, k);  // issued with the norm
     if (b == 0.0) return 0;  // B leaf zero (or not stored): no triple of the step survives
     if (zb < 0) zb = zb_slot(c, j, k);
     uint32_t mask = 0;
@@ -129,21 +125,15 @@ __device__ __forceinline__ int item_pairs(uint32_t w, int S)
 // Work item of a two-column tile (I, J) at k (leaf 32, R = 4; tc::item_make2),
 // or 0.  Symmetric mode keeps only the triples of stored leaves (i <= j): a
 // leaf below the diagonal is the mirror of one above it.
+// bn and zbl: the two columns' B norms and zb_dense values.
 __device__ __forceinline__ uint32_t tile_item2(const CullArgs &c, const StepA<4> &s, int64_t I, int64_t J,
-                                               int64_t k, int &ntask, int &npair)
+                                               int64_t k, const double (&bn)[2], const int (&zbl)[2], int &ntask,
+                                               int &npair)
 {
     if (k >= c.nb) return 0;
     uint32_t mask[2] = {0u, 0u};
     int zbv[2] = {7, 7};
     int za = c.S;
-    double bn[2];
-    int zbl[2];
-#pragma unroll
-    for (int cc = 0; cc < 2; cc++) {  // both columns' loads issued together
-        const int64_t j = 2 * J + cc;
-        bn[cc] = j < c.nb ? __ldg(c.n2BT + j * c.P + k) : 0.0;
-        zbl[cc] = j < c.nb ? zb_dense(c, j, k) : 0;
-    }
 #pragma unroll
     for (int cc = 0; cc < 2; cc++) {
         const int64_t j = 2 * J + cc;
@@ -268,13 +258,29 @@ k_tile_count(CullArgs c, int32_t *__restrict__ counts, int32_t *__restrict__ tas
                 const int64_t k = kc * 32 + lane;
                 StepA<R> sa;
                 load_step_a<R>(c, I, k, sa);
-                if (!__any_sync(0xffffffffu, sa.any())) continue;  // no A leaf of the step is nonzero
+                if (!__any_sync(0xffffffffu, sa.amax != 0.0)) continue;  // no A leaf of the step is nonzero
                 for (int jt = jt0; jt < nt; jt++) {
                     const int64_t J = J0 + jt;
+                    // the B side (norms and leading zeros loaded together), and
+                    // first the largest A norm of the step against it: when no
+                    // lane passes, no triple of the tile's step survives
+                    double bn[W];
+                    int zbl[W];
+                    bool pass = false;
+#pragma unroll
+                    for (int cc = 0; cc < W; cc++) {
+                        const int64_t j = W * J + cc;
+                        const bool in = k < c.nb && j < c.nb;
+                        bn[cc] = in ? __ldg(c.n2BT + j * c.P + k) : 0.0;
+                        zbl[cc] = in ? zb_dense(c, j, k) : 0;
+                    }
+#pragma unroll
+                    for (int cc = 0; cc < W; cc++) pass = pass || keep_product(sa.amax, bn[cc], c.tau2);
+                    if (!__any_sync(0xffffffffu, pass)) continue;
                     int tk = 0, tp = 0;
                     uint32_t w;
-                    if constexpr (W == 2) w = tile_item2(c, sa, I, J, k, tk, tp);
-                    else w = tile_item<R>(c, sa, I, J, k, tk, tp);
+                    if constexpr (W == 2) w = tile_item2(c, sa, I, J, k, bn, zbl, tk, tp);
+                    else w = tile_item<R>(c, sa, I, J, k, bn[0], zbl[0], tk, tp);
                     const unsigned bal = __ballot_sync(0xffffffffu, w != 0);
                     // nothing survives and nothing is listed (a kept triple below
                     // the diagonal of a symmetric product counts 0 but may be listed)
