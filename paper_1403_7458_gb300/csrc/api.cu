@@ -245,6 +245,7 @@ static void ws_free(SpammWorkspace *ws, cudaStream_t s)
     spamm_release(ws->exec, s);
     spamm_release(ws->scan_part, s);
     spamm_release(ws->cmask, s);
+    spamm_release(ws->bgmax, s);
     *ws = SpammWorkspace();
 }
 

@@ -32,6 +32,9 @@ struct CullArgs {
     double tau2;
     int sym, S, R;  // R = 128 / b leaf rows per tile
     const int32_t *stop;  // set once an SP2 loop has stopped: nothing to do
+    // per group g of kCullCols leaf columns and k: the largest squared norm
+    // of the B leaves (k, j), j in the group (row g nb + k)
+    const double *bgmax;
 };
 
 // The A side of the candidates k of one step (one per lane): the squared
@@ -205,6 +208,25 @@ __global__ void k_coarse_mask(const int32_t *__restrict__ stop, const double *__
 // of the coarse tier's 32, so that they share one coarse block column).
 constexpr int kCullCols = 16;
 
+// bgmax[g nb + k] = max over the group's columns j of n2B[k, j] (B's
+// transposed norms n2BT[j P + k]): when the largest A norm of a k-step fails
+// Eq. 4 against it in every lane, no tile of the group has a triple there.
+__global__ void k_group_bmax(const int32_t *__restrict__ stop, const double *__restrict__ n2BT, int64_t P,
+                             int64_t nb, int64_t ng, double *__restrict__ bgmax)
+{
+    if (stop && *stop) return;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= ng * nb) return;
+    const int64_t g = q / nb, k = q % nb;
+    double m = 0.0;
+#pragma unroll 4
+    for (int jj = 0; jj < kCullCols; jj++) {
+        const int64_t j = g * kCullCols + jj;
+        if (j < nb) m = fmax(m, __ldg(n2BT + j * P + k));
+    }
+    bgmax[q] = m;
+}
+
 // One warp per tile row I and kCullCols leaf columns (kCullCols / W tiles):
 // for each step of 32 candidates k (lane = k) it loads the A side once and
 // tests it against every tile of the warp (ballot), writing each tile's work
@@ -258,7 +280,10 @@ k_tile_count(CullArgs c, int32_t *__restrict__ counts, int32_t *__restrict__ tas
                 const int64_t k = kc * 32 + lane;
                 StepA<R> sa;
                 load_step_a<R>(c, I, k, sa);
-                if (!__any_sync(0xffffffffu, sa.amax != 0.0)) continue;  // no A leaf of the step is nonzero
+                // no triple of the step survives in any tile of the warp: the
+                // largest A norm fails against the largest B norm of the group
+                const double bg = k < c.nb ? __ldg(c.bgmax + ((int64_t)W * J0 / kCullCols) * c.nb + k) : 0.0;
+                if (!__any_sync(0xffffffffu, keep_product(sa.amax, bg, c.tau2))) continue;
                 for (int jt = jt0; jt < nt; jt++) {
                     const int64_t J = J0 + jt;
                     // the B side (norms and leading zeros loaded together), and
@@ -543,6 +568,19 @@ int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, i
     // one warp per tile row and kCullCols leaf columns
     const int64_t cull_warps = nI * ((nbt + kCullCols / W - 1) / (kCullCols / W));
     const unsigned blocks = (unsigned)((cull_warps + kWarps - 1) / kWarps);
+    {
+        const int64_t ng = (nb + kCullCols - 1) / kCullCols, need = ng * nb;
+        if (ws->bgmax_cap < need) {
+            spamm_release(ws->bgmax, s);
+            ws->bgmax = nullptr;
+            ws->bgmax_cap = 0;
+            if ((rc = spamm_alloc((void **)&ws->bgmax, sizeof(double) * need, s))) return rc;
+            ws->bgmax_cap = need;
+        }
+        k_group_bmax<<<(unsigned)((need + 255) / 256), 256, 0, s>>>(ws->stop, c.n2BT, P, nb, ng, ws->bgmax);
+        SPAMM_CK_LAUNCH();
+        c.bgmax = ws->bgmax;
+    }
     const int64_t worst = T * nb;  // every tile owns a segment of nb items (one per k)
     if (ws->tlist_cap < worst) {
         spamm_release(ws->tlist, s);

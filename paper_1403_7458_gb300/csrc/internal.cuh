@@ -60,6 +60,8 @@ struct SpammWorkspace {
     int64_t tT = 0;                       // tiles of the last tile cull (totals at toff + tT)
     uint32_t *cmask = nullptr;            // tile cull: passing coarse k-blocks per coarse (row, column) pair
     int64_t cmask_cap = 0;                // uint32 words
+    double *bgmax = nullptr;              // tile cull: per group of 16 leaf columns j and k, max_j n2B[k, j]
+    int64_t bgmax_cap = 0;                // doubles
     int64_t *scan_part = nullptr;         // chunk partials of the multi-block scans (scan.cuh)
     int64_t scan_cap = 0;                 // int64 words
 };
