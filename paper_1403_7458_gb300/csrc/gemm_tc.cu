@@ -35,6 +35,7 @@ struct CullArgs {
     // per group g of kCullCols leaf columns and k: the largest squared norm
     // of the B leaves (k, j), j in the group (row g nb + k)
     const double *bgmax;
+    int cols;  // leaf columns per warp of k_tile_count: kCullCols, or a divisor of it for small products
 };
 
 // The A side of the candidates k of one step (one per lane): the squared
@@ -227,8 +228,8 @@ __global__ void k_group_bmax(const int32_t *__restrict__ stop, const double *__r
     bgmax[q] = m;
 }
 
-// One warp per tile row I and kCullCols leaf columns (kCullCols / W tiles):
-// for each step of 32 candidates k (lane = k) it loads the A side once and
+// One warp per tile row I and c.cols leaf columns (c.cols / W tiles; c.cols
+// divides kCullCols): for each step of 32 candidates k (lane = k) it loads the A side once and
 // tests it against every tile of the warp (ballot), writing each tile's work
 // items into the tile's own segment of the list, [t nb, t nb + count), in
 // increasing k.  Per tile it counts the items, the surviving triples and the
@@ -243,8 +244,8 @@ k_tile_count(CullArgs c, int32_t *__restrict__ counts, int32_t *__restrict__ tas
              int32_t *__restrict__ pairs, int32_t *__restrict__ useful, int32_t *__restrict__ d0out,
              uint32_t *__restrict__ list)
 {
-    constexpr int NT = kCullCols / W;  // tiles per warp
-    static_assert(NT <= 32, "a lane holds the counts of one tile");
+    const int NT = c.cols / W;  // tiles per warp
+    static_assert(kCullCols / W <= 32, "a lane holds the counts of one tile");
     static_assert(W == 1 || R == 4, "two-column tiles have four leaf rows");
     if (c.stop && *c.stop) return;
     const int64_t gw = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
@@ -282,6 +283,7 @@ k_tile_count(CullArgs c, int32_t *__restrict__ counts, int32_t *__restrict__ tas
                 load_step_a<R>(c, I, k, sa);
                 // no triple of the step survives in any tile of the warp: the
                 // largest A norm fails against the largest B norm of the group
+                // (the warp's columns lie in one group of kCullCols)
                 const double bg = k < c.nb ? __ldg(c.bgmax + ((int64_t)W * J0 / kCullCols) * c.nb + k) : 0.0;
                 if (!__any_sync(0xffffffffu, keep_product(sa.amax, bg, c.tau2))) continue;
                 for (int jt = jt0; jt < nt; jt++) {
@@ -565,8 +567,12 @@ int tc_tile_cull(spamm_mat_t A, spamm_mat_t B, double tau, SpammWorkspace *ws, i
         SPAMM_CK_LAUNCH();
         c.cmask = ws->cmask;
     }
-    // one warp per tile row and kCullCols leaf columns
-    const int64_t cull_warps = nI * ((nbt + kCullCols / W - 1) / (kCullCols / W));
+    // one warp per tile row and c.cols leaf columns: kCullCols (the A side
+    // of a step then serves the most tiles), fewer when that would leave
+    // the GPU with under 32 warps per SM
+    c.cols = kCullCols;
+    while (c.cols > W && nI * ((nbt + c.cols / W - 1) / (c.cols / W)) < (int64_t)spamm_num_sms() * 32) c.cols /= 2;
+    const int64_t cull_warps = nI * ((nbt + c.cols / W - 1) / (c.cols / W));
     const unsigned blocks = (unsigned)((cull_warps + kWarps - 1) / kWarps);
     {
         const int64_t ng = (nb + kCullCols - 1) / kCullCols, need = ng * nb;

@@ -117,7 +117,7 @@ k_slice(const int32_t *__restrict__ stop, const double *__restrict__ leaf, const
         const double *__restrict__ n2, int64_t P, int64_t nb, int64_t rows,
         const unsigned long long *__restrict__ maxbits, int32_t *__restrict__ sigma_out,
         uint8_t *__restrict__ tileA, uint8_t *__restrict__ perleaf, int perleaf_transposed,
-        uint8_t *__restrict__ zlead, int32_t *__restrict__ overflow, int float_split)
+        uint8_t *__restrict__ zlead, int32_t *__restrict__ overflow, int float_split, int chunk)
 {
     using W = typename std::conditional<E == 4, uint32_t, uint16_t>::type;
     constexpr int R = 128 / B;               // leaf rows per tile
@@ -134,15 +134,15 @@ k_slice(const int32_t *__restrict__ stop, const double *__restrict__ leaf, const
     const int sigma = sigma_of(*maxbits);
     if (blockIdx.x == 0 && threadIdx.x == 0 && sigma_out) *sigma_out = sigma;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    // chunks of kThreads leaf positions: every thread tests one position
-    // (one round trip for the whole chunk), the block then slices the
-    // chunk's listed leaves one after the other
-    for (int64_t base = (int64_t)blockIdx.x * kThreads; base < rows * nb; base += (int64_t)gridDim.x * kThreads) {
+    // chunks of `chunk` <= kThreads leaf positions: thread t tests position
+    // t of the chunk (one round trip for the whole chunk), the block then
+    // slices the chunk's listed leaves one after the other
+    for (int64_t base = (int64_t)blockIdx.x * chunk; base < rows * nb; base += (int64_t)gridDim.x * chunk) {
         {
             const int64_t pos = base + threadIdx.x;
             const int64_t i = pos / nb, k = pos % nb;
             // slot and norm loads issued together (the norm does not wait for the slot)
-            const bool in = pos < rows * nb && i < nb;
+            const bool in = threadIdx.x < chunk && pos < rows * nb && i < nb;
             const int32_t sl = in ? slot[i * nb + k] : -1;
             const double nrm = in ? n2[i * P + k] : 0.0;
             // a leaf of squared norm 0 (and a padding position) takes part in
@@ -372,22 +372,22 @@ int slices_tmaps(spamm_mat_t m, cudaStream_t st)
 namespace {
 
 template <int S, int E, int B>
-void slice_launch(unsigned grid, cudaStream_t st, const int32_t *stop, spamm_mat_t m, int64_t rows,
+void slice_launch(unsigned grid, int chunk, cudaStream_t st, const int32_t *stop, spamm_mat_t m, int64_t rows,
                   unsigned long long *mx, int32_t *sig, uint8_t *ta, uint8_t *pl, int tr, uint8_t *zl,
                   int float_split)
 {
     k_slice<S, E, B><<<grid, kSliceThreads, 0, st>>>(stop, m->leaf, m->slot, m->n2 + tier_offset(m->depth), m->P, m->nb,
-                                           rows, mx, sig, ta, pl, tr, zl, sig + 1, float_split);
+                                           rows, mx, sig, ta, pl, tr, zl, sig + 1, float_split, chunk);
 }
 
 template <int B>
-bool slice_dispatch_b(int s, int e, unsigned grid, cudaStream_t st, const int32_t *stop, spamm_mat_t m,
+bool slice_dispatch_b(int s, int e, unsigned grid, int chunk, cudaStream_t st, const int32_t *stop, spamm_mat_t m,
                       int64_t rows, unsigned long long *mx, int32_t *sig, uint8_t *ta, uint8_t *pl, int tr,
                       uint8_t *zl, int fs)
 {
 #define SPAMM_SLICE_CASE(SS, EE)                                              \
     if (s == SS && e == EE && SS * B <= 256) {                                \
-        slice_launch<SS, EE, B>(grid, st, stop, m, rows, mx, sig, ta, pl, tr, zl, fs); \
+        slice_launch<SS, EE, B>(grid, chunk, st, stop, m, rows, mx, sig, ta, pl, tr, zl, fs); \
         return true;                                                          \
     }
     SPAMM_SLICE_CASE(1, 2)
@@ -440,7 +440,11 @@ int launch_slices(spamm_mat_t m, int s, int e, bool tile_a, bool per_leaf, bool 
     unsigned long long *mx = reinterpret_cast<unsigned long long *>(m->scale);
     int32_t *sig = reinterpret_cast<int32_t *>(m->scale + 1);
     const int64_t npos = rows * m->nb;
-    const int64_t chunks = (npos + kSliceThreads - 1) / kSliceThreads;  // a block takes kSliceThreads positions at a time
+    // positions a block tests at once: up to kSliceThreads, fewer when that
+    // would leave the GPU with too few blocks (about 16 per SM)
+    int64_t chunk = npos / ((int64_t)spamm_num_sms() * 16);
+    chunk = chunk < 1 ? 1 : (chunk > kSliceThreads ? kSliceThreads : chunk);
+    const int64_t chunks = (npos + chunk - 1) / chunk;
     const unsigned grid = (unsigned)(chunks < 65535 * 4 ? chunks : 65535 * 4);
     // the tile-major array and a transposed per-leaf array need two passes
     const int passes = (tile_a && per_leaf && transposed) ? 2 : 1;
@@ -452,9 +456,9 @@ int launch_slices(spamm_mat_t m, int s, int e, bool tile_a, bool per_leaf, bool 
         const int fs = float_split ? 1 : 0;
         bool ok = false;
         switch (m->b) {
-        case 16: ok = slice_dispatch_b<16>(s, e, grid, st, stop, m, rows, mx, sig, ta, pl, tr, zl, fs); break;
-        case 32: ok = slice_dispatch_b<32>(s, e, grid, st, stop, m, rows, mx, sig, ta, pl, tr, zl, fs); break;
-        case 64: ok = slice_dispatch_b<64>(s, e, grid, st, stop, m, rows, mx, sig, ta, pl, tr, zl, fs); break;
+        case 16: ok = slice_dispatch_b<16>(s, e, grid, (int)chunk, st, stop, m, rows, mx, sig, ta, pl, tr, zl, fs); break;
+        case 32: ok = slice_dispatch_b<32>(s, e, grid, (int)chunk, st, stop, m, rows, mx, sig, ta, pl, tr, zl, fs); break;
+        case 64: ok = slice_dispatch_b<64>(s, e, grid, (int)chunk, st, stop, m, rows, mx, sig, ta, pl, tr, zl, fs); break;
         }
         if (!ok) {
             spamm_set_error("slices: %d slices of %d-byte elements at leaf %d not built", s, e, m->b);
