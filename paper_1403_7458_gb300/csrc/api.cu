@@ -159,27 +159,45 @@ __global__ void k_iota_slots(int32_t *slot, int64_t count)
 
 // Dense row-major n x n (leading dimension lda) -> leaf storage, zero-filling
 // the ragged edge.  One thread per element of the padded nb*b square.
-__global__ void k_pack(const double *__restrict__ a, int64_t n, int64_t lda, int b, int64_t nb,
+// Dense <-> leaf layout.  Rows r of the padded Np x Np matrix are taken by
+// blockIdx.y (strided), columns c by the x threads, so that consecutive
+// threads touch consecutive doubles; b = 2^lb (16, 32 or 64).
+__global__ void k_pack(const double *__restrict__ a, int64_t n, int64_t lda, int lb, int64_t nb,
                        const int32_t *__restrict__ slot, double *__restrict__ leaf)
 {
-    int64_t Np = nb * b;
-    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= Np * Np) return;
-    int64_t r = q / Np, c = q % Np;
-    double v = (r < n && c < n) ? a[r * lda + c] : 0.0;
-    int32_t s = slot[(r / b) * nb + c / b];
-    if (s >= 0) leaf[(int64_t)s * b * b + (r % b) * b + (c % b)] = v;
+    const int b = 1 << lb;
+    const int64_t Np = nb * b;
+    for (int64_t r = blockIdx.y; r < Np; r += gridDim.y) {
+        const int64_t I = r >> lb, rr = r & (b - 1);
+        for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < Np; c += (int64_t)gridDim.x * blockDim.x) {
+            const double v = (r < n && c < n) ? a[r * lda + c] : 0.0;
+            const int32_t s = slot[I * nb + (c >> lb)];
+            if (s >= 0) leaf[((int64_t)s << (2 * lb)) + (rr << lb) + (c & (b - 1))] = v;
+        }
+    }
 }
 
 __global__ void k_unpack(const double *__restrict__ leaf, const int32_t *__restrict__ slot,
-                         int64_t n, int b, int64_t nb, double *__restrict__ dst, int64_t ld)
+                         int64_t n, int lb, int64_t nb, double *__restrict__ dst, int64_t ld)
 {
-    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= n * n) return;
-    int64_t r = q / n, c = q % n;
-    int32_t s = slot[(r / b) * nb + c / b];
-    dst[r * ld + c] = s >= 0 ? leaf[(int64_t)s * b * b + (r % b) * b + (c % b)] : 0.0;
+    const int b = 1 << lb;
+    for (int64_t r = blockIdx.y; r < n; r += gridDim.y) {
+        const int64_t I = r >> lb, rr = r & (b - 1);
+        for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+            const int32_t s = slot[I * nb + (c >> lb)];
+            dst[r * ld + c] = s >= 0 ? leaf[((int64_t)s << (2 * lb)) + (rr << lb) + (c & (b - 1))] : 0.0;
+        }
+    }
 }
+
+// Launch shape of k_pack / k_unpack over `rows` x `cols` elements.
+static dim3 pack_grid(int64_t rows, int64_t cols)
+{
+    const int64_t gx = (cols + 255) / 256, gy = rows < 4096 ? rows : 4096;
+    return dim3((unsigned)(gx < 1024 ? gx : 1024), (unsigned)(gy < 1 ? 1 : gy));
+}
+
+static int log2_leaf(int b) { return b == 16 ? 4 : b == 32 ? 5 : 6; }
 
 bool is_device_ptr(const void *p)
 {
@@ -286,26 +304,31 @@ extern "C" void spamm_release_scratch(spamm_mat_t m, void *stream)
 
 // Sparse storage: flags of the leaves kept (squared norm > drop2), their
 // exclusive prefix count (one block), the compacted leaf array.
-__global__ void k_keep_scan(const double *__restrict__ n2, int64_t nb, int64_t P, double drop2,
-                            int32_t *__restrict__ slot, int64_t *__restrict__ total)
+// Leaves kept by a drop threshold: flag[q] = 1 when leaf q's squared norm
+// exceeds drop2 (scanned by scan.cuh into slots).
+__global__ void k_keep_flags(const double *__restrict__ n2, int64_t nb, int64_t P, double drop2,
+                             int32_t *__restrict__ flag)
 {
-    __shared__ int64_t part[1024];
-    const int t = threadIdx.x;
-    const int64_t G = nb * nb, chunk = (G + 1023) / 1024;
-    const int64_t lo = t * chunk, hi = lo + chunk < G ? lo + chunk : G;
-    int64_t c = 0;
-    for (int64_t q = lo; q < hi; q++) c += n2[(q / nb) * P + q % nb] > drop2;
-    part[t] = c;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        const int64_t v = t >= o ? part[t - o] : 0;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nb * nb) return;
+    flag[q] = n2[(q / nb) * P + q % nb] > drop2 ? 1 : 0;
+}
+
+// slot[q] = rank of leaf q among the kept ones, or -1; a dropped leaf's
+// squared norm (and its transposed copy) becomes 0.
+__global__ void k_keep_slots(const int32_t *__restrict__ flag, const int64_t *__restrict__ off, int64_t nb,
+                             int64_t P, int32_t *__restrict__ slot, double *__restrict__ n2, double *__restrict__ n2T)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nb * nb) return;
+    const int64_t i = q / nb, k = q % nb;
+    if (flag[q]) {
+        slot[q] = (int32_t)off[q];
+    } else {
+        slot[q] = -1;
+        n2[i * P + k] = 0.0;
+        n2T[k * P + i] = 0.0;
     }
-    int64_t run = part[t] - c;
-    for (int64_t q = lo; q < hi; q++) slot[q] = n2[(q / nb) * P + q % nb] > drop2 ? (int32_t)run++ : -1;
-    if (t == 1023) *total = part[t];
 }
 
 __global__ void k_gather_leaves(const double *__restrict__ dense, const int32_t *__restrict__ slot, int64_t G,
@@ -322,29 +345,48 @@ __global__ void k_gather_leaves(const double *__restrict__ dense, const int32_t 
 // out): dropped leaves get norm 0 and the pyramid is rebuilt.
 static int compact_leaves(spamm_mat_t m, double drop2, cudaStream_t s)
 {
-    const int64_t G = m->nb * m->nb;
-    int64_t *total = nullptr;
-    int32_t *slot = nullptr;
+    const int64_t G = m->nb * m->nb, nch = (G + scan::kChunk - 1) / scan::kChunk;
+    int32_t *flag = nullptr, *slot = nullptr;
+    int64_t *off = nullptr, *part = nullptr;
+    auto release = [&]() {
+        spamm_release(flag, s);
+        spamm_release(off, s);
+        spamm_release(part, s);
+    };
     int rc;
-    if ((rc = spamm_alloc((void **)&total, sizeof(int64_t), s))) return rc;
-    if ((rc = spamm_alloc((void **)&slot, sizeof(int32_t) * G, s))) {
-        spamm_release(total, s);
+    if ((rc = spamm_alloc((void **)&flag, sizeof(int32_t) * G, s)) ||
+        (rc = spamm_alloc((void **)&off, sizeof(int64_t) * (G + 1), s)) ||
+        (rc = spamm_alloc((void **)&part, sizeof(int64_t) * scan::part_words(G), s)) ||
+        (rc = spamm_alloc((void **)&slot, sizeof(int32_t) * G, s))) {
+        release();
         return rc;
     }
-    k_keep_scan<<<1, 1024, 0, s>>>(m->n2 + tier_offset(m->depth), m->nb, m->P, drop2, slot, total);
-    spamm_note_launches(1);
+    double *n2 = m->n2 + tier_offset(m->depth);
+    k_keep_flags<<<blocks_for(G, 256), 256, 0, s>>>(n2, m->nb, m->P, drop2, flag);
+    scan::k_sums<false><<<(unsigned)nch, scan::kThreads, 0, s>>>(nullptr, flag, nullptr, nullptr, nullptr, G, part);
+    scan::k_top<false><<<1, scan::kTopThreads, 0, s>>>(nullptr, part, nch, off + G, nullptr, nullptr, nullptr);
+    scan::k_apply<false><<<(unsigned)nch, scan::kThreads, 0, s>>>(nullptr, flag, G, part, off, nullptr, nullptr);
+    spamm_note_launches(4);
     int64_t kept = 0;
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&kept, total, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&kept, off + G, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    spamm_release(total, s);
     if (e != cudaSuccess) {
+        release();
         spamm_release(slot, s);
         return spamm_cuda_fail(e, "sparse leaf count", __FILE__, __LINE__);
     }
     if (kept == G) {  // nothing dropped: stay dense
+        release();
         spamm_release(slot, s);
         return SPAMM_OK;
+    }
+    k_keep_slots<<<blocks_for(G, 256), 256, 0, s>>>(flag, off, m->nb, m->P, slot, n2, m->n2T);
+    spamm_note_launches(1);
+    release();
+    if ((e = cudaGetLastError()) != cudaSuccess) {
+        spamm_release(slot, s);
+        return spamm_cuda_fail(e, "k_keep_slots", __FILE__, __LINE__);
     }
     const int bb = m->b * m->b;
     double *packed = nullptr;
@@ -366,8 +408,9 @@ static int compact_leaves(spamm_mat_t m, double drop2, cudaStream_t s)
     m->leaf = packed;
     m->slot = slot;
     m->nslots = kept;
-    // the norms of the matrix as stored: dropped leaves are zero
-    return launch_leaf_norms(m, s);
+    // the leaf norms are those of the matrix as stored (a kept leaf's data
+    // is unchanged, a dropped leaf's norm was set to 0): rebuild the tiers
+    return launch_pyramid(m, s);
 }
 
 extern "C" int spamm_tree_build(const double *a, int64_t n, int64_t lda, double drop, const spamm_opts_t *opts,
@@ -409,7 +452,7 @@ extern "C" int spamm_tree_build(const double *a, int64_t n, int64_t lda, double 
         lda = n;
     }
     int64_t Np = m->nb * b;
-    k_pack<<<blocks_for(Np * Np, 256), 256, 0, s>>>(src, n, lda, b, m->nb, m->slot, m->leaf);
+    k_pack<<<pack_grid(Np, Np), 256, 0, s>>>(src, n, lda, log2_leaf(b), m->nb, m->slot, m->leaf);
     spamm_note_launches(1);
     cudaError_t e = cudaGetLastError();
     if (staging) spamm_release(staging, s);
@@ -445,14 +488,14 @@ extern "C" int spamm_to_dense(spamm_mat_t m, double *dst, int64_t ld, void *stre
     cudaStream_t s = (cudaStream_t)stream;
     int64_t n = m->n;
     if (is_device_ptr(dst)) {
-        k_unpack<<<blocks_for(n * n, 256), 256, 0, s>>>(m->leaf, m->slot, n, m->b, m->nb, dst, ld);
+        k_unpack<<<pack_grid(n, n), 256, 0, s>>>(m->leaf, m->slot, n, log2_leaf(m->b), m->nb, dst, ld);
         SPAMM_CK_LAUNCH();
         return SPAMM_OK;
     }
     double *tmp = nullptr;
     int rc = spamm_alloc((void **)&tmp, sizeof(double) * n * n, s);
     if (rc) return rc;
-    k_unpack<<<blocks_for(n * n, 256), 256, 0, s>>>(m->leaf, m->slot, n, m->b, m->nb, tmp, n);
+    k_unpack<<<pack_grid(n, n), 256, 0, s>>>(m->leaf, m->slot, n, log2_leaf(m->b), m->nb, tmp, n);
     spamm_note_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
