@@ -322,25 +322,43 @@ __device__ __noinline__ double combine_exact_slow(const uint32_t *f, int d0, int
 
 // The 16 values of one TMEM load group at once (straight-line code, so that
 // the 16 chains interleave): fast path for all of them when every one
-// qualifies, else the 128-bit path for each.
+// qualifies, else the 128-bit path for each.  The fast path pairs the
+// diagonals from the bottom, P_j = S_(S-1-2j) + 128 S_(S-2-2j): with every
+// |S_d| < 2^22 a pair fits an int32 and is formed on the raw FP32 bits
+// (each S_d + 1.5 2^23 carries the integer in its low bits; the offsets are
+// removed once per pair, modulo 2^32, which is exact since the true value
+// fits), and the total is sum_j P_j 2^(14 j) in int64.
 template <int S>
 __device__ __forceinline__ void combine_exact16(const uint32_t (&v)[S][16], int d0, int k, double (&res)[16])
 {
+    constexpr uint32_t kMagicBits = 0x4B400000u;  // bits of 1.5 2^23
     bool fast = true;
     long long a[16];
 #pragma unroll
     for (int q = 0; q < 16; q++) a[q] = 0;
 #pragma unroll
-    for (int d = 0; d < S; d++) {
-        if (d < d0) continue;  // warp-uniform: diagonals below d0 are zero
-        const int sh = 7 * (S - 1 - d);
-        const float lim = sh + 22 <= 59 ? 4194304.0f : __int_as_float((127 + 59 - sh) << 23);  // 2^min(22, 59 - sh)
+    for (int j = 0; j < (S + 1) / 2; j++) {
+        const int da = S - 1 - 2 * j, db = da - 1;  // db < 0: the top diagonal alone (S odd)
+        if (da < d0) continue;  // warp-uniform: both diagonals below d0 are zero
+        // |S_d| < 2^min(22, 59 - 7 (S - 1 - d)): exact conversion, no int64 overflow
+        const float lima = 7 * (S - 1 - da) + 22 <= 59 ? 4194304.0f : __int_as_float((127 + 59 - 7 * (S - 1 - da)) << 23);
+        const float limb = db < 0 || 7 * (S - 1 - db) + 22 <= 59 ? 4194304.0f
+                                                               : __int_as_float((127 + 59 - 7 * (S - 1 - db)) << 23);
 #pragma unroll
         for (int q = 0; q < 16; q++) {
-            const float f = __uint_as_float(v[d][q]);
-            fast = fast && fabsf(f) < lim;
-            const int iv = __float_as_int(f + 12582912.0f) - 0x4B400000;
-            a[q] += (long long)iv << sh;
+            const float fa = __uint_as_float(v[da][q]);
+            fast = fast && fabsf(fa) < lima;
+            const uint32_t ua = __float_as_uint(fa + 12582912.0f);
+            int32_t p;
+            if (db >= 0) {
+                const float fb = __uint_as_float(v[db][q]);
+                fast = fast && fabsf(fb) < limb;
+                const uint32_t ub = __float_as_uint(fb + 12582912.0f);
+                p = (int32_t)(ua + (ub << 7) - 129u * kMagicBits);
+            } else {
+                p = (int32_t)(ua - kMagicBits);
+            }
+            a[q] += (long long)p << (14 * j);
         }
     }
     if (fast) {
