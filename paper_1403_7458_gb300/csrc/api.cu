@@ -264,6 +264,7 @@ static void ws_free(SpammWorkspace *ws, cudaStream_t s)
     spamm_release(ws->scan_part, s);
     spamm_release(ws->cmask, s);
     spamm_release(ws->bgmax, s);
+    spamm_release(ws->lmax, s);
     *ws = SpammWorkspace();
 }
 
@@ -591,17 +592,72 @@ int ws_reserve_scan(SpammWorkspace *ws, int64_t G, cudaStream_t s)
 // and B's per-leaf array (B-role layout).  A symmetric product A == B reads
 // its B leaves (the A-role layout of the transpose leaves) from the
 // tile-major array itself, through tensor maps: no per-leaf array.
-static int slice_operands(spamm_mat_t A, spamm_mat_t B, int sl, int el, int symm, cudaStream_t s,
-                          const int32_t *stop, bool unit, bool fsplit)
+// out[r] = the largest of x[r P + j] (and of y[r P + j] when given) over the
+// nb leaf columns j: one warp per row r.
+__global__ void k_line_max(const int32_t *__restrict__ stop, const double *__restrict__ x,
+                           const double *__restrict__ y, int64_t nb, int64_t P, double *__restrict__ out)
 {
+    if (stop && *stop) return;
+    const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= nb) return;
+    double m = 0.0;
+    for (int64_t j = lane; j < nb; j += 32) {
+        m = fmax(m, x[r * P + j]);
+        if (y) m = fmax(m, y[r * P + j]);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) out[r] = m;
+}
+
+// Slices of the operands of one product.  With prune (the slices serve this
+// product alone), leaves that fail Eq. 4 against their largest partner are
+// not sliced: an A leaf (i, k) against max_j ||B_kj||^2, a B leaf (k, j)
+// against max_i ||A_ik||^2 (symmetric: both, from the norms and their
+// transposes).  No kept triple involves such a leaf (the product of its norm
+// with any partner's is at most the product with the largest).
+static int slice_operands(spamm_mat_t A, spamm_mat_t B, int sl, int el, int symm, cudaStream_t s,
+                          const int32_t *stop, bool unit, bool fsplit, SpammWorkspace *ws = nullptr,
+                          double tau = 0.0)
+{
+    const double *keep_a = nullptr, *keep_b = nullptr;
+    const double tau2 = tau * tau;
+    // (A == B without symmetry: one leading-zero count per leaf serves both
+    // roles, so every leaf either role needs must be sliced: no pruning)
+    if (ws && !(A == B && !symm)) {
+        const int64_t nb = A->nb;
+        int rc;
+        if (ws->lmax_cap < 2 * nb) {
+            spamm_release(ws->lmax, s);
+            ws->lmax = nullptr;
+            ws->lmax_cap = 0;
+            if ((rc = spamm_alloc((void **)&ws->lmax, sizeof(double) * 2 * nb, s))) return rc;
+            ws->lmax_cap = 2 * nb;
+        }
+        const unsigned blocks = (unsigned)((nb + 7) / 8);
+        const double *nB = B->n2 + tier_offset(B->depth);
+        if (A == B && symm) {
+            k_line_max<<<blocks, 256, 0, s>>>(stop, nB, B->n2T, nb, B->P, ws->lmax);
+            SPAMM_CK_LAUNCH();
+            keep_a = ws->lmax;
+        } else {
+            k_line_max<<<blocks, 256, 0, s>>>(stop, nB, nullptr, nb, B->P, ws->lmax);  // rows of B
+            SPAMM_CK_LAUNCH();
+            k_line_max<<<blocks, 256, 0, s>>>(stop, A->n2T, nullptr, nb, A->P, ws->lmax + nb);  // columns of A
+            SPAMM_CK_LAUNCH();
+            keep_a = ws->lmax;
+            keep_b = ws->lmax + nb;
+        }
+    }
     if (A == B && symm) {
-        if (int rc = launch_slices(A, sl, el, true, false, false, s, stop, unit, fsplit)) return rc;
+        if (int rc = launch_slices(A, sl, el, true, false, false, s, stop, unit, fsplit, keep_a, nullptr, tau2))
+            return rc;
         return slices_tmaps(A, s);
     }
     if (A == B) return launch_slices(A, sl, el, true, true, true, s, stop, unit, fsplit);
-    int rc = launch_slices(A, sl, el, true, false, false, s, stop, unit, fsplit);
+    int rc = launch_slices(A, sl, el, true, false, false, s, stop, unit, fsplit, keep_a, nullptr, tau2);
     if (rc) return rc;
-    return launch_slices(B, sl, el, false, true, true, s, stop, unit, fsplit);
+    return launch_slices(B, sl, el, false, true, true, s, stop, unit, fsplit, nullptr, keep_b, tau2);
 }
 
 // Device-side error words of a product's workspace (blocking read): list
@@ -650,7 +706,7 @@ int spamm_multiply_into(spamm_mat_t A, spamm_mat_t B, double tau, spamm_mat_t C,
         // slices first: the tile cull reads each leaf's leading zero slices
         if (slices_ready) {
             // the caller already wrote A's slices
-        } else if ((rc = slice_operands(A, B, sl, el, symm, s, ws->stop, unit, fsplit))) {
+        } else if ((rc = slice_operands(A, B, sl, el, symm, s, ws->stop, unit, fsplit, ws, tau))) {
             return rc;
         }
         const bool heavy = opts && (opts->flags & SPAMM_F_HEAVIEST);

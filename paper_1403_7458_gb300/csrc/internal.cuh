@@ -62,6 +62,8 @@ struct SpammWorkspace {
     int64_t cmask_cap = 0;                // uint32 words
     double *bgmax = nullptr;              // tile cull: per group of 16 leaf columns j and k, max_j n2B[k, j]
     int64_t bgmax_cap = 0;                // doubles
+    double *lmax = nullptr;               // slicing: largest partner norm per row / column (2 nb)
+    int64_t lmax_cap = 0;                 // doubles
     int64_t *scan_part = nullptr;         // chunk partials of the multi-block scans (scan.cuh)
     int64_t scan_cap = 0;                 // int64 words
 };
@@ -191,8 +193,12 @@ int64_t spamm_launch_count();
 
 // Tensor-core path (slice.cu, gemm_tc*.cu).  e = bytes per slice element:
 // 2 (BF16, tcgen05 kind::f16) or 4 (TF32, kind::tf32).
+// keep_a / keep_b (optional, nb entries): largest partner norm per column
+// (A role) / per row (B role); leaves that fail Eq. 4 against it are not
+// sliced (the slices then serve only the product they were made for).
 int launch_slices(spamm_mat_t m, int s, int e, bool tile_a, bool per_leaf, bool transposed, cudaStream_t st,
-                  const int32_t *stop = nullptr, bool unit_scale = false, bool float_split = false);
+                  const int32_t *stop = nullptr, bool unit_scale = false, bool float_split = false,
+                  const double *keep_a = nullptr, const double *keep_b = nullptr, double tau2 = 0.0);
 
 // Tensor-core precision modes: slices per operand, element size, and whether
 // the slices are exact integer digits (Ozaki) or a float split.

@@ -117,7 +117,8 @@ k_slice(const int32_t *__restrict__ stop, const double *__restrict__ leaf, const
         const double *__restrict__ n2, int64_t P, int64_t nb, int64_t rows,
         const unsigned long long *__restrict__ maxbits, int32_t *__restrict__ sigma_out,
         uint8_t *__restrict__ tileA, uint8_t *__restrict__ perleaf, int perleaf_transposed,
-        uint8_t *__restrict__ zlead, int32_t *__restrict__ overflow, int float_split, int chunk)
+        uint8_t *__restrict__ zlead, int32_t *__restrict__ overflow, int float_split, int chunk,
+        const double *__restrict__ keep_max, int keep_by_row, double tau2)
 {
     using W = typename std::conditional<E == 4, uint32_t, uint16_t>::type;
     constexpr int R = 128 / B;               // leaf rows per tile
@@ -148,7 +149,11 @@ k_slice(const int32_t *__restrict__ stop, const double *__restrict__ leaf, const
             // a leaf of squared norm 0 (and a padding position) takes part in
             // no product: it is never in a work item's mask (A) and never a
             // listed B leaf, so its slices are never read unmasked; skip it
-            const bool need = sl >= 0 && nrm != 0.0;
+            // with keep_max, also a leaf whose norm fails Eq. 4 against every
+            // partner (keep_max holds the largest partner norm per row or
+            // column): no kept triple uses it, so no product reads its slices
+            const bool need = sl >= 0 && nrm != 0.0 &&
+                              (!keep_max || keep_product(nrm, keep_max[keep_by_row ? i : k], tau2));
             const unsigned bal = __ballot_sync(0xffffffffu, need);
             if (lane == 0) s_wcount[wid] = __popc(bal);
             __syncthreads();
@@ -374,20 +379,21 @@ namespace {
 template <int S, int E, int B>
 void slice_launch(unsigned grid, int chunk, cudaStream_t st, const int32_t *stop, spamm_mat_t m, int64_t rows,
                   unsigned long long *mx, int32_t *sig, uint8_t *ta, uint8_t *pl, int tr, uint8_t *zl,
-                  int float_split)
+                  int float_split, const double *keep_max, int keep_by_row, double tau2)
 {
     k_slice<S, E, B><<<grid, kSliceThreads, 0, st>>>(stop, m->leaf, m->slot, m->n2 + tier_offset(m->depth), m->P, m->nb,
-                                           rows, mx, sig, ta, pl, tr, zl, sig + 1, float_split, chunk);
+                                           rows, mx, sig, ta, pl, tr, zl, sig + 1, float_split, chunk, keep_max,
+                                           keep_by_row, tau2);
 }
 
 template <int B>
 bool slice_dispatch_b(int s, int e, unsigned grid, int chunk, cudaStream_t st, const int32_t *stop, spamm_mat_t m,
                       int64_t rows, unsigned long long *mx, int32_t *sig, uint8_t *ta, uint8_t *pl, int tr,
-                      uint8_t *zl, int fs)
+                      uint8_t *zl, int fs, const double *km, int kr, double tau2)
 {
 #define SPAMM_SLICE_CASE(SS, EE)                                              \
     if (s == SS && e == EE && SS * B <= 256) {                                \
-        slice_launch<SS, EE, B>(grid, chunk, st, stop, m, rows, mx, sig, ta, pl, tr, zl, fs); \
+        slice_launch<SS, EE, B>(grid, chunk, st, stop, m, rows, mx, sig, ta, pl, tr, zl, fs, km, kr, tau2); \
         return true;                                                          \
     }
     SPAMM_SLICE_CASE(1, 2)
@@ -411,7 +417,8 @@ bool slice_dispatch_b(int s, int e, unsigned grid, int chunk, cudaStream_t st, c
 // and the transposed per-leaf array; a symmetric product uses the untransposed
 // per-leaf array of the transpose leaf as its B operand.
 int launch_slices(spamm_mat_t m, int s, int e, bool tile_a, bool per_leaf, bool transposed, cudaStream_t st,
-                  const int32_t *stop, bool unit_scale, bool float_split)
+                  const int32_t *stop, bool unit_scale, bool float_split, const double *keep_a,
+                  const double *keep_b, double tau2)
 {
     int rc = slices_alloc(m, s, e, tile_a, per_leaf, st);
     if (rc) return rc;
@@ -454,11 +461,23 @@ int launch_slices(spamm_mat_t m, int s, int e, bool tile_a, bool per_leaf, bool 
         const int tr = pl && transposed ? 1 : 0;
         uint8_t *zl = pass == 0 ? m->zlead : nullptr;
         const int fs = float_split ? 1 : 0;
+        // leaves no product of this call uses are skipped: the tile-major
+        // (A-role) pass tests against keep_a per column, the per-leaf
+        // (B-role) pass against keep_b per row; a pass writing both arrays
+        // skips nothing
+        const double *km = (ta && pl) ? nullptr : ta ? keep_a : keep_b;
+        const int kr = ta ? 0 : 1;
         bool ok = false;
         switch (m->b) {
-        case 16: ok = slice_dispatch_b<16>(s, e, grid, (int)chunk, st, stop, m, rows, mx, sig, ta, pl, tr, zl, fs); break;
-        case 32: ok = slice_dispatch_b<32>(s, e, grid, (int)chunk, st, stop, m, rows, mx, sig, ta, pl, tr, zl, fs); break;
-        case 64: ok = slice_dispatch_b<64>(s, e, grid, (int)chunk, st, stop, m, rows, mx, sig, ta, pl, tr, zl, fs); break;
+        case 16: ok = slice_dispatch_b<16>(s, e, grid, (int)chunk, st, stop, m, rows, mx, sig, ta, pl, tr, zl, fs, km, kr,
+                                            tau2);
+            break;
+        case 32: ok = slice_dispatch_b<32>(s, e, grid, (int)chunk, st, stop, m, rows, mx, sig, ta, pl, tr, zl, fs, km, kr,
+                                            tau2);
+            break;
+        case 64: ok = slice_dispatch_b<64>(s, e, grid, (int)chunk, st, stop, m, rows, mx, sig, ta, pl, tr, zl, fs, km, kr,
+                                            tau2);
+            break;
         }
         if (!ok) {
             spamm_set_error("slices: %d slices of %d-byte elements at leaf %d not built", s, e, m->b);

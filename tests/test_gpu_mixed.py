@@ -146,21 +146,39 @@ def test_exact_slices_dense_near_constant_within_fp32_accumulation_bound(cuda_li
 
 
 def test_sp2_slicing_overflow_is_reported(cuda_lib):
-    """SP2 slices its iterates with the fixed scale |x| < 2.  Culling every
-    product (tau huge) turns the iteration into X <- 2X while tr X < Ne, so
-    the iterate diag(0, ..., 0, 1) of F = diag(2, ..., 2, -2) reaches 4 in
-    its third iteration; the solve must fail with E_INVAL and say so, not
-    compute with saturated digits."""
+    """SP2 slices its iterates with the fixed scale |x| < 2.  F = diag(2, ...,
+    2, -2) starts from X0 = diag(0, ..., 0, 1); at tau = 2.5 its only product
+    (squared norms 1 x 1 < tau^2) is culled, so the first iteration takes
+    X <- 2X (tr X < Ne) and the iterate's 2 is out of range.  Its leaf then
+    passes Eq. 4 (4 x 4 > tau^2), so the second product uses its slices: the
+    solve must fail with E_INVAL and say so, not compute with saturated
+    digits."""
     n = 64
     f = np.diag(np.r_[np.full(n - 1, 2.0), -2.0])
     F = cuda_lib.tree_build(_dev(f), leaf=32)
     with pytest.raises(cuda_lib.SpammError) as ei:
-        cuda_lib.sp2_solve(F, n / 2, 1e10, prec=cuda_lib.OZAKI_BF16, slices=7, fixed_iters=4)
+        cuda_lib.sp2_solve(F, n / 2, 2.5, prec=cuda_lib.OZAKI_BF16, slices=7, fixed_iters=4)
     assert ei.value.status == cuda_lib.E_INVAL
     assert "slicing range" in str(ei.value)
     # the same solve with FP64 leaf products runs (no slicing)
-    P, r = cuda_lib.sp2_solve(F, n / 2, 1e10, fixed_iters=4)
+    P, r = cuda_lib.sp2_solve(F, n / 2, 2.5, fixed_iters=4)
     assert r["iters"] == 4
+
+
+def test_sp2_unused_out_of_range_leaves_are_not_sliced(cuda_lib):
+    """Slicing skips leaves that no product uses (their norm fails Eq. 4
+    against every partner), so an out-of-range iterate that takes part in no
+    product is no error: with every product culled (tau huge) the mixed solve
+    runs X <- 2X like the FP64 one and gives the same iterate."""
+    n = 64
+    f = np.diag(np.r_[np.full(n - 1, 2.0), -2.0])
+    F = cuda_lib.tree_build(_dev(f), leaf=32)
+    Pm, rm = cuda_lib.sp2_solve(F, n / 2, 1e10, prec=cuda_lib.OZAKI_BF16, slices=7, fixed_iters=4)
+    Pf, rf = cuda_lib.sp2_solve(F, n / 2, 1e10, fixed_iters=4)
+    assert rm["iters"] == rf["iters"] == 4
+    pm = cuda_lib.to_dense(Pm).cpu().numpy()
+    assert np.array_equal(pm, cuda_lib.to_dense(Pf).cpu().numpy())
+    assert pm[-1, -1] >= 2.0  # left the slicing range without being sliced
 
 
 @pytest.mark.parametrize("n,tau,s", [(512, 1e-6, 5), (384, 1e-8, 6), (256, 1e-3, 4)])
