@@ -364,6 +364,7 @@ def run_ours(args):
         "sp2": {"iters_per_solve": iters / args.steps, "solve_ms": t_max / args.steps,
                 "step_ms": step_ms, "idempotency": main_rep["idem_err"], "trace_err": trace_err,
                 "stop_reason": main_rep["stop_reason"], "symmetric": main_rep["symmetric"],
+                "sums_rounded": main_rep["sums_rounded"],
                 "ms_cull_per_solve": cull_ms / args.steps, "ms_gemm_per_solve": gemm_ms / args.steps,
                 "ms_update_per_solve": upd_ms / args.steps,
                 "tensor_over_useful_flops": tflops / flops if flops else None,

@@ -63,9 +63,11 @@ typedef enum {
      * per output element (then the result is the exact product of the
      * sliced operands, rounded once); beyond that FP32 rounds it, by at most
      * about 2^-23 of the running sum per accumulation step (leading
-     * diagonal: FP32-level relative accuracy).  The library does not check
-     * that condition on the device.  Splitting after Ozaki, Ogita, Oishi
-     * and Rump (2012). */
+     * diagonal: FP32-level relative accuracy).  The library does not prove
+     * that condition; it counts the output elements whose final diagonal sum
+     * reached 2^24 (spamm_stats_t.sums_rounded, sp2_report_t.sums_rounded),
+     * a lower bound on the inexact ones.  Splitting after Ozaki, Ogita,
+     * Oishi and Rump (2012). */
     SPAMM_OZAKI_BF16 = 1,
     /* One BF16 term per operand (x rounded to BF16), FP32 accumulation on the
      * tensor cores: the plain low-precision product of the precision study. */
@@ -105,7 +107,11 @@ typedef struct {
     float ms_cull;       /* device time of the cull (+ slicing, mixed path)  */
     float ms_gemm;       /* device time of the leaf products                 */
     float ms_norm;       /* device time of the output norms                  */
-    float reserved;
+    int32_t sums_rounded; /* SPAMM_OZAKI_BF16: output elements for which some
+                             diagonal sum S_d ended at or beyond 2^24 in its
+                             FP32 accumulator, i.e. was certainly rounded
+                             (a lower bound on the elements whose result is
+                             not exact; saturates at 2^31 - 1); else 0     */
 } spamm_stats_t;
 
 /* ---- matrices --------------------------------------------------------- */
@@ -376,7 +382,8 @@ typedef struct {
     int32_t graphed;      /* iterations run by replaying a captured CUDA graph */
     double *history;      /* in: optional host buffer of history_cap rows  */
     int32_t history_cap;  /* in: rows available in history                 */
-    int32_t reserved;
+    int32_t sums_rounded; /* spamm_stats_t.sums_rounded summed over the
+                             solve's products (saturates at 2^31 - 1)      */
 } sp2_report_t;
 
 /*

@@ -662,15 +662,19 @@ static int slice_operands(spamm_mat_t A, spamm_mat_t B, int sl, int el, int symm
 
 // Device-side error words of a product's workspace (blocking read): list
 // overflow of the cull (counter 8) and a bounded wait that gave up in the
-// tensor-core kernel (counter 9).  Both are cleared after reading.
+// tensor-core kernel (counter 9).  Both are cleared after reading, and so is
+// counter 11, the tensor-core products' count of output elements with a
+// diagonal sum at or beyond 2^24 (kept in ws->last_rounded).
 int ws_check_errors(SpammWorkspace *ws, cudaStream_t s)
 {
     if (!ws->counter) return SPAMM_OK;
-    int32_t w[2] = {0, 0};
+    int32_t w[4] = {0, 0, 0, 0};
     SPAMM_CK(cudaMemcpyAsync(w, ws->counter + 8, sizeof(w), cudaMemcpyDeviceToHost, s));
     SPAMM_CK(cudaStreamSynchronize(s));
+    ws->last_rounded = w[3];
+    if (w[3]) SPAMM_CK(cudaMemsetAsync(ws->counter + 11, 0, sizeof(int32_t), s));
     if (!w[0] && !w[1]) return SPAMM_OK;
-    SPAMM_CK(cudaMemsetAsync(ws->counter + 8, 0, sizeof(w), s));
+    SPAMM_CK(cudaMemsetAsync(ws->counter + 8, 0, sizeof(int32_t) * 2, s));
     if (w[1]) {
         spamm_set_error("tensor-core leaf products: a device-side wait timed out");
         return SPAMM_E_TIMEOUT;
@@ -801,6 +805,7 @@ extern "C" int spamm_multiply(spamm_mat_t A, spamm_mat_t B, double tau, spamm_ma
         }
         stats->ms_cull = stats->ms_gemm = stats->ms_norm = 0.f;
         rc = ws_check_errors(&(*C)->ws, s);
+        stats->sums_rounded = (*C)->ws.last_rounded;
         if (timing && rc == SPAMM_OK) {
             cudaError_t e = cudaEventSynchronize(ev[3]);
             if (e != cudaSuccess) rc = spamm_cuda_fail(e, "cudaEventSynchronize", __FILE__, __LINE__);
@@ -1025,6 +1030,8 @@ extern "C" int spamm_multiply_batched(int32_t count, const spamm_mat_t *A, const
             stats->flops_useful += 2.0 * b3 * double(v[1]);
             stats->flops_issued += tcp ? 2.0 * 128 * double(leaf) * leaf * double(v[2]) : 2.0 * b3 * double(v[1]);
             rc = ws_check_errors(w[q], s);
+            const int64_t r = (int64_t)stats->sums_rounded + w[q]->last_rounded;
+            stats->sums_rounded = (int32_t)(r < INT32_MAX ? r : INT32_MAX);
         }
         if (rc == SPAMM_OK && timing) {
             cudaError_t e = cudaEventSynchronize(ev[3]);

@@ -679,6 +679,7 @@ static void fill_prob(tc::TcProb &p, spamm_mat_t A, spamm_mat_t B, spamm_mat_t C
     p.sym = ws->tsym;
     p.tw = ws->tw;
     p.mirror = ws->tmirror;
+    p.rounded = ws->counter ? ws->counter + 11 : nullptr;
     p.skip_idle = ws->tskip_idle;
 }
 

@@ -50,6 +50,7 @@ struct SpammWorkspace {
     const int64_t *pair_units = nullptr;  // device: slice pairs needed (tensor path), else null
     int64_t last_items = 0;               // host copy: tile work items of the last product
     int64_t last_pairs = 0;               // host copy: slice-pair MMA work (units of 128 x b x b)
+    int32_t last_rounded = 0;             // host copy: output elements with a diagonal sum >= 2^24 (counter 11)
     int64_t tactive = 0;                  // tiles in the order list of the last tile cull
     const int32_t *stop = nullptr;        // device flag: when set, the product's kernels return at once
     int tsym = 0;                         // last tile cull was symmetric

@@ -772,7 +772,7 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
             memcpy(report->history, hrows.data(), sizeof(double) * rows * SP2_H_COLS);
         }
     }
-    SP2_TRY(ws_check_errors(&X2->ws, s));
+    SP2_TRY(ws_check_errors(&X2->ws, s));  // (also reads the rounded-sum count of the solve's products)
     SP2_TRY(launch_pyramid(X, s));
     X->tiers_ok = true;
     SP2_CUDA(cudaEventRecord(ev1, s));
@@ -808,6 +808,7 @@ extern "C" int sp2_solve(spamm_mat_t F, double Ne, double tau, const sp2_opts_t 
         report->launches = spamm_launch_count() - launches0;
         report->symmetric = sym ? 1 : 0;
         report->graphed = graphed;
+        report->sums_rounded = X2->ws.last_rounded;
     }
     rc = reason == SP2_STOP_MAXITER ? SPAMM_E_NOCONV : SPAMM_OK;
     if (rc == SPAMM_E_NOCONV) spamm_set_error("sp2_solve: %d iterations without convergence", it);

@@ -328,8 +328,11 @@ __device__ __noinline__ double combine_exact_slow(const uint32_t *f, int d0, int
 // (each S_d + 1.5 2^23 carries the integer in its low bits; the offsets are
 // removed once per pair, modulo 2^32, which is exact since the true value
 // fits), and the total is sum_j P_j 2^(14 j) in int64.
+// Returns the number of the 16 values with a diagonal sum at or beyond 2^24
+// (certainly rounded by its FP32 accumulation); only the slow path can see
+// one.
 template <int S>
-__device__ __forceinline__ void combine_exact16(const uint32_t (&v)[S][16], int d0, int k, double (&res)[16])
+__device__ __forceinline__ int combine_exact16(const uint32_t (&v)[S][16], int d0, int k, double (&res)[16])
 {
     constexpr uint32_t kMagicBits = 0x4B400000u;  // bits of 1.5 2^23
     bool fast = true;
@@ -361,17 +364,24 @@ __device__ __forceinline__ void combine_exact16(const uint32_t (&v)[S][16], int 
             a[q] += (long long)p << (14 * j);
         }
     }
+    int rounded = 0;
     if (fast) {
 #pragma unroll
         for (int q = 0; q < 16; q++) res[q] = i64_scaled_fast(a[q], k);
     } else {
         for (int q = 0; q < 16; q++) {
             uint32_t f[S];
+            bool big = false;
 #pragma unroll
-            for (int d = 0; d < S; d++) f[d] = v[d][q];
+            for (int d = 0; d < S; d++) {
+                f[d] = v[d][q];
+                big = big || (d >= d0 && fabsf(__uint_as_float(f[d])) >= 16777216.0f);
+            }
+            rounded += big;
             res[q] = combine_exact_slow<S>(f, d0, k);
         }
     }
+    return rounded;
 }
 
 // One product of a launch.
@@ -399,6 +409,7 @@ struct TcProb {
     int32_t tw;            // output leaf columns per tile of its work lists
     int32_t mirror;        // symmetric product: also store C_ji = C_ij^T (else leaves i <= j only)
     int32_t skip_idle;     // output leaves without work in a tile with work are not written (else zeroed)
+    int32_t *rounded;      // exact slices: += output elements with a diagonal sum >= 2^24 (may be null)
 };
 
 struct TcArgs {
@@ -950,7 +961,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                             res[q] = a;
                         }
                     } else {
-                        combine_exact16<S>(v, dc, kexp, res);
+                        const int nr = combine_exact16<S>(v, dc, kexp, res);
+                        if (nr && P.rounded) atomicAdd(P.rounded, nr);  // rare: the slow path only
                     }
                     if (store) {
 #pragma unroll

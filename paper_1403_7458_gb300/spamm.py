@@ -53,7 +53,7 @@ class _Stats(ctypes.Structure):
     _fields_ = [("tasks", ctypes.c_int64), ("candidates", ctypes.c_int64),
                 ("flops_useful", ctypes.c_double), ("flops_issued", ctypes.c_double),
                 ("ms_cull", ctypes.c_float), ("ms_gemm", ctypes.c_float),
-                ("ms_norm", ctypes.c_float), ("reserved", ctypes.c_float)]
+                ("ms_norm", ctypes.c_float), ("sums_rounded", ctypes.c_int32)]
 
 
 class _Tune(ctypes.Structure):
@@ -81,7 +81,7 @@ class _Sp2Report(ctypes.Structure):
                 ("ms_gemm", ctypes.c_double), ("ms_update", ctypes.c_double),
                 ("launches", ctypes.c_int64), ("symmetric", ctypes.c_int32),
                 ("graphed", ctypes.c_int32), ("history", ctypes.POINTER(ctypes.c_double)),
-                ("history_cap", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("history_cap", ctypes.c_int32), ("sums_rounded", ctypes.c_int32)]
 
 
 def load():

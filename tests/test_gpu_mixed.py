@@ -100,6 +100,7 @@ def test_mixed_spamm_bit_exact_vs_integer_model(cuda_lib, n, tau, s, seed, leaf)
     want, tasks, _, _ = _model(a, b, leaf, tau, s)
     assert st["tasks"] == len(tasks)
     assert np.array_equal(got, want), np.abs(got - want).max()
+    assert st["sums_rounded"] == 0  # every diagonal sum stayed below 2^24
 
 
 def test_exact_slices_dense_near_constant_within_fp32_accumulation_bound(cuda_lib):
@@ -119,6 +120,9 @@ def test_exact_slices_dense_near_constant_within_fp32_accumulation_bound(cuda_li
     A = cuda_lib.tree_build(_dev(a), leaf=leaf)
     C, st = cuda_lib.multiply(A, A, 0.0, prec=cuda_lib.OZAKI_BF16, slices=s, stats=True)
     assert st["tasks"] == (n // leaf) ** 3
+    # the leading diagonal sums (about 2^26) are reported as rounded: every
+    # output element has one, and the product reports each at most once
+    assert 0 < st["sums_rounded"] <= n * n
     got = cuda_lib.to_dense(C).cpu().numpy()
     da, sg = _digits(a, s)
     e = 2 * sg - 7 * s - 7
