@@ -162,30 +162,34 @@ __global__ void k_iota_slots(int32_t *slot, int64_t count)
 // Dense <-> leaf layout.  Rows r of the padded Np x Np matrix are taken by
 // blockIdx.y (strided), columns c by the x threads, so that consecutive
 // threads touch consecutive doubles; b = 2^lb (16, 32 or 64).
+// Rows r0 .. r0 + rows - 1 of the padded matrix; row r of the input is
+// a[(r - r0) lda ...] (a holds those rows only).
 __global__ void k_pack(const double *__restrict__ a, int64_t n, int64_t lda, int lb, int64_t nb,
-                       const int32_t *__restrict__ slot, double *__restrict__ leaf)
+                       const int32_t *__restrict__ slot, double *__restrict__ leaf, int64_t r0, int64_t rows)
 {
     const int b = 1 << lb;
     const int64_t Np = nb * b;
-    for (int64_t r = blockIdx.y; r < Np; r += gridDim.y) {
+    for (int64_t r = r0 + blockIdx.y; r < r0 + rows; r += gridDim.y) {
         const int64_t I = r >> lb, rr = r & (b - 1);
         for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < Np; c += (int64_t)gridDim.x * blockDim.x) {
-            const double v = (r < n && c < n) ? a[r * lda + c] : 0.0;
+            const double v = (r < n && c < n) ? a[(r - r0) * lda + c] : 0.0;
             const int32_t s = slot[I * nb + (c >> lb)];
             if (s >= 0) leaf[((int64_t)s << (2 * lb)) + (rr << lb) + (c & (b - 1))] = v;
         }
     }
 }
 
+// Rows r0 .. r0 + rows - 1 of the matrix into dst[(r - r0) ld ...].
 __global__ void k_unpack(const double *__restrict__ leaf, const int32_t *__restrict__ slot,
-                         int64_t n, int lb, int64_t nb, double *__restrict__ dst, int64_t ld)
+                         int64_t n, int lb, int64_t nb, double *__restrict__ dst, int64_t ld, int64_t r0,
+                         int64_t rows)
 {
     const int b = 1 << lb;
-    for (int64_t r = blockIdx.y; r < n; r += gridDim.y) {
+    for (int64_t r = r0 + blockIdx.y; r < r0 + rows; r += gridDim.y) {
         const int64_t I = r >> lb, rr = r & (b - 1);
         for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
             const int32_t s = slot[I * nb + (c >> lb)];
-            dst[r * ld + c] = s >= 0 ? leaf[((int64_t)s << (2 * lb)) + (rr << lb) + (c & (b - 1))] : 0.0;
+            dst[(r - r0) * ld + c] = s >= 0 ? leaf[((int64_t)s << (2 * lb)) + (rr << lb) + (c & (b - 1))] : 0.0;
         }
     }
 }
@@ -198,6 +202,53 @@ static dim3 pack_grid(int64_t rows, int64_t cols)
 }
 
 static int log2_leaf(int b) { return b == 16 ? 4 : b == 32 ? 5 : 6; }
+
+// ---------------------------------------------------------------------------
+// Host transfers of dense matrices in row blocks: the copies of one block run
+// on a library-owned copy stream of the device while the caller's stream
+// packs (or unpacks) the block before, through two device buffers of one
+// block each (so the transfer overlaps the layout change, and the staging
+// takes two blocks, not the whole matrix).  The lock keeps one such transfer
+// per device at a time (its events are shared).
+// ---------------------------------------------------------------------------
+struct CopyLane {
+    cudaStream_t st;
+    cudaEvent_t start, copied[2], used[2];
+};
+
+static CopyLane *copy_lane(std::unique_lock<std::mutex> *lock)
+{
+    static std::mutex mu;
+    static std::map<int, CopyLane *> lanes;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::unique_lock<std::mutex> l(mu);
+    auto it = lanes.find(dev);
+    if (it == lanes.end()) {
+        CopyLane *c = new CopyLane();
+        bool ok = cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&c->start, cudaEventDisableTiming) == cudaSuccess;
+        for (int i = 0; i < 2 && ok; i++)
+            ok = cudaEventCreateWithFlags(&c->copied[i], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&c->used[i], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            spamm_set_error("copy stream: creation failed");
+            return nullptr;
+        }
+        it = lanes.emplace(dev, c).first;
+    }
+    *lock = std::move(l);
+    return it->second;
+}
+
+// Rows per block: a multiple of the leaf edge b, about a quarter of the
+// matrix for small ones and at most 2048 rows.
+static int64_t copy_block_rows(int64_t n, int b)
+{
+    const int64_t r = ((n + 3) / 4 + b - 1) / b * b;
+    const int64_t cap = (2048 / b) * b;
+    return r < b ? b : (r > cap ? cap : r);
+}
 
 bool is_device_ptr(const void *p)
 {
@@ -435,31 +486,56 @@ extern "C" int spamm_tree_build(const double *a, int64_t n, int64_t lda, double 
         spamm_free(m);
         return rc;
     }
-    const double *src = a;
-    double *staging = nullptr;
-    if (!is_device_ptr(a)) {
-        if ((rc = spamm_alloc((void **)&staging, sizeof(double) * n * n, s))) {
+    const int64_t Np = m->nb * b;
+    const bool host = !is_device_ptr(a);
+    if (!host) {
+        k_pack<<<pack_grid(Np, Np), 256, 0, s>>>(a, n, lda, log2_leaf(b), m->nb, m->slot, m->leaf, 0, Np);
+        spamm_note_launches(1);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            spamm_free(m);
+            return spamm_cuda_fail(e, "k_pack", __FILE__, __LINE__);
+        }
+    } else {
+        // row blocks: H2D on the copy stream, packing on s
+        std::unique_lock<std::mutex> lk;
+        CopyLane *cl = copy_lane(&lk);
+        if (!cl) {
+            spamm_free(m);
+            return SPAMM_E_CUDA;
+        }
+        const int64_t R = copy_block_rows(n, b);
+        double *buf[2] = {nullptr, nullptr};
+        for (int i = 0; i < 2 && rc == SPAMM_OK; i++) rc = spamm_alloc((void **)&buf[i], sizeof(double) * R * n, s);
+        cudaError_t e = cudaSuccess;
+        if (rc == SPAMM_OK) {
+            e = cudaEventRecord(cl->start, s);  // the buffers exist (stream-ordered allocation)
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(cl->st, cl->start, 0);
+            for (int64_t r0 = 0, q = 0; r0 < Np && e == cudaSuccess; r0 += R, q++) {
+                const int i = (int)(q & 1);
+                const int64_t rows = Np - r0 < R ? Np - r0 : R;
+                if (q >= 2) e = cudaStreamWaitEvent(cl->st, cl->used[i], 0);  // block q - 2 packed
+                if (e == cudaSuccess && r0 < n)
+                    e = cudaMemcpy2DAsync(buf[i], sizeof(double) * n, a + r0 * lda, sizeof(double) * lda,
+                                          sizeof(double) * n, (n - r0 < rows ? n - r0 : rows),
+                                          cudaMemcpyHostToDevice, cl->st);
+                if (e == cudaSuccess) e = cudaEventRecord(cl->copied[i], cl->st);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(s, cl->copied[i], 0);
+                if (e == cudaSuccess) {
+                    k_pack<<<pack_grid(rows, Np), 256, 0, s>>>(buf[i], n, n, log2_leaf(b), m->nb, m->slot, m->leaf,
+                                                              r0, rows);
+                    spamm_note_launches(1);
+                    e = cudaGetLastError();
+                }
+                if (e == cudaSuccess) e = cudaEventRecord(cl->used[i], s);
+            }
+        }
+        for (int i = 0; i < 2; i++) spamm_release(buf[i], s);  // after the packs that read them (on s)
+        if (rc == SPAMM_OK && e != cudaSuccess) rc = spamm_cuda_fail(e, "host-to-device blocks", __FILE__, __LINE__);
+        if (rc) {
             spamm_free(m);
             return rc;
         }
-        cudaError_t e = cudaMemcpy2DAsync(staging, sizeof(double) * n, a, sizeof(double) * lda,
-                                          sizeof(double) * n, n, cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) {
-            spamm_release(staging, s);
-            spamm_free(m);
-            return spamm_cuda_fail(e, "cudaMemcpy2DAsync(H2D)", __FILE__, __LINE__);
-        }
-        src = staging;
-        lda = n;
-    }
-    int64_t Np = m->nb * b;
-    k_pack<<<pack_grid(Np, Np), 256, 0, s>>>(src, n, lda, log2_leaf(b), m->nb, m->slot, m->leaf);
-    spamm_note_launches(1);
-    cudaError_t e = cudaGetLastError();
-    if (staging) spamm_release(staging, s);
-    if (e != cudaSuccess) {
-        spamm_free(m);
-        return spamm_cuda_fail(e, "k_pack", __FILE__, __LINE__);
     }
     if ((rc = launch_leaf_norms(m, s))) {
         spamm_free(m);
@@ -469,9 +545,11 @@ extern "C" int spamm_tree_build(const double *a, int64_t n, int64_t lda, double 
         spamm_free(m);
         return rc;
     }
-    if (staging) {
-        // the caller may reuse its host buffer as soon as we return
-        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) {
+    if (host) {
+        // the caller may reuse its host buffer as soon as we return (s
+        // waited for every block's copy)
+        const cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
             spamm_free(m);
             return spamm_cuda_fail(e, "cudaStreamSynchronize", __FILE__, __LINE__);
         }
@@ -489,23 +567,45 @@ extern "C" int spamm_to_dense(spamm_mat_t m, double *dst, int64_t ld, void *stre
     cudaStream_t s = (cudaStream_t)stream;
     int64_t n = m->n;
     if (is_device_ptr(dst)) {
-        k_unpack<<<pack_grid(n, n), 256, 0, s>>>(m->leaf, m->slot, n, log2_leaf(m->b), m->nb, dst, ld);
+        k_unpack<<<pack_grid(n, n), 256, 0, s>>>(m->leaf, m->slot, n, log2_leaf(m->b), m->nb, dst, ld, 0, n);
         SPAMM_CK_LAUNCH();
         return SPAMM_OK;
     }
-    double *tmp = nullptr;
-    int rc = spamm_alloc((void **)&tmp, sizeof(double) * n * n, s);
-    if (rc) return rc;
-    k_unpack<<<pack_grid(n, n), 256, 0, s>>>(m->leaf, m->slot, n, log2_leaf(m->b), m->nb, tmp, n);
-    spamm_note_launches(1);
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess)
-        e = cudaMemcpy2DAsync(dst, sizeof(double) * ld, tmp, sizeof(double) * n, sizeof(double) * n,
-                              n, cudaMemcpyDeviceToHost, s);
-    spamm_release(tmp, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return spamm_cuda_fail(e, "spamm_to_dense copy", __FILE__, __LINE__);
-    return SPAMM_OK;
+    // row blocks: unpacking on s, D2H on the copy stream
+    std::unique_lock<std::mutex> lk;
+    CopyLane *cl = copy_lane(&lk);
+    if (!cl) return SPAMM_E_CUDA;
+    const int64_t R = copy_block_rows(n, m->b);
+    double *buf[2] = {nullptr, nullptr};
+    int rc = SPAMM_OK;
+    for (int i = 0; i < 2 && rc == SPAMM_OK; i++) rc = spamm_alloc((void **)&buf[i], sizeof(double) * R * n, s);
+    cudaError_t e = cudaSuccess;
+    if (rc == SPAMM_OK) {
+        for (int64_t r0 = 0, q = 0; r0 < n && e == cudaSuccess; r0 += R, q++) {
+            const int i = (int)(q & 1);
+            const int64_t rows = n - r0 < R ? n - r0 : R;
+            if (q >= 2) e = cudaStreamWaitEvent(s, cl->used[i], 0);  // block q - 2 copied out
+            if (e == cudaSuccess) {
+                k_unpack<<<pack_grid(rows, n), 256, 0, s>>>(m->leaf, m->slot, n, log2_leaf(m->b), m->nb, buf[i], n,
+                                                            r0, rows);
+                spamm_note_launches(1);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(cl->copied[i], s);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(cl->st, cl->copied[i], 0);
+            if (e == cudaSuccess)
+                e = cudaMemcpy2DAsync(dst + r0 * ld, sizeof(double) * ld, buf[i], sizeof(double) * n,
+                                      sizeof(double) * n, rows, cudaMemcpyDeviceToHost, cl->st);
+            if (e == cudaSuccess) e = cudaEventRecord(cl->used[i], cl->st);
+        }
+        // s continues once every block is on the host
+        if (e == cudaSuccess) e = cudaEventRecord(cl->start, cl->st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, cl->start, 0);
+    }
+    for (int i = 0; i < 2; i++) spamm_release(buf[i], s);
+    if (e == cudaSuccess && rc == SPAMM_OK) e = cudaStreamSynchronize(s);
+    if (rc == SPAMM_OK && e != cudaSuccess) rc = spamm_cuda_fail(e, "spamm_to_dense copy", __FILE__, __LINE__);
+    return rc;
 }
 
 extern "C" int spamm_norms(spamm_mat_t m, int32_t tier, double *dst, void *stream)
