@@ -133,7 +133,9 @@ typedef struct spamm_mat *spamm_mat_t;
  * Squared norms are stored.  Each is the exact sum of the exact squares
  * (resp. of the four children) rounded once to FP64, so its value does not
  * depend on the order of summation.  Device work is enqueued on `stream`;
- * a host `a` is copied before the call returns.
+ * a host `a` is copied before the call returns (in blocks of up to 2048
+ * rows on a copy stream the library owns, overlapped with the packing into
+ * leaves; two blocks of device staging; pinned host memory copies fastest).
  * Errors: E_INVAL (n < 1, lda < n, bad leaf, NULL a/out), E_NOMEM, E_CUDA.
  */
 int spamm_tree_build(const double *a, int64_t n, int64_t lda, double drop,
@@ -228,7 +230,9 @@ int spamm_autotune_batched(int32_t count, const double *const *a, const double *
 
 /*
  * Write the matrix to dense row-major storage (host or device), n x n with
- * leading dimension ld >= n.  Blocking when dst is host memory.
+ * leading dimension ld >= n.  Blocking when dst is host memory (then the
+ * rows are unpacked and copied out in blocks, the copies on a copy stream
+ * the library owns, overlapped with the unpacking of the next block).
  */
 int spamm_to_dense(spamm_mat_t M, double *dst, int64_t ld, void *stream);
 
