@@ -71,6 +71,29 @@ def test_tree_build_from_host_memory(cuda_lib):
     assert np.array_equal(cuda_lib.norms(A, A.depth), oracle.leaf_norms2(a, 16))
 
 
+def test_host_transfers_in_row_blocks_with_row_pitch(cuda_lib):
+    """Host input and output go through the device in row blocks (here four
+    blocks of 256 rows at n = 1000, b = 16): a host matrix with a row pitch
+    larger than n builds the same handle as its device copy, and the dense
+    output lands in a pitched host buffer without touching the padding."""
+    import torch
+    n, b = 1000, 16
+    a = synth.decaying_matrix(n, 4)
+    big = torch.zeros((n, n + 40), dtype=torch.float64)  # host memory, row pitch n + 40
+    big[:, :n] = torch.from_numpy(a)
+    A = cuda_lib.tree_build(big[:, :n], leaf=b)
+    assert np.array_equal(cuda_lib.norms(A, A.depth), oracle.leaf_norms2(a, b))
+    out = torch.full((n, n + 24), -1.0, dtype=torch.float64)
+    cuda_lib.to_dense(A, out=out[:, :n])
+    assert np.array_equal(out[:, :n].numpy(), a)
+    assert bool((out[:, n:] == -1.0).all())
+    # with a drop threshold: the host build equals the device build
+    Ah = cuda_lib.tree_build(big[:, :n], leaf=b, drop=1e-3)
+    Ad = cuda_lib.tree_build(_dev(a), leaf=b, drop=1e-3)
+    assert Ah.stored == Ad.stored < Ad.nb * Ad.nb
+    assert np.array_equal(cuda_lib.to_dense(Ah).cpu().numpy(), cuda_lib.to_dense(Ad).cpu().numpy())
+
+
 @pytest.mark.parametrize("n,b,tau,kind", [(1024, 32, 1e-6, "dec"), (1000, 16, 1e-6, "dec"), (512, 64, 1e-8, "dec"),
                                           (384, 32, 0.0, "dec"), (384, 32, 1e-2, "dec"), (256, 32, 1e300, "dec"),
                                           (3000, 16, 1e-6, "dec"), (4096, 32, 1e-8, "tb"), (4100, 64, 1e-6, "tb")])
