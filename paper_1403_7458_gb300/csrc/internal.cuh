@@ -363,12 +363,6 @@ __device__ __forceinline__ u128 warp_sum_u128(u128 v)
     return v;
 }
 
-__device__ __forceinline__ int warp_min_int(int v)
-{
-    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
 __device__ __forceinline__ int warp_max_int(int v)
 {
     for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
